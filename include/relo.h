@@ -1,0 +1,169 @@
+/*
+ * relo.h — C ABI of the GB300 relocalization scoring library.
+ *
+ * The library scores positional hypotheses x orientations x LiDAR beams
+ * against an occupancy grid for passive 2-D global relocalization (arXiv
+ * 2511.01219): the EDT likelihood-field table (Sec. III-A item 3), ray-cast
+ * synthesized scans (Eq. 13), SMAD coarse ranking (Eq. 16-20), TAM orientation
+ * selection and pose evaluation (Eq. 22-31), and batched multi-stage
+ * inference with local top-k and early termination (Sec. III intro,
+ * Remarks 2-3).  Every step runs in the library's own CUDA kernels (sm_103a);
+ * there is no CPU fallback.
+ *
+ * Conventions
+ *   - Grids are int8, row-major, W columns x H rows; value >= 65 is occupied,
+ *     value < 0 is unknown (treated as free by the EDT and by ray casting).
+ *     Cell (cx, cy) covers [ox + cx*res, ox + (cx+1)*res) x [oy + cy*res, ...).
+ *   - Hypotheses are snapped to cell centres.  Orientations are the shifts m
+ *     of Eq. 15, theta_m = m * 2*pi / N_s, reported wrapped to [-pi, pi).
+ *   - Beam angles must lie on a uniform panoramic grid of N_s = 2*pi / step
+ *     directions (Eq. 14): each within 1e-3 steps of a multiple of 2*pi/N_s,
+ *     no two on the same direction, listed in increasing (cyclic) order.
+ *   - Pointers named *_dev are device pointers (for example from torch
+ *     tensors) valid on the context's stream; all other pointers are host
+ *     pointers.  The caller keeps ownership of every buffer it passes; the
+ *     library copies what it keeps.  Results are written into caller memory.
+ *   - Every call returns RELO_OK (0) or a negative error code; the message is
+ *     available from relo_last_error().  A context is not thread-safe.
+ */
+#ifndef RELO_H
+#define RELO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RELO_OK 0
+#define RELO_PENDING 1              /* relo_poll only: request still running */
+#define RELO_E_INVALID_ARG (-1)
+#define RELO_E_BEAM_GRID (-2)       /* angles not on a uniform 2*pi/N_s grid, or n_orient does not divide N_s */
+#define RELO_E_NO_HYPOTHESES (-3)
+#define RELO_E_OVER_BUDGET (-4)     /* the request or map does not fit the context's HBM budget */
+#define RELO_E_CUDA (-5)            /* a CUDA call failed; the context should be destroyed */
+#define RELO_E_TIMEOUT (-6)
+#define RELO_E_NO_VALID_BEAMS (-7)  /* no beam with 0 < z < max_range */
+#define RELO_E_NOT_FOUND (-8)       /* unknown map id or ticket */
+
+/* Parameters of Eq. 20-31 and of the batched inference.  relo_default_params()
+ * fills the values used throughout: z_hit 1, sigma_hit 0.2 m, z_rand 0
+ * (Sec. IV-B), eps 1e-6 (Eq. 23), batch 200, local top-20, tau 0.95
+ * (Sec. IV-C).  The paper prints neither the Eq. 25 ratio endpoints nor
+ * d_max; the defaults (0.9 -> 0.8, 0.8 -> 0.6, 2 m) make the retention fall
+ * as the FoV widens, as the text after Eq. 25 describes. */
+typedef struct relo_params {
+    double z_hit, sigma_hit, z_rand, eps;              /* Eq. 23 */
+    double d_max;                                      /* Eq. 29, metres; d_max/res must be an integer <= 90 */
+    double a_mid_min, a_mid_max, a_low_min, a_low_max; /* Eq. 25 */
+    double tau;                                        /* early-termination threshold (Sec. III) */
+    double panoramic_ratio;                            /* Eq. 20: lambda >= this scores m = 0 only */
+    int32_t n_orient;                                  /* |Theta| of Eq. 15 (must divide N_s); 0 = N_s */
+    int32_t topk;                                      /* SMAD survivors scored by TAM (<= 4096) */
+    int32_t batch;                                     /* survivors per batch (<= 1024) */
+    int32_t local_topk;                                /* local top-k kept per batch (<= batch) */
+    int32_t n_skip_beam;                               /* Eq. 11 beam stride */
+    int32_t early_stop;                                /* 1: stop after the first batch whose best >= tau */
+    int64_t hbm_budget;                                /* bytes the context may hold; 0 = no limit */
+} relo_params;
+
+/* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */
+typedef struct relo_result {
+    double x, y, theta;     /* selected pose: cell centre (metres) and theta_m wrapped to [-pi, pi) */
+    double tam;             /* its TAM score, Eq. 31 */
+    double smad;            /* SMAD of its position, Eq. 20, metres */
+    int64_t smad_num;       /* SMAD numerator |sum R_real - W_m| in Q16 cell units */
+    int64_t n_smad_evals;   /* hypothesis x orientation SMAD evaluations performed */
+    int64_t n_tam_evals;    /* hypothesis x orientation TAM evaluations performed */
+    int32_t hyp;            /* index of the selected hypothesis in the context's set */
+    int32_t m;              /* orientation shift of Eq. 15 */
+    int32_t n_batches;      /* batches scored before stopping */
+    int32_t status;         /* RELO_OK or an error code */
+} relo_result;
+
+typedef struct relo_ctx relo_ctx;
+
+void relo_default_params(relo_params *p);
+
+/* Creates a context on the current CUDA device.  stream: a cudaStream_t to
+ * run on (NULL creates a private non-blocking stream).  The context owns all
+ * device memory it allocates and frees it in relo_destroy. */
+int relo_create(const relo_params *p, void *stream, relo_ctx **out);
+int relo_destroy(relo_ctx *ctx);
+const char *relo_last_error(const relo_ctx *ctx);
+/* replaces the parameters (maps keep the field clamp they were built with unless rebuilt) */
+int relo_set_params(relo_ctx *ctx, const relo_params *p);
+
+/* Map precompute (Sec. III-A item 3 and the likelihood field of Eq. 23/29):
+ * copies the grid to the device and computes, in the library's kernels, the
+ * exact squared EDT d2 (cells^2, -1 when the map has no occupied cell), its
+ * clamped copy min(d2, (d_max/res)^2) in 8x8-cell tiles, and a 1-bit
+ * occupancy bitmap in 8x8 tiles.  W, H in [1, 16384].  Returns a map id. */
+int relo_load_map(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, double res, double origin_x,
+                  double origin_y, int32_t *map_id);
+int relo_load_map_dev(relo_ctx *ctx, const int8_t *grid_dev, int32_t w, int32_t h, double res,
+                      double origin_x, double origin_y, int32_t *map_id);
+/* Recomputes a loaded map's tables in place from a new grid of the same size
+ * (for example after a door opened).  Asynchronous on the context stream. */
+int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev);
+int relo_unload_map(relo_ctx *ctx, int32_t map_id);
+
+/* Copies a map's tables into caller device buffers, row-major W x H:
+ * d2_dev (int32, -1 = no obstacle), field_dev (uint16, clamped), occ_dev
+ * (uint8, 1 = occupied).  Any pointer may be NULL. */
+int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t *field_dev, uint8_t *occ_dev);
+
+/* Positional hypotheses of Eq. 6 (for example from the RRT of Algorithm 1).
+ * xy: n (x, y) pairs in metres, snapped to the containing cell; every one
+ * must fall inside the map on a cell that is not occupied. */
+int relo_set_hypotheses(relo_ctx *ctx, int32_t map_id, const double *xy, int32_t n);
+/* Same, from n (cx, cy) int32 cell pairs already on the device. */
+int relo_set_hypotheses_cells_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n);
+
+/* One relocalization (Eq. 3 via Eq. 6-9): plan the scan (Eq. 11-16), ray-cast
+ * and SMAD-rank every hypothesis (Eq. 13, 17-20), keep the topk best, score
+ * them with TAM in batches over all orientations (Eq. 22-31) with local
+ * top-k and early termination, and return the best pose.  ranges: n_beams
+ * float32 metres; a beam is valid when finite and 0 < z < max_range.
+ * Blocking: returns once the result is in *out. */
+int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                    float max_range, relo_result *out);
+/* Same with the ranges already on the device; the angles (sensor geometry)
+ * stay on the host.  The result is written to result_dev (a relo_result in
+ * device memory) and the call returns without synchronising. */
+int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles,
+                        int32_t n_beams, float max_range, relo_result *result_dev);
+
+/* Intermediate outputs of the last relocalization, copied to caller device
+ * memory (bytes = capacity of dst_dev; the call fails if it is too small):
+ *   RELO_STAGE_SMAD_NUM   int64 [N_h]   SMAD numerators (Eq. 20)
+ *   RELO_STAGE_SMAD_M     int32 [N_h]   minimising orientation shift m
+ *   RELO_STAGE_SURVIVORS  int32 [K]     hypothesis indices in SMAD order
+ *   RELO_STAGE_TAM        float [K x n_orient]  TAM of every scored (survivor, orientation); unscored = -1
+ *   RELO_STAGE_BEST_M     int32 [K]     per-survivor argmax shift m of Eq. 22 (-1 if not scored)
+ *   RELO_STAGE_LOCAL_TOPK int32 [n_batches x local_topk]  survivor positions of each batch's local top-k
+ *   RELO_STAGE_SCAN_INFO  int64 [8]     N_s, n_orient, n_enum, N_valid, k_retained, sum_real, K, batches */
+#define RELO_STAGE_SMAD_NUM 0
+#define RELO_STAGE_SMAD_M 1
+#define RELO_STAGE_SURVIVORS 2
+#define RELO_STAGE_TAM 3
+#define RELO_STAGE_BEST_M 4
+#define RELO_STAGE_LOCAL_TOPK 5
+#define RELO_STAGE_SCAN_INFO 6
+int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes);
+
+/* Ray-cast synthesized scans (Eq. 13) for n cells on a loaded map, for the
+ * beam grid the angles define: ranges_dev receives n x N_s uint32 Q16 cell
+ * ranges (0 = no hit), hit_dev (optional) n x N_s int32 hit cell indices
+ * cy*W+cx (-1 = none).  capacity: elements each output buffer holds; the call
+ * fails with RELO_E_INVALID_ARG, writing nothing, when n x N_s exceeds it.
+ * *ns_out receives N_s. */
+int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n, const float *angles,
+                         int32_t n_beams, float max_range, uint32_t *ranges_dev, int32_t *hit_dev, int64_t capacity,
+                         int32_t *ns_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RELO_H */

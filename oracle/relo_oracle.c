@@ -71,8 +71,11 @@ int64_t oracle_d2_brute(const int8_t *grid, int W, int H, int x, int y) {
 }
 
 /*
- * Same minimum, separated by axes: min_{x'} [ (x-x')^2 + min_{y'} (y-y')^2 ],
- * where the inner minimum runs over occupied cells of column x'.  O(W^2 H).
+ * Same minimum, separated by axes: min_{x'} [ (x-x')^2 + g2(x', y) ], where
+ * g2(x', y) = min over occupied y' in column x' of (y-y')^2 comes from one
+ * downward and one upward sweep per column.  The row minimum visits x' in
+ * increasing |x - x'| and stops once (x - x')^2 alone is no smaller than the
+ * best sum found, since no further column can then be closer.
  */
 void oracle_edt_full(const int8_t *grid, int W, int H, int64_t *d2, int n_threads) {
     int64_t *g2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * H);   /* column term, -1 = none */
@@ -81,27 +84,34 @@ void oracle_edt_full(const int8_t *grid, int W, int H, int64_t *d2, int n_thread
     #pragma omp parallel for num_threads(n_threads > 0 ? n_threads : 1) schedule(static)
 #endif
     for (int x = 0; x < W; ++x) {
+        int64_t last = -1;
         for (int y = 0; y < H; ++y) {
-            int64_t best = -1;
-            for (int yy = 0; yy < H; ++yy)
-                if (is_occupied(grid[(size_t)yy * W + x])) {
-                    int64_t d = (int64_t)(y - yy) * (y - yy);
-                    if (best < 0 || d < best) best = d;
-                }
-            g2[(size_t)y * W + x] = best;
+            if (is_occupied(grid[(size_t)y * W + x])) last = y;
+            g2[(size_t)y * W + x] = last < 0 ? -1 : (y - last);
+        }
+        int64_t next = -1;
+        for (int y = H - 1; y >= 0; --y) {
+            if (is_occupied(grid[(size_t)y * W + x])) next = y;
+            int64_t up = g2[(size_t)y * W + x];
+            int64_t dn = next < 0 ? -1 : next - y;
+            int64_t g = up < 0 ? dn : (dn < 0 ? up : (up < dn ? up : dn));
+            g2[(size_t)y * W + x] = g < 0 ? -1 : g * g;
         }
     }
 #ifdef _OPENMP
     #pragma omp parallel for num_threads(n_threads > 0 ? n_threads : 1) schedule(static)
 #endif
     for (int y = 0; y < H; ++y) {
+        const int64_t *row = g2 + (size_t)y * W;
         for (int x = 0; x < W; ++x) {
-            int64_t best = -1;
-            for (int xx = 0; xx < W; ++xx) {
-                int64_t g = g2[(size_t)y * W + xx];
-                if (g < 0) continue;
-                int64_t d = (int64_t)(x - xx) * (x - xx) + g;
-                if (best < 0 || d < best) best = d;
+            int64_t best = row[x];
+            for (int64_t dx = 1; dx < W && (best < 0 || dx * dx < best); ++dx) {
+                int64_t xs[2] = {x - dx, x + dx};
+                for (int k = 0; k < 2; ++k) {
+                    if (xs[k] < 0 || xs[k] >= W || row[xs[k]] < 0) continue;
+                    int64_t d = dx * dx + row[xs[k]];
+                    if (best < 0 || d < best) best = d;
+                }
             }
             d2[(size_t)y * W + x] = best;
         }
@@ -140,18 +150,31 @@ int64_t oracle_d2_capped(const int8_t *grid, int W, int H, int x, int y, int64_t
 
 /*
  * From the beam angles, find N_s (Eq. 14: 2 pi over the angular step) and the
- * panoramic index b_i of every beam.  The step is the unwrapped span over
- * (n - 1); every angle must sit within 1e-3 steps of a multiple of 2 pi / N_s,
- * and no two beams may share an index.
+ * panoramic index b_i of every beam.  Consecutive angles (unwrapped, so a
+ * scan may cross +-pi) differ by a whole number of steps, one step for a
+ * contiguous FoV and more across an occluded sector (Eq. 12); that number is
+ * the difference over the smallest difference, rounded, and the step is the
+ * span over the total.  Every angle must sit within 1e-3 steps of a multiple
+ * of 2 pi / N_s, and no two beams may share an index.
  */
 int oracle_beam_grid(const float *ang, int n, int32_t *ns_out, int32_t *b_out) {
     if (n < 2) return OR_E_BEAM_GRID;
-    double wraps = 0.0;
-    for (int i = 1; i < n; ++i)
-        if ((double)ang[i] < (double)ang[i - 1]) wraps += TWO_PI;
-    double span = ((double)ang[n - 1] + wraps) - (double)ang[0];
-    double step = span / (double)(n - 1);
-    if (!(step > 0.0)) return OR_E_BEAM_GRID;
+    /* unwrapped consecutive differences; the smallest is about one grid step */
+    double *dif = (double *)malloc(sizeof(double) * (size_t)(n - 1));
+    double dmin = INFINITY, span = 0.0;
+    for (int i = 1; i < n; ++i) {
+        double d = (double)ang[i] - (double)ang[i - 1];
+        if (d < 0.0) d += TWO_PI;
+        dif[i - 1] = d;
+        span += d;
+        if (d < dmin) dmin = d;
+    }
+    if (!(dmin > 0.0)) { free(dif); return OR_E_BEAM_GRID; }
+    /* whole grid steps between consecutive beams, then step = span / steps */
+    long long steps = 0;
+    for (int i = 0; i < n - 1; ++i) steps += llround(dif[i] / dmin);
+    free(dif);
+    double step = span / (double)steps;
     long long ns = llround(TWO_PI / step);
     if (ns < n || ns > 65536) return OR_E_BEAM_GRID;
     double dphi = TWO_PI / (double)ns;

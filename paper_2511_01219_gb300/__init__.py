@@ -1,0 +1,260 @@
+"""GB300 relocalization scoring: Python binding of the C ABI in include/relo.h.
+
+This module only marshals arguments: every step of the scoring path runs in
+the CUDA kernels of ``librelo.so`` (built in-tree for sm_103a by
+``paper_2511_01219_gb300._build.build()``).  PyTorch provides device buffers
+and streams; there is no CPU fallback, and importing a context without the
+compiled library raises.
+
+Entry points mirror the C names: ``Relo.load_map`` (EDT precompute, Sec.
+III-A item 3), ``Relo.set_hypotheses`` (Eq. 6), ``Relo.relocalize`` (Eq. 3
+via SMAD ranking, Eq. 16-20, and batched TAM, Eq. 22-31).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librelo.so")
+
+OK = 0
+PENDING = 1
+E_INVALID_ARG = -1
+E_BEAM_GRID = -2
+E_NO_HYPOTHESES = -3
+E_OVER_BUDGET = -4
+E_CUDA = -5
+E_TIMEOUT = -6
+E_NO_VALID_BEAMS = -7
+E_NOT_FOUND = -8
+
+STAGE_SMAD_NUM, STAGE_SMAD_M, STAGE_SURVIVORS, STAGE_TAM, STAGE_BEST_M, STAGE_LOCAL_TOPK, STAGE_SCAN_INFO = range(7)
+
+EXPORTED = [
+    "relo_default_params", "relo_create", "relo_destroy", "relo_last_error", "relo_set_params", "relo_load_map",
+    "relo_load_map_dev", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
+    "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
+    "relo_synth_scans_dev",
+]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("z_hit", ctypes.c_double), ("sigma_hit", ctypes.c_double), ("z_rand", ctypes.c_double),
+        ("eps", ctypes.c_double), ("d_max", ctypes.c_double), ("a_mid_min", ctypes.c_double),
+        ("a_mid_max", ctypes.c_double), ("a_low_min", ctypes.c_double), ("a_low_max", ctypes.c_double),
+        ("tau", ctypes.c_double), ("panoramic_ratio", ctypes.c_double), ("n_orient", ctypes.c_int32),
+        ("topk", ctypes.c_int32), ("batch", ctypes.c_int32), ("local_topk", ctypes.c_int32),
+        ("n_skip_beam", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double), ("tam", ctypes.c_double),
+        ("smad", ctypes.c_double), ("smad_num", ctypes.c_int64), ("n_smad_evals", ctypes.c_int64),
+        ("n_tam_evals", ctypes.c_int64), ("hyp", ctypes.c_int32), ("m", ctypes.c_int32),
+        ("n_batches", ctypes.c_int32), ("status", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+RESULT_BYTES = ctypes.sizeof(Result)
+
+
+class ReloError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"relo error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded librelo.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2511_01219_gb300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, D, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_float
+        sig = {
+            "relo_default_params": (None, [P]),
+            "relo_create": (ctypes.c_int, [P, P, P]),
+            "relo_destroy": (ctypes.c_int, [P]),
+            "relo_last_error": (ctypes.c_char_p, [P]),
+            "relo_set_params": (ctypes.c_int, [P, P]),
+            "relo_load_map": (ctypes.c_int, [P, P, I32, I32, D, D, D, P]),
+            "relo_load_map_dev": (ctypes.c_int, [P, P, I32, I32, D, D, D, P]),
+            "relo_update_map_dev": (ctypes.c_int, [P, I32, P]),
+            "relo_unload_map": (ctypes.c_int, [P, I32]),
+            "relo_map_tables_dev": (ctypes.c_int, [P, I32, P, P, P]),
+            "relo_set_hypotheses": (ctypes.c_int, [P, I32, P, I32]),
+            "relo_set_hypotheses_cells_dev": (ctypes.c_int, [P, I32, P, I32]),
+            "relo_relocalize": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
+            "relo_relocalize_dev": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
+            "relo_get_stage": (ctypes.c_int, [P, I32, P, I64]),
+            "relo_synth_scans_dev": (ctypes.c_int, [P, I32, P, I32, P, I32, F, P, P, I64, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    lib().relo_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _t_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the handle of CUDA's legacy default stream
+
+
+def _stream_handle(stream):
+    """stream: None (torch's current stream), "private" (a new stream owned by
+    the context), a torch.cuda.Stream, or a raw cudaStream_t integer."""
+    if isinstance(stream, str) and stream == "private":
+        return None
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    h = int(getattr(stream, "cuda_stream", stream))
+    return ctypes.c_void_p(h if h != 0 else CUDA_STREAM_LEGACY)
+
+
+class Relo:
+    """One library context (maps, hypothesis sets, scratch) on one CUDA stream.
+
+    By default the context runs on torch's current stream, so device tensors
+    that torch wrote are ready when the library's kernels read them.
+    """
+
+    def __init__(self, params: Params | None = None, stream=None, **overrides):
+        self._L = lib()
+        p = params if params is not None else default_params(**overrides)
+        h = ctypes.c_void_p()
+        s = _stream_handle(stream)
+        rc = self._L.relo_create(ctypes.byref(p), s, ctypes.byref(h))
+        if rc != OK:
+            raise ReloError(rc, "relo_create failed")
+        self._h = h
+        self.params = p
+
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            raise ReloError(rc, f"{what}: {self._L.relo_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.relo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: Params):
+        self._check(self._L.relo_set_params(self._h, ctypes.byref(params)), "set_params")
+        self.params = params
+
+    # ---- maps --------------------------------------------------------------------------
+    def load_map(self, grid: np.ndarray, res: float, origin=(0.0, 0.0)) -> int:
+        g = np.ascontiguousarray(grid, dtype=np.int8)
+        mid = ctypes.c_int32(-1)
+        self._check(self._L.relo_load_map(self._h, _np_ptr(g), g.shape[1], g.shape[0], res, origin[0], origin[1],
+                                          ctypes.byref(mid)), "load_map")
+        return mid.value
+
+    def load_map_dev(self, grid_t, res: float, origin=(0.0, 0.0)) -> int:
+        mid = ctypes.c_int32(-1)
+        self._check(self._L.relo_load_map_dev(self._h, _t_ptr(grid_t), grid_t.shape[1], grid_t.shape[0], res,
+                                              origin[0], origin[1], ctypes.byref(mid)), "load_map_dev")
+        return mid.value
+
+    def update_map_dev(self, map_id: int, grid_t):
+        self._check(self._L.relo_update_map_dev(self._h, map_id, _t_ptr(grid_t)), "update_map_dev")
+
+    def unload_map(self, map_id: int):
+        self._check(self._L.relo_unload_map(self._h, map_id), "unload_map")
+
+    def map_tables(self, map_id: int, shape):
+        """(d2 int32, field uint16 as int32, occ uint8) torch tensors on the current device."""
+        import torch
+        H, W = shape
+        d2 = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        fld = torch.empty((H, W), dtype=torch.int16, device="cuda")
+        occ = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        self._check(self._L.relo_map_tables_dev(self._h, map_id, _t_ptr(d2), _t_ptr(fld), _t_ptr(occ)),
+                    "map_tables")
+        return d2, fld.to(torch.int32) & 0xFFFF, occ
+
+    # ---- hypotheses ----------------------------------------------------------------------
+    def set_hypotheses(self, map_id: int, xy: np.ndarray):
+        a = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        self._check(self._L.relo_set_hypotheses(self._h, map_id, _np_ptr(a), len(a)), "set_hypotheses")
+
+    def set_hypotheses_cells_dev(self, map_id: int, cells_t):
+        self._check(self._L.relo_set_hypotheses_cells_dev(self._h, map_id, _t_ptr(cells_t), cells_t.shape[0]),
+                    "set_hypotheses_cells_dev")
+
+    # ---- relocalization ------------------------------------------------------------------
+    def relocalize(self, map_id: int, ranges: np.ndarray, angles: np.ndarray, max_range: float) -> Result:
+        z = np.ascontiguousarray(ranges, dtype=np.float32)
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        out = Result()
+        self._check(self._L.relo_relocalize(self._h, map_id, _np_ptr(z), _np_ptr(a), len(z), max_range,
+                                            ctypes.byref(out)), "relocalize")
+        return out
+
+    def relocalize_dev(self, map_id: int, ranges_t, angles: np.ndarray, max_range: float, result_t):
+        """Asynchronous: result_t is a device uint8 tensor of RESULT_BYTES bytes."""
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        self._check(self._L.relo_relocalize_dev(self._h, map_id, _t_ptr(ranges_t), _np_ptr(a), int(ranges_t.numel()),
+                                                max_range, _t_ptr(result_t)), "relocalize_dev")
+
+    def stage(self, which: int, dst_t):
+        self._check(self._L.relo_get_stage(self._h, which, _t_ptr(dst_t), dst_t.numel() * dst_t.element_size()),
+                    "get_stage")
+        return dst_t
+
+    def synth_scans(self, map_id: int, cells_t, angles: np.ndarray, max_range: float, ns: int, with_hits=True):
+        import torch
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        n = cells_t.shape[0]
+        r = torch.empty((n, ns), dtype=torch.int32, device=cells_t.device)
+        h = torch.empty((n, ns), dtype=torch.int32, device=cells_t.device) if with_hits else None
+        ns_out = ctypes.c_int32(0)
+        self._check(self._L.relo_synth_scans_dev(self._h, map_id, _t_ptr(cells_t), n, _np_ptr(a), len(a), max_range,
+                                                 _t_ptr(r), None if h is None else _t_ptr(h), r.numel(),
+                                                 ctypes.byref(ns_out)),
+                    "synth_scans")
+        if ns_out.value != ns:
+            raise ReloError(E_BEAM_GRID, f"N_s is {ns_out.value}, expected {ns}")
+        return r, h
+
+
+def result_from_bytes(b: bytes) -> Result:
+    return Result.from_buffer_copy(b)

@@ -1,0 +1,141 @@
+// Map precompute: exact squared Euclidean distance transform (the EDT lookup
+// table of Sec. III-A item 3, used by the likelihood field of Eq. 23 and the
+// distance statistics of Eq. 29-30), its clamped tiled copy for TAM, and the
+// tiled occupancy bitmap for ray casting (Eq. 13).
+//
+// d2(x, y) = min over occupied (x', y') of (x - x')^2 + (y - y')^2 separates
+// into a column term g2(x', y) = min over occupied y' in column x' of
+// (y - y')^2 and a row minimisation d2(x, y) = min over x' of (x - x')^2 +
+// g2(x', y).  The column term comes from two sweeps per column (coalesced
+// across columns); the row minimisation stages one row in shared memory and
+// each thread scans outward from its cell, stopping once (x - x')^2 alone
+// reaches the best value found, which no further column can beat.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "relo_internal.h"
+
+namespace relo {
+
+namespace {
+
+constexpr int kInf = 0x7fffffff;
+
+__global__ void k_edt_cols(const int8_t *__restrict__ grid, int W, int H, int32_t *__restrict__ colsq) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    int last = -1;
+    for (int y = 0; y < H; ++y) {
+        size_t i = (size_t)y * W + x;
+        if (grid[i] >= 65) last = y;
+        colsq[i] = last < 0 ? kInf : y - last;
+    }
+    int next = -1;
+    for (int y = H - 1; y >= 0; --y) {
+        size_t i = (size_t)y * W + x;
+        if (grid[i] >= 65) next = y;
+        int up = colsq[i];
+        int dn = next < 0 ? kInf : next - y;
+        int g = up < dn ? up : dn;
+        colsq[i] = g == kInf ? kInf : g * g;
+    }
+}
+
+__global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int TW, int32_t *__restrict__ d2,
+                           uint16_t *__restrict__ field) {
+    extern __shared__ int32_t row[];
+    const int y = blockIdx.x;
+    const int32_t *src = colsq + (size_t)y * W;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) row[x] = src[x];
+    __syncthreads();
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        int best = row[x];
+        for (int dx = 1; (long long)dx * dx < best; ++dx) {
+            const int dx2 = dx * dx;
+            const int xl = x - dx, xr = x + dx;
+            if (xl < 0 && xr >= W) break;
+            if (xl >= 0) {
+                int v = row[xl];
+                if (v != kInf && v + dx2 < best) best = v + dx2;
+            }
+            if (xr < W) {
+                int v = row[xr];
+                if (v != kInf && v + dx2 < best) best = v + dx2;
+            }
+        }
+        d2[(size_t)y * W + x] = best == kInf ? kD2None : best;
+        field[tile_index(x, y, TW)] = (uint16_t)(best > C ? C : best);
+    }
+}
+
+// one thread per 8x8 tile: occupancy bits, and the clamp value in the parts of
+// edge tiles that lie outside the map
+__global__ void k_tiles(const int8_t *__restrict__ grid, int W, int H, int TW, int TH, int C,
+                        uint64_t *__restrict__ bits, uint16_t *__restrict__ field) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= TW * TH) return;
+    int tx = t % TW, ty = t / TW;
+    uint64_t w = 0;
+    for (int r = 0; r < 8; ++r) {
+        int y = ty * 8 + r;
+        for (int c = 0; c < 8; ++c) {
+            int x = tx * 8 + c;
+            if (x < W && y < H) {
+                if (grid[(size_t)y * W + x] >= 65) w |= 1ull << (r * 8 + c);
+            } else {
+                field[(size_t)t * 64 + r * 8 + c] = (uint16_t)C;
+            }
+        }
+    }
+    bits[t] = w;
+}
+
+__global__ void k_map_tables(const int32_t *__restrict__ d2s, const uint16_t *__restrict__ fs,
+                             const uint64_t *__restrict__ bs, int W, int H, int TW, int32_t *d2, uint16_t *field,
+                             uint8_t *occ) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)W * H) return;
+    int x = (int)(i % W), y = (int)(i / W);
+    if (d2) d2[i] = d2s[i];
+    if (field) field[i] = fs[tile_index(x, y, TW)];
+    if (occ) occ[i] = (uint8_t)((bs[(size_t)(y >> 3) * TW + (x >> 3)] >> (((y & 7) << 3) | (x & 7))) & 1ull);
+}
+
+__global__ void k_check_cells(const int2 *__restrict__ cells, int n, const uint64_t *__restrict__ bits, int W,
+                              int H, int TW, int *bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2 c = cells[i];
+    bool ok = (unsigned)c.x < (unsigned)W && (unsigned)c.y < (unsigned)H;
+    if (ok) ok = !((bits[(size_t)(c.y >> 3) * TW + (c.x >> 3)] >> (((c.y & 7) << 3) | (c.x & 7))) & 1ull);
+    if (!ok) atomicAdd(bad, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
+    k_edt_cols<<<(m.W + 127) / 128, 128, 0, s>>>(m.grid, m.W, m.H, m.colsq);
+    int nt = m.TW * m.TH;
+    k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.C, m.bits, m.field);
+    size_t smem = (size_t)m.W * sizeof(int32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.TW, m.d2, m.field);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s) {
+    size_t n = (size_t)m.W * m.H;
+    k_map_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.d2, m.field, m.bits, m.W, m.H, m.TW, d2, field, occ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_check_cells<<<(n + 255) / 256, 256, 0, s>>>(cells, n, m.bits, m.W, m.H, m.TW, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace relo

@@ -1,0 +1,771 @@
+// Host side of the C ABI declared in include/relo.h: contexts, map slots,
+// hypothesis sets, the per-sensor plan (Eq. 11-15) and the launch sequence of
+// one relocalization.  All scoring arithmetic runs in the library's kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/relo.h"
+#include "relo_internal.h"
+
+using namespace relo;
+
+namespace {
+
+struct SensorPlan {
+    bool valid = false;
+    std::vector<float> angles;   // key: the angles the plan was built from
+    int n_skip = 1, n_orient_param = 0;
+    int n = 0, ns = 0, n_orient = 0, n_enum = 1, n_m = 1;
+    double lam = 0, a_mid = 0, a_low = 0;
+    long long fov = 0;
+    std::vector<int32_t> b;
+    std::vector<int2> D, iv;
+    int32_t *b_dev = nullptr;
+    int2 *D_dev = nullptr, *iv_dev = nullptr;
+    size_t b_cap = 0, D_cap = 0, iv_cap = 0;
+};
+
+struct MapSlot {
+    bool live = false;
+    MapDev dev;
+    double res = 0, ox = 0, oy = 0;
+    int2 *hyps = nullptr;
+    int n_hyp = 0, hyp_cap = 0;
+    float2 *lut = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct relo_ctx {
+    relo_params p;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, n_sm = 0;
+    std::vector<MapSlot> maps;
+    SensorPlan plan;
+    std::string err;
+    long long held = 0;
+    // request scratch
+    float *ranges_dev = nullptr;
+    size_t ranges_cap = 0;
+    int2 *vbR = nullptr;
+    size_t vbR_cap = 0;
+    ScanInfo *scan = nullptr;
+    SelectState *state = nullptr;
+    relo_result *result_dev = nullptr;
+    int *bad = nullptr;
+    unsigned long long *keys = nullptr;
+    size_t keys_cap = 0;
+    long long *smad_num = nullptr;
+    size_t num_cap = 0;
+    int32_t *smad_m = nullptr;
+    size_t m_cap = 0;
+    int32_t *survivors = nullptr;
+    size_t surv_cap = 0;
+    int32_t *best_m = nullptr;
+    size_t bm_cap = 0;
+    unsigned long long *best_key = nullptr;
+    size_t bk_cap = 0;
+    float *T = nullptr;
+    size_t T_cap = 0;
+    int32_t *local = nullptr;
+    size_t local_cap = 0;
+    float *ranges_host = nullptr;
+    size_t ranges_host_cap = 0;
+    relo_result *result_host = nullptr;
+    // shapes of the last request (for relo_get_stage)
+    int last_n_hyp = 0, last_K = 0, last_n_orient = 0, last_batches = 0, last_local = 0, last_ns = 0;
+    int last_enum = 0, last_map = -1;
+};
+
+namespace {
+
+int fail(relo_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(relo_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, RELO_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+int dev_alloc(relo_ctx *ctx, void **p, size_t bytes, const char *what) {
+    if (ctx->p.hbm_budget > 0 && ctx->held + (long long)bytes > ctx->p.hbm_budget)
+        return fail(ctx, RELO_E_OVER_BUDGET, std::string(what) + ": over the context's HBM budget");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(ctx, e, what);
+    }
+    ctx->held += (long long)bytes;
+    return RELO_OK;
+}
+
+void dev_free(relo_ctx *ctx, void *p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        ctx->held -= (long long)bytes;
+    }
+}
+
+template <typename T>
+int ensure(relo_ctx *ctx, T **p, size_t *cap, size_t need, const char *what) {
+    if (need <= *cap && *p) return RELO_OK;
+    size_t n = std::max(need, *cap * 3 / 2);
+    dev_free(ctx, *p, *cap * sizeof(T));
+    *p = nullptr;
+    *cap = 0;
+    int rc = dev_alloc(ctx, (void **)p, n * sizeof(T), what);
+    if (rc == RELO_OK) *cap = n;
+    return rc;
+}
+
+int check_params(relo_ctx *ctx, const relo_params &p) {
+    if (!(p.z_hit > 0) || !(p.sigma_hit > 0) || !(p.z_rand >= 0) || !(p.eps > 0))
+        return fail(ctx, RELO_E_INVALID_ARG, "Eq. 23 needs z_hit > 0, sigma_hit > 0, z_rand >= 0, eps > 0");
+    if (!(p.d_max > 0)) return fail(ctx, RELO_E_INVALID_ARG, "d_max must be positive");
+    for (double a : {p.a_mid_min, p.a_mid_max, p.a_low_min, p.a_low_max})
+        if (!(a > 0 && a <= 1)) return fail(ctx, RELO_E_INVALID_ARG, "retention ratios must lie in (0, 1]");
+    if (p.topk < 1 || p.topk > kMaxTopk) return fail(ctx, RELO_E_INVALID_ARG, "topk must be in [1, 4096]");
+    if (p.batch < 1 || p.batch > kMaxBatch) return fail(ctx, RELO_E_INVALID_ARG, "batch must be in [1, 1024]");
+    if (p.local_topk < 1 || p.local_topk > p.batch)
+        return fail(ctx, RELO_E_INVALID_ARG, "local_topk must be in [1, batch]");
+    if (p.n_skip_beam < 1) return fail(ctx, RELO_E_INVALID_ARG, "n_skip_beam must be >= 1");
+    if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
+    return RELO_OK;
+}
+
+// clamp C = (d_max / res)^2; d_max / res must be an integer
+int clamp_for(relo_ctx *ctx, double d_max, double res, int *C) {
+    double q = d_max / res;
+    long long qi = llround(q);
+    if (fabs(q - (double)qi) > 1e-6 || qi < 1 || qi * qi > kMaxClamp)
+        return fail(ctx, RELO_E_INVALID_ARG, "d_max / res must be an integer in [1, 90]");
+    *C = (int)(qi * qi);
+    return RELO_OK;
+}
+
+// likelihood table of Eq. 23 and sqrt(C) - sqrt(b), for b in [0, C]
+int build_lut(relo_ctx *ctx, MapSlot &m) {
+    const relo_params &p = ctx->p;
+    const int C = m.dev.C;
+    std::vector<float2> h(C + 1);
+    const double sc = sqrt((double)C);
+    for (int b = 0; b <= C; ++b) {
+        double d = m.res * sqrt((double)b);
+        double l = log(p.z_hit * exp(-(d * d) / (2.0 * p.sigma_hit * p.sigma_hit)) + p.z_rand + p.eps);
+        h[b] = make_float2((float)l, (float)(sc - sqrt((double)b)));
+    }
+    if (!m.lut) {
+        int rc = dev_alloc(ctx, (void **)&m.lut, sizeof(float2) * (kMaxClamp + 1), "likelihood table");
+        if (rc) return rc;
+        m.bytes += sizeof(float2) * (kMaxClamp + 1);
+    }
+    CK(cudaMemcpyAsync(m.lut, h.data(), sizeof(float2) * (C + 1), cudaMemcpyHostToDevice, ctx->stream), "lut upload");
+    return RELO_OK;
+}
+
+// ---- sensor plan (Eq. 11-15) ----------------------------------------------------------------
+
+int plan_for(relo_ctx *ctx, const float *angles_raw, int n_raw) {
+    SensorPlan &P = ctx->plan;
+    const int skip = ctx->p.n_skip_beam;
+    const int n = (n_raw + skip - 1) / skip;   // Eq. 11: beams 0, skip, 2 skip, ...
+    std::vector<float> a(n);
+    for (int i = 0; i < n; ++i) a[i] = angles_raw[(size_t)i * skip];
+    if (P.valid && P.n_skip == skip && P.n_orient_param == ctx->p.n_orient && P.angles == a) return RELO_OK;
+    P.valid = false;
+    if (n < 2) return fail(ctx, RELO_E_BEAM_GRID, "need at least two beams");
+    const double two_pi = 2.0 * M_PI;
+    // Consecutive angles differ by a whole number of grid steps (one inside a
+    // contiguous FoV, more across an occluded sector, Eq. 12): count them
+    // against the smallest difference and divide the span by the total.
+    std::vector<double> dif((size_t)(n - 1));
+    double dmin = INFINITY, span = 0.0;
+    for (int i = 1; i < n; ++i) {
+        double d = (double)a[i] - (double)a[i - 1];
+        if (d < 0.0) d += two_pi;
+        dif[i - 1] = d;
+        span += d;
+        if (d < dmin) dmin = d;
+    }
+    if (!(dmin > 0.0)) return fail(ctx, RELO_E_BEAM_GRID, "two beams share an angle");
+    long long steps = 0;
+    for (double d : dif) steps += llround(d / dmin);
+    const double step = span / (double)steps;
+    const long long ns = llround(two_pi / step);   // Eq. 14
+    if (ns < n || ns > kMaxNs) return fail(ctx, RELO_E_BEAM_GRID, "N_s out of range");
+    const double dphi = two_pi / (double)ns;
+    std::vector<int32_t> b(n);
+    std::vector<char> seen((size_t)ns, 0);
+    for (int i = 0; i < n; ++i) {
+        const double q = (double)a[i] / dphi;
+        const long long k = llround(q);
+        if (fabs(q - (double)k) > 1e-3) return fail(ctx, RELO_E_BEAM_GRID, "beam angle off the panoramic grid");
+        const long long bi = ((k % ns) + ns) % ns;
+        if (seen[bi]) return fail(ctx, RELO_E_BEAM_GRID, "two beams on one panoramic direction");
+        seen[bi] = 1;
+        b[i] = (int32_t)bi;
+    }
+    const int n_orient = ctx->p.n_orient > 0 ? ctx->p.n_orient : (int)ns;
+    if (ns % n_orient != 0) return fail(ctx, RELO_E_BEAM_GRID, "n_orient must divide N_s");
+    // FoV intervals (Eq. 12): maximal cyclic runs of covered panoramic indices
+    std::vector<int2> iv;
+    if (n == ns) {
+        iv.push_back(make_int2(0, (int)ns));
+    } else {
+        for (long long j = 0; j < ns; ++j) {
+            if (seen[j] && !seen[(j + ns - 1) % ns]) {
+                int len = 0;
+                while (seen[(j + len) % ns]) ++len;
+                iv.push_back(make_int2((int)j, len));
+            }
+        }
+    }
+    // directions D_j = llround((cos, sin)(2 pi j / N_s) * 2^30)
+    std::vector<int2> D((size_t)ns);
+    for (long long j = 0; j < ns; ++j) {
+        const double ang = two_pi * (double)j / (double)ns;
+        D[j] = make_int2((int)llround(ldexp(cos(ang), 30)), (int)llround(ldexp(sin(ang), 30)));
+    }
+    long long fov = 0;
+    for (auto &v : iv) fov += v.y;
+    const relo_params &p = ctx->p;
+    P.lam = (double)fov / (double)ns;
+    P.a_mid = p.a_mid_min + P.lam * (p.a_mid_max - p.a_mid_min);   // Eq. 25
+    P.a_low = p.a_low_min + P.lam * (p.a_low_max - p.a_low_min);
+    P.fov = fov;
+    P.n = n;
+    P.ns = (int)ns;
+    P.n_orient = n_orient;
+    P.n_enum = (int)ns / n_orient;
+    P.n_m = P.lam >= p.panoramic_ratio ? 1 : n_orient;   // Eq. 20
+    P.b = b;
+    P.D = D;
+    P.iv = iv;
+    int rc;
+    if ((rc = ensure(ctx, &P.b_dev, &P.b_cap, (size_t)n, "plan beams"))) return rc;
+    if ((rc = ensure(ctx, &P.D_dev, &P.D_cap, (size_t)ns, "plan directions"))) return rc;
+    if ((rc = ensure(ctx, &P.iv_dev, &P.iv_cap, iv.size(), "plan intervals"))) return rc;
+    CK(cudaMemcpyAsync(P.b_dev, b.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
+    CK(cudaMemcpyAsync(P.D_dev, D.data(), sizeof(int2) * ns, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
+    CK(cudaMemcpyAsync(P.iv_dev, iv.data(), sizeof(int2) * iv.size(), cudaMemcpyHostToDevice, ctx->stream),
+       "plan upload");
+    // the host vectors must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(ctx->stream), "plan upload");
+    P.angles = a;
+    P.n_skip = skip;
+    P.n_orient_param = ctx->p.n_orient;
+    P.valid = true;
+    return RELO_OK;
+}
+
+MapSlot *get_map(relo_ctx *ctx, int id) {
+    if (id < 0 || id >= (int)ctx->maps.size() || !ctx->maps[id].live) return nullptr;
+    return &ctx->maps[id];
+}
+
+void free_map(relo_ctx *ctx, MapSlot &m) {
+    dev_free(ctx, m.dev.d2, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
+    dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
+    dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
+    dev_free(ctx, m.dev.field, sizeof(uint16_t) * 64 * (size_t)m.dev.TW * m.dev.TH);
+    dev_free(ctx, m.dev.bits, sizeof(uint64_t) * (size_t)m.dev.TW * m.dev.TH);
+    dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
+    dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 1));
+    m = MapSlot();
+}
+
+int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, int32_t h, double res, double ox,
+                  double oy, int32_t *map_id) {
+    if (!ctx || !grid || !map_id) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    if (w < 1 || h < 1 || w > 16384 || h > 16384) return fail(ctx, RELO_E_INVALID_ARG, "map size out of range");
+    if (!(res > 0) || !isfinite(ox) || !isfinite(oy)) return fail(ctx, RELO_E_INVALID_ARG, "bad resolution or origin");
+    MapSlot m;
+    m.res = res;
+    m.ox = ox;
+    m.oy = oy;
+    m.dev.W = w;
+    m.dev.H = h;
+    m.dev.TW = (w + 7) / 8;
+    m.dev.TH = (h + 7) / 8;
+    int rc = clamp_for(ctx, ctx->p.d_max, res, &m.dev.C);
+    if (rc) return rc;
+    const size_t cells = (size_t)w * h, tiles = (size_t)m.dev.TW * m.dev.TH;
+    struct { void **p; size_t bytes; } allocs[] = {
+        {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
+        {(void **)&m.dev.field, tiles * 64 * 2}, {(void **)&m.dev.bits, tiles * 8}};
+    for (auto &a : allocs) {
+        rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
+        if (rc) {
+            free_map(ctx, m);
+            return rc;
+        }
+        m.bytes += a.bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = launch_edt(m.dev, ctx->stream);
+    if (e != cudaSuccess) {
+        free_map(ctx, m);
+        return cuda_fail(ctx, e, "map precompute");
+    }
+    rc = build_lut(ctx, m);
+    if (rc) {
+        free_map(ctx, m);
+        return rc;
+    }
+    if (!on_device) {
+        // the host grid may be released once the call returns
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            free_map(ctx, m);
+            return cuda_fail(ctx, e, "map upload");
+        }
+    } else {
+        // the LUT host staging vector was already copied; make that copy complete too
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            free_map(ctx, m);
+            return cuda_fail(ctx, e, "map precompute");
+        }
+    }
+    m.live = true;
+    int id = -1;
+    for (int i = 0; i < (int)ctx->maps.size(); ++i)
+        if (!ctx->maps[i].live) { id = i; break; }
+    if (id < 0) {
+        id = (int)ctx->maps.size();
+        ctx->maps.push_back(MapSlot());
+    }
+    ctx->maps[id] = m;
+    *map_id = id;
+    return RELO_OK;
+}
+
+int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, int n) {
+    int rc = RELO_OK;
+    if (n > (1 << kHypBits)) return fail(ctx, RELO_E_INVALID_ARG, "too many hypotheses (max 2^21)");
+    if (n > m.hyp_cap) {
+        dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
+        m.hyps = nullptr;
+        m.hyp_cap = 0;
+        if ((rc = dev_alloc(ctx, (void **)&m.hyps, sizeof(int2) * (size_t)n, "hypotheses"))) return rc;
+        m.hyp_cap = n;
+    }
+    CK(cudaMemcpyAsync(m.hyps, cells, sizeof(int2) * (size_t)n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream),
+       "hypothesis upload");
+    if (!ctx->bad && (rc = dev_alloc(ctx, (void **)&ctx->bad, sizeof(int), "flags"))) return rc;
+    CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), ctx->stream), "hypothesis check");
+    CK(launch_check_cells(m.hyps, n, m.dev, ctx->bad, ctx->stream), "hypothesis check");
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, ctx->bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "hypothesis check");
+    CK(cudaStreamSynchronize(ctx->stream), "hypothesis check");
+    if (bad) {
+        m.n_hyp = 0;
+        return fail(ctx, RELO_E_INVALID_ARG, std::to_string(bad) + " hypotheses off the map or on occupied cells");
+    }
+    m.n_hyp = n;
+    return RELO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void relo_default_params(relo_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->z_hit = 1.0;
+    p->sigma_hit = 0.2;
+    p->z_rand = 0.0;
+    p->eps = 1e-6;
+    p->d_max = 2.0;
+    p->a_mid_min = 0.9;
+    p->a_mid_max = 0.8;
+    p->a_low_min = 0.8;
+    p->a_low_max = 0.6;
+    p->tau = 0.95;
+    p->panoramic_ratio = 0.9;
+    p->n_orient = 360;
+    p->topk = 256;
+    p->batch = 200;
+    p->local_topk = 20;
+    p->n_skip_beam = 1;
+    p->early_stop = 1;
+    p->hbm_budget = 0;
+}
+
+int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
+    if (!out) return RELO_E_INVALID_ARG;
+    *out = nullptr;
+    relo_ctx *ctx = new (std::nothrow) relo_ctx();
+    if (!ctx) return RELO_E_INVALID_ARG;
+    if (p) ctx->p = *p;
+    else relo_default_params(&ctx->p);
+    int rc = check_params(ctx, ctx->p);
+    if (rc) {
+        delete ctx;
+        return rc;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            ctx->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->result_host, sizeof(relo_result));
+    if (e != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return RELO_E_CUDA;
+    }
+    if ((rc = dev_alloc(ctx, (void **)&ctx->scan, sizeof(ScanInfo), "request state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->state, sizeof(SelectState), "request state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->result_dev, sizeof(relo_result), "request state"))) {
+        relo_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return RELO_OK;
+}
+
+int relo_destroy(relo_ctx *ctx) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &m : ctx->maps)
+        if (m.live) free_map(ctx, m);
+    SensorPlan &P = ctx->plan;
+    void *ptrs[] = {P.b_dev, P.D_dev, P.iv_dev, ctx->ranges_dev, ctx->vbR, ctx->scan, ctx->state, ctx->result_dev,
+                    ctx->bad, ctx->keys, ctx->smad_num, ctx->smad_m, ctx->survivors, ctx->best_m, ctx->best_key,
+                    ctx->T, ctx->local};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
+    if (ctx->result_host) cudaFreeHost(ctx->result_host);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return RELO_OK;
+}
+
+const char *relo_last_error(const relo_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int relo_set_params(relo_ctx *ctx, const relo_params *p) {
+    if (!ctx || !p) return RELO_E_INVALID_ARG;
+    int rc = check_params(ctx, *p);
+    if (rc) return rc;
+    const bool lut_changed = p->z_hit != ctx->p.z_hit || p->sigma_hit != ctx->p.sigma_hit ||
+                             p->z_rand != ctx->p.z_rand || p->eps != ctx->p.eps || p->d_max != ctx->p.d_max;
+    ctx->p = *p;
+    ctx->plan.valid = false;
+    if (lut_changed) {
+        for (auto &m : ctx->maps) {
+            if (!m.live) continue;
+            int C;
+            if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
+            m.dev.C = C;
+            CK(launch_edt(m.dev, ctx->stream), "map rebuild");
+            if ((rc = build_lut(ctx, m))) return rc;
+        }
+        CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
+    }
+    return RELO_OK;
+}
+
+int relo_load_map(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, double res, double ox, double oy,
+                  int32_t *map_id) {
+    return load_map_impl(ctx, grid, false, w, h, res, ox, oy, map_id);
+}
+
+int relo_load_map_dev(relo_ctx *ctx, const int8_t *grid_dev, int32_t w, int32_t h, double res, double ox, double oy,
+                      int32_t *map_id) {
+    return load_map_impl(ctx, grid_dev, true, w, h, res, ox, oy, map_id);
+}
+
+int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
+    if (!ctx || !grid_dev) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
+       "map update");
+    CK(launch_edt(m->dev, ctx->stream), "map update");
+    return RELO_OK;
+}
+
+int relo_unload_map(relo_ctx *ctx, int32_t map_id) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    CK(cudaStreamSynchronize(ctx->stream), "map unload");
+    free_map(ctx, *m);
+    return RELO_OK;
+}
+
+int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t *field_dev, uint8_t *occ_dev) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    CK(launch_map_tables(m->dev, d2_dev, field_dev, occ_dev, ctx->stream), "map tables");
+    CK(cudaStreamSynchronize(ctx->stream), "map tables");
+    return RELO_OK;
+}
+
+int relo_set_hypotheses(relo_ctx *ctx, int32_t map_id, const double *xy, int32_t n) {
+    if (!ctx || (!xy && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad hypothesis arguments");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    std::vector<int2> cells((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const double fx = floor((xy[2 * i] - m->ox) / m->res), fy = floor((xy[2 * i + 1] - m->oy) / m->res);
+        if (!(fx >= 0 && fy >= 0 && fx < m->dev.W && fy < m->dev.H))
+            return fail(ctx, RELO_E_INVALID_ARG, "hypothesis outside the map");
+        cells[i] = make_int2((int)fx, (int)fy);
+    }
+    return set_hyps_impl(ctx, *m, cells.data(), false, n);
+}
+
+int relo_set_hypotheses_cells_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n) {
+    if (!ctx || (!cells_dev && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad hypothesis arguments");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    return set_hyps_impl(ctx, *m, reinterpret_cast<const int2 *>(cells_dev), true, n);
+}
+
+int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles,
+                        int32_t n_beams, float max_range, relo_result *result_dev) {
+    if (!ctx || !ranges_dev || !angles || !result_dev || n_beams < 2)
+        return fail(ctx, RELO_E_INVALID_ARG, "bad relocalize arguments");
+    MapSlot *mp = get_map(ctx, map_id);
+    if (!mp) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    MapSlot &m = *mp;
+    if (m.n_hyp <= 0) return fail(ctx, RELO_E_NO_HYPOTHESES, "the map has no hypotheses");
+    if (!(max_range > 0) || !isfinite(max_range)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
+    int rc = plan_for(ctx, angles, n_beams);
+    if (rc) return rc;
+    const SensorPlan &P = ctx->plan;
+    const relo_params &p = ctx->p;
+    if (P.n > kMaxValidBeams) return fail(ctx, RELO_E_INVALID_ARG, "at most 2048 beams after downsampling");
+    const double rq = (double)max_range * 65536.0 / m.res;
+    if (!(rq < 2147483647.0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
+    const long long rmax_q16 = llrint(rq);
+    if ((double)P.n * (double)rmax_q16 >= 8.0e12)
+        return fail(ctx, RELO_E_INVALID_ARG, "beam count x max range too large for the SMAD key");
+    const long long lim = (rmax_q16 * rmax_q16) >> 32;
+    const int n_hyp = m.n_hyp;
+    const int K = std::min(p.topk, n_hyp);
+    const int B = std::min(p.batch, K);
+    const int n_batches = (K + B - 1) / B;
+    const int L = p.local_topk;
+    if ((rc = ensure(ctx, &ctx->vbR, &ctx->vbR_cap, (size_t)P.n, "scan buffers")) ||
+        (rc = ensure(ctx, &ctx->keys, &ctx->keys_cap, (size_t)n_hyp, "SMAD keys")) ||
+        (rc = ensure(ctx, &ctx->smad_num, &ctx->num_cap, (size_t)n_hyp, "SMAD numerators")) ||
+        (rc = ensure(ctx, &ctx->smad_m, &ctx->m_cap, (size_t)n_hyp, "SMAD orientations")) ||
+        (rc = ensure(ctx, &ctx->survivors, &ctx->surv_cap, (size_t)K, "survivors")) ||
+        (rc = ensure(ctx, &ctx->best_m, &ctx->bm_cap, (size_t)K, "orientation argmax")) ||
+        (rc = ensure(ctx, &ctx->best_key, &ctx->bk_cap, (size_t)K, "orientation argmax")) ||
+        (rc = ensure(ctx, &ctx->T, &ctx->T_cap, (size_t)K * P.n_orient, "TAM scores")) ||
+        (rc = ensure(ctx, &ctx->local, &ctx->local_cap, (size_t)n_batches * L, "local top-k")))
+        return rc;
+    cudaStream_t st = ctx->stream;
+    // a2: per-scan preparation (Eq. 11, 16, 26)
+    CK(launch_scan_prep(ranges_dev, P.n, p.n_skip_beam, max_range, m.res, P.b_dev, P.a_mid, P.a_low, ctx->vbR,
+                        ctx->scan, st),
+       "scan preparation");
+    // a3 + a4: ray casting and SMAD (Eq. 13, 17-20)
+    RayArgs ra;
+    ra.bits = m.dev.bits;
+    ra.W = m.dev.W;
+    ra.H = m.dev.H;
+    ra.TW = m.dev.TW;
+    ra.D = P.D_dev;
+    ra.ns = P.ns;
+    ra.ns_pad = (P.ns + 31) & ~31;
+    ra.lim = (int)lim;
+    ra.hyps = m.hyps;
+    ra.n_hyp = n_hyp;
+    ra.iv = P.iv_dev;
+    ra.n_iv = (int)P.iv.size();
+    ra.scan = ctx->scan;
+    ra.n_enum = P.n_enum;
+    ra.n_m = P.n_m;
+    ra.keys = ctx->keys;
+    ra.smad_num = ctx->smad_num;
+    ra.smad_m = ctx->smad_m;
+    CK(launch_raycast_smad(ra, ctx->n_sm, st), "ray cast + SMAD");
+    // a5: SMAD ordering, K survivors
+    CK(launch_topk(ctx->keys, n_hyp, K, ctx->survivors, st), "SMAD top-K");
+    // a6 + a7: batched TAM, orientation argmax, local top-k, early termination
+    CK(cudaMemsetAsync(ctx->best_key, 0, sizeof(unsigned long long) * K, st), "request reset");
+    CK(cudaMemsetAsync(ctx->best_m, 0xff, sizeof(int32_t) * K, st), "request reset");
+    CK(cudaMemsetAsync(ctx->T, 0xff, sizeof(float) * (size_t)K * P.n_orient, st), "request reset");
+    CK(cudaMemsetAsync(ctx->local, 0xff, sizeof(int32_t) * (size_t)n_batches * L, st), "request reset");
+    CK(cudaMemsetAsync(ctx->state, 0, sizeof(SelectState), st), "request reset");
+    TamArgs ta;
+    ta.field = m.dev.field;
+    ta.W = m.dev.W;
+    ta.H = m.dev.H;
+    ta.TW = m.dev.TW;
+    ta.C = m.dev.C;
+    ta.D = P.D_dev;
+    ta.ns = P.ns;
+    ta.vbR = ctx->vbR;
+    ta.scan = ctx->scan;
+    ta.survivors = ctx->survivors;
+    ta.hyps = m.hyps;
+    ta.n_orient = P.n_orient;
+    ta.n_enum = P.n_enum;
+    ta.lut = m.lut;
+    ta.res = (float)m.res;
+    ta.res2 = (float)(m.res * m.res);
+    ta.d_max = (float)(m.res * sqrt((double)m.dev.C));
+    ta.d_min = (float)(m.res / 2.0);
+    ta.T = ctx->T;
+    ta.best_key = ctx->best_key;
+    ta.state = ctx->state;
+    for (int bi = 0; bi < n_batches; ++bi) {
+        ta.s_begin = bi * B;
+        ta.s_end = std::min(K, ta.s_begin + B);
+        CK(launch_tam(ta, P.n, ctx->n_sm, st), "TAM");
+        CK(launch_select_batch(ctx->best_key, ta.s_begin, ta.s_end, P.n_orient, P.n_enum, L, bi, p.tau,
+                               p.early_stop, ctx->best_m, ctx->local, ctx->state, st),
+           "batch selection");
+    }
+    FinalizeArgs fa;
+    fa.st = ctx->state;
+    fa.survivors = ctx->survivors;
+    fa.best_m = ctx->best_m;
+    fa.hyps = m.hyps;
+    fa.smad_num = ctx->smad_num;
+    fa.scan = ctx->scan;
+    fa.res = m.res;
+    fa.ox = m.ox;
+    fa.oy = m.oy;
+    fa.fov_beams = (double)P.fov;
+    fa.ns = P.ns;
+    fa.n_smad_evals = (long long)n_hyp * P.n_m;
+    fa.result = result_dev;
+    CK(launch_finalize(fa, st), "finalize");
+    ctx->last_n_hyp = n_hyp;
+    ctx->last_K = K;
+    ctx->last_n_orient = P.n_orient;
+    ctx->last_batches = n_batches;
+    ctx->last_local = L;
+    ctx->last_ns = P.ns;
+    ctx->last_enum = P.n_enum;
+    ctx->last_map = map_id;
+    return RELO_OK;
+}
+
+int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                    float max_range, relo_result *out) {
+    if (!ctx || !ranges || !angles || !out || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    if ((size_t)n_beams > ctx->ranges_host_cap) {
+        if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
+        ctx->ranges_host = nullptr;
+        ctx->ranges_host_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->ranges_host, sizeof(float) * n_beams), "pinned staging");
+        ctx->ranges_host_cap = n_beams;
+    }
+    int rc = ensure(ctx, &ctx->ranges_dev, &ctx->ranges_cap, (size_t)n_beams, "scan upload");
+    if (rc) return rc;
+    memcpy(ctx->ranges_host, ranges, sizeof(float) * n_beams);
+    CK(cudaMemcpyAsync(ctx->ranges_dev, ctx->ranges_host, sizeof(float) * n_beams, cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "scan upload");
+    rc = relo_relocalize_dev(ctx, map_id, ctx->ranges_dev, angles, n_beams, max_range, ctx->result_dev);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->result_host, ctx->result_dev, sizeof(relo_result), cudaMemcpyDeviceToHost, ctx->stream),
+       "result download");
+    CK(cudaStreamSynchronize(ctx->stream), "relocalize");
+    *out = *ctx->result_host;
+    if (out->status != RELO_OK) return fail(ctx, out->status, "the scan has no valid beam");
+    return RELO_OK;
+}
+
+int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes) {
+    if (!ctx || !dst_dev) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    if (ctx->last_map < 0) return fail(ctx, RELO_E_NOT_FOUND, "no relocalization has run");
+    const void *src = nullptr;
+    size_t need = 0;
+    long long info_host[8];
+    switch (which) {
+        case RELO_STAGE_SMAD_NUM: src = ctx->smad_num; need = 8ull * ctx->last_n_hyp; break;
+        case RELO_STAGE_SMAD_M: src = ctx->smad_m; need = 4ull * ctx->last_n_hyp; break;
+        case RELO_STAGE_SURVIVORS: src = ctx->survivors; need = 4ull * ctx->last_K; break;
+        case RELO_STAGE_TAM: src = ctx->T; need = 4ull * ctx->last_K * ctx->last_n_orient; break;
+        case RELO_STAGE_BEST_M: src = ctx->best_m; need = 4ull * ctx->last_K; break;
+        case RELO_STAGE_LOCAL_TOPK: src = ctx->local; need = 4ull * ctx->last_batches * ctx->last_local; break;
+        case RELO_STAGE_SCAN_INFO: {
+            ScanInfo si;
+            SelectState ss;
+            CK(cudaMemcpyAsync(&si, ctx->scan, sizeof si, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            CK(cudaMemcpyAsync(&ss, ctx->state, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            CK(cudaStreamSynchronize(ctx->stream), "stage read");
+            long long v[8] = {ctx->last_ns, ctx->last_n_orient, ctx->last_enum, si.n_valid, si.k_ret, si.sum_real,
+                              ctx->last_K, ss.n_batches};
+            memcpy(info_host, v, sizeof v);
+            src = info_host;
+            need = sizeof info_host;
+            if ((size_t)bytes < need) return fail(ctx, RELO_E_INVALID_ARG, "destination too small");
+            CK(cudaMemcpy(dst_dev, src, need, cudaMemcpyHostToDevice), "stage copy");
+            return RELO_OK;
+        }
+        default: return fail(ctx, RELO_E_INVALID_ARG, "unknown stage");
+    }
+    if ((size_t)bytes < need) return fail(ctx, RELO_E_INVALID_ARG, "destination too small");
+    CK(cudaMemcpyAsync(dst_dev, src, need, cudaMemcpyDeviceToDevice, ctx->stream), "stage copy");
+    CK(cudaStreamSynchronize(ctx->stream), "stage copy");
+    return RELO_OK;
+}
+
+int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n, const float *angles,
+                         int32_t n_beams, float max_range, uint32_t *ranges_dev, int32_t *hit_dev, int64_t capacity,
+                         int32_t *ns_out) {
+    if (!ctx || !cells_dev || !angles || !ranges_dev || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    int rc = plan_for(ctx, angles, n_beams);
+    if (rc) return rc;
+    const SensorPlan &P = ctx->plan;
+    if (ns_out) *ns_out = P.ns;
+    if ((long long)n * P.ns > capacity) return fail(ctx, RELO_E_INVALID_ARG, "output buffers hold fewer than n x N_s");
+    const double rq = (double)max_range * 65536.0 / m->res;
+    if (!(max_range > 0) || !(rq < 2147483647.0)) return fail(ctx, RELO_E_INVALID_ARG, "bad max_range");
+    const long long rmax_q16 = llrint(rq);
+    RayArgs ra;
+    memset(&ra, 0, sizeof ra);
+    ra.bits = m->dev.bits;
+    ra.W = m->dev.W;
+    ra.H = m->dev.H;
+    ra.TW = m->dev.TW;
+    ra.D = P.D_dev;
+    ra.ns = P.ns;
+    ra.ns_pad = (P.ns + 31) & ~31;
+    ra.lim = (int)((rmax_q16 * rmax_q16) >> 32);
+    ra.hyps = reinterpret_cast<const int2 *>(cells_dev);
+    ra.n_hyp = n;
+    CK(launch_synth(ra, ranges_dev, hit_dev, ctx->stream), "synthesized scans");
+    CK(cudaStreamSynchronize(ctx->stream), "synthesized scans");
+    return RELO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,333 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Bit-exact: EDT d2, clamped field and occupancy; synthesized ranges and hit
+cells; SMAD numerators and minimising shifts; the SMAD survivor list; the
+per-batch local top-k (up to TAM ties); counters.  Floating point: every TAM
+score within 1e-5 relative of the FP64 oracle (the float32 epilogue's error
+budget is about 1e-6, derived in the design doc's tolerance section); the selected
+pose identical unless the oracle scores the two candidates within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def relo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    return relo
+
+
+def torch_():
+    import torch
+    return torch
+
+
+def run(relo, grid, res, hyps, ranges, angles, max_range, **params):
+    ctx = relo.Relo(**params)
+    mid = ctx.load_map(grid, res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
+    out = ctx.relocalize(mid, ranges, angles, max_range)
+    return ctx, mid, out
+
+
+def stages(relo, ctx, n_hyp, K, n_orient, n_batches, local_topk):
+    torch = torch_()
+    num = ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(n_hyp, dtype=torch.int64, device="cuda")).cpu().numpy()
+    mm = ctx.stage(relo.STAGE_SMAD_M, torch.empty(n_hyp, dtype=torch.int32, device="cuda")).cpu().numpy()
+    surv = ctx.stage(relo.STAGE_SURVIVORS, torch.empty(K, dtype=torch.int32, device="cuda")).cpu().numpy()
+    T = ctx.stage(relo.STAGE_TAM, torch.empty(K * n_orient, dtype=torch.float32, device="cuda")).cpu().numpy()
+    bm = ctx.stage(relo.STAGE_BEST_M, torch.empty(K, dtype=torch.int32, device="cuda")).cpu().numpy()
+    loc = ctx.stage(relo.STAGE_LOCAL_TOPK, torch.empty(n_batches * local_topk, dtype=torch.int32,
+                                                       device="cuda")).cpu().numpy()
+    info = ctx.stage(relo.STAGE_SCAN_INFO, torch.empty(8, dtype=torch.int64, device="cuda")).cpu().numpy()
+    return dict(num=num, m=mm, surv=surv, T=T.reshape(K, n_orient), best_m=bm,
+                local=loc.reshape(n_batches, local_topk), info=info)
+
+
+def assert_tam_close(got, want):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-30)
+    bad = ~((np.abs(got - want) <= RTOL * np.abs(want)) | ((want == 0) & (np.abs(got) <= 1e-7)))
+    assert not bad.any(), f"{bad.sum()} TAM scores off; worst rel {err.max():.3g}"
+
+
+def check_pose(got, want_hyp, want_m, T_or_fn):
+    """Selected pose equal, or the oracle scores both candidates within RTOL."""
+    if (got.hyp, got.m) == (want_hyp, want_m):
+        return
+    t_got, t_want = T_or_fn(got.hyp, got.m), T_or_fn(want_hyp, want_m)
+    assert abs(t_got - t_want) <= RTOL * t_want, ((got.hyp, got.m, t_got), (want_hyp, want_m, t_want))
+
+
+# ------------------------------------------------------------------------------------------
+# EDT tables
+# ------------------------------------------------------------------------------------------
+
+def edt_case(relo, grid, res=0.05, d_max=2.0):
+    torch = torch_()
+    ctx = relo.Relo(d_max=d_max)
+    mid = ctx.load_map(grid, res)
+    d2, fld, occ = ctx.map_tables(mid, grid.shape)
+    want = oracle.edt(grid)
+    C = int(round(d_max / res)) ** 2
+    assert np.array_equal(d2.cpu().numpy().astype(np.int64), want)
+    assert np.array_equal(fld.cpu().numpy(), np.where((want < 0) | (want > C), C, want))
+    assert np.array_equal(occ.cpu().numpy(), (grid >= 65).astype(np.uint8))
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape,p", [((37, 53), 0.05), ((8, 8), 0.3), ((1, 1), 0.0), ((65, 1), 0.1),
+                                     ((1, 77), 0.1), ((129, 200), 0.0), ((300, 257), 0.002)])
+def test_edt_random_grids(relo, shape, p):
+    rng = np.random.default_rng(hash(shape) % 2 ** 32)
+    g = np.where(rng.random(shape) < p, 100, 0).astype(np.int8)
+    g[rng.random(shape) < 0.03] = -1
+    edt_case(relo, g)
+
+
+def test_edt_room_and_office(relo, workload):
+    edt_case(relo, workload(0).grid)
+    edt_case(relo, workload(1).grid)
+
+
+def test_edt_warehouse_sampled(relo, workload):
+    torch = torch_()
+    wl = workload(2)
+    ctx = relo.Relo()
+    mid = ctx.load_map(wl.grid, wl.res)
+    d2, fld, occ = ctx.map_tables(mid, wl.grid.shape)
+    want = oracle.edt(wl.grid)
+    assert np.array_equal(d2.cpu().numpy().astype(np.int64), want)
+    rng = np.random.default_rng(5)
+    for _ in range(200):        # spot checks against the plain definition
+        x, y = int(rng.integers(4096)), int(rng.integers(4096))
+        assert d2[y, x].item() == oracle.d2_capped(wl.grid, x, y, 1 << 40)
+    ctx.close()
+
+
+# ------------------------------------------------------------------------------------------
+# synthesized scans
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cfg,n_check", [(0, 200), (1, 40), (2, 12)])
+def test_synth_scans_bit_exact(relo, workload, cfg, n_check):
+    torch = torch_()
+    wl = workload(cfg)
+    prm = oracle.Params(n_orient=wl.n_orient)
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    ctx = relo.Relo(n_orient=wl.n_orient)
+    mid = ctx.load_map(wl.grid, wl.res)
+    sel = np.random.default_rng(cfg).choice(len(wl.hyps), n_check, replace=False)
+    cells = torch.tensor(wl.hyps[sel], dtype=torch.int32, device="cuda")
+    r, h = ctx.synth_scans(mid, cells, wl.angles, wl.max_range, pl["ns"])
+    r, h = r.cpu().numpy().view(np.uint32), h.cpu().numpy()
+    W = wl.grid.shape[1]
+    for k, i in enumerate(sel):
+        want_r, hx, hy = oracle.synth_scan(wl.grid, int(wl.hyps[i, 0]), int(wl.hyps[i, 1]), pl)
+        assert np.array_equal(r[k].astype(np.int64), want_r)
+        assert np.array_equal(h[k], np.where(hx < 0, -1, hy * W + hx))
+    ctx.close()
+
+
+# ------------------------------------------------------------------------------------------
+# the whole path
+# ------------------------------------------------------------------------------------------
+
+def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95, n_skip=1, sample_tam=None):
+    prm = oracle.Params(n_orient=wl.n_orient, topk=K, batch=batch, local_topk=local_topk, tau=tau,
+                        n_skip_beam=n_skip)
+    ctx, mid, got = run(relo, wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, n_orient=wl.n_orient,
+                        topk=K, batch=batch, local_topk=local_topk, tau=tau, early_stop=int(early_stop),
+                        n_skip_beam=n_skip)
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    Kc = min(K, len(wl.hyps))
+    B = min(batch, Kc)
+    nb = -(-Kc // B)
+    st = stages(relo, ctx, len(wl.hyps), Kc, pl["n_orient"], nb, local_topk)
+    # SMAD and ranking: bit-exact
+    num, mm = oracle.smad(wl.grid, wl.hyps, pl)
+    assert np.array_equal(st["num"], num)
+    assert np.array_equal(st["m"], mm)
+    surv = oracle.rank(num, Kc)
+    assert np.array_equal(st["surv"], surv)
+    info = st["info"]
+    assert info[0] == pl["ns"] and info[1] == pl["n_orient"] and info[3] == pl["n_valid"]
+    assert info[5] == pl["sum_real"] and info[6] == Kc
+    k_ret = sorted([pl["n_valid"], max(1, math.floor(pl["a_mid"] * pl["n_valid"])),
+                    max(1, math.floor(pl["a_low"] * pl["n_valid"]))])[1]
+    assert info[4] == k_ret
+    d2 = oracle.edt(wl.grid)
+    n_scored = int(info[7]) * B
+    n_scored = min(n_scored, Kc)
+    rows = np.arange(n_scored) if sample_tam is None else np.unique(np.concatenate(
+        [np.random.default_rng(1).choice(n_scored, min(sample_tam, n_scored), replace=False), [0]]))
+    T_or = oracle.tam_grid(wl.grid, wl.hyps, surv[rows], pl, prm, wl.res, d2)
+    assert_tam_close(st["T"][rows], T_or)
+    assert np.isnan(st["T"][n_scored:]).all()
+    # orientation argmax per scored survivor (Eq. 22)
+    for r_i, r in enumerate(rows):
+        q_or = oracle.best_orientation(T_or[r_i])
+        q_gpu = st["best_m"][r] // pl["n_enum"]
+        if q_gpu != q_or:
+            assert abs(T_or[r_i, q_gpu] - T_or[r_i, q_or]) <= RTOL * T_or[r_i, q_or]
+    assert got.status == 0 and got.n_batches == info[7]
+    assert got.n_tam_evals == n_scored * pl["n_orient"]
+    assert got.n_smad_evals == len(wl.hyps) * (1 if pl["panoramic"] else pl["n_orient"])
+    return ctx, got, st, pl, prm, d2, surv, rows, T_or
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_full_path_matches_oracle(relo, workload, cfg):
+    wl = workload(cfg)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk)
+    want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range,
+                             oracle.Params(n_orient=wl.n_orient, topk=wl.topk), d2tab=d2, early_stop=False)
+
+    def T_at(h, m):
+        return float(oracle.tam(wl.grid, np.array([wl.hyps[h]]), np.array([m]), pl, prm, wl.res, d2)[0])
+    check_pose(got, want["hyp"], want["m"], T_at)
+    assert abs(got.tam - T_at(got.hyp, got.m)) <= RTOL * T_at(got.hyp, got.m)
+    assert math.isclose(got.x, (wl.hyps[got.hyp, 0] + 0.5) * wl.res) and got.smad_num == st["num"][got.hyp]
+    th = got.m * 2 * math.pi / pl["ns"]
+    assert math.isclose(got.theta, th - 2 * math.pi if th >= math.pi else th, abs_tol=1e-12)
+    ctx.close()
+
+
+def test_warehouse_full_size_sampled(relo, workload):
+    """4096^2 map, 20000 hypotheses, 720 orientations, K = 1024: SMAD and the
+    survivor list bit-exact everywhere; TAM on 48 sampled survivors x 720."""
+    wl = workload(2)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, sample_tam=48)
+    assert pl["panoramic"]                    # 360-degree scan: SMAD at m = 0 only (Eq. 20)
+    # the selected pose scores at least as well as every sampled survivor's best
+    T_sel = float(oracle.tam(wl.grid, np.array([wl.hyps[got.hyp]]), np.array([got.m]), pl, prm, wl.res, d2)[0])
+    assert abs(got.tam - T_sel) <= RTOL * T_sel
+    assert T_sel >= T_or.max() * (1 - RTOL)
+    ctx.close()
+
+
+def test_batches_early_termination_and_local_topk(relo, workload):
+    wl = workload(1)
+    for tau, early in ((0.0, True), (2.0, True), (0.95, False)):
+        ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, 100, early_stop=early, batch=30,
+                                                                 local_topk=7, tau=tau)
+        want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
+                                 early_stop=early)
+        assert got.n_batches == want["n_batches"] == (1 if tau == 0.0 else 4)
+        for b, local in enumerate(want["batches"]):
+            g = [int(s) for s in st["local"][b] if s >= 0]
+            w = [pos for (_, pos, _, _) in local]
+            if g != w:   # allow swaps of TAM ties within tolerance
+                Tg = [T_or[s].max() for s in g]
+                Tw = [T_or[s].max() for s in w]
+                assert np.allclose(Tg, Tw, rtol=RTOL)
+        ctx.close()
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------
+
+def small_case(seed=3, n_beams=90, ns=120, n_orient=40, max_range=4.0):
+    g = workloads.make_room(seed, n=40, n_boxes=4)
+    free = np.argwhere(g == 0)[:, ::-1]
+    hyps = free[np.random.default_rng(seed).choice(len(free), 30, replace=False)].astype(np.int32)
+    ang = workloads.beam_angles(n_beams, ns)
+    z = workloads.render_scan(g, 0.05, ((hyps[4, 0] + 0.5) * 0.05, (hyps[4, 1] + 0.5) * 0.05, 0.3), ang, max_range)
+    return workloads.Workload("small", g, 0.05, hyps, z, ang, max_range, n_orient, 8, ns, (0, 0, 0))
+
+
+def test_ragged_batches_skip_and_topk_over_n(relo):
+    wl = small_case()
+    for K, batch, local, skip in ((8, 3, 2, 1), (64, 7, 3, 2), (1, 1, 1, 1)):
+        wl2 = wl
+        if skip > 1:   # n_orient must divide the downsampled N_s
+            wl2 = workloads.Workload("small", wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, 20,
+                                     K, wl.n_s, wl.gt_pose)
+        ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl2, K, batch=batch, local_topk=local,
+                                                                 n_skip=skip)
+        ctx.close()
+
+
+def test_gapped_fov_two_intervals(relo):
+    wl = small_case(n_beams=100, ns=120)
+    keep = np.r_[0:30, 45:100]                 # an occluded sector (Eq. 12)
+    wl = workloads.Workload("gap", wl.grid, wl.res, wl.hyps, wl.ranges[keep], wl.angles[keep], wl.max_range, 40, 10,
+                            120, wl.gt_pose)
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, oracle.Params(n_orient=40))
+    assert pl["K"] == 2 and pl["ns"] == 120
+    ctx, *_ = full_case(relo, wl, 10)
+    ctx.close()
+
+
+def test_errors_are_reported(relo):
+    wl = small_case()
+    ctx = relo.Relo(n_orient=40, topk=8)
+    mid = ctx.load_map(wl.grid, wl.res)
+    with pytest.raises(relo.ReloError) as e:
+        ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert e.value.code == relo.E_NO_HYPOTHESES
+    occ = np.argwhere(wl.grid >= 65)[0][::-1]
+    with pytest.raises(relo.ReloError) as e:
+        ctx.set_hypotheses(mid, workloads.cell_centres(occ[None].astype(np.int32), wl.res))
+    assert e.value.code == relo.E_INVALID_ARG
+    ctx.set_hypotheses(mid, workloads.cell_centres(wl.hyps, wl.res))
+    with pytest.raises(relo.ReloError) as e:
+        ctx.relocalize(mid, np.full_like(wl.ranges, wl.max_range), wl.angles, wl.max_range)
+    assert e.value.code == relo.E_NO_VALID_BEAMS
+    bad = wl.angles.copy()
+    bad[10] += 0.3 * 2 * math.pi / 120
+    with pytest.raises(relo.ReloError) as e:
+        ctx.relocalize(mid, wl.ranges, bad, wl.max_range)
+    assert e.value.code == relo.E_BEAM_GRID
+    with pytest.raises(relo.ReloError) as e:
+        ctx.relocalize(mid + 5, wl.ranges, wl.angles, wl.max_range)
+    assert e.value.code == relo.E_NOT_FOUND
+    ok = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)      # context still usable
+    assert ok.status == 0
+    ctx.close()
+
+
+def test_degenerate_single_cell_map(relo):
+    g = np.zeros((1, 1), np.int8)
+    ang = workloads.beam_angles(8, 16)
+    wl = workloads.Workload("1x1", g, 0.05, np.zeros((1, 2), np.int32), np.full(8, 0.5, np.float32), ang, 3.0, 8, 1,
+                            16, (0, 0, 0))
+    ctx, got, st, pl, *_ = full_case(relo, wl, 1)
+    assert got.tam == 0.0 and got.m == 0 and got.hyp == 0
+    ctx.close()
+
+
+def test_device_entry_points_match_host_ones(relo, workload):
+    torch = torch_()
+    wl = workload(0)
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0)
+    g = torch.tensor(wl.grid, device="cuda")
+    mid = ctx.load_map_dev(g, wl.res)
+    ctx.set_hypotheses_cells_dev(mid, torch.tensor(wl.hyps, device="cuda"))
+    z = torch.tensor(wl.ranges, device="cuda")
+    res = torch.empty(relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.relocalize_dev(mid, z, wl.angles, wl.max_range, res)
+    torch.cuda.synchronize()
+    got = relo.result_from_bytes(bytes(res.cpu().numpy()))
+    host = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert got.as_dict() == host.as_dict()
+    ctx.update_map_dev(mid, g)                  # same grid: same answer
+    again = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert again.as_dict() == host.as_dict()
+    ctx.close()
