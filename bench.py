@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark of the relocalization scoring path on GB300.
+
+One step = one pass of the whole path over the office workload (1024x1024
+grid at 0.05 m, 5000 RRT hypotheses, 1081-beam 270-degree noisy scan, 360
+orientations, TAM on the SMAD top 256): EDT map precompute, scan
+preparation, ray cast + SMAD for every hypothesis, SMAD top-K, batched TAM
+over every orientation of every survivor, orientation argmax, local top-k.
+
+value: hypothesis x orientation evaluations (SMAD + TAM) per second with all
+inputs resident in HBM; each step is timed with CUDA events on the library's
+stream and L2 is flushed (256 MiB write) before every timed step.
+e2e: the same metric through the host entry points (relo_update_map,
+relo_set_hypotheses, relo_relocalize) from pinned host buffers, host<->device
+copies included, wall-clock per step.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload, scaled to the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hypothesis×orientation evals/s (SMAD+TAM); relocalizations/s at p99 latency"
+UNIT = "evals/s"
+CONFIG_INDEX = 1
+WORKLOAD = ("office 1024x1024 @0.05 m, 5000 RRT hypotheses x 360 orientations, 1081-beam 270-deg noisy scan "
+            "(N_s 1440), TAM on SMAD top 256 (all batches scored)")
+OPS_PER_DDA_STEP = 13     # integer operations one ray-cast step needs (ray-cast roofline)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (default: min(steps, 200))")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world):
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# our GPU path
+# ---------------------------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def committed_traffic(stage: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source
+    is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(stage)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2511_01219_gb300", "csrc", rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if h == rec["source_sha"] else None
+
+
+def run_ours(args, world, rank, local, dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    import workloads
+
+    torch.cuda.set_device(local)
+    wl = workloads.config(CONFIG_INDEX)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0, stream=stream)
+    grid_d = torch.tensor(wl.grid, device="cuda")
+    hyps_d = torch.tensor(wl.hyps, device="cuda")
+    z_d = torch.tensor(wl.ranges, device="cuda")
+    res_d = torch.empty(relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    mid = ctx.load_map_dev(grid_d, wl.res)
+    ctx.set_hypotheses_cells_dev(mid, hyps_d)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.update_map_dev(mid, grid_d)
+        ctx.relocalize_dev(mid, z_d, wl.angles, wl.max_range, res_d)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    r = relo.result_from_bytes(bytes(res_d.cpu().numpy()))
+    if r.status != relo.OK:
+        raise RuntimeError(f"relocalization failed with status {r.status}")
+    evals_per_step = int(r.n_smad_evals + r.n_tam_evals)
+
+    ctx.set_profiling(True)
+    ctx.stage_times(reset=True)
+    k0 = ctx.kernels_launched()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per_step)
+    stage_ms, stage_n, k1 = ctx.stage_times(reset=True)
+    ctx.set_profiling(False)
+    launches = k1 - k0
+    t_max = max_over_ranks(dist, total_ms)
+    evals_all = sum_over_ranks(dist, float(evals_per_step * args.steps))
+    value = evals_all / (t_max / 1e3)
+
+    # dominant kernel and its roofline
+    info = ctx.scan_info()
+    n_valid, n_orient, K = info[3], info[1], info[6]
+    peaks, peak_kind = measured_peaks()
+    shares = {k: v / total_ms for k, v in stage_ms.items()}
+    dominant = max(stage_ms, key=stage_ms.get)
+    tam_bytes = 2.0 * n_valid * K * n_orient * args.steps          # 2 B field read per valid beam per (h, m)
+    roof = {}
+    if stage_ms["tam"] > 0:
+        gbs = tam_bytes / (stage_ms["tam"] / 1e3) / 1e9
+        roof["tam"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": committed_traffic("tam"),
+                       "peak_source": f"{peak_kind} hbm_gbs",
+                       "avg_launch_ms": round(stage_ms["tam"] / max(stage_n["tam"], 1), 4)}
+    dda = info[8]
+    if stage_ms["raycast_smad"] > 0 and dda:
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_tops = 128 * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ops = dda * OPS_PER_DDA_STEP * args.steps
+        tops = ops / (stage_ms["raycast_smad"] / 1e3) / 1e12
+        roof["raycast_smad"] = {"bound": "alu", "achieved": round(tops, 3), "peak": round(peak_tops, 2),
+                                "unit": "Tops/s", "frac": round(tops / peak_tops, 4),
+                                "traffic": committed_traffic("raycast_smad"),
+                                "peak_source": f"128 int32 lanes x {sm_count} SMs x {peaks.get('sm_max_mhz')} MHz",
+                                "dda_steps_per_step": dda,
+                                "avg_launch_ms": round(stage_ms["raycast_smad"] / max(stage_n["raycast_smad"], 1),
+                                                       4)}
+    main_roof = roof.get(dominant) or roof.get("tam")
+    pct = sorted(per_step)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32/i64+f32", "data": "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
+        "config": {"workload": WORKLOAD, "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
+                   "n_orient": wl.n_orient, "n_beams": len(wl.ranges), "n_s": wl.n_s, "topk": wl.topk,
+                   "evals_per_step": evals_per_step, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "relocalizations_per_s": world * args.steps / (t_max / 1e3),
+        "latency_ms": {"p50": pct[len(pct) // 2], "p99": pct[min(len(pct) - 1, int(math.ceil(0.99 * len(pct))) - 1)]},
+        "gpu_launches": int(launches),
+        "stage_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
+        "stage_share": {k: round(v, 4) for k, v in shares.items()},
+        "dominant_kernel": dominant,
+        "roofline": main_roof,
+        "roofline_all": roof,
+        "clocks": clk,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, ctx, mid, wl, relo, torch, flush, dist, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    ctx.close()
+    return line
+
+
+def run_e2e(args, ctx, mid, wl, relo, torch, flush, dist, world):
+    """Same metric through the host API with pinned inputs copied every step."""
+    import numpy as np
+    n_steps = args.e2e_steps or min(args.steps, 200)
+    grid_h = torch.from_numpy(np.ascontiguousarray(wl.grid)).pin_memory()
+    xy_h = torch.from_numpy(np.ascontiguousarray(
+        (wl.hyps.astype(np.float64) + 0.5) * wl.res)).pin_memory()
+    z_h = torch.from_numpy(np.ascontiguousarray(wl.ranges)).pin_memory()
+    out = relo.Result()
+
+    def step():
+        ctx.update_map_ptr(mid, grid_h.data_ptr())
+        ctx.set_hypotheses_ptr(mid, xy_h.data_ptr(), len(wl.hyps))
+        ctx.relocalize_ptr(mid, z_h.data_ptr(), wl.angles, len(wl.ranges), wl.max_range, out)
+
+    for _ in range(3):
+        step()
+    evals = int(out.n_smad_evals + out.n_tam_evals)
+    barrier(dist)
+    total = 0.0
+    for i in range(n_steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step()
+        total += time.perf_counter() - t0
+    barrier(dist)
+    t_max = max_over_ranks(dist, total)
+    e = sum_over_ranks(dist, float(evals * n_steps)) / t_max
+    h2d = wl.grid.size + 8 * len(wl.hyps) + 4 * len(wl.ranges)
+    d2h = relo.RESULT_BYTES + 4
+    return {"value": e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": n_steps, "ms_per_step": 1e3 * t_max / n_steps, "timing": "wall clock per blocking step"}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(wl, n_smad: int, n_tam_hyp: int, threads: int):
+    """Times the oracle on a bounded sample and scales to the full workload.
+
+    Phases: EDT of the whole map; SMAD of n_smad hypotheses; TAM of n_tam_hyp
+    SMAD survivors x all orientations.  Returns (evals/s of the full workload,
+    estimated seconds per full step, description)."""
+    import numpy as np
+
+    import oracle
+    prm = oracle.Params(n_orient=wl.n_orient, topk=wl.topk)
+    t0 = time.perf_counter()
+    d2 = oracle.edt(wl.grid, threads)
+    t_edt = time.perf_counter() - t0
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    sel = np.arange(0, len(wl.hyps), max(1, len(wl.hyps) // n_smad))[:n_smad]
+    t0 = time.perf_counter()
+    oracle.smad(wl.grid, wl.hyps[sel], pl, threads)
+    t_smad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.tam_grid(wl.grid, wl.hyps, np.arange(n_tam_hyp), pl, prm, wl.res, d2, threads)
+    t_tam = time.perf_counter() - t0
+    n_m = 1 if pl["panoramic"] else pl["n_orient"]
+    K = min(wl.topk, len(wl.hyps))
+    est = t_edt + t_smad * len(wl.hyps) / len(sel) + t_tam * K / n_tam_hyp
+    evals = len(wl.hyps) * n_m + K * pl["n_orient"]
+    desc = (f"EDT of the full map + SMAD of {len(sel)}/{len(wl.hyps)} hypotheses + TAM of {n_tam_hyp}/{K} "
+            f"survivors x {pl['n_orient']} orientations, scaled to the full step")
+    return evals / est, est, desc
+
+
+def cpu_baseline(wl):
+    import oracle
+    threads = oracle.max_threads()
+    v, est, desc = oracle_sample(wl, n_smad=1000, n_tam_hyp=48, threads=threads)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+            "est_s_per_step": est}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    import workloads
+    oracle.build()
+    wl = workloads.config(CONFIG_INDEX)
+    threads = oracle.max_threads()
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(wl, 100, 2, threads)
+    vals, ests = [], []
+    desc = ""
+    for _ in range(args.steps):
+        v, est, desc = oracle_sample(wl, 100, 2, threads)
+        vals.append(v)
+        ests.append(est)
+    total = sum(ests)
+    value = len(ests) / total * (vals[0] * ests[0])    # evals per step / mean seconds per step
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ests), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
+        "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    dist = dist_init(world)
+    line = run_ours(args, world, rank, local, dist)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -107,6 +107,11 @@ int relo_load_map_dev(relo_ctx *ctx, const int8_t *grid_dev, int32_t w, int32_t 
 /* Recomputes a loaded map's tables in place from a new grid of the same size
  * (for example after a door opened).  Asynchronous on the context stream. */
 int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev);
+/* Same from a host grid.  The copy is queued on the context stream: a pinned
+ * grid must stay unchanged until the stream passes it (any blocking call on
+ * the context, such as relo_relocalize, waits for that); a pageable grid may
+ * be reused as soon as the call returns. */
+int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid);
 int relo_unload_map(relo_ctx *ctx, int32_t map_id);
 
 /* Copies a map's tables into caller device buffers, row-major W x H:
@@ -140,10 +145,11 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
  *   RELO_STAGE_SMAD_NUM   int64 [N_h]   SMAD numerators (Eq. 20)
  *   RELO_STAGE_SMAD_M     int32 [N_h]   minimising orientation shift m
  *   RELO_STAGE_SURVIVORS  int32 [K]     hypothesis indices in SMAD order
- *   RELO_STAGE_TAM        float [K x n_orient]  TAM of every scored (survivor, orientation); unscored = -1
+ *   RELO_STAGE_TAM        float [K x n_orient]  TAM of every scored (survivor, orientation); unscored = NaN
  *   RELO_STAGE_BEST_M     int32 [K]     per-survivor argmax shift m of Eq. 22 (-1 if not scored)
  *   RELO_STAGE_LOCAL_TOPK int32 [n_batches x local_topk]  survivor positions of each batch's local top-k
- *   RELO_STAGE_SCAN_INFO  int64 [8]     N_s, n_orient, n_enum, N_valid, k_retained, sum_real, K, batches */
+ *   RELO_STAGE_SCAN_INFO  int64 [10]    N_s, n_orient, n_enum, N_valid, k_retained, sum_real, K, batches,
+ *                                       cells entered by all rays (DDA steps), N_h */
 #define RELO_STAGE_SMAD_NUM 0
 #define RELO_STAGE_SMAD_M 1
 #define RELO_STAGE_SURVIVORS 2
@@ -151,6 +157,7 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
 #define RELO_STAGE_BEST_M 4
 #define RELO_STAGE_LOCAL_TOPK 5
 #define RELO_STAGE_SCAN_INFO 6
+#define RELO_SCAN_INFO_LEN 10
 int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes);
 
 /* Ray-cast synthesized scans (Eq. 13) for n cells on a loaded map, for the
@@ -162,6 +169,21 @@ int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes);
 int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n, const float *angles,
                          int32_t n_beams, float max_range, uint32_t *ranges_dev, int32_t *hit_dev, int64_t capacity,
                          int32_t *ns_out);
+
+/* Stage timing (tracing).  With profiling on, the context records a CUDA
+ * event pair on its stream around every kernel it launches and sums the
+ * elapsed device time per stage:
+ *   0 EDT map precompute, 1 scan preparation, 2 ray cast + SMAD,
+ *   3 SMAD top-K, 4 TAM, 5 batch selection and finalize.
+ * relo_stage_times synchronises the stream, writes min(n, RELO_N_STAGES)
+ * totals in milliseconds to ms_out and launch counts to launches_out (either
+ * may be NULL), and with reset != 0 clears the totals.  Independently of
+ * profiling, *kernels_out (optional) receives the number of kernels the
+ * context has launched since it was created. */
+#define RELO_N_STAGES 6
+int relo_set_profiling(relo_ctx *ctx, int32_t enable);
+int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
+                     int64_t *kernels_out);
 
 #ifdef __cplusplus
 }

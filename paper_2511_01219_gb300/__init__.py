@@ -32,13 +32,15 @@ E_NO_VALID_BEAMS = -7
 E_NOT_FOUND = -8
 
 STAGE_SMAD_NUM, STAGE_SMAD_M, STAGE_SURVIVORS, STAGE_TAM, STAGE_BEST_M, STAGE_LOCAL_TOPK, STAGE_SCAN_INFO = range(7)
+SCAN_INFO_LEN = 10
 
 EXPORTED = [
     "relo_default_params", "relo_create", "relo_destroy", "relo_last_error", "relo_set_params", "relo_load_map",
-    "relo_load_map_dev", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
+    "relo_load_map_dev", "relo_update_map", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
-    "relo_synth_scans_dev",
+    "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times",
 ]
+STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
 
 
 class Params(ctypes.Structure):
@@ -93,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "relo_load_map": (ctypes.c_int, [P, P, I32, I32, D, D, D, P]),
             "relo_load_map_dev": (ctypes.c_int, [P, P, I32, I32, D, D, D, P]),
             "relo_update_map_dev": (ctypes.c_int, [P, I32, P]),
+            "relo_update_map": (ctypes.c_int, [P, I32, P]),
             "relo_unload_map": (ctypes.c_int, [P, I32]),
             "relo_map_tables_dev": (ctypes.c_int, [P, I32, P, P, P]),
             "relo_set_hypotheses": (ctypes.c_int, [P, I32, P, I32]),
@@ -101,6 +104,8 @@ def lib() -> ctypes.CDLL:
             "relo_relocalize_dev": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
             "relo_get_stage": (ctypes.c_int, [P, I32, P, I64]),
             "relo_synth_scans_dev": (ctypes.c_int, [P, I32, P, I32, P, I32, F, P, P, I64, P]),
+            "relo_set_profiling": (ctypes.c_int, [P, I32]),
+            "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -197,6 +202,24 @@ class Relo:
     def update_map_dev(self, map_id: int, grid_t):
         self._check(self._L.relo_update_map_dev(self._h, map_id, _t_ptr(grid_t)), "update_map_dev")
 
+    def update_map(self, map_id: int, grid: np.ndarray):
+        """Host grid (numpy, or a pinned torch CPU tensor passed as its data pointer via update_map_ptr)."""
+        g = np.ascontiguousarray(grid, dtype=np.int8)
+        self._check(self._L.relo_update_map(self._h, map_id, _np_ptr(g)), "update_map")
+
+    def update_map_ptr(self, map_id: int, host_ptr: int):
+        self._check(self._L.relo_update_map(self._h, map_id, ctypes.c_void_p(host_ptr)), "update_map")
+
+    def set_hypotheses_ptr(self, map_id: int, xy_host_ptr: int, n: int):
+        self._check(self._L.relo_set_hypotheses(self._h, map_id, ctypes.c_void_p(xy_host_ptr), n), "set_hypotheses")
+
+    def relocalize_ptr(self, map_id: int, ranges_host_ptr: int, angles: np.ndarray, n: int, max_range: float,
+                       out: "Result") -> "Result":
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        self._check(self._L.relo_relocalize(self._h, map_id, ctypes.c_void_p(ranges_host_ptr), _np_ptr(a), n,
+                                            max_range, ctypes.byref(out)), "relocalize")
+        return out
+
     def unload_map(self, map_id: int):
         self._check(self._L.relo_unload_map(self._h, map_id), "unload_map")
 
@@ -234,6 +257,32 @@ class Relo:
         a = np.ascontiguousarray(angles, dtype=np.float32)
         self._check(self._L.relo_relocalize_dev(self._h, map_id, _t_ptr(ranges_t), _np_ptr(a), int(ranges_t.numel()),
                                                 max_range, _t_ptr(result_t)), "relocalize_dev")
+
+    def set_profiling(self, on: bool):
+        self._check(self._L.relo_set_profiling(self._h, int(bool(on))), "set_profiling")
+
+    def stage_times(self, reset: bool = False):
+        """({stage: ms}, {stage: launches}, kernels launched since creation)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_int64 * len(STAGES))()
+        k = ctypes.c_int64(0)
+        self._check(self._L.relo_stage_times(self._h, ms, n, len(STAGES), int(reset), ctypes.byref(k)), "stage_times")
+        return dict(zip(STAGES, list(ms))), dict(zip(STAGES, list(n))), k.value
+
+    def scan_info(self) -> list:
+        """[N_s, n_orient, n_enum, N_valid, k_retained, sum_real, K, batches, DDA steps, N_h] of the last request."""
+        import torch
+        t = torch.empty(SCAN_INFO_LEN, dtype=torch.int64, device="cuda")
+        self.stage(STAGE_SCAN_INFO, t)
+        return t.cpu().tolist()
+
+    def dda_steps(self) -> int:
+        return int(self.scan_info()[8])
+
+    def kernels_launched(self) -> int:
+        k = ctypes.c_int64(0)
+        self._check(self._L.relo_stage_times(self._h, None, None, 0, 0, ctypes.byref(k)), "stage_times")
+        return k.value
 
     def stage(self, which: int, dst_t):
         self._check(self._L.relo_get_stage(self._h, which, _t_ptr(dst_t), dst_t.numel() * dst_t.element_size()),

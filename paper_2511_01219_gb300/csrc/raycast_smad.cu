@@ -45,9 +45,9 @@ __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     return (uint32_t)r;
 }
 
-// returns the Q16 range (0 = no hit); *hit receives cy*W+cx or -1
+// returns the Q16 range (0 = no hit); *hit receives cy*W+cx or -1, *steps the cells entered
 __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int lim, int hx,
-                                             int hy, int2 d, int *hit) {
+                                             int hy, int2 d, int *hit, int *steps) {
     const int ax = d.x < 0 ? -d.x : d.x, ay = d.y < 0 ? -d.y : d.y;
     const int sx = d.x > 0 ? 1 : -1, sy = d.y > 0 ? 1 : -1;
     const uint32_t two_ax = 2u * (uint32_t)ax, two_ay = 2u * (uint32_t)ay;
@@ -69,6 +69,7 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
         }
         if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H || c2 > lim) {
             *hit = -1;
+            *steps = adx + ady;
             return 0u;
         }
         const int t = (cy >> 3) * TW + (cx >> 3);
@@ -78,6 +79,7 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
         }
         if ((word >> (((cy & 7) << 3) | (cx & 7))) & 1ull) {
             *hit = cy * W + cx;
+            *steps = adx + ady;
             return isqrt_q16(c2);
         }
     }
@@ -107,6 +109,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
     const int nch = a.ns_pad >> 5;
     inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
     const long long sum_real = a.scan->sum_real;
+    unsigned long long my_steps = 0;
 
     for (int h = blockIdx.x * kWarps + warp; h < a.n_hyp; h += gridDim.x * kWarps) {
         const int2 hc = a.hyps[h];
@@ -115,8 +118,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
         for (int c = 0; c < nch; ++c) {
             const int j = (c << 5) + lane;
             uint32_t r = 0u;
-            int hit;
-            if (j < a.ns) r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit);
+            int hit, steps = 0;
+            if (j < a.ns) r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
+            my_steps += (unsigned)steps;
             uint32_t s = r;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -160,6 +164,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
         }
         __syncwarp();
     }
+    if (a.dda_steps) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, o);
+        if (lane == 0 && my_steps) atomicAdd(a.dda_steps, my_steps);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__ ranges, int32_t *__restrict__ hits) {
@@ -167,8 +176,8 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
     if (warp >= a.n_hyp) return;
     const int2 hc = a.hyps[warp];
     for (int j = lane; j < a.ns; j += 32) {
-        int hit;
-        uint32_t r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit);
+        int hit, steps;
+        uint32_t r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
         ranges[(size_t)warp * a.ns + j] = r;
         if (hits) hits[(size_t)warp * a.ns + j] = hit;
     }

@@ -81,6 +81,14 @@ struct relo_ctx {
     float *ranges_host = nullptr;
     size_t ranges_host_cap = 0;
     relo_result *result_host = nullptr;
+    // stage timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double stage_ms[RELO_N_STAGES] = {0};
+    long long stage_n[RELO_N_STAGES] = {0};
+    long long kernels = 0;
     // shapes of the last request (for relo_get_stage)
     int last_n_hyp = 0, last_K = 0, last_n_orient = 0, last_batches = 0, last_local = 0, last_ns = 0;
     int last_enum = 0, last_map = -1;
@@ -102,6 +110,35 @@ int cuda_fail(relo_ctx *c, cudaError_t e, const char *what) {
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
     } while (0)
+
+cudaEvent_t take_event(relo_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Wraps one kernel launch: counts it and, with profiling on, brackets it with events.
+template <typename F>
+cudaError_t timed(relo_ctx *ctx, int stage, int n_kernels, F &&launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->profiling) {
+        a = take_event(ctx);
+        b = take_event(ctx);
+        if (a) cudaEventRecord(a, ctx->stream);
+    }
+    cudaError_t e = launch();
+    ctx->kernels += n_kernels;
+    if (ctx->profiling && a && b) {
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending.push_back({stage, a, b});
+    }
+    return e;
+}
 
 int dev_alloc(relo_ctx *ctx, void **p, size_t bytes, const char *what) {
     if (ctx->p.hbm_budget > 0 && ctx->held + (long long)bytes > ctx->p.hbm_budget)
@@ -319,7 +356,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     }
     cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
-    if (e == cudaSuccess) e = launch_edt(m.dev, ctx->stream);
+    if (e == cudaSuccess) e = timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -460,6 +497,11 @@ int relo_destroy(relo_ctx *ctx) {
                     ctx->T, ctx->local};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto &pe : ctx->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
     if (ctx->result_host) cudaFreeHost(ctx->result_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -483,7 +525,7 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             int C;
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
-            CK(launch_edt(m.dev, ctx->stream), "map rebuild");
+            CK(timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -507,7 +549,17 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(launch_edt(m->dev, ctx->stream), "map update");
+    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    return RELO_OK;
+}
+
+int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
+    if (!ctx || !grid) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
+       "map update");
+    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -587,8 +639,10 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
         return rc;
     cudaStream_t st = ctx->stream;
     // a2: per-scan preparation (Eq. 11, 16, 26)
-    CK(launch_scan_prep(ranges_dev, P.n, p.n_skip_beam, max_range, m.res, P.b_dev, P.a_mid, P.a_low, ctx->vbR,
-                        ctx->scan, st),
+    CK(timed(ctx, 1, 1, [&] {
+           return launch_scan_prep(ranges_dev, P.n, p.n_skip_beam, max_range, m.res, P.b_dev, P.a_mid, P.a_low,
+                                   ctx->vbR, ctx->scan, st);
+       }),
        "scan preparation");
     // a3 + a4: ray casting and SMAD (Eq. 13, 17-20)
     RayArgs ra;
@@ -605,14 +659,15 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
     ra.iv = P.iv_dev;
     ra.n_iv = (int)P.iv.size();
     ra.scan = ctx->scan;
+    ra.dda_steps = &ctx->scan->dda_steps;
     ra.n_enum = P.n_enum;
     ra.n_m = P.n_m;
     ra.keys = ctx->keys;
     ra.smad_num = ctx->smad_num;
     ra.smad_m = ctx->smad_m;
-    CK(launch_raycast_smad(ra, ctx->n_sm, st), "ray cast + SMAD");
+    CK(timed(ctx, 2, 1, [&] { return launch_raycast_smad(ra, ctx->n_sm, st); }), "ray cast + SMAD");
     // a5: SMAD ordering, K survivors
-    CK(launch_topk(ctx->keys, n_hyp, K, ctx->survivors, st), "SMAD top-K");
+    CK(timed(ctx, 3, 1, [&] { return launch_topk(ctx->keys, n_hyp, K, ctx->survivors, st); }), "SMAD top-K");
     // a6 + a7: batched TAM, orientation argmax, local top-k, early termination
     CK(cudaMemsetAsync(ctx->best_key, 0, sizeof(unsigned long long) * K, st), "request reset");
     CK(cudaMemsetAsync(ctx->best_m, 0xff, sizeof(int32_t) * K, st), "request reset");
@@ -644,9 +699,11 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
     for (int bi = 0; bi < n_batches; ++bi) {
         ta.s_begin = bi * B;
         ta.s_end = std::min(K, ta.s_begin + B);
-        CK(launch_tam(ta, P.n, ctx->n_sm, st), "TAM");
-        CK(launch_select_batch(ctx->best_key, ta.s_begin, ta.s_end, P.n_orient, P.n_enum, L, bi, p.tau,
-                               p.early_stop, ctx->best_m, ctx->local, ctx->state, st),
+        CK(timed(ctx, 4, 1, [&] { return launch_tam(ta, P.n, ctx->n_sm, st); }), "TAM");
+        CK(timed(ctx, 5, 1, [&] {
+               return launch_select_batch(ctx->best_key, ta.s_begin, ta.s_end, P.n_orient, P.n_enum, L, bi, p.tau,
+                                          p.early_stop, ctx->best_m, ctx->local, ctx->state, st);
+           }),
            "batch selection");
     }
     FinalizeArgs fa;
@@ -663,7 +720,7 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
     fa.ns = P.ns;
     fa.n_smad_evals = (long long)n_hyp * P.n_m;
     fa.result = result_dev;
-    CK(launch_finalize(fa, st), "finalize");
+    CK(timed(ctx, 5, 1, [&] { return launch_finalize(fa, st); }), "finalize");
     ctx->last_n_hyp = n_hyp;
     ctx->last_K = K;
     ctx->last_n_orient = P.n_orient;
@@ -679,7 +736,12 @@ int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const fl
                     float max_range, relo_result *out) {
     if (!ctx || !ranges || !angles || !out || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     if ((size_t)n_beams > ctx->ranges_host_cap) {
-        if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
+        for (auto &pe : ctx->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
         ctx->ranges_host = nullptr;
         ctx->ranges_host_cap = 0;
         CK(cudaMallocHost((void **)&ctx->ranges_host, sizeof(float) * n_beams), "pinned staging");
@@ -706,7 +768,7 @@ int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes) {
     if (ctx->last_map < 0) return fail(ctx, RELO_E_NOT_FOUND, "no relocalization has run");
     const void *src = nullptr;
     size_t need = 0;
-    long long info_host[8];
+    long long info_host[10];
     switch (which) {
         case RELO_STAGE_SMAD_NUM: src = ctx->smad_num; need = 8ull * ctx->last_n_hyp; break;
         case RELO_STAGE_SMAD_M: src = ctx->smad_m; need = 4ull * ctx->last_n_hyp; break;
@@ -720,8 +782,8 @@ int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes) {
             CK(cudaMemcpyAsync(&si, ctx->scan, sizeof si, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
             CK(cudaMemcpyAsync(&ss, ctx->state, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
             CK(cudaStreamSynchronize(ctx->stream), "stage read");
-            long long v[8] = {ctx->last_ns, ctx->last_n_orient, ctx->last_enum, si.n_valid, si.k_ret, si.sum_real,
-                              ctx->last_K, ss.n_batches};
+            long long v[10] = {ctx->last_ns, ctx->last_n_orient, ctx->last_enum, si.n_valid, si.k_ret, si.sum_real,
+                               ctx->last_K, ss.n_batches, (long long)si.dda_steps, ctx->last_n_hyp};
             memcpy(info_host, v, sizeof v);
             src = info_host;
             need = sizeof info_host;
@@ -765,6 +827,38 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     ra.n_hyp = n;
     CK(launch_synth(ra, ranges_dev, hit_dev, ctx->stream), "synthesized scans");
     CK(cudaStreamSynchronize(ctx->stream), "synthesized scans");
+    return RELO_OK;
+}
+
+int relo_set_profiling(relo_ctx *ctx, int32_t enable) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    ctx->profiling = enable != 0;
+    return RELO_OK;
+}
+
+int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
+                     int64_t *kernels_out) {
+    if (!ctx || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    CK(cudaStreamSynchronize(ctx->stream), "stage times");
+    for (auto &pe : ctx->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pe.a, pe.b), "stage times");
+        ctx->stage_ms[pe.stage] += ms;
+        ctx->stage_n[pe.stage] += 1;
+        ctx->ev_pool.push_back(pe.a);
+        ctx->ev_pool.push_back(pe.b);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < n && i < RELO_N_STAGES; ++i) {
+        if (ms_out) ms_out[i] = ctx->stage_ms[i];
+        if (launches_out) launches_out[i] = ctx->stage_n[i];
+    }
+    if (kernels_out) *kernels_out = ctx->kernels;
+    if (reset)
+        for (int i = 0; i < RELO_N_STAGES; ++i) {
+            ctx->stage_ms[i] = 0;
+            ctx->stage_n[i] = 0;
+        }
     return RELO_OK;
 }
 

@@ -31,10 +31,11 @@ __host__ __device__ inline size_t tile_index(int x, int y, int TW) {
 
 // Per-scan values produced on the device by the scan-preparation kernel.
 struct ScanInfo {
-    long long sum_real;   // sum of valid Q16 ranges (Eq. 16 numerator)
-    int n_valid;          // N of Eq. 26 (valid beams)
-    int k_ret;            // median of {k_full, k_mid, k_low} (Eq. 26-27)
-    int pad[4];
+    long long sum_real;             // sum of valid Q16 ranges (Eq. 16 numerator)
+    int n_valid;                    // N of Eq. 26 (valid beams)
+    int k_ret;                      // median of {k_full, k_mid, k_low} (Eq. 26-27)
+    unsigned long long dda_steps;   // cells entered by all rays of the request (work counter)
+    int pad[2];
 };
 
 // Running state of the batched selection of one request.
@@ -56,6 +57,7 @@ struct RayArgs {
     const int2 *iv;         // [n_iv] (u, len) FoV intervals
     int n_iv;
     const ScanInfo *scan;
+    unsigned long long *dda_steps;   // optional work counter (may be null)
     int n_enum, n_m;        // orientation stride and count scored by SMAD
     unsigned long long *keys;   // [n_hyp]
     long long *smad_num;        // [n_hyp]

@@ -53,7 +53,8 @@ def stages(relo, ctx, n_hyp, K, n_orient, n_batches, local_topk):
     bm = ctx.stage(relo.STAGE_BEST_M, torch.empty(K, dtype=torch.int32, device="cuda")).cpu().numpy()
     loc = ctx.stage(relo.STAGE_LOCAL_TOPK, torch.empty(n_batches * local_topk, dtype=torch.int32,
                                                        device="cuda")).cpu().numpy()
-    info = ctx.stage(relo.STAGE_SCAN_INFO, torch.empty(8, dtype=torch.int64, device="cuda")).cpu().numpy()
+    info = ctx.stage(relo.STAGE_SCAN_INFO, torch.empty(relo.SCAN_INFO_LEN, dtype=torch.int64,
+                                                       device="cuda")).cpu().numpy()
     return dict(num=num, m=mm, surv=surv, T=T.reshape(K, n_orient), best_m=bm,
                 local=loc.reshape(n_batches, local_topk), info=info)
 
@@ -254,11 +255,14 @@ def small_case(seed=3, n_beams=90, ns=120, n_orient=40, max_range=4.0):
 
 def test_ragged_batches_skip_and_topk_over_n(relo):
     wl = small_case()
+    # 88 beams start on an even panoramic index, so every second beam (Eq. 11)
+    # still lies on the coarser grid of N_s = 60 directions (Eq. 14)
+    wl88 = small_case(n_beams=88)
     for K, batch, local, skip in ((8, 3, 2, 1), (64, 7, 3, 2), (1, 1, 1, 1)):
         wl2 = wl
         if skip > 1:   # n_orient must divide the downsampled N_s
-            wl2 = workloads.Workload("small", wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, 20,
-                                     K, wl.n_s, wl.gt_pose)
+            wl2 = workloads.Workload("small", wl88.grid, wl88.res, wl88.hyps, wl88.ranges, wl88.angles,
+                                     wl88.max_range, 20, K, 60, wl88.gt_pose)
         ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl2, K, batch=batch, local_topk=local,
                                                                  n_skip=skip)
         ctx.close()
