@@ -20,6 +20,7 @@ sample of the same workload, scaled to the same metric.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import hashlib
 import json
 import math
@@ -398,6 +399,7 @@ def run_reference(args, world, rank):
 
 
 def main():
+    faulthandler.enable()
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -21,22 +21,55 @@ namespace {
 
 constexpr int kInf = 0x7fffffff;
 
-__global__ void k_edt_cols(const int8_t *__restrict__ grid, int W, int H, int32_t *__restrict__ colsq) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
+// Column term, step 1: for every (column, segment of L rows) the first and the
+// last occupied row inside the segment (-1 if none).
+__global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H, int L,
+                                  int2 *__restrict__ summ) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sgm = blockIdx.y;
     if (x >= W) return;
-    int last = -1;
-    for (int y = 0; y < H; ++y) {
-        size_t i = (size_t)y * W + x;
+    const int y0 = sgm * L, y1 = min(H, y0 + L);
+    int first = -1, last = -1;
+    for (int y = y0; y < y1; ++y) {
+        if (grid[(size_t)y * W + x] >= 65) {
+            if (first < 0) first = y;
+            last = y;
+        }
+    }
+    summ[(size_t)sgm * W + x] = make_int2(first, last);
+}
+
+// Column term, step 2: the nearest occupied rows above and below the segment
+// come from the other segments' summaries; one downward and one upward sweep
+// inside the segment then give g(x, y) = distance to the nearest occupied
+// cell of the column, stored squared (kInf when the column has none).
+__global__ void k_edt_col_final(const int8_t *__restrict__ grid, int W, int H, int L, int S,
+                                const int2 *__restrict__ summ, int32_t *__restrict__ colsq) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sgm = blockIdx.y;
+    if (x >= W) return;
+    int last = -1;    // nearest occupied row above the segment
+    for (int t = 0; t < sgm; ++t) {
+        const int v = summ[(size_t)t * W + x].y;
+        if (v >= 0) last = v;
+    }
+    int next = -1;    // nearest occupied row below the segment
+    for (int t = S - 1; t > sgm; --t) {
+        const int v = summ[(size_t)t * W + x].x;
+        if (v >= 0) next = v;
+    }
+    const int y0 = sgm * L, y1 = min(H, y0 + L);
+    for (int y = y0; y < y1; ++y) {
+        const size_t i = (size_t)y * W + x;
         if (grid[i] >= 65) last = y;
         colsq[i] = last < 0 ? kInf : y - last;
     }
-    int next = -1;
-    for (int y = H - 1; y >= 0; --y) {
-        size_t i = (size_t)y * W + x;
+    for (int y = y1 - 1; y >= y0; --y) {
+        const size_t i = (size_t)y * W + x;
         if (grid[i] >= 65) next = y;
-        int up = colsq[i];
-        int dn = next < 0 ? kInf : next - y;
-        int g = up < dn ? up : dn;
+        const int up = colsq[i];
+        const int dn = next < 0 ? kInf : next - y;
+        const int g = up < dn ? up : dn;
         colsq[i] = g == kInf ? kInf : g * g;
     }
 }
@@ -114,7 +147,10 @@ __global__ void k_check_cells(const int2 *__restrict__ cells, int n, const uint6
 }  // namespace
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
-    k_edt_cols<<<(m.W + 127) / 128, 128, 0, s>>>(m.grid, m.W, m.H, m.colsq);
+    const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;
+    const dim3 cgrid((m.W + 127) / 128, S);
+    k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.summ);
+    k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
     int nt = m.TW * m.TH;
     k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.C, m.bits, m.field);
     size_t smem = (size_t)m.W * sizeof(int32_t);

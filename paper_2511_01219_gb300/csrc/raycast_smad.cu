@@ -1,15 +1,12 @@
 // Ray-cast panoramic synthesized scans (Eq. 13) fused with SMAD (Eq. 16-20).
 //
-// One warp per hypothesis.  The warp casts the N_s panoramic rays 32 at a
-// time (lane = ray within a chunk, so neighbouring lanes trace neighbouring
-// directions of similar length), scans each chunk of ranges with warp
-// shuffles into per-chunk exclusive prefixes, and keeps a running 64-bit
-// chunk prefix: together they give the cyclic prefix sum S of Eq. 17 at any
-// index.  The lanes then take the orientations m of Eq. 15 and evaluate each
-// window sum of Eq. 18 with two lookups per FoV interval, form the integer
-// SMAD numerator |sum R_real - W_m| of Eq. 19 (the shared denominator of the
-// two means cancels from every comparison), and reduce the minimum over m
-// (Eq. 20; ties keep the smaller m).
+// Rays are cast 32 at a time (lane = ray within a chunk, so neighbouring
+// lanes trace neighbouring directions of similar length); chunk prefixes give
+// the cyclic prefix sum S of Eq. 17 at any index; the orientations m of
+// Eq. 15 then each need two lookups per FoV interval for the window sum of
+// Eq. 18, and the integer SMAD numerator |sum R_real - W_m| of Eq. 19 (the
+// shared denominator of the two means cancels from every comparison) is
+// minimised over m (Eq. 20; ties keep the smaller m).
 //
 // Ray traversal.  From the hypothesis cell centre along the Q30 direction D,
 // cells are entered in the order of the ray's grid-line crossings: with k x-
@@ -32,7 +29,7 @@ namespace relo {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 8;
+constexpr int kRayThreads = 256;
 
 __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     // floor(sqrt(c2 * 2^32)): float estimate, one Newton correction, exact fix-up
@@ -45,31 +42,81 @@ __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     return (uint32_t)r;
 }
 
-// returns the Q16 range (0 = no hit); *hit receives cy*W+cx or -1, *steps the cells entered
+// Returns the Q16 range (0 = no hit); *hit receives cy*W+cx or -1, *steps the
+// number of cells the traversal entered (the definition's cell count).
+//
+// Empty tiles are crossed in one move.  Inside a tile whose 64-bit word is 0
+// no cell can stop the ray except by leaving the map or the range, and both
+// of those only grow along the ray, so jumping straight to the first cell
+// past the tile gives the same answer as stepping through it.  With nx
+// x-steps and ny y-steps left to the tile's x and y boundaries, the ray
+// leaves through the x boundary iff its nx-th x crossing comes no later than
+// its ny-th y crossing: e + 2(ny-1)|Dx| - 2(nx-1)|Dy| >= 0.  It then also
+// makes the j y-steps whose crossings come strictly earlier, j = the smallest
+// integer with 2 j |Dx| >= 2(nx-1)|Dy| - e; leaving through y, it makes the i
+// x-steps whose crossings come no later (ties step x first), i = 0 if
+// B = e + 2(ny-1)|Dx| < 0, else floor(B / (2|Dy|)) + 1.  Both counts are at
+// most 7.
 __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int lim, int hx,
                                              int hy, int2 d, int *hit, int *steps) {
     const int ax = d.x < 0 ? -d.x : d.x, ay = d.y < 0 ? -d.y : d.y;
     const int sx = d.x > 0 ? 1 : -1, sy = d.y > 0 ? 1 : -1;
     const uint32_t two_ax = 2u * (uint32_t)ax, two_ay = 2u * (uint32_t)ay;
     int e = ax - ay;
-    int cx = hx, cy = hy, adx = 0, ady = 0, c2 = 0;
-    int tile = -1;
-    unsigned long long word = 0;
+    int cx = hx, cy = hy, adx = 0, ady = 0, c2 = 0, n = 0;
+    int tile = (cy >> 3) * TW + (cx >> 3);
+    unsigned long long word = __ldg(bits + tile);
     for (;;) {
-        if (e >= 0) {
+        if (word == 0ull) {
+            const int nx = sx > 0 ? 8 - (cx & 7) : (cx & 7) + 1;
+            const int ny = sy > 0 ? 8 - (cy & 7) : (cy & 7) + 1;
+            bool xexit;
+            if (ay == 0) xexit = true;
+            else if (ax == 0) xexit = false;
+            else xexit = (long long)e + 2ll * (ny - 1) * ax - 2ll * (nx - 1) * ay >= 0;
+            if (xexit) {
+                const long long A = 2ll * (nx - 1) * ay - e;
+                const long long dd = 2ll * ax;
+                int j = 0;
+                while ((long long)j * dd < A) ++j;
+                e = (int)((long long)e - 2ll * nx * ay + 2ll * j * ax);
+                cx += sx * nx;
+                cy += sy * j;
+                adx += nx;
+                ady += j;
+                n += nx + j;
+            } else {
+                const long long B = (long long)e + 2ll * (ny - 1) * ax;
+                const long long dd = 2ll * ay;
+                int i = 0;
+                if (B >= 0) {
+                    i = 1;
+                    while ((long long)i * dd <= B) ++i;
+                }
+                e = (int)((long long)e + 2ll * ny * ax - 2ll * i * ay);
+                cx += sx * i;
+                cy += sy * ny;
+                adx += i;
+                ady += ny;
+                n += ny + i;
+            }
+            c2 = adx * adx + ady * ady;
+        } else if (e >= 0) {
             cx += sx;
             e = (int)((uint32_t)e - two_ay);
             c2 += 2 * adx + 1;
             ++adx;
+            ++n;
         } else {
             cy += sy;
             e = (int)((uint32_t)e + two_ax);
             c2 += 2 * ady + 1;
             ++ady;
+            ++n;
         }
         if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H || c2 > lim) {
             *hit = -1;
-            *steps = adx + ady;
+            *steps = n;
             return 0u;
         }
         const int t = (cy >> 3) * TW + (cx >> 3);
@@ -79,7 +126,7 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
         }
         if ((word >> (((cy & 7) << 3) | (cx & 7))) & 1ull) {
             *hit = cy * W + cx;
-            *steps = adx + ady;
+            *steps = n;
             return isqrt_q16(c2);
         }
     }
@@ -94,28 +141,40 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int ns_pad) {
-    size_t inner = ((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7;
-    return inner + (size_t)(ns_pad / 32 + 1) * 8;
+__host__ __device__ __forceinline__ size_t inner_bytes(int ns_pad) {
+    return ((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7;
+}
+__host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
+    return inner_bytes(ns_pad) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
+// One CTA per hypothesis, taken from a device work counter so that costly
+// hypotheses (long rays) do not leave CTAs idle at the end.  Warps cast
+// interleaved 32-ray chunks; each chunk is scanned by its warp into
+// exclusive in-chunk prefixes, then one warp turns the chunk totals into
+// 64-bit chunk prefixes; P(t) = chunkP[t / 32] + inner[t] is the cyclic
+// prefix sum of Eq. 17 for t in [0, N_s].  The threads then split the
+// orientations, evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).
+__global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_best[kRayThreads / 32];
+    __shared__ int s_h;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t per_warp = warp_smem_bytes(a.ns_pad);
-    const size_t inner_bytes = ((size_t)(a.ns_pad + 32) * 4 + 7) & ~(size_t)7;
-    uint32_t *inner = reinterpret_cast<uint32_t *>(smem + warp * per_warp);
-    long long *chunkP = reinterpret_cast<long long *>(smem + warp * per_warp + inner_bytes);
+    constexpr int nwarps = kRayThreads / 32;
+    uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
+    long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(a.ns_pad));
     const int nch = a.ns_pad >> 5;
-    inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
+    if (threadIdx.x < 32) inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
     const long long sum_real = a.scan->sum_real;
     unsigned long long my_steps = 0;
 
-    for (int h = blockIdx.x * kWarps + warp; h < a.n_hyp; h += gridDim.x * kWarps) {
+    for (;;) {
+        if (threadIdx.x == 0) s_h = (int)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int h = s_h;
+        if (h >= a.n_hyp) break;
         const int2 hc = a.hyps[h];
-        long long carry = 0;
-        if (lane == 0) chunkP[0] = 0;
-        for (int c = 0; c < nch; ++c) {
+        for (int c = warp; c < nch; c += nwarps) {
             const int j = (c << 5) + lane;
             uint32_t r = 0u;
             int hit, steps = 0;
@@ -128,12 +187,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
                 if (lane >= o) s += t;
             }
             inner[j] = s - r;
-            carry += (long long)__shfl_sync(kFull, s, 31);
-            if (lane == 0) chunkP[c + 1] = carry;
+            if (lane == 31) chunkP[c + 1] = (long long)s;   // chunk total, turned into a prefix below
         }
-        __syncwarp();
+        __syncthreads();
+        if (warp == 0) {
+            long long carry = 0;
+            for (int c0 = 0; c0 < nch; c0 += 32) {
+                const int c = c0 + lane;
+                long long v = c < nch ? chunkP[c + 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    long long t = __shfl_up_sync(kFull, v, o);
+                    if (lane >= o) v += t;
+                }
+                if (c < nch) chunkP[c + 1] = carry + v;
+                carry += __shfl_sync(kFull, v, 31);
+            }
+            if (lane == 0) chunkP[0] = 0;
+        }
+        __syncthreads();
         unsigned long long best = ~0ull;
-        for (int q = lane; q < a.n_m; q += 32) {
+        for (int q = threadIdx.x; q < a.n_m; q += kRayThreads) {
             const int m = q * a.n_enum;
             long long Wm = 0;
             for (int k = 0; k < a.n_iv; ++k) {
@@ -155,14 +229,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_raycast_smad(RayArgs a) {
             best = key < best ? key : best;
         }
         best = warp_min_u64(best);
-        if (lane == 0) {
-            const unsigned long long num = best >> 20;
-            const int q = (int)(best & 0xfffffu);
+        if (lane == 0) s_best[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = s_best[0];
+            for (int w = 1; w < nwarps; ++w) b = s_best[w] < b ? s_best[w] : b;
+            const unsigned long long num = b >> 20;
+            const int q = (int)(b & 0xfffffu);
             a.keys[h] = (num << kHypBits) | (unsigned long long)h;
             a.smad_num[h] = (long long)num;
             a.smad_m[h] = q * a.n_enum;
         }
-        __syncwarp();
+        // the next iteration's first __syncthreads orders these reads before inner/chunkP are rewritten
     }
     if (a.dda_steps) {
 #pragma unroll
@@ -186,18 +264,17 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
 }  // namespace
 
 cudaError_t launch_raycast_smad(const RayArgs &a, int n_sm, cudaStream_t s) {
-    size_t smem = (size_t)kWarps * warp_smem_bytes(a.ns_pad);
+    size_t smem = cta_smem_bytes(a.ns_pad);
     cudaError_t e = cudaFuncSetAttribute(k_raycast_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raycast_smad, kWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raycast_smad, kRayThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    int want = (a.n_hyp + kWarps - 1) / kWarps;
     int grid = n_sm * occ;
-    if (grid > want) grid = want;
+    if (grid > a.n_hyp) grid = a.n_hyp;
     if (grid < 1) grid = 1;
-    k_raycast_smad<<<grid, kWarps * 32, smem, s>>>(a);
+    k_raycast_smad<<<grid, kRayThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

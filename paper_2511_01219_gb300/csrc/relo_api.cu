@@ -311,6 +311,11 @@ int plan_for(relo_ctx *ctx, const float *angles_raw, int n_raw) {
     return RELO_OK;
 }
 
+int edt_segments(int H) {
+    const int L = edt_segment_rows(H);
+    return (H + L - 1) / L;
+}
+
 MapSlot *get_map(relo_ctx *ctx, int id) {
     if (id < 0 || id >= (int)ctx->maps.size() || !ctx->maps[id].live) return nullptr;
     return &ctx->maps[id];
@@ -319,6 +324,7 @@ MapSlot *get_map(relo_ctx *ctx, int id) {
 void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.d2, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
+    dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.field, sizeof(uint16_t) * 64 * (size_t)m.dev.TW * m.dev.TH);
     dev_free(ctx, m.dev.bits, sizeof(uint64_t) * (size_t)m.dev.TW * m.dev.TH);
@@ -345,7 +351,8 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     const size_t cells = (size_t)w * h, tiles = (size_t)m.dev.TW * m.dev.TH;
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
-        {(void **)&m.dev.field, tiles * 64 * 2}, {(void **)&m.dev.bits, tiles * 8}};
+        {(void **)&m.dev.field, tiles * 64 * 2}, {(void **)&m.dev.bits, tiles * 8},
+        {(void **)&m.dev.summ, sizeof(int2) * (size_t)w * edt_segments(h)}};
     for (auto &a : allocs) {
         rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
         if (rc) {
@@ -356,7 +363,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     }
     cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
-    if (e == cudaSuccess) e = timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -525,7 +532,7 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             int C;
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
-            CK(timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
+            CK(timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -549,7 +556,7 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -559,7 +566,7 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -660,6 +667,7 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
     ra.n_iv = (int)P.iv.size();
     ra.scan = ctx->scan;
     ra.dda_steps = &ctx->scan->dda_steps;
+    ra.work = &ctx->scan->ray_work;
     ra.n_enum = P.n_enum;
     ra.n_m = P.n_m;
     ra.keys = ctx->keys;

@@ -22,8 +22,15 @@ struct MapDev {
     uint16_t *field = nullptr;  // [TH*TW*64] min(d2, C), 8x8 tiles
     uint64_t *bits = nullptr;   // [TH*TW] occupancy, bit (y&7)*8 + (x&7)
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
+    int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
 };
+
+// rows per column segment of the EDT column pass: at least 16, at most 64 segments
+__host__ __device__ inline int edt_segment_rows(int H) {
+    int L = (H + 63) / 64;
+    return L < 16 ? 16 : L;
+}
 
 __host__ __device__ inline size_t tile_index(int x, int y, int TW) {
     return ((size_t)(y >> 3) * TW + (x >> 3)) * 64 + ((y & 7) << 3) + (x & 7);
@@ -35,7 +42,8 @@ struct ScanInfo {
     int n_valid;                    // N of Eq. 26 (valid beams)
     int k_ret;                      // median of {k_full, k_mid, k_low} (Eq. 26-27)
     unsigned long long dda_steps;   // cells entered by all rays of the request (work counter)
-    int pad[2];
+    unsigned int ray_work;          // next hypothesis for the ray-cast CTAs
+    int pad[1];
 };
 
 // Running state of the batched selection of one request.
@@ -58,6 +66,7 @@ struct RayArgs {
     int n_iv;
     const ScanInfo *scan;
     unsigned long long *dda_steps;   // optional work counter (may be null)
+    unsigned int *work;              // hypothesis counter, zero at launch
     int n_enum, n_m;        // orientation stride and count scored by SMAD
     unsigned long long *keys;   // [n_hyp]
     long long *smad_num;        // [n_hyp]

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ra
         info->n_valid = N;
         info->k_ret = k;
         info->dda_steps = 0ull;
+        info->ray_work = 0u;
     }
 }
 

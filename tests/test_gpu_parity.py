@@ -335,3 +335,25 @@ def test_device_entry_points_match_host_ones(relo, workload):
     again = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
     assert again.as_dict() == host.as_dict()
     ctx.close()
+
+
+def test_host_entry_points_repeated(relo, workload):
+    """The end-to-end loop of the benchmark: map, hypotheses and scan re-sent
+    from pinned host buffers every call, identical results each time."""
+    torch = torch_()
+    wl = workload(1)
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0)
+    mid = ctx.load_map(wl.grid, wl.res)
+    grid_h = torch.from_numpy(np.ascontiguousarray(wl.grid)).pin_memory()
+    xy_h = torch.from_numpy(workloads.cell_centres(wl.hyps, wl.res)).pin_memory()
+    z_h = torch.from_numpy(np.ascontiguousarray(wl.ranges)).pin_memory()
+    out = relo.Result()
+    first = None
+    for _ in range(5):
+        ctx.update_map_ptr(mid, grid_h.data_ptr())
+        ctx.set_hypotheses_ptr(mid, xy_h.data_ptr(), len(wl.hyps))
+        ctx.relocalize_ptr(mid, z_h.data_ptr(), wl.angles, len(wl.ranges), wl.max_range, out)
+        d = out.as_dict()
+        first = first or d
+        assert d == first and d["status"] == 0
+    ctx.close()
