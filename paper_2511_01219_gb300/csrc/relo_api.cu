@@ -78,9 +78,6 @@ struct relo_ctx {
     size_t T_cap = 0;
     int32_t *local = nullptr;
     size_t local_cap = 0;
-    float *ranges_host = nullptr;
-    size_t ranges_host_cap = 0;
-    relo_result *result_host = nullptr;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -477,7 +474,6 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
             ctx->own_stream = e == cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->result_host, sizeof(relo_result));
     if (e != cudaSuccess) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
@@ -509,8 +505,6 @@ int relo_destroy(relo_ctx *ctx) {
         cudaEventDestroy(pe.b);
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
-    if (ctx->result_host) cudaFreeHost(ctx->result_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return RELO_OK;
@@ -743,30 +737,21 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
 int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
                     float max_range, relo_result *out) {
     if (!ctx || !ranges || !angles || !out || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
-    if ((size_t)n_beams > ctx->ranges_host_cap) {
-        for (auto &pe : ctx->pending) {
-        cudaEventDestroy(pe.a);
-        cudaEventDestroy(pe.b);
-    }
-    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->ranges_host) cudaFreeHost(ctx->ranges_host);
-        ctx->ranges_host = nullptr;
-        ctx->ranges_host_cap = 0;
-        CK(cudaMallocHost((void **)&ctx->ranges_host, sizeof(float) * n_beams), "pinned staging");
-        ctx->ranges_host_cap = n_beams;
-    }
+    // The call blocks until the result is back, so the caller's buffers serve
+    // directly as copy source and destination; the library keeps no pinned
+    // host staging of its own.
     int rc = ensure(ctx, &ctx->ranges_dev, &ctx->ranges_cap, (size_t)n_beams, "scan upload");
     if (rc) return rc;
-    memcpy(ctx->ranges_host, ranges, sizeof(float) * n_beams);
-    CK(cudaMemcpyAsync(ctx->ranges_dev, ctx->ranges_host, sizeof(float) * n_beams, cudaMemcpyHostToDevice,
-                       ctx->stream),
+    CK(cudaMemcpyAsync(ctx->ranges_dev, ranges, sizeof(float) * n_beams, cudaMemcpyHostToDevice, ctx->stream),
        "scan upload");
     rc = relo_relocalize_dev(ctx, map_id, ctx->ranges_dev, angles, n_beams, max_range, ctx->result_dev);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->result_host, ctx->result_dev, sizeof(relo_result), cudaMemcpyDeviceToHost, ctx->stream),
+    if (rc) {
+        cudaStreamSynchronize(ctx->stream);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(out, ctx->result_dev, sizeof(relo_result), cudaMemcpyDeviceToHost, ctx->stream),
        "result download");
     CK(cudaStreamSynchronize(ctx->stream), "relocalize");
-    *out = *ctx->result_host;
     if (out->status != RELO_OK) return fail(ctx, out->status, "the scan has no valid beam");
     return RELO_OK;
 }

@@ -357,3 +357,26 @@ def test_host_entry_points_repeated(relo, workload):
         first = first or d
         assert d == first and d["status"] == 0
     ctx.close()
+
+
+def test_profiling_then_blocking_call_then_close(relo, workload):
+    """Stage timing on device steps, then the first blocking host-pointer call,
+    then destroy: the context must tear down cleanly."""
+    torch = torch_()
+    wl = workload(0)
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0)
+    g = torch.tensor(wl.grid, device="cuda")
+    mid = ctx.load_map_dev(g, wl.res)
+    ctx.set_hypotheses_cells_dev(mid, torch.tensor(wl.hyps, device="cuda"))
+    z = torch.tensor(wl.ranges, device="cuda")
+    res = torch.empty(relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.set_profiling(True)
+    for _ in range(3):
+        ctx.update_map_dev(mid, g)
+        ctx.relocalize_dev(mid, z, wl.angles, wl.max_range, res)
+    ms, n, k = ctx.stage_times(reset=True)
+    ctx.set_profiling(False)
+    assert n["raycast_smad"] == 3 and n["edt"] == 3 and all(v >= 0 for v in ms.values()) and k > 0
+    out = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert out.status == 0
+    ctx.close()
