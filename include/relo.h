@@ -185,6 +185,22 @@ int relo_set_profiling(relo_ctx *ctx, int32_t enable);
 int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
                      int64_t *kernels_out);
 
+/* Allocation-free EDT.  The paper has no counterpart to this entry point; it
+ * serves callers that may not allocate device memory once running, such as a
+ * robot's real-time localisation loop that allocates only at start-up, or a
+ * framework that owns all device memory through its own pool.
+ * Computes the exact squared EDT of grid_dev (int8, row-major, w x h, value
+ * >= 65 occupied) into d2_dev (int32, row-major, cells^2, -1 when the grid
+ * has no occupied cell), asynchronously on stream (a cudaStream_t; NULL = the
+ * default stream), with no context and no allocation: the caller owns the
+ * input and the output, and the scratch is a file-scope device array of
+ * fixed size (4.5 MiB per device, held until the process exits).
+ * Returns RELO_E_INVALID_ARG for null pointers or w, h outside [1, 1024],
+ * RELO_E_CUDA if a CUDA call fails.  The first call on a device looks up the
+ * scratch address with that device current: make it before any stream
+ * capture.  Calls share the scratch, so calls that overlap on the GPU race. */
+int relo_edt_noalloc(const int8_t *grid_dev, int32_t w, int32_t h, int32_t *d2_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,7 +38,7 @@ EXPORTED = [
     "relo_default_params", "relo_create", "relo_destroy", "relo_last_error", "relo_set_params", "relo_load_map",
     "relo_load_map_dev", "relo_update_map", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
-    "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times",
+    "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
 ]
 STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
 
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "relo_synth_scans_dev": (ctypes.c_int, [P, I32, P, I32, P, I32, F, P, P, I64, P]),
             "relo_set_profiling": (ctypes.c_int, [P, I32]),
             "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
+            "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
