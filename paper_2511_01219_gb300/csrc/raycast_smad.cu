@@ -42,8 +42,8 @@ __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     return (uint32_t)r;
 }
 
-// Returns the Q16 range (0 = no hit); *hit receives cy*W+cx or -1, *steps the
-// number of cells the traversal entered (the definition's cell count).
+// State of one ray's traversal.  advance() enters the next cell, or crosses a
+// whole empty tile at once, and reports whether the ray has stopped.
 //
 // Empty tiles are crossed in one move.  Inside a tile whose 64-bit word is 0
 // no cell can stop the ray except by leaving the map or the range, and both
@@ -57,16 +57,26 @@ __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
 // x-steps whose crossings come no later (ties step x first), i = 0 if
 // B = e + 2(ny-1)|Dx| < 0, else floor(B / (2|Dy|)) + 1.  Both counts are at
 // most 7.
-__device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int lim, int hx,
-                                             int hy, int2 d, int *hit, int *steps) {
-    const int ax = d.x < 0 ? -d.x : d.x, ay = d.y < 0 ? -d.y : d.y;
-    const int sx = d.x > 0 ? 1 : -1, sy = d.y > 0 ? 1 : -1;
-    const uint32_t two_ax = 2u * (uint32_t)ax, two_ay = 2u * (uint32_t)ay;
-    int e = ax - ay;
-    int cx = hx, cy = hy, adx = 0, ady = 0, c2 = 0, n = 0;
-    int tile = (cy >> 3) * TW + (cx >> 3);
-    unsigned long long word = __ldg(bits + tile);
-    for (;;) {
+struct Ray {
+    int ax, ay, sx, sy, e, cx, cy, adx, ady, c2, n, tile;
+    unsigned long long word;
+
+    __device__ __forceinline__ void init(int2 d, int hx, int hy, int tile0, unsigned long long word0) {
+        ax = d.x < 0 ? -d.x : d.x;
+        ay = d.y < 0 ? -d.y : d.y;
+        sx = d.x > 0 ? 1 : -1;
+        sy = d.y > 0 ? 1 : -1;
+        e = ax - ay;
+        cx = hx;
+        cy = hy;
+        adx = ady = c2 = n = 0;
+        tile = tile0;
+        word = word0;
+    }
+
+    // true once the ray stopped; *range = Q16 range of a hit, else 0
+    __device__ __forceinline__ bool advance(const uint64_t *__restrict__ bits, int W, int H, int TW, int lim,
+                                            uint32_t *range) {
         if (word == 0ull) {
             const int nx = sx > 0 ? 8 - (cx & 7) : (cx & 7) + 1;
             const int ny = sy > 0 ? 8 - (cy & 7) : (cy & 7) + 1;
@@ -103,21 +113,20 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
             c2 = adx * adx + ady * ady;
         } else if (e >= 0) {
             cx += sx;
-            e = (int)((uint32_t)e - two_ay);
+            e = (int)((uint32_t)e - 2u * (uint32_t)ay);
             c2 += 2 * adx + 1;
             ++adx;
             ++n;
         } else {
             cy += sy;
-            e = (int)((uint32_t)e + two_ax);
+            e = (int)((uint32_t)e + 2u * (uint32_t)ax);
             c2 += 2 * ady + 1;
             ++ady;
             ++n;
         }
         if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H || c2 > lim) {
-            *hit = -1;
-            *steps = n;
-            return 0u;
+            *range = 0u;
+            return true;
         }
         const int t = (cy >> 3) * TW + (cx >> 3);
         if (t != tile) {
@@ -125,11 +134,25 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
             word = __ldg(bits + t);
         }
         if ((word >> (((cy & 7) << 3) | (cx & 7))) & 1ull) {
-            *hit = cy * W + cx;
-            *steps = n;
-            return isqrt_q16(c2);
+            *range = isqrt_q16(c2);
+            return true;
         }
+        return false;
     }
+};
+
+// whole ray: Q16 range (0 = no hit); *hit receives cy*W+cx or -1, *steps the cells entered
+__device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int lim, int hx,
+                                             int hy, int2 d, int *hit, int *steps) {
+    Ray ray;
+    const int tile0 = (hy >> 3) * TW + (hx >> 3);
+    ray.init(d, hx, hy, tile0, __ldg(bits + tile0));
+    uint32_t r = 0u;
+    while (!ray.advance(bits, W, H, TW, lim, &r)) {
+    }
+    *hit = r ? ray.cy * W + ray.cx : -1;
+    *steps = ray.n;
+    return r;
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
@@ -149,16 +172,20 @@ __host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
 }
 
 // One CTA per hypothesis, taken from a device work counter so that costly
-// hypotheses (long rays) do not leave CTAs idle at the end.  Warps cast
-// interleaved 32-ray chunks; each chunk is scanned by its warp into
-// exclusive in-chunk prefixes, then one warp turns the chunk totals into
-// 64-bit chunk prefixes; P(t) = chunkP[t / 32] + inner[t] is the cyclic
-// prefix sum of Eq. 17 for t in [0, N_s].  The threads then split the
-// orientations, evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).
+// hypotheses (long rays) do not leave CTAs idle at the end.  Inside the CTA
+// the N_s rays form a queue: every lane traces one ray at a time and, as soon
+// as it stops, takes the next ray index from a shared counter (one atomic per
+// warp per refill), so lanes and warps stay busy until the queue is empty
+// whatever the mix of ray lengths.  Ranges land in shared memory by ray
+// index.  Each 32-ray chunk is then scanned by a warp into exclusive in-chunk
+// prefixes and one warp turns the chunk totals into 64-bit chunk prefixes;
+// P(t) = chunkP[t / 32] + inner[t] is the cyclic prefix sum of Eq. 17 for t
+// in [0, N_s].  The threads then split the orientations, evaluate Eq. 18-19
+// per m and reduce the minimum (Eq. 20).
 __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kRayThreads / 32];
-    __shared__ int s_h;
+    __shared__ int s_h, s_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nwarps = kRayThreads / 32;
     uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
@@ -166,28 +193,62 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
     const int nch = a.ns_pad >> 5;
     if (threadIdx.x < 32) inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
     const long long sum_real = a.scan->sum_real;
+    const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long my_steps = 0;
 
     for (;;) {
-        if (threadIdx.x == 0) s_h = (int)atomicAdd(a.work, 1u);
+        if (threadIdx.x == 0) {
+            s_h = (int)atomicAdd(a.work, 1u);
+            s_next = 0;
+        }
         __syncthreads();
         const int h = s_h;
         if (h >= a.n_hyp) break;
         const int2 hc = a.hyps[h];
+        const int tile0 = (hc.y >> 3) * a.TW + (hc.x >> 3);
+        const unsigned long long word0 = __ldg(a.bits + tile0);
+        Ray ray;
+        int j = -1;
+        bool more = true;
+        for (;;) {
+            const unsigned need = __ballot_sync(kFull, j < 0 && more);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&s_next, __popc(need));
+                base = __shfl_sync(kFull, base, leader);
+                if (j < 0 && more) {
+                    const int jj = base + __popc(need & lt_mask);
+                    if (jj < a.ns) {
+                        j = jj;
+                        ray.init(a.D[jj], hc.x, hc.y, tile0, word0);
+                    } else {
+                        more = false;
+                    }
+                }
+            }
+            if (__ballot_sync(kFull, j >= 0) == 0u) break;
+            if (j >= 0) {
+                uint32_t r;
+                if (ray.advance(a.bits, a.W, a.H, a.TW, a.lim, &r)) {
+                    inner[j] = r;
+                    my_steps += (unsigned)ray.n;
+                    j = -1;
+                }
+            }
+        }
+        __syncthreads();
         for (int c = warp; c < nch; c += nwarps) {
-            const int j = (c << 5) + lane;
-            uint32_t r = 0u;
-            int hit, steps = 0;
-            if (j < a.ns) r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
-            my_steps += (unsigned)steps;
-            uint32_t s = r;
+            const int jj = (c << 5) + lane;
+            const uint32_t r = jj < a.ns ? inner[jj] : 0u;
+            uint32_t sc = r;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(kFull, s, o);
-                if (lane >= o) s += t;
+                uint32_t t = __shfl_up_sync(kFull, sc, o);
+                if (lane >= o) sc += t;
             }
-            inner[j] = s - r;
-            if (lane == 31) chunkP[c + 1] = (long long)s;   // chunk total, turned into a prefix below
+            inner[jj] = sc - r;
+            if (lane == 31) chunkP[c + 1] = (long long)sc;   // chunk total, turned into a prefix below
         }
         __syncthreads();
         if (warp == 0) {

@@ -89,6 +89,7 @@ struct TamArgs {
     float *T;                   // [K * n_orient]
     unsigned long long *best_key;   // [K] (T bits << 32) | (0xffffffff - q)
     const SelectState *state;
+    int chunk, n_chunks;        // survivors per task and tasks per orientation (set by the launcher)
 };
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s);

@@ -105,6 +105,12 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ra
     }
 }
 
+// Work is split into tasks (orientation q, chunk of survivors).  A CTA first
+// computes the endpoint offsets of its orientation for every valid beam,
+// round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis, packed as two
+// int16 in shared memory; each warp then scores one survivor at a time with
+// those offsets, so the 64-bit offset arithmetic is paid once per
+// (orientation, beam) instead of once per (survivor, orientation, beam).
 template <int VPL>
 __global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -117,107 +123,134 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
     if (s_stop || N <= 0) return;
 
     float2 *lut = reinterpret_cast<float2 *>(smem);
-    int2 *sD = reinterpret_cast<int2 *>(smem + (size_t)(a.C + 1) * sizeof(float2));
-    int2 *sB = sD + a.ns;
+    uint32_t *offs = reinterpret_cast<uint32_t *>(smem + (size_t)(a.C + 1) * sizeof(float2));
     for (int i = threadIdx.x; i <= a.C; i += blockDim.x) lut[i] = a.lut[i];
-    for (int i = threadIdx.x; i < a.ns; i += blockDim.x) sD[i] = a.D[i];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sB[i] = a.vbR[i];
-    __syncthreads();
 
-    const long long items = (long long)(a.s_end - a.s_begin) * a.n_orient;
+    const int nb = a.s_end - a.s_begin;
+    const int n_tasks = a.n_orient * a.n_chunks;
     const float Nf = (float)N;
-    for (long long w = (long long)blockIdx.x * kTamWarps + warp; w < items; w += (long long)gridDim.x * kTamWarps) {
-        const int s = a.s_begin + (int)(w / a.n_orient);
-        const int q = (int)(w % a.n_orient);
-        const int2 hc = a.hyps[a.survivors[s]];
+    for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+        const int q = task % a.n_orient;
+        const int chunk = task / a.n_orient;
         const int m = q * a.n_enum;
-        uint32_t v[VPL];
-        int sumb = 0;
+        __syncthreads();   // the previous task's reads of offs are done
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int2 bR = a.vbR[i];
+            int j = bR.x + m;
+            if (j >= a.ns) j -= a.ns;
+            const int2 d = a.D[j];
+            const int ox = (int)(((long long)bR.y * d.x + (1ll << 45)) >> 46);
+            const int oy = (int)(((long long)bR.y * d.y + (1ll << 45)) >> 46);
+            offs[i] = ((uint32_t)ox & 0xffffu) | ((uint32_t)oy << 16);
+        }
+        __syncthreads();
+        const int s_lo = a.s_begin + chunk * a.chunk;
+        const int s_hi = min(a.s_end, s_lo + a.chunk);
+        for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
+            const int2 hc = a.hyps[a.survivors[s]];
+            uint32_t v[VPL];
+            int sumb = 0;
 #pragma unroll
-        for (int t = 0; t < VPL; ++t) {
-            const int i = (t << 5) + lane;
-            uint32_t bv = kNoBeam;
-            if (i < N) {
-                const int2 bR = sB[i];
-                int j = bR.x + m;
-                if (j >= a.ns) j -= a.ns;
-                const int2 d = sD[j];
-                const int ox = (int)(((long long)bR.y * d.x + (1ll << 45)) >> 46);
-                const int oy = (int)(((long long)bR.y * d.y + (1ll << 45)) >> 46);
-                const int ex = hc.x + ox, ey = hc.y + oy;
-                bv = ((unsigned)ex < (unsigned)a.W && (unsigned)ey < (unsigned)a.H)
-                         ? (uint32_t)__ldg(a.field + tile_index(ex, ey, a.TW))
-                         : (uint32_t)a.C;
-                sumb += (int)bv;
+            for (int t = 0; t < VPL; ++t) {
+                const int i = (t << 5) + lane;
+                uint32_t bv = kNoBeam;
+                if (i < N) {
+                    const uint32_t o = offs[i];
+                    const int ex = hc.x + (int)(short)(o & 0xffffu);
+                    const int ey = hc.y + ((int)o >> 16);
+                    bv = ((unsigned)ex < (unsigned)a.W && (unsigned)ey < (unsigned)a.H)
+                             ? (uint32_t)__ldg(a.field + tile_index(ex, ey, a.TW))
+                             : (uint32_t)a.C;
+                    sumb += (int)bv;
+                }
+                v[t] = bv;
             }
-            v[t] = bv;
-        }
-        // smallest t with #{b <= t} >= k
-        int lo = 0, hi = a.C;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            int c = 0;
+            // smallest b_k with #{b <= b_k} >= k
+            int lo = 0, hi = a.C;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                int c = 0;
 #pragma unroll
-            for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
-            c = __reduce_add_sync(kFull, c);
-            if (c >= k) hi = mid;
-            else lo = mid + 1;
-        }
-        const uint32_t bk = (uint32_t)lo;
-        float sg = 0.0f, sl = 0.0f;
-        int clt = 0;
+                for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
+                c = __reduce_add_sync(kFull, c);
+                if (c >= k) hi = mid;
+                else lo = mid + 1;
+            }
+            const uint32_t bk = (uint32_t)lo;
+            float sg = 0.0f, sl = 0.0f;
+            int clt = 0;
 #pragma unroll
-        for (int t = 0; t < VPL; ++t) {
-            if (v[t] != kNoBeam) {
-                const float2 lg = lut[v[t]];
-                sg += lg.y;
-                if (v[t] < bk) {
-                    sl += lg.x;
-                    ++clt;
+            for (int t = 0; t < VPL; ++t) {
+                if (v[t] != kNoBeam) {
+                    const float2 lg = lut[v[t]];
+                    sg += lg.y;
+                    if (v[t] < bk) {
+                        sl += lg.x;
+                        ++clt;
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sg += __shfl_xor_sync(kFull, sg, o);
-            sl += __shfl_xor_sync(kFull, sl, o);
-        }
-        clt = __reduce_add_sync(kFull, clt);
-        sumb = __reduce_add_sync(kFull, sumb);
-        if (lane == 0) {
-            const float ltop = sl + (float)(k - clt) * lut[bk].x;
-            const float lbar = ltop / (float)k;
-            const float wp = expf(lbar);
-            const float dd = a.res * sg / Nf;   // d_max - dbar
-            const float dbar = a.d_max - dd;
-            const float span = a.d_max - a.d_min;
-            const float sd = fminf(dd, span) / span;
-            float var = a.res2 * ((float)sumb / Nf) - dbar * dbar;
-            var = fmaxf(var, 0.0f);
-            const float c = expf(-0.5f * var);
-            const float T = cbrtf(wp * sd * c);
-            a.T[(size_t)s * a.n_orient + q] = T;
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(T) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
-            atomicMax(a.best_key + s, key);
+            for (int o = 16; o > 0; o >>= 1) {
+                sg += __shfl_xor_sync(kFull, sg, o);
+                sl += __shfl_xor_sync(kFull, sl, o);
+            }
+            clt = __reduce_add_sync(kFull, clt);
+            sumb = __reduce_add_sync(kFull, sumb);
+            if (lane == 0) {
+                const float ltop = sl + (float)(k - clt) * lut[bk].x;
+                const float lbar = ltop / (float)k;
+                const float wp = expf(lbar);
+                const float dd = a.res * sg / Nf;   // d_max - dbar
+                const float dbar = a.d_max - dd;
+                const float span = a.d_max - a.d_min;
+                const float sd = fminf(dd, span) / span;
+                float var = a.res2 * ((float)sumb / Nf) - dbar * dbar;
+                var = fmaxf(var, 0.0f);
+                const float c = expf(-0.5f * var);
+                const float T = cbrtf(wp * sd * c);
+                a.T[(size_t)s * a.n_orient + q] = T;
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(T) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
+                atomicMax(a.best_key + s, key);
+            }
         }
     }
+    (void)nb;
 }
 
 template <int VPL>
-cudaError_t run_tam(const TamArgs &a, int n_sm, cudaStream_t s, size_t smem) {
+cudaError_t run_tam(TamArgs a, int n_sm, cudaStream_t s, size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tam<VPL>, kTamWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    long long items = (long long)(a.s_end - a.s_begin) * a.n_orient;
-    long long want = (items + kTamWarps - 1) / kTamWarps;
-    long long grid = (long long)n_sm * occ;
-    if (grid > want) grid = want;
+    // Pick the number of survivor chunks per orientation so that the tasks
+    // fill whole waves of resident CTAs and whole rounds of the CTA's warps.
+    const int nb = a.s_end - a.s_begin;
+    const int slots = n_sm * occ;
+    const int max_chunks = (nb + kTamWarps - 1) / kTamWarps;
+    int best_nc = 1;
+    double best_eff = -1.0;
+    for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
+        const int chunk = (nb + nc - 1) / nc;
+        const long long tasks = (long long)a.n_orient * ((nb + chunk - 1) / chunk);
+        const long long waves = (tasks + slots - 1) / slots;
+        const double eff = (double)tasks / (double)(waves * slots) *
+                           (double)chunk / (double)(((chunk + kTamWarps - 1) / kTamWarps) * kTamWarps);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best_nc = nc;
+        }
+    }
+    a.chunk = (nb + best_nc - 1) / best_nc;
+    a.n_chunks = (nb + a.chunk - 1) / a.chunk;
+    long long tasks = (long long)a.n_orient * a.n_chunks;
+    int grid = (int)(tasks < slots ? tasks : slots);
     if (grid < 1) grid = 1;
-    k_tam<VPL><<<(unsigned)grid, kTamWarps * 32, smem, s>>>(a);
+    k_tam<VPL><<<grid, kTamWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -231,16 +264,14 @@ cudaError_t launch_scan_prep(const float *ranges, int n, int skip, float max_ran
 
 cudaError_t launch_tam(const TamArgs &a, int n_beams_max, int n_sm, cudaStream_t s) {
     if (a.s_end <= a.s_begin) return cudaSuccess;
-    size_t smem = (size_t)(a.C + 1) * sizeof(float2) + (size_t)a.ns * sizeof(int2) + (size_t)n_beams_max * sizeof(int2);
+    size_t smem = (size_t)(a.C + 1) * sizeof(float2) + (size_t)n_beams_max * sizeof(uint32_t);
     const int vpl = (n_beams_max + 31) / 32;
-    if (vpl <= 8) return run_tam<8>(a, n_sm, s, smem);
-    if (vpl <= 16) return run_tam<16>(a, n_sm, s, smem);
-    if (vpl <= 24) return run_tam<24>(a, n_sm, s, smem);
-    if (vpl <= 32) return run_tam<32>(a, n_sm, s, smem);
-    if (vpl <= 40) return run_tam<40>(a, n_sm, s, smem);
-    if (vpl <= 48) return run_tam<48>(a, n_sm, s, smem);
-    if (vpl <= 56) return run_tam<56>(a, n_sm, s, smem);
-    if (vpl <= 64) return run_tam<64>(a, n_sm, s, smem);
+#define RELO_TAM_CASE(V) \
+    if (vpl <= V) return run_tam<V>(a, n_sm, s, smem);
+    RELO_TAM_CASE(8) RELO_TAM_CASE(12) RELO_TAM_CASE(16) RELO_TAM_CASE(20) RELO_TAM_CASE(24) RELO_TAM_CASE(28)
+    RELO_TAM_CASE(32) RELO_TAM_CASE(36) RELO_TAM_CASE(40) RELO_TAM_CASE(44) RELO_TAM_CASE(48) RELO_TAM_CASE(52)
+    RELO_TAM_CASE(56) RELO_TAM_CASE(60) RELO_TAM_CASE(64)
+#undef RELO_TAM_CASE
     return cudaErrorInvalidValue;
 }
 
