@@ -173,15 +173,14 @@ __host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
 
 // One CTA per hypothesis, taken from a device work counter so that costly
 // hypotheses (long rays) do not leave CTAs idle at the end.  Inside the CTA
-// the N_s rays form a queue: every lane traces one ray at a time and, as soon
-// as it stops, takes the next ray index from a shared counter (one atomic per
-// warp per refill), so lanes and warps stay busy until the queue is empty
-// whatever the mix of ray lengths.  Ranges land in shared memory by ray
-// index.  Each 32-ray chunk is then scanned by a warp into exclusive in-chunk
-// prefixes and one warp turns the chunk totals into 64-bit chunk prefixes;
-// P(t) = chunkP[t / 32] + inner[t] is the cyclic prefix sum of Eq. 17 for t
-// in [0, N_s].  The threads then split the orientations, evaluate Eq. 18-19
-// per m and reduce the minimum (Eq. 20).
+// the warps take 32-ray chunks from a shared counter (lane = ray, so the
+// lanes of a warp trace neighbouring directions of similar length) until the
+// hypothesis's N_s rays are cast; ranges land in shared memory by ray index.
+// Each chunk is then scanned by a warp into exclusive in-chunk prefixes and
+// one warp turns the chunk totals into 64-bit chunk prefixes; P(t) =
+// chunkP[t / 32] + inner[t] is the cyclic prefix sum of Eq. 17 for t in
+// [0, N_s].  The threads then split the orientations, evaluate Eq. 18-19 per
+// m and reduce the minimum (Eq. 20).
 __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kRayThreads / 32];
@@ -193,7 +192,6 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
     const int nch = a.ns_pad >> 5;
     if (threadIdx.x < 32) inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
     const long long sum_real = a.scan->sum_real;
-    const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long my_steps = 0;
 
     for (;;) {
@@ -205,37 +203,17 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
         const int h = s_h;
         if (h >= a.n_hyp) break;
         const int2 hc = a.hyps[h];
-        const int tile0 = (hc.y >> 3) * a.TW + (hc.x >> 3);
-        const unsigned long long word0 = __ldg(a.bits + tile0);
-        Ray ray;
-        int j = -1;
-        bool more = true;
         for (;;) {
-            const unsigned need = __ballot_sync(kFull, j < 0 && more);
-            if (need) {
-                const int leader = __ffs(need) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&s_next, __popc(need));
-                base = __shfl_sync(kFull, base, leader);
-                if (j < 0 && more) {
-                    const int jj = base + __popc(need & lt_mask);
-                    if (jj < a.ns) {
-                        j = jj;
-                        ray.init(a.D[jj], hc.x, hc.y, tile0, word0);
-                    } else {
-                        more = false;
-                    }
-                }
-            }
-            if (__ballot_sync(kFull, j >= 0) == 0u) break;
-            if (j >= 0) {
-                uint32_t r;
-                if (ray.advance(a.bits, a.W, a.H, a.TW, a.lim, &r)) {
-                    inner[j] = r;
-                    my_steps += (unsigned)ray.n;
-                    j = -1;
-                }
-            }
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&s_next, 1);
+            c = __shfl_sync(kFull, c, 0);
+            if (c >= nch) break;
+            const int j = (c << 5) + lane;
+            uint32_t r = 0u;
+            int hit, steps = 0;
+            if (j < a.ns) r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
+            my_steps += (unsigned)steps;
+            inner[j] = r;
         }
         __syncthreads();
         for (int c = warp; c < nch; c += nwarps) {
