@@ -140,8 +140,27 @@ int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const fl
 int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles,
                         int32_t n_beams, float max_range, relo_result *result_dev);
 
-/* Intermediate outputs of the last relocalization, copied to caller device
- * memory (bytes = capacity of dst_dev; the call fails if it is too small):
+/* A batch of independent relocalizations (configs with many requests, and
+ * the served form): each request names a loaded map (with its hypotheses), a
+ * scan and its sensor geometry; maps, beam counts, hypothesis counts and FoVs
+ * may all differ.  Every stage runs once for the whole batch: one launch per
+ * stage serves all requests from a device work list (Eq. 13-31 per request,
+ * exactly as for a single request).  1 <= n <= 256; ceil(topk / batch) <= 64. */
+typedef struct relo_request {
+    int32_t map_id;
+    const float *ranges;   /* n_beams float32 metres: host memory for relo_relocalize_batch, device memory for _dev */
+    const float *angles;   /* n_beams float32 radians, host memory */
+    int32_t n_beams;
+    float max_range;
+} relo_request;
+/* Blocking; out[i] receives request i's result.  Returns the first error. */
+int relo_relocalize_batch(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *out);
+/* Asynchronous on the context stream; results_dev[i] (device memory) receives request i's result. */
+int relo_relocalize_batch_dev(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *results_dev);
+
+/* Intermediate outputs of the last relocalization (the first request of the
+ * last batch), copied to caller device memory (bytes = capacity of dst_dev;
+ * the call fails if it is too small):
  *   RELO_STAGE_SMAD_NUM   int64 [N_h]   SMAD numerators (Eq. 20)
  *   RELO_STAGE_SMAD_M     int32 [N_h]   minimising orientation shift m
  *   RELO_STAGE_SURVIVORS  int32 [K]     hypothesis indices in SMAD order
@@ -149,7 +168,7 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
  *   RELO_STAGE_BEST_M     int32 [K]     per-survivor argmax shift m of Eq. 22 (-1 if not scored)
  *   RELO_STAGE_LOCAL_TOPK int32 [n_batches x local_topk]  survivor positions of each batch's local top-k
  *   RELO_STAGE_SCAN_INFO  int64 [10]    N_s, n_orient, n_enum, N_valid, k_retained, sum_real, K, batches,
- *                                       cells entered by all rays (DDA steps), N_h */
+ *                                       cells entered by all rays of the batch (DDA steps), N_h */
 #define RELO_STAGE_SMAD_NUM 0
 #define RELO_STAGE_SMAD_M 1
 #define RELO_STAGE_SURVIVORS 2

@@ -39,6 +39,7 @@ EXPORTED = [
     "relo_load_map_dev", "relo_update_map", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
+    "relo_relocalize_batch", "relo_relocalize_batch_dev",
 ]
 STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
 
@@ -67,6 +68,11 @@ class Result(ctypes.Structure):
 
 
 RESULT_BYTES = ctypes.sizeof(Result)
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("map_id", ctypes.c_int32), ("ranges", ctypes.c_void_p), ("angles", ctypes.c_void_p),
+                ("n_beams", ctypes.c_int32), ("max_range", ctypes.c_float)]
 
 
 class ReloError(RuntimeError):
@@ -107,6 +113,8 @@ def lib() -> ctypes.CDLL:
             "relo_set_profiling": (ctypes.c_int, [P, I32]),
             "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
             "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
+            "relo_relocalize_batch": (ctypes.c_int, [P, P, I32, P]),
+            "relo_relocalize_batch_dev": (ctypes.c_int, [P, P, I32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -284,6 +292,31 @@ class Relo:
         k = ctypes.c_int64(0)
         self._check(self._L.relo_stage_times(self._h, None, None, 0, 0, ctypes.byref(k)), "stage_times")
         return k.value
+
+    def relocalize_batch(self, items) -> list:
+        """items: [(map_id, ranges ndarray, angles ndarray, max_range)]; blocking; list of Result."""
+        keep = []
+        arr = (Request * len(items))()
+        for i, (mid, z, a, mr) in enumerate(items):
+            z = np.ascontiguousarray(z, dtype=np.float32)
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            keep += [z, a]
+            arr[i] = Request(mid, z.ctypes.data, a.ctypes.data, len(z), mr)
+        out = (Result * len(items))()
+        self._check(self._L.relo_relocalize_batch(self._h, arr, len(items), out), "relocalize_batch")
+        return list(out)
+
+    def relocalize_batch_dev(self, items, results_t):
+        """items: [(map_id, ranges device tensor, angles ndarray, max_range)]; asynchronous;
+        results_t: device uint8 tensor of len(items) * RESULT_BYTES bytes."""
+        keep = []
+        arr = (Request * len(items))()
+        for i, (mid, zt, a, mr) in enumerate(items):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            keep.append(a)
+            arr[i] = Request(mid, zt.data_ptr(), a.ctypes.data, int(zt.numel()), mr)
+        self._check(self._L.relo_relocalize_batch_dev(self._h, arr, len(items), _t_ptr(results_t)),
+                    "relocalize_batch_dev")
 
     def stage(self, which: int, dst_t):
         self._check(self._L.relo_get_stage(self._h, which, _t_ptr(dst_t), dst_t.numel() * dst_t.element_size()),

@@ -171,38 +171,51 @@ __host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
     return inner_bytes(ns_pad) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
-// One CTA per hypothesis, taken from a device work counter so that costly
-// hypotheses (long rays) do not leave CTAs idle at the end.  Inside the CTA
-// the warps take 32-ray chunks from a shared counter (lane = ray, so the
-// lanes of a warp trace neighbouring directions of similar length) until the
-// hypothesis's N_s rays are cast; ranges land in shared memory by ray index.
-// Each chunk is then scanned by a warp into exclusive in-chunk prefixes and
-// one warp turns the chunk totals into 64-bit chunk prefixes; P(t) =
-// chunkP[t / 32] + inner[t] is the cyclic prefix sum of Eq. 17 for t in
-// [0, N_s].  The threads then split the orientations, evaluate Eq. 18-19 per
-// m and reduce the minimum (Eq. 20).
-__global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
+// One CTA per hypothesis.  A batch's hypotheses form one list (request r owns
+// slots [hyp_base_r, hyp_base_r + n_hyp_r)); CTAs take slots from a device
+// work counter, so costly hypotheses (long rays) and uneven requests do not
+// leave CTAs idle at the end.  Inside the CTA the warps take 32-ray chunks
+// from a shared counter (lane = ray, so the lanes of a warp trace
+// neighbouring directions of similar length) until the hypothesis's N_s rays
+// are cast; ranges land in shared memory by ray index.  Each chunk is then
+// scanned by a warp into exclusive in-chunk prefixes and one warp turns the
+// chunk totals into 64-bit chunk prefixes; P(t) = chunkP[t / 32] + inner[t]
+// is the cyclic prefix sum of Eq. 17 for t in [0, N_s].  The threads then
+// split the orientations, evaluate Eq. 18-19 per m and reduce the minimum
+// (Eq. 20).
+__global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
+                                                              BatchState *bs) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kRayThreads / 32];
-    __shared__ int s_h, s_next;
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    __shared__ int s_g, s_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nwarps = kRayThreads / 32;
-    uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
-    long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(a.ns_pad));
-    const int nch = a.ns_pad >> 5;
-    if (threadIdx.x < 32) inner[a.ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
-    const long long sum_real = a.scan->sum_real;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].hyp_base;
+    if (threadIdx.x == 0) s_base[R] = total_hyp;
     unsigned long long my_steps = 0;
 
     for (;;) {
         if (threadIdx.x == 0) {
-            s_h = (int)atomicAdd(a.work, 1u);
+            s_g = (int)atomicAdd(&bs->ray_work, 1u);
             s_next = 0;
         }
         __syncthreads();
-        const int h = s_h;
-        if (h >= a.n_hyp) break;
-        const int2 hc = a.hyps[h];
+        const int g = s_g;
+        if (g >= total_hyp) break;
+        int lo = 0, hi = R - 1;   // last request whose base <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_base[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDesc &d = reqs[lo];
+        const int h = g - s_base[lo];
+        const int ns = d.ns, ns_pad = d.ns_pad, nch = ns_pad >> 5;
+        uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
+        long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(ns_pad));
+        if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
+        const int2 hc = d.hyps[h];
         for (;;) {
             int c = 0;
             if (lane == 0) c = atomicAdd(&s_next, 1);
@@ -211,14 +224,14 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
             const int j = (c << 5) + lane;
             uint32_t r = 0u;
             int hit, steps = 0;
-            if (j < a.ns) r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
+            if (j < ns) r = cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, d.D[j], &hit, &steps);
             my_steps += (unsigned)steps;
             inner[j] = r;
         }
         __syncthreads();
         for (int c = warp; c < nch; c += nwarps) {
             const int jj = (c << 5) + lane;
-            const uint32_t r = jj < a.ns ? inner[jj] : 0u;
+            const uint32_t r = jj < ns ? inner[jj] : 0u;
             uint32_t sc = r;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -245,21 +258,22 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
             if (lane == 0) chunkP[0] = 0;
         }
         __syncthreads();
+        const long long sum_real = d.scan->sum_real;
         unsigned long long best = ~0ull;
-        for (int q = threadIdx.x; q < a.n_m; q += kRayThreads) {
-            const int m = q * a.n_enum;
+        for (int q = threadIdx.x; q < d.n_m; q += kRayThreads) {
+            const int m = q * d.n_enum;
             long long Wm = 0;
-            for (int k = 0; k < a.n_iv; ++k) {
-                const int2 iv = a.iv[k];
+            for (int k = 0; k < d.n_iv; ++k) {
+                const int2 iv = d.iv[k];
                 int s0 = iv.x + m;
-                if (s0 >= a.ns) s0 -= a.ns;
+                if (s0 >= ns) s0 -= ns;
                 const int e = s0 + iv.y;
                 const long long p0 = chunkP[s0 >> 5] + inner[s0];
-                if (e <= a.ns) {
+                if (e <= ns) {
                     Wm += chunkP[e >> 5] + inner[e] - p0;
                 } else {
-                    const int e2 = e - a.ns;
-                    Wm += (chunkP[a.ns >> 5] + inner[a.ns] - p0) + (chunkP[e2 >> 5] + inner[e2]);
+                    const int e2 = e - ns;
+                    Wm += (chunkP[ns >> 5] + inner[ns] - p0) + (chunkP[e2 >> 5] + inner[e2]);
                 }
             }
             long long dnum = sum_real - Wm;
@@ -275,17 +289,15 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(RayArgs a) {
             for (int w = 1; w < nwarps; ++w) b = s_best[w] < b ? s_best[w] : b;
             const unsigned long long num = b >> 20;
             const int q = (int)(b & 0xfffffu);
-            a.keys[h] = (num << kHypBits) | (unsigned long long)h;
-            a.smad_num[h] = (long long)num;
-            a.smad_m[h] = q * a.n_enum;
+            d.keys[h] = (num << kHypBits) | (unsigned long long)h;
+            d.smad_num[h] = (long long)num;
+            d.smad_m[h] = q * d.n_enum;
         }
         // the next iteration's first __syncthreads orders these reads before inner/chunkP are rewritten
     }
-    if (a.dda_steps) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, o);
-        if (lane == 0 && my_steps) atomicAdd(a.dda_steps, my_steps);
-    }
+    for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, o);
+    if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
 }
 
 __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__ ranges, int32_t *__restrict__ hits) {
@@ -302,8 +314,10 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
 
 }  // namespace
 
-cudaError_t launch_raycast_smad(const RayArgs &a, int n_sm, cudaStream_t s) {
-    size_t smem = cta_smem_bytes(a.ns_pad);
+cudaError_t launch_raycast_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
+                                cudaStream_t s) {
+    if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
+    size_t smem = cta_smem_bytes(max_ns_pad);
     cudaError_t e = cudaFuncSetAttribute(k_raycast_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -311,9 +325,9 @@ cudaError_t launch_raycast_smad(const RayArgs &a, int n_sm, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int grid = n_sm * occ;
-    if (grid > a.n_hyp) grid = a.n_hyp;
+    if (grid > total_hyp) grid = total_hyp;
     if (grid < 1) grid = 1;
-    k_raycast_smad<<<grid, kRayThreads, smem, s>>>(a);
+    k_raycast_smad<<<grid, kRayThreads, smem, s>>>(reqs, R, total_hyp, bs);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/relo.h: contexts, map slots,
 // hypothesis sets, the per-sensor plan (Eq. 11-15) and the launch sequence of
-// one relocalization.  All scoring arithmetic runs in the library's kernels.
+// a batch of relocalizations.  All scoring arithmetic runs in the library's
+// kernels.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -19,8 +20,7 @@ using namespace relo;
 namespace {
 
 struct SensorPlan {
-    bool valid = false;
-    std::vector<float> angles;   // key: the angles the plan was built from
+    std::vector<float> angles;   // key: the (downsampled) angles the plan was built from
     int n_skip = 1, n_orient_param = 0;
     int n = 0, ns = 0, n_orient = 0, n_enum = 1, n_m = 1;
     double lam = 0, a_mid = 0, a_low = 0;
@@ -29,7 +29,8 @@ struct SensorPlan {
     std::vector<int2> D, iv;
     int32_t *b_dev = nullptr;
     int2 *D_dev = nullptr, *iv_dev = nullptr;
-    size_t b_cap = 0, D_cap = 0, iv_cap = 0;
+    size_t bytes = 0;
+    unsigned long long last_use = 0;
 };
 
 struct MapSlot {
@@ -42,6 +43,31 @@ struct MapSlot {
     size_t bytes = 0;
 };
 
+// One request prepared for a batch.
+struct Prepared {
+    MapSlot *m;
+    SensorPlan *P;
+    const float *ranges_dev;
+    void *result_dev;
+    float max_range;
+    int lim, K, B, n_batches;
+};
+
+constexpr int kMaxPlans = 32;
+constexpr size_t kBlobBytes = 30000;   // kernel-parameter upload size
+
+// Device-to-device upload through kernel parameters: the bytes travel with the
+// launch, so no host buffer has to outlive the call and nothing is pinned.
+struct Blob {
+    unsigned int n;
+    unsigned char bytes[kBlobBytes];
+};
+
+__global__ void k_upload(const __grid_constant__ Blob blob, unsigned char *dst) {
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < blob.n; i += gridDim.x * blockDim.x)
+        dst[i] = blob.bytes[i];
+}
+
 }  // namespace
 
 struct relo_ctx {
@@ -50,34 +76,21 @@ struct relo_ctx {
     bool own_stream = false;
     int device = 0, n_sm = 0;
     std::vector<MapSlot> maps;
-    SensorPlan plan;
+    std::vector<SensorPlan *> plans;
+    unsigned long long plan_clock = 0;
     std::string err;
     long long held = 0;
-    // request scratch
-    float *ranges_dev = nullptr;
+    // batch state
+    ReqDesc *reqs_dev = nullptr;          // [kMaxBatchRequests]
+    TamSeg *segs_dev = nullptr;           // [kMaxBatches * kMaxBatchRequests]
+    BatchState *bs = nullptr;
+    relo_result *results_dev = nullptr;   // [kMaxBatchRequests]
+    unsigned char *arena = nullptr;       // per-request scratch of the current batch
+    size_t arena_cap = 0;
+    float *ranges_dev = nullptr;          // host-scan uploads
     size_t ranges_cap = 0;
-    int2 *vbR = nullptr;
-    size_t vbR_cap = 0;
-    ScanInfo *scan = nullptr;
-    SelectState *state = nullptr;
-    relo_result *result_dev = nullptr;
     int *bad = nullptr;
-    unsigned long long *keys = nullptr;
-    size_t keys_cap = 0;
-    long long *smad_num = nullptr;
-    size_t num_cap = 0;
-    int32_t *smad_m = nullptr;
-    size_t m_cap = 0;
-    int32_t *survivors = nullptr;
-    size_t surv_cap = 0;
-    int32_t *best_m = nullptr;
-    size_t bm_cap = 0;
-    unsigned long long *best_key = nullptr;
-    size_t bk_cap = 0;
-    float *T = nullptr;
-    size_t T_cap = 0;
-    int32_t *local = nullptr;
-    size_t local_cap = 0;
+    Blob *blob = nullptr;                 // host staging of one upload (heap)
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -86,9 +99,9 @@ struct relo_ctx {
     double stage_ms[RELO_N_STAGES] = {0};
     long long stage_n[RELO_N_STAGES] = {0};
     long long kernels = 0;
-    // shapes of the last request (for relo_get_stage)
-    int last_n_hyp = 0, last_K = 0, last_n_orient = 0, last_batches = 0, last_local = 0, last_ns = 0;
-    int last_enum = 0, last_map = -1;
+    // the first request of the last batch (for relo_get_stage)
+    ReqDesc last{};
+    bool has_last = false;
 };
 
 namespace {
@@ -215,14 +228,28 @@ int build_lut(relo_ctx *ctx, MapSlot &m) {
 
 // ---- sensor plan (Eq. 11-15) ----------------------------------------------------------------
 
-int plan_for(relo_ctx *ctx, const float *angles_raw, int n_raw) {
-    SensorPlan &P = ctx->plan;
+void free_plan(relo_ctx *ctx, SensorPlan *P) {
+    dev_free(ctx, P->b_dev, sizeof(int32_t) * P->b.size());
+    dev_free(ctx, P->D_dev, sizeof(int2) * P->D.size());
+    dev_free(ctx, P->iv_dev, sizeof(int2) * P->iv.size());
+    delete P;
+}
+
+// The plan for these angles, from the cache or newly built (least recently
+// used plans are evicted beyond kMaxPlans; a plan in use by queued work is
+// never evicted because eviction first waits for the stream).
+int plan_for(relo_ctx *ctx, const float *angles_raw, int n_raw, SensorPlan **out) {
     const int skip = ctx->p.n_skip_beam;
     const int n = (n_raw + skip - 1) / skip;   // Eq. 11: beams 0, skip, 2 skip, ...
     std::vector<float> a(n);
     for (int i = 0; i < n; ++i) a[i] = angles_raw[(size_t)i * skip];
-    if (P.valid && P.n_skip == skip && P.n_orient_param == ctx->p.n_orient && P.angles == a) return RELO_OK;
-    P.valid = false;
+    for (SensorPlan *P : ctx->plans) {
+        if (P->n_skip == skip && P->n_orient_param == ctx->p.n_orient && P->angles == a) {
+            P->last_use = ++ctx->plan_clock;
+            *out = P;
+            return RELO_OK;
+        }
+    }
     if (n < 2) return fail(ctx, RELO_E_BEAM_GRID, "need at least two beams");
     const double two_pi = 2.0 * M_PI;
     // Consecutive angles differ by a whole number of grid steps (one inside a
@@ -278,33 +305,46 @@ int plan_for(relo_ctx *ctx, const float *angles_raw, int n_raw) {
     }
     long long fov = 0;
     for (auto &v : iv) fov += v.y;
+    SensorPlan *P = new (std::nothrow) SensorPlan();
+    if (!P) return fail(ctx, RELO_E_INVALID_ARG, "out of host memory");
     const relo_params &p = ctx->p;
-    P.lam = (double)fov / (double)ns;
-    P.a_mid = p.a_mid_min + P.lam * (p.a_mid_max - p.a_mid_min);   // Eq. 25
-    P.a_low = p.a_low_min + P.lam * (p.a_low_max - p.a_low_min);
-    P.fov = fov;
-    P.n = n;
-    P.ns = (int)ns;
-    P.n_orient = n_orient;
-    P.n_enum = (int)ns / n_orient;
-    P.n_m = P.lam >= p.panoramic_ratio ? 1 : n_orient;   // Eq. 20
-    P.b = b;
-    P.D = D;
-    P.iv = iv;
+    P->lam = (double)fov / (double)ns;
+    P->a_mid = p.a_mid_min + P->lam * (p.a_mid_max - p.a_mid_min);   // Eq. 25
+    P->a_low = p.a_low_min + P->lam * (p.a_low_max - p.a_low_min);
+    P->fov = fov;
+    P->n = n;
+    P->ns = (int)ns;
+    P->n_orient = n_orient;
+    P->n_enum = (int)ns / n_orient;
+    P->n_m = P->lam >= p.panoramic_ratio ? 1 : n_orient;   // Eq. 20
+    P->b = b;
+    P->D = D;
+    P->iv = iv;
+    P->angles = a;
+    P->n_skip = skip;
+    P->n_orient_param = ctx->p.n_orient;
     int rc;
-    if ((rc = ensure(ctx, &P.b_dev, &P.b_cap, (size_t)n, "plan beams"))) return rc;
-    if ((rc = ensure(ctx, &P.D_dev, &P.D_cap, (size_t)ns, "plan directions"))) return rc;
-    if ((rc = ensure(ctx, &P.iv_dev, &P.iv_cap, iv.size(), "plan intervals"))) return rc;
-    CK(cudaMemcpyAsync(P.b_dev, b.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
-    CK(cudaMemcpyAsync(P.D_dev, D.data(), sizeof(int2) * ns, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
-    CK(cudaMemcpyAsync(P.iv_dev, iv.data(), sizeof(int2) * iv.size(), cudaMemcpyHostToDevice, ctx->stream),
+    if ((rc = dev_alloc(ctx, (void **)&P->b_dev, sizeof(int32_t) * n, "plan beams")) ||
+        (rc = dev_alloc(ctx, (void **)&P->D_dev, sizeof(int2) * ns, "plan directions")) ||
+        (rc = dev_alloc(ctx, (void **)&P->iv_dev, sizeof(int2) * iv.size(), "plan intervals"))) {
+        free_plan(ctx, P);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(P->b_dev, b.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
+    CK(cudaMemcpyAsync(P->D_dev, D.data(), sizeof(int2) * ns, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
+    CK(cudaMemcpyAsync(P->iv_dev, iv.data(), sizeof(int2) * iv.size(), cudaMemcpyHostToDevice, ctx->stream),
        "plan upload");
-    // the host vectors must outlive the asynchronous copies
+    // the host vectors of this call must outlive the asynchronous copies
     CK(cudaStreamSynchronize(ctx->stream), "plan upload");
-    P.angles = a;
-    P.n_skip = skip;
-    P.n_orient_param = ctx->p.n_orient;
-    P.valid = true;
+    if ((int)ctx->plans.size() >= kMaxPlans) {
+        auto it = std::min_element(ctx->plans.begin(), ctx->plans.end(),
+                                   [](SensorPlan *x, SensorPlan *y) { return x->last_use < y->last_use; });
+        free_plan(ctx, *it);
+        ctx->plans.erase(it);
+    }
+    P->last_use = ++ctx->plan_clock;
+    ctx->plans.push_back(P);
+    *out = P;
     return RELO_OK;
 }
 
@@ -425,6 +465,191 @@ int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, 
     return RELO_OK;
 }
 
+
+// ---- batches ------------------------------------------------------------------------------------
+
+int upload(relo_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    const unsigned char *p = static_cast<const unsigned char *>(src);
+    unsigned char *d = static_cast<unsigned char *>(dst);
+    while (bytes > 0) {
+        const size_t n = bytes < kBlobBytes ? bytes : kBlobBytes;
+        ctx->blob->n = (unsigned int)n;
+        memcpy(ctx->blob->bytes, p, n);
+        k_upload<<<(unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16), 256, 0, ctx->stream>>>(*ctx->blob, d);
+        CK(cudaGetLastError(), "descriptor upload");
+        ctx->kernels += 1;
+        p += n;
+        d += n;
+        bytes -= n;
+    }
+    return RELO_OK;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Checks one request and resolves its map and sensor plan.
+int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles, int32_t n_beams,
+            float max_range, void *result_dev, Prepared *out) {
+    if (!ranges_dev || !angles || !result_dev || n_beams < 2)
+        return fail(ctx, RELO_E_INVALID_ARG, "bad relocalize arguments");
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    if (m->n_hyp <= 0) return fail(ctx, RELO_E_NO_HYPOTHESES, "the map has no hypotheses");
+    if (!(max_range > 0) || !isfinite(max_range)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
+    SensorPlan *P = nullptr;
+    int rc = plan_for(ctx, angles, n_beams, &P);
+    if (rc) return rc;
+    if (P->n > kMaxValidBeams) return fail(ctx, RELO_E_INVALID_ARG, "at most 2048 beams after downsampling");
+    const double rq = (double)max_range * 65536.0 / m->res;
+    if (!(rq < 2147483647.0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
+    const long long rmax_q16 = llrint(rq);
+    if ((double)P->n * (double)rmax_q16 >= 8.0e12)
+        return fail(ctx, RELO_E_INVALID_ARG, "beam count x max range too large for the SMAD key");
+    const relo_params &p = ctx->p;
+    out->m = m;
+    out->P = P;
+    out->ranges_dev = ranges_dev;
+    out->result_dev = result_dev;
+    out->max_range = max_range;
+    out->lim = (int)((rmax_q16 * rmax_q16) >> 32);
+    out->K = std::min(p.topk, m->n_hyp);
+    out->B = std::min(p.batch, out->K);
+    out->n_batches = (out->K + out->B - 1) / out->B;
+    if (out->n_batches > kMaxBatches)
+        return fail(ctx, RELO_E_INVALID_ARG, "topk / batch must be at most 64 batches");
+    return RELO_OK;
+}
+
+// Lays out the batch's scratch, uploads its descriptors and launches every stage once.
+int run_batch(relo_ctx *ctx, const Prepared *pr, int R) {
+    if (R < 1 || R > kMaxBatchRequests) return fail(ctx, RELO_E_INVALID_ARG, "1 to 256 requests per batch");
+    const relo_params &p = ctx->p;
+    std::vector<ReqDesc> desc((size_t)R);
+    std::vector<size_t> off((size_t)R);
+    size_t total = 0;
+    int total_hyp = 0, max_ns_pad = 32, max_n_hyp = 1, max_K = 1, max_beams = 1, max_C = 0, max_batches = 0;
+    for (int r = 0; r < R; ++r) {
+        const Prepared &q = pr[r];
+        const int n = q.P->n, nh = q.m->n_hyp, K = q.K;
+        off[r] = total;
+        total += align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
+                 align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
+                 align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
+        if ((long long)total_hyp + nh > (1ll << 30)) return fail(ctx, RELO_E_INVALID_ARG, "batch too large");
+        total_hyp += nh;
+        max_ns_pad = std::max(max_ns_pad, (q.P->ns + 31) & ~31);
+        max_n_hyp = std::max(max_n_hyp, nh);
+        max_K = std::max(max_K, K);
+        max_beams = std::max(max_beams, n);
+        max_C = std::max(max_C, q.m->dev.C);
+        max_batches = std::max(max_batches, q.n_batches);
+    }
+    int rc = ensure(ctx, &ctx->arena, &ctx->arena_cap, total, "request scratch");
+    if (rc) return rc;
+    for (int r = 0; r < R; ++r) {
+        const Prepared &q = pr[r];
+        const MapSlot &m = *q.m;
+        const SensorPlan &P = *q.P;
+        ReqDesc &d = desc[r];
+        memset(&d, 0, sizeof d);
+        d.bits = m.dev.bits;
+        d.field = m.dev.field;
+        d.lut = m.lut;
+        d.W = m.dev.W;
+        d.H = m.dev.H;
+        d.TW = m.dev.TW;
+        d.C = m.dev.C;
+        d.res = (float)m.res;
+        d.res2 = (float)(m.res * m.res);
+        d.d_max = (float)(m.res * sqrt((double)m.dev.C));
+        d.d_min = (float)(m.res / 2.0);
+        d.resd = m.res;
+        d.ox = m.ox;
+        d.oy = m.oy;
+        d.hyps = m.hyps;
+        d.n_hyp = m.n_hyp;
+        d.D = P.D_dev;
+        d.b = P.b_dev;
+        d.iv = P.iv_dev;
+        d.ns = P.ns;
+        d.ns_pad = (P.ns + 31) & ~31;
+        d.n_iv = (int)P.iv.size();
+        d.n_beams = P.n;
+        d.n_orient = P.n_orient;
+        d.n_enum = P.n_enum;
+        d.n_m = P.n_m;
+        d.lim = q.lim;
+        d.a_mid = P.a_mid;
+        d.a_low = P.a_low;
+        d.fov = (double)P.fov;
+        d.ranges = q.ranges_dev;
+        d.skip = p.n_skip_beam;
+        d.max_range = q.max_range;
+        d.K = q.K;
+        d.B = q.B;
+        d.n_batches = q.n_batches;
+        d.L = p.local_topk;
+        d.early_stop = p.early_stop;
+        d.tau = p.tau;
+        d.n_smad_evals = (long long)m.n_hyp * P.n_m;
+        unsigned char *a = ctx->arena + off[r];
+        auto take = [&a](size_t bytes) {
+            unsigned char *x = a;
+            a += align_up(bytes);
+            return x;
+        };
+        d.vbR = (int2 *)take(sizeof(int2) * P.n);
+        d.scan = (ScanInfo *)take(sizeof(ScanInfo));
+        d.keys = (unsigned long long *)take(8ull * m.n_hyp);
+        d.smad_num = (long long *)take(8ull * m.n_hyp);
+        d.smad_m = (int32_t *)take(4ull * m.n_hyp);
+        d.survivors = (int32_t *)take(4ull * q.K);
+        d.best_m = (int32_t *)take(4ull * q.K);
+        d.T = (float *)take(4ull * q.K * P.n_orient);
+        d.best_key = (unsigned long long *)take(8ull * q.K);
+        d.local = (int32_t *)take(4ull * q.n_batches * p.local_topk);
+        d.state = (SelectState *)take(sizeof(SelectState));
+        d.result = q.result_dev;
+    }
+    int base = 0;
+    for (int r = 0; r < R; ++r) {
+        desc[r].hyp_base = base;
+        base += desc[r].n_hyp;
+    }
+    // TAM work of every batch index
+    std::vector<TamSeg> segs((size_t)max_batches * R);
+    std::vector<TamPlan> plans((size_t)max_batches);
+    std::vector<int> nb((size_t)R), no((size_t)R), sb((size_t)R);
+    for (int bi = 0; bi < max_batches; ++bi) {
+        for (int r = 0; r < R; ++r) {
+            const int s0 = bi * desc[r].B;
+            nb[r] = bi < desc[r].n_batches ? std::min(desc[r].K, s0 + desc[r].B) - s0 : 0;
+            no[r] = desc[r].n_orient;
+            sb[r] = s0;
+        }
+        plans[bi] = plan_tam(nb.data(), no.data(), sb.data(), R, max_beams, max_C, ctx->n_sm, &segs[(size_t)bi * R]);
+        if (plans[bi].vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
+    }
+    if ((rc = upload(ctx, ctx->reqs_dev, desc.data(), sizeof(ReqDesc) * R)) ||
+        (rc = upload(ctx, ctx->segs_dev, segs.data(), sizeof(TamSeg) * segs.size())))
+        return rc;
+    cudaStream_t st = ctx->stream;
+    CK(timed(ctx, 1, 1, [&] { return launch_scan_prep(ctx->reqs_dev, R, ctx->bs, st); }), "scan preparation");
+    CK(timed(ctx, 2, 1, [&] { return launch_raycast_smad(ctx->reqs_dev, R, total_hyp, max_ns_pad, ctx->bs, ctx->n_sm, st); }),
+       "ray cast + SMAD");
+    CK(timed(ctx, 3, 1, [&] { return launch_topk(ctx->reqs_dev, R, max_n_hyp, max_K, st); }), "SMAD top-K");
+    for (int bi = 0; bi < max_batches; ++bi) {
+        const TamSeg *sg = ctx->segs_dev + (size_t)bi * R;
+        CK(timed(ctx, 4, 1, [&] { return launch_tam(ctx->reqs_dev, R, sg, plans[bi], st); }), "TAM");
+        CK(timed(ctx, 5, 1, [&] { return launch_select_batch(ctx->reqs_dev, R, bi, st); }), "batch selection");
+    }
+    CK(timed(ctx, 5, 1, [&] { return launch_finalize(ctx->reqs_dev, R, st); }), "finalize");
+    ctx->last = desc[0];
+    ctx->has_last = true;
+    return RELO_OK;
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -464,7 +689,8 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
         delete ctx;
         return rc;
     }
-    cudaError_t e = cudaGetDevice(&ctx->device);
+    ctx->blob = new (std::nothrow) Blob;
+    cudaError_t e = ctx->blob ? cudaGetDevice(&ctx->device) : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) {
         if (stream) {
@@ -476,12 +702,16 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
     }
     if (e != cudaSuccess) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx->blob;
         delete ctx;
         return RELO_E_CUDA;
     }
-    if ((rc = dev_alloc(ctx, (void **)&ctx->scan, sizeof(ScanInfo), "request state")) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->state, sizeof(SelectState), "request state")) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->result_dev, sizeof(relo_result), "request state"))) {
+    if ((rc = dev_alloc(ctx, (void **)&ctx->reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests, "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests,
+                        "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->bs, sizeof(BatchState), "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->results_dev, sizeof(relo_result) * kMaxBatchRequests, "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&ctx->bad, sizeof(int), "batch state"))) {
         relo_destroy(ctx);
         return rc;
     }
@@ -494,18 +724,18 @@ int relo_destroy(relo_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &m : ctx->maps)
         if (m.live) free_map(ctx, m);
-    SensorPlan &P = ctx->plan;
-    void *ptrs[] = {P.b_dev, P.D_dev, P.iv_dev, ctx->ranges_dev, ctx->vbR, ctx->scan, ctx->state, ctx->result_dev,
-                    ctx->bad, ctx->keys, ctx->smad_num, ctx->smad_m, ctx->survivors, ctx->best_m, ctx->best_key,
-                    ctx->T, ctx->local};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    for (SensorPlan *P : ctx->plans) free_plan(ctx, P);
+    ctx->plans.clear();
+    void *ptrs[] = {ctx->reqs_dev, ctx->segs_dev, ctx->bs, ctx->results_dev, ctx->arena, ctx->ranges_dev, ctx->bad};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
     for (auto &pe : ctx->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
     }
-    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx->blob;
     delete ctx;
     return RELO_OK;
 }
@@ -519,7 +749,8 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
     const bool lut_changed = p->z_hit != ctx->p.z_hit || p->sigma_hit != ctx->p.sigma_hit ||
                              p->z_rand != ctx->p.z_rand || p->eps != ctx->p.eps || p->d_max != ctx->p.d_max;
     ctx->p = *p;
-    ctx->plan.valid = false;
+    for (SensorPlan *P : ctx->plans) free_plan(ctx, P);   // plans depend on n_orient, n_skip and Eq. 25
+    ctx->plans.clear();
     if (lut_changed) {
         for (auto &m : ctx->maps) {
             if (!m.live) continue;
@@ -605,183 +836,92 @@ int relo_set_hypotheses_cells_dev(relo_ctx *ctx, int32_t map_id, const int32_t *
 
 int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles,
                         int32_t n_beams, float max_range, relo_result *result_dev) {
-    if (!ctx || !ranges_dev || !angles || !result_dev || n_beams < 2)
-        return fail(ctx, RELO_E_INVALID_ARG, "bad relocalize arguments");
-    MapSlot *mp = get_map(ctx, map_id);
-    if (!mp) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
-    MapSlot &m = *mp;
-    if (m.n_hyp <= 0) return fail(ctx, RELO_E_NO_HYPOTHESES, "the map has no hypotheses");
-    if (!(max_range > 0) || !isfinite(max_range)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
-    int rc = plan_for(ctx, angles, n_beams);
+    if (!ctx) return RELO_E_INVALID_ARG;
+    Prepared pr;
+    int rc = prepare(ctx, map_id, ranges_dev, angles, n_beams, max_range, result_dev, &pr);
     if (rc) return rc;
-    const SensorPlan &P = ctx->plan;
-    const relo_params &p = ctx->p;
-    if (P.n > kMaxValidBeams) return fail(ctx, RELO_E_INVALID_ARG, "at most 2048 beams after downsampling");
-    const double rq = (double)max_range * 65536.0 / m.res;
-    if (!(rq < 2147483647.0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
-    const long long rmax_q16 = llrint(rq);
-    if ((double)P.n * (double)rmax_q16 >= 8.0e12)
-        return fail(ctx, RELO_E_INVALID_ARG, "beam count x max range too large for the SMAD key");
-    const long long lim = (rmax_q16 * rmax_q16) >> 32;
-    const int n_hyp = m.n_hyp;
-    const int K = std::min(p.topk, n_hyp);
-    const int B = std::min(p.batch, K);
-    const int n_batches = (K + B - 1) / B;
-    const int L = p.local_topk;
-    if ((rc = ensure(ctx, &ctx->vbR, &ctx->vbR_cap, (size_t)P.n, "scan buffers")) ||
-        (rc = ensure(ctx, &ctx->keys, &ctx->keys_cap, (size_t)n_hyp, "SMAD keys")) ||
-        (rc = ensure(ctx, &ctx->smad_num, &ctx->num_cap, (size_t)n_hyp, "SMAD numerators")) ||
-        (rc = ensure(ctx, &ctx->smad_m, &ctx->m_cap, (size_t)n_hyp, "SMAD orientations")) ||
-        (rc = ensure(ctx, &ctx->survivors, &ctx->surv_cap, (size_t)K, "survivors")) ||
-        (rc = ensure(ctx, &ctx->best_m, &ctx->bm_cap, (size_t)K, "orientation argmax")) ||
-        (rc = ensure(ctx, &ctx->best_key, &ctx->bk_cap, (size_t)K, "orientation argmax")) ||
-        (rc = ensure(ctx, &ctx->T, &ctx->T_cap, (size_t)K * P.n_orient, "TAM scores")) ||
-        (rc = ensure(ctx, &ctx->local, &ctx->local_cap, (size_t)n_batches * L, "local top-k")))
-        return rc;
-    cudaStream_t st = ctx->stream;
-    // a2: per-scan preparation (Eq. 11, 16, 26)
-    CK(timed(ctx, 1, 1, [&] {
-           return launch_scan_prep(ranges_dev, P.n, p.n_skip_beam, max_range, m.res, P.b_dev, P.a_mid, P.a_low,
-                                   ctx->vbR, ctx->scan, st);
-       }),
-       "scan preparation");
-    // a3 + a4: ray casting and SMAD (Eq. 13, 17-20)
-    RayArgs ra;
-    ra.bits = m.dev.bits;
-    ra.W = m.dev.W;
-    ra.H = m.dev.H;
-    ra.TW = m.dev.TW;
-    ra.D = P.D_dev;
-    ra.ns = P.ns;
-    ra.ns_pad = (P.ns + 31) & ~31;
-    ra.lim = (int)lim;
-    ra.hyps = m.hyps;
-    ra.n_hyp = n_hyp;
-    ra.iv = P.iv_dev;
-    ra.n_iv = (int)P.iv.size();
-    ra.scan = ctx->scan;
-    ra.dda_steps = &ctx->scan->dda_steps;
-    ra.work = &ctx->scan->ray_work;
-    ra.n_enum = P.n_enum;
-    ra.n_m = P.n_m;
-    ra.keys = ctx->keys;
-    ra.smad_num = ctx->smad_num;
-    ra.smad_m = ctx->smad_m;
-    CK(timed(ctx, 2, 1, [&] { return launch_raycast_smad(ra, ctx->n_sm, st); }), "ray cast + SMAD");
-    // a5: SMAD ordering, K survivors
-    CK(timed(ctx, 3, 1, [&] { return launch_topk(ctx->keys, n_hyp, K, ctx->survivors, st); }), "SMAD top-K");
-    // a6 + a7: batched TAM, orientation argmax, local top-k, early termination
-    CK(cudaMemsetAsync(ctx->best_key, 0, sizeof(unsigned long long) * K, st), "request reset");
-    CK(cudaMemsetAsync(ctx->best_m, 0xff, sizeof(int32_t) * K, st), "request reset");
-    CK(cudaMemsetAsync(ctx->T, 0xff, sizeof(float) * (size_t)K * P.n_orient, st), "request reset");
-    CK(cudaMemsetAsync(ctx->local, 0xff, sizeof(int32_t) * (size_t)n_batches * L, st), "request reset");
-    CK(cudaMemsetAsync(ctx->state, 0, sizeof(SelectState), st), "request reset");
-    TamArgs ta;
-    ta.field = m.dev.field;
-    ta.W = m.dev.W;
-    ta.H = m.dev.H;
-    ta.TW = m.dev.TW;
-    ta.C = m.dev.C;
-    ta.D = P.D_dev;
-    ta.ns = P.ns;
-    ta.vbR = ctx->vbR;
-    ta.scan = ctx->scan;
-    ta.survivors = ctx->survivors;
-    ta.hyps = m.hyps;
-    ta.n_orient = P.n_orient;
-    ta.n_enum = P.n_enum;
-    ta.lut = m.lut;
-    ta.res = (float)m.res;
-    ta.res2 = (float)(m.res * m.res);
-    ta.d_max = (float)(m.res * sqrt((double)m.dev.C));
-    ta.d_min = (float)(m.res / 2.0);
-    ta.T = ctx->T;
-    ta.best_key = ctx->best_key;
-    ta.state = ctx->state;
-    for (int bi = 0; bi < n_batches; ++bi) {
-        ta.s_begin = bi * B;
-        ta.s_end = std::min(K, ta.s_begin + B);
-        CK(timed(ctx, 4, 1, [&] { return launch_tam(ta, P.n, ctx->n_sm, st); }), "TAM");
-        CK(timed(ctx, 5, 1, [&] {
-               return launch_select_batch(ctx->best_key, ta.s_begin, ta.s_end, P.n_orient, P.n_enum, L, bi, p.tau,
-                                          p.early_stop, ctx->best_m, ctx->local, ctx->state, st);
-           }),
-           "batch selection");
-    }
-    FinalizeArgs fa;
-    fa.st = ctx->state;
-    fa.survivors = ctx->survivors;
-    fa.best_m = ctx->best_m;
-    fa.hyps = m.hyps;
-    fa.smad_num = ctx->smad_num;
-    fa.scan = ctx->scan;
-    fa.res = m.res;
-    fa.ox = m.ox;
-    fa.oy = m.oy;
-    fa.fov_beams = (double)P.fov;
-    fa.ns = P.ns;
-    fa.n_smad_evals = (long long)n_hyp * P.n_m;
-    fa.result = result_dev;
-    CK(timed(ctx, 5, 1, [&] { return launch_finalize(fa, st); }), "finalize");
-    ctx->last_n_hyp = n_hyp;
-    ctx->last_K = K;
-    ctx->last_n_orient = P.n_orient;
-    ctx->last_batches = n_batches;
-    ctx->last_local = L;
-    ctx->last_ns = P.ns;
-    ctx->last_enum = P.n_enum;
-    ctx->last_map = map_id;
-    return RELO_OK;
+    return run_batch(ctx, &pr, 1);
 }
 
 int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
                     float max_range, relo_result *out) {
     if (!ctx || !ranges || !angles || !out || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
-    // The call blocks until the result is back, so the caller's buffers serve
-    // directly as copy source and destination; the library keeps no pinned
-    // host staging of its own.
-    int rc = ensure(ctx, &ctx->ranges_dev, &ctx->ranges_cap, (size_t)n_beams, "scan upload");
+    relo_request rq = {map_id, ranges, angles, n_beams, max_range};
+    return relo_relocalize_batch(ctx, &rq, 1, out);
+}
+
+int relo_relocalize_batch_dev(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *results_dev) {
+    if (!ctx || !reqs || !results_dev || n < 1 || n > kMaxBatchRequests)
+        return fail(ctx, RELO_E_INVALID_ARG, "1 to 256 requests per batch");
+    std::vector<Prepared> pr((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        int rc = prepare(ctx, reqs[i].map_id, reqs[i].ranges, reqs[i].angles, reqs[i].n_beams, reqs[i].max_range,
+                         results_dev + i, &pr[i]);
+        if (rc) return rc;
+    }
+    return run_batch(ctx, pr.data(), n);
+}
+
+int relo_relocalize_batch(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *out) {
+    if (!ctx || !reqs || !out || n < 1 || n > kMaxBatchRequests)
+        return fail(ctx, RELO_E_INVALID_ARG, "1 to 256 requests per batch");
+    // The call blocks until the results are back, so the caller's buffers serve
+    // directly as copy sources and destinations; nothing is staged or pinned.
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!reqs[i].ranges || reqs[i].n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad request");
+        total += (size_t)reqs[i].n_beams;
+    }
+    int rc = ensure(ctx, &ctx->ranges_dev, &ctx->ranges_cap, total, "scan upload");
     if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->ranges_dev, ranges, sizeof(float) * n_beams, cudaMemcpyHostToDevice, ctx->stream),
-       "scan upload");
-    rc = relo_relocalize_dev(ctx, map_id, ctx->ranges_dev, angles, n_beams, max_range, ctx->result_dev);
+    std::vector<relo_request> dreq(reqs, reqs + n);
+    size_t pos = 0;
+    for (int i = 0; i < n; ++i) {
+        CK(cudaMemcpyAsync(ctx->ranges_dev + pos, reqs[i].ranges, sizeof(float) * reqs[i].n_beams,
+                           cudaMemcpyHostToDevice, ctx->stream),
+           "scan upload");
+        dreq[i].ranges = ctx->ranges_dev + pos;
+        pos += (size_t)reqs[i].n_beams;
+    }
+    rc = relo_relocalize_batch_dev(ctx, dreq.data(), n, ctx->results_dev);
     if (rc) {
         cudaStreamSynchronize(ctx->stream);
         return rc;
     }
-    CK(cudaMemcpyAsync(out, ctx->result_dev, sizeof(relo_result), cudaMemcpyDeviceToHost, ctx->stream),
+    CK(cudaMemcpyAsync(out, ctx->results_dev, sizeof(relo_result) * n, cudaMemcpyDeviceToHost, ctx->stream),
        "result download");
     CK(cudaStreamSynchronize(ctx->stream), "relocalize");
-    if (out->status != RELO_OK) return fail(ctx, out->status, "the scan has no valid beam");
+    for (int i = 0; i < n; ++i)
+        if (out[i].status != RELO_OK) return fail(ctx, out[i].status, "a scan has no valid beam");
     return RELO_OK;
 }
 
 int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes) {
     if (!ctx || !dst_dev) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
-    if (ctx->last_map < 0) return fail(ctx, RELO_E_NOT_FOUND, "no relocalization has run");
+    if (!ctx->has_last) return fail(ctx, RELO_E_NOT_FOUND, "no relocalization has run");
+    const ReqDesc &d = ctx->last;
     const void *src = nullptr;
     size_t need = 0;
-    long long info_host[10];
     switch (which) {
-        case RELO_STAGE_SMAD_NUM: src = ctx->smad_num; need = 8ull * ctx->last_n_hyp; break;
-        case RELO_STAGE_SMAD_M: src = ctx->smad_m; need = 4ull * ctx->last_n_hyp; break;
-        case RELO_STAGE_SURVIVORS: src = ctx->survivors; need = 4ull * ctx->last_K; break;
-        case RELO_STAGE_TAM: src = ctx->T; need = 4ull * ctx->last_K * ctx->last_n_orient; break;
-        case RELO_STAGE_BEST_M: src = ctx->best_m; need = 4ull * ctx->last_K; break;
-        case RELO_STAGE_LOCAL_TOPK: src = ctx->local; need = 4ull * ctx->last_batches * ctx->last_local; break;
+        case RELO_STAGE_SMAD_NUM: src = d.smad_num; need = 8ull * d.n_hyp; break;
+        case RELO_STAGE_SMAD_M: src = d.smad_m; need = 4ull * d.n_hyp; break;
+        case RELO_STAGE_SURVIVORS: src = d.survivors; need = 4ull * d.K; break;
+        case RELO_STAGE_TAM: src = d.T; need = 4ull * d.K * d.n_orient; break;
+        case RELO_STAGE_BEST_M: src = d.best_m; need = 4ull * d.K; break;
+        case RELO_STAGE_LOCAL_TOPK: src = d.local; need = 4ull * d.n_batches * d.L; break;
         case RELO_STAGE_SCAN_INFO: {
             ScanInfo si;
             SelectState ss;
-            CK(cudaMemcpyAsync(&si, ctx->scan, sizeof si, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
-            CK(cudaMemcpyAsync(&ss, ctx->state, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            BatchState bs;
+            CK(cudaMemcpyAsync(&si, d.scan, sizeof si, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            CK(cudaMemcpyAsync(&ss, d.state, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            CK(cudaMemcpyAsync(&bs, ctx->bs, sizeof bs, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
             CK(cudaStreamSynchronize(ctx->stream), "stage read");
-            long long v[10] = {ctx->last_ns, ctx->last_n_orient, ctx->last_enum, si.n_valid, si.k_ret, si.sum_real,
-                               ctx->last_K, ss.n_batches, (long long)si.dda_steps, ctx->last_n_hyp};
-            memcpy(info_host, v, sizeof v);
-            src = info_host;
-            need = sizeof info_host;
+            long long v[RELO_SCAN_INFO_LEN] = {d.ns, d.n_orient, d.n_enum, si.n_valid, si.k_ret, si.sum_real,
+                                               d.K, ss.n_batches, (long long)bs.dda_steps, d.n_hyp};
+            need = sizeof v;
             if ((size_t)bytes < need) return fail(ctx, RELO_E_INVALID_ARG, "destination too small");
-            CK(cudaMemcpy(dst_dev, src, need, cudaMemcpyHostToDevice), "stage copy");
+            CK(cudaMemcpy(dst_dev, v, need, cudaMemcpyHostToDevice), "stage copy");
             return RELO_OK;
         }
         default: return fail(ctx, RELO_E_INVALID_ARG, "unknown stage");
@@ -798,11 +938,11 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     if (!ctx || !cells_dev || !angles || !ranges_dev || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
-    int rc = plan_for(ctx, angles, n_beams);
+    SensorPlan *P = nullptr;
+    int rc = plan_for(ctx, angles, n_beams, &P);
     if (rc) return rc;
-    const SensorPlan &P = ctx->plan;
-    if (ns_out) *ns_out = P.ns;
-    if ((long long)n * P.ns > capacity) return fail(ctx, RELO_E_INVALID_ARG, "output buffers hold fewer than n x N_s");
+    if (ns_out) *ns_out = P->ns;
+    if ((long long)n * P->ns > capacity) return fail(ctx, RELO_E_INVALID_ARG, "output buffers hold fewer than n x N_s");
     const double rq = (double)max_range * 65536.0 / m->res;
     if (!(max_range > 0) || !(rq < 2147483647.0)) return fail(ctx, RELO_E_INVALID_ARG, "bad max_range");
     const long long rmax_q16 = llrint(rq);
@@ -812,9 +952,9 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     ra.W = m->dev.W;
     ra.H = m->dev.H;
     ra.TW = m->dev.TW;
-    ra.D = P.D_dev;
-    ra.ns = P.ns;
-    ra.ns_pad = (P.ns + 31) & ~31;
+    ra.D = P->D_dev;
+    ra.ns = P->ns;
+    ra.ns_pad = (P->ns + 31) & ~31;
     ra.lim = (int)((rmax_q16 * rmax_q16) >> 32);
     ra.hyps = reinterpret_cast<const int2 *>(cells_dev);
     ra.n_hyp = n;

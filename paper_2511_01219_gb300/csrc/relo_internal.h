@@ -54,6 +54,7 @@ struct SelectState {
     int done;                  // early termination reached
 };
 
+// single-request arguments of the synthesized-scan export (relo_synth_scans_dev)
 struct RayArgs {
     const uint64_t *bits;
     int W, H, TW;
@@ -73,50 +74,89 @@ struct RayArgs {
     int32_t *smad_m;            // [n_hyp]
 };
 
-struct TamArgs {
+// Everything one relocalization request needs on the device: its map's
+// tables, its hypotheses, its sensor plan, its scan and its output buffers.
+// A batch is an array of these; every stage kernel serves all requests of a
+// batch from one launch.
+struct ReqDesc {
+    // map tables
+    const uint64_t *bits;
     const uint16_t *field;
+    const float2 *lut;           // [C+1] (l(b), sqrt(C) - sqrt(b))
     int W, H, TW, C;
-    const int2 *D;
-    int ns;
-    const int2 *vbR;            // [n_valid] (b_i, R_i) of the valid beams
-    const ScanInfo *scan;
-    const int32_t *survivors;   // SMAD order
-    int s_begin, s_end;
-    const int2 *hyps;
-    int n_orient, n_enum;
-    const float2 *lut;          // [C+1] (l(b), sqrt(C) - sqrt(b))
     float res, res2, d_max, d_min;
-    float *T;                   // [K * n_orient]
-    unsigned long long *best_key;   // [K] (T bits << 32) | (0xffffffff - q)
-    const SelectState *state;
-    int chunk, n_chunks;        // survivors per task and tasks per orientation (set by the launcher)
+    double resd, ox, oy;
+    // hypotheses
+    const int2 *hyps;
+    int n_hyp;
+    // sensor plan
+    const int2 *D;               // [ns] Q30 directions
+    const int32_t *b;            // [n_beams] panoramic index per beam
+    const int2 *iv;              // [n_iv] (u, len) FoV intervals
+    int ns, ns_pad, n_iv, n_beams, n_orient, n_enum, n_m;
+    int lim;                     // floor(rmax_q16^2 / 2^32)
+    double a_mid, a_low, fov;
+    // scan input
+    const float *ranges;
+    int skip;
+    float max_range;
+    // selection
+    int K, B, n_batches, L, early_stop;
+    double tau;
+    long long n_smad_evals;
+    // buffers
+    int2 *vbR;                   // [n_beams]
+    ScanInfo *scan;
+    unsigned long long *keys;    // [n_hyp]
+    long long *smad_num;         // [n_hyp]
+    int32_t *smad_m;             // [n_hyp]
+    int32_t *survivors;          // [K]
+    float *T;                    // [K * n_orient]
+    unsigned long long *best_key;   // [K]
+    int32_t *best_m;             // [K]
+    int32_t *local;              // [n_batches * L]
+    SelectState *state;
+    void *result;                // relo_result in device memory
+    // work lists
+    int hyp_base;                // first slot of this request in the batch's hypothesis list
 };
+
+// Counters shared by the whole batch.
+struct BatchState {
+    unsigned int ray_work;          // next global hypothesis slot for the ray-cast CTAs
+    unsigned int pad;
+    unsigned long long dda_steps;   // cells entered by all rays of the batch
+};
+
+// TAM work of one request in one batch launch: survivors [s_begin, s_end),
+// split into n_chunks chunks of `chunk`, for each of its orientations; the
+// request's tasks are [task_base, task_base + n_orient * n_chunks).
+struct TamSeg {
+    int task_base, s_begin, s_end, chunk, n_chunks;
+};
+
+constexpr int kMaxBatchRequests = 256;
+constexpr int kMaxBatches = 64;      // ceil(K / batch) limit, bounds the TamSeg table
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s);
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);
-cudaError_t launch_raycast_smad(const RayArgs &a, int n_sm, cudaStream_t s);
 cudaError_t launch_synth(const RayArgs &a, uint32_t *ranges, int32_t *hit, cudaStream_t s);
-cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int32_t *out, cudaStream_t s);
-cudaError_t launch_scan_prep(const float *ranges, int n, int skip, float max_range, double res, const int32_t *b,
-                             double a_mid, double a_low, int2 *vbR, ScanInfo *info, cudaStream_t s);
-cudaError_t launch_tam(const TamArgs &a, int n_beams_max, int n_sm, cudaStream_t s);
-cudaError_t launch_select_batch(const unsigned long long *best_key, int s_begin, int s_end, int n_orient,
-                                int n_enum, int local_topk, int batch_idx, double tau, int early_stop,
-                                int32_t *best_m, int32_t *local_out, SelectState *st, cudaStream_t s);
 
-struct FinalizeArgs {
-    const SelectState *st;
-    const int32_t *survivors;
-    const int32_t *best_m;
-    const int2 *hyps;
-    const long long *smad_num;
-    const ScanInfo *scan;
-    double res, ox, oy, fov_beams;
-    int ns;
-    long long n_smad_evals;
-    void *result;   // relo_result*
+// batched stages; R requests, descriptors in device memory
+cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s);
+cudaError_t launch_raycast_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
+                                cudaStream_t s);
+cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s);
+// plans the TAM launch of one batch index: fills segs[R] and returns the task count and grid size
+struct TamPlan {
+    int total_tasks, grid, vpl;
+    size_t smem;
 };
-cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
+TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
+                 int max_beams, int max_C, int n_sm, TamSeg *segs);
+cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, cudaStream_t s);
+cudaError_t launch_finalize(const ReqDesc *reqs, int R, cudaStream_t s);
 
 }  // namespace relo

@@ -47,14 +47,20 @@ __device__ void bitonic_sort(unsigned long long *v, int n_pow2) {
     }
 }
 
-__global__ void __launch_bounds__(kTopkThreads) k_topk(const unsigned long long *__restrict__ keys_g, int n, int K,
-                                                       int Kp, int staged, int32_t *__restrict__ out) {
+// one CTA per request
+__global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap) {
     extern __shared__ __align__(16) unsigned long long sm[];
-    unsigned long long *sortbuf = sm;                                   // [Kp]
-    unsigned int *hist = reinterpret_cast<unsigned int *>(sm + Kp);     // [256]
-    unsigned long long *keys_s = sm + Kp + 128;                         // [n] when staged
+    const ReqDesc &d = reqs[blockIdx.x];
+    const unsigned long long *keys_g = d.keys;
+    const int n = d.n_hyp, K = d.K;
+    int Kp = 1;
+    while (Kp < K) Kp <<= 1;
+    unsigned long long *sortbuf = sm;                                        // [Kp_cap]
+    unsigned int *hist = reinterpret_cast<unsigned int *>(sm + Kp_cap);      // [256]
+    unsigned long long *keys_s = sm + Kp_cap + 128;                          // [stage_cap]
     __shared__ unsigned long long s_or;
     __shared__ int s_digit, s_below, s_cnt;
+    const bool staged = n <= stage_cap;
     const unsigned long long *keys = staged ? keys_s : keys_g;
 
     if (threadIdx.x == 0) { s_or = 0; s_cnt = 0; }
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const unsigned long long 
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             unsigned int local = 0;
-            for (int d = 0; d < 8; ++d) local += hist[lane * 8 + d];
+            for (int dg = 0; dg < 8; ++dg) local += hist[lane * 8 + dg];
             unsigned int incl = local;
             for (int o = 1; o < 32; o <<= 1) {
                 unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -92,10 +98,10 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const unsigned long long 
             bool here = excl < (unsigned)remaining && incl >= (unsigned)remaining;
             if (here) {
                 unsigned int cum = excl;
-                for (int d = 0; d < 8; ++d) {
-                    unsigned int c = hist[lane * 8 + d];
+                for (int dg = 0; dg < 8; ++dg) {
+                    unsigned int c = hist[lane * 8 + dg];
                     if (cum + c >= (unsigned)remaining) {
-                        s_digit = lane * 8 + d;
+                        s_digit = lane * 8 + dg;
                         s_below = (int)cum;
                         break;
                     }
@@ -117,29 +123,32 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const unsigned long long 
     for (int i = K + threadIdx.x; i < Kp; i += blockDim.x) sortbuf[i] = ~0ull;
     __syncthreads();
     bitonic_sort(sortbuf, Kp);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) out[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        d.survivors[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
 }
 
-__global__ void __launch_bounds__(1024) k_select_batch(const unsigned long long *__restrict__ best_key, int s_begin,
-                                                       int s_end, int n_orient, int n_enum, int local_topk,
-                                                       int batch_idx, double tau, int early_stop,
-                                                       int32_t *__restrict__ best_m, int32_t *__restrict__ local_out,
-                                                       SelectState *st) {
+// one CTA per request: selection of batch `batch_idx` (skipped when the
+// request has fewer batches or already terminated early)
+__global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_idx) {
     __shared__ unsigned long long v[kMaxBatch];
     __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = st->done;
+    const ReqDesc &d = reqs[blockIdx.x];
+    if (threadIdx.x == 0) s_skip = batch_idx >= d.n_batches || d.state->done || d.scan->n_valid <= 0;
     __syncthreads();
     if (s_skip) return;
+    SelectState *st = d.state;
+    const int s_begin = batch_idx * d.B;
+    const int s_end = min(d.K, s_begin + d.B);
     const int nb = s_end - s_begin;
     int np2 = 1;
     while (np2 < nb) np2 <<= 1;
     for (int i = threadIdx.x; i < np2; i += blockDim.x) {
         if (i < nb) {
             const int s = s_begin + i;
-            const unsigned long long k = best_key[s];
+            const unsigned long long k = d.best_key[s];
             const unsigned tb = (unsigned)(k >> 32);
             const unsigned q = 0xffffffffu - (unsigned)(k & 0xffffffffu);
-            best_m[s] = (int)q * n_enum;
+            d.best_m[s] = (int)q * d.n_enum;
             v[i] = ((unsigned long long)(~tb) << 32) | (unsigned)s;   // ascending = TAM desc, survivor asc
         } else {
             v[i] = ~0ull;
@@ -147,76 +156,78 @@ __global__ void __launch_bounds__(1024) k_select_batch(const unsigned long long 
     }
     __syncthreads();
     bitonic_sort(v, np2);
-    const int L = local_topk < nb ? local_topk : nb;
-    for (int r = threadIdx.x; r < local_topk; r += blockDim.x)
-        local_out[(size_t)batch_idx * local_topk + r] = r < L ? (int)(v[r] & 0xffffffffu) : -1;
+    const int L = d.L;
+    const int Lb = L < nb ? L : nb;
+    for (int r = threadIdx.x; r < L; r += blockDim.x)
+        d.local[(size_t)batch_idx * L + r] = r < Lb ? (int)(v[r] & 0xffffffffu) : -1;
     if (threadIdx.x == 0) {
         const unsigned tb = ~(unsigned)(v[0] >> 32);
         const unsigned s = (unsigned)(v[0] & 0xffffffffu);
         const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
         if (cand > st->best) st->best = cand;
         st->n_batches += 1;
-        st->n_tam_evals += (long long)nb * n_orient;
-        if (early_stop && (double)__uint_as_float(tb) >= tau) st->done = 1;
+        st->n_tam_evals += (long long)nb * d.n_orient;
+        if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
     }
 }
 
-__global__ void k_finalize(FinalizeArgs a) {
+__global__ void k_finalize(const ReqDesc *__restrict__ reqs, int R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    const ReqDesc &d = reqs[i];
     relo_result r;
-    const SelectState st = *a.st;
+    const SelectState st = *d.state;
     const unsigned tb = (unsigned)(st.best >> 32);
     const int s = (int)(0xffffffffu - (unsigned)(st.best & 0xffffffffu));
     r.n_batches = st.n_batches;
     r.n_tam_evals = st.n_tam_evals;
-    r.n_smad_evals = a.n_smad_evals;
-    if (a.scan->n_valid <= 0 || st.n_batches == 0) {
+    r.n_smad_evals = d.n_smad_evals;
+    if (d.scan->n_valid <= 0 || st.n_batches == 0) {
         r.status = RELO_E_NO_VALID_BEAMS;
         r.x = r.y = r.theta = r.tam = r.smad = 0.0;
         r.smad_num = 0;
         r.hyp = -1;
         r.m = -1;
+        r.n_tam_evals = 0;
     } else {
-        const int h = a.survivors[s];
-        const int m = a.best_m[s];
-        const int2 c = a.hyps[h];
+        const int h = d.survivors[s];
+        const int m = d.best_m[s];
+        const int2 c = d.hyps[h];
         r.status = RELO_OK;
         r.hyp = h;
         r.m = m;
         r.tam = (double)__uint_as_float(tb);
-        r.x = a.ox + ((double)c.x + 0.5) * a.res;
-        r.y = a.oy + ((double)c.y + 0.5) * a.res;
-        double th = (double)m * (2.0 * M_PI) / (double)a.ns;
+        r.x = d.ox + ((double)c.x + 0.5) * d.resd;
+        r.y = d.oy + ((double)c.y + 0.5) * d.resd;
+        double th = (double)m * (2.0 * M_PI) / (double)d.ns;
         if (th >= M_PI) th -= 2.0 * M_PI;
         r.theta = th;
-        r.smad_num = a.smad_num[h];
-        r.smad = (double)r.smad_num / a.fov_beams / 65536.0 * a.res;
+        r.smad_num = d.smad_num[h];
+        r.smad = (double)r.smad_num / d.fov / 65536.0 * d.resd;
     }
-    *reinterpret_cast<relo_result *>(a.result) = r;
+    *reinterpret_cast<relo_result *>(d.result) = r;
 }
 
 }  // namespace
 
-cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int32_t *out, cudaStream_t s) {
+cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s) {
     int Kp = 1;
-    while (Kp < K) Kp <<= 1;
-    int staged = n <= kStageMax ? 1 : 0;
-    size_t smem = (size_t)Kp * 8 + 256 * 4 + (staged ? (size_t)n * 8 : 0);
+    while (Kp < max_K) Kp <<= 1;
+    const int stage_cap = max_n_hyp <= kStageMax ? max_n_hyp : 0;
+    size_t smem = (size_t)Kp * 8 + 256 * 4 + (size_t)stage_cap * 8;
     cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_topk<<<1, kTopkThreads, smem, s>>>(keys, n, K, Kp, staged, out);
+    k_topk<<<R, kTopkThreads, smem, s>>>(reqs, Kp, stage_cap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_batch(const unsigned long long *best_key, int s_begin, int s_end, int n_orient, int n_enum,
-                                int local_topk, int batch_idx, double tau, int early_stop, int32_t *best_m,
-                                int32_t *local_out, SelectState *st, cudaStream_t s) {
-    k_select_batch<<<1, 1024, 0, s>>>(best_key, s_begin, s_end, n_orient, n_enum, local_topk, batch_idx, tau,
-                                      early_stop, best_m, local_out, st);
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, cudaStream_t s) {
+    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_idx);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
-    k_finalize<<<1, 1, 0, s>>>(a);
+cudaError_t launch_finalize(const ReqDesc *reqs, int R, cudaStream_t s) {
+    k_finalize<<<(R + 127) / 128, 128, 0, s>>>(reqs, R);
     return cudaGetLastError();
 }
 

@@ -42,15 +42,34 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTamWarps = 8;
 constexpr uint32_t kNoBeam = 0xffffu;
 
-__global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ranges, int n, int skip,
-                                                    float max_range, double res, const int32_t *__restrict__ b,
-                                                    double a_mid, double a_low, int2 *__restrict__ vbR,
-                                                    ScanInfo *info) {
+// One CTA per request: the scan preparation above, plus the reset of the
+// request's selection buffers (argmax keys 0, shifts and local top-k -1, TAM
+// scores NaN, selection state 0), so a batch needs no separate memsets.
+__global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ reqs, BatchState *bs) {
     __shared__ int warp_cnt[32];
     __shared__ long long warp_sum[32];
     __shared__ int s_base;
+    const ReqDesc &d = reqs[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = d.n_beams;
     if (threadIdx.x == 0) s_base = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bs->ray_work = 0u;
+        bs->dda_steps = 0ull;
+    }
+    for (int i = threadIdx.x; i < d.K; i += blockDim.x) {
+        d.best_key[i] = 0ull;
+        d.best_m[i] = -1;
+    }
+    const int nT = d.K * d.n_orient;
+    for (int i = threadIdx.x; i < nT; i += blockDim.x) d.T[i] = __int_as_float(0x7fffffff);
+    for (int i = threadIdx.x; i < d.n_batches * d.L; i += blockDim.x) d.local[i] = -1;
+    if (threadIdx.x == 0) {
+        d.state->best = 0ull;
+        d.state->n_tam_evals = 0;
+        d.state->n_batches = 0;
+        d.state->done = 0;
+    }
     long long my_sum = 0;
     __syncthreads();
     for (int c0 = 0; c0 < n; c0 += blockDim.x) {
@@ -58,9 +77,9 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ra
         int R = 0;
         bool ok = false;
         if (i < n) {
-            const float z = ranges[(size_t)i * skip];
-            ok = isfinite(z) && z > 0.0f && z < max_range;
-            if (ok) R = (int)__double2ll_rn(__ddiv_rn(__dmul_rn((double)z, 65536.0), res));
+            const float z = d.ranges[(size_t)i * d.skip];
+            ok = isfinite(z) && z > 0.0f && z < d.max_range;
+            if (ok) R = (int)__double2ll_rn(__ddiv_rn(__dmul_rn((double)z, 65536.0), d.resd));
         }
         my_sum += R;
         const unsigned bal = __ballot_sync(kFull, ok);
@@ -78,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ra
         __syncthreads();
         if (ok) {
             const int pos = s_base + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
-            vbR[pos] = make_int2(b[i], R);
+            d.vbR[pos] = make_int2(d.b[i], R);
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_base += warp_cnt[warp] + __popc(bal);
@@ -91,63 +110,82 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const float *__restrict__ ra
         long long tot = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_sum[w];
         const int N = s_base;
-        int km = (int)floor(__dmul_rn(a_mid, (double)N));
+        int km = (int)floor(__dmul_rn(d.a_mid, (double)N));
         if (km < 1) km = 1;
-        int kl = (int)floor(__dmul_rn(a_low, (double)N));
+        int kl = (int)floor(__dmul_rn(d.a_low, (double)N));
         if (kl < 1) kl = 1;
         int lo = km < kl ? km : kl, hi = km < kl ? kl : km;
         int k = N < lo ? lo : (N > hi ? hi : N);   // median of {N, km, kl}
-        info->sum_real = tot;
-        info->n_valid = N;
-        info->k_ret = k;
-        info->dda_steps = 0ull;
-        info->ray_work = 0u;
+        d.scan->sum_real = tot;
+        d.scan->n_valid = N;
+        d.scan->k_ret = k;
+        d.scan->dda_steps = 0ull;
     }
 }
 
-// Work is split into tasks (orientation q, chunk of survivors).  A CTA first
-// computes the endpoint offsets of its orientation for every valid beam,
-// round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis, packed as two
-// int16 in shared memory; each warp then scores one survivor at a time with
-// those offsets, so the 64-bit offset arithmetic is paid once per
-// (orientation, beam) instead of once per (survivor, orientation, beam).
+// Work is split into tasks (request, orientation q, chunk of survivors).  A
+// CTA first computes the endpoint offsets of its task's orientation for every
+// valid beam of the request, round-half-up(R_i * D_{(b_i + m) mod N_s} /
+// 2^46) per axis, packed as two int16 in shared memory; each warp then scores
+// one survivor at a time with those offsets, so the 64-bit offset arithmetic
+// is paid once per (orientation, beam) instead of once per (survivor,
+// orientation, beam).  The likelihood table is reloaded only when a CTA moves
+// to another request's task.
 template <int VPL>
-__global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
+__global__ void __launch_bounds__(kTamWarps * 32) k_tam(const ReqDesc *__restrict__ reqs, int R,
+                                                       const TamSeg *__restrict__ segs, int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_stop;
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    __shared__ int s_skip, s_lut_r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_stop = a.state->done;
-    const int N = a.scan->n_valid;
-    const int k = a.scan->k_ret;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
+    if (threadIdx.x == 0) {
+        s_base[R] = total_tasks;
+        s_lut_r = -1;
+    }
     __syncthreads();
-    if (s_stop || N <= 0) return;
-
     float2 *lut = reinterpret_cast<float2 *>(smem);
-    uint32_t *offs = reinterpret_cast<uint32_t *>(smem + (size_t)(a.C + 1) * sizeof(float2));
-    for (int i = threadIdx.x; i <= a.C; i += blockDim.x) lut[i] = a.lut[i];
-
-    const int nb = a.s_end - a.s_begin;
-    const int n_tasks = a.n_orient * a.n_chunks;
-    const float Nf = (float)N;
-    for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-        const int q = task % a.n_orient;
-        const int chunk = task / a.n_orient;
-        const int m = q * a.n_enum;
-        __syncthreads();   // the previous task's reads of offs are done
+    for (int task = blockIdx.x; task < total_tasks; task += gridDim.x) {
+        int lo = 0, hi = R - 1;   // last request whose task_base <= task
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_base[mid] <= task) lo = mid;
+            else hi = mid - 1;
+        }
+        const int r = lo;
+        const ReqDesc &d = reqs[r];
+        const TamSeg sg = segs[r];
+        const int N = d.scan->n_valid;
+        const int k = d.scan->k_ret;
+        __syncthreads();   // the previous task's reads of offs / lut are done
+        if (threadIdx.x == 0) s_skip = d.state->done || N <= 0;
+        if (s_lut_r != r) {
+            for (int i = threadIdx.x; i <= d.C; i += blockDim.x) lut[i] = d.lut[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_lut_r = r;
+        if (s_skip) continue;
+        uint32_t *offs = reinterpret_cast<uint32_t *>(smem + (size_t)(d.C + 1) * sizeof(float2));
+        const int local = task - sg.task_base;
+        const int q = local % d.n_orient;
+        const int chunk = local / d.n_orient;
+        const int m = q * d.n_enum;
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const int2 bR = a.vbR[i];
+            const int2 bR = d.vbR[i];
             int j = bR.x + m;
-            if (j >= a.ns) j -= a.ns;
-            const int2 d = a.D[j];
-            const int ox = (int)(((long long)bR.y * d.x + (1ll << 45)) >> 46);
-            const int oy = (int)(((long long)bR.y * d.y + (1ll << 45)) >> 46);
+            if (j >= d.ns) j -= d.ns;
+            const int2 dir = d.D[j];
+            const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
+            const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
             offs[i] = ((uint32_t)ox & 0xffffu) | ((uint32_t)oy << 16);
         }
         __syncthreads();
-        const int s_lo = a.s_begin + chunk * a.chunk;
-        const int s_hi = min(a.s_end, s_lo + a.chunk);
+        const int s_lo = sg.s_begin + chunk * sg.chunk;
+        const int s_hi = min(sg.s_end, s_lo + sg.chunk);
+        const float Nf = (float)N;
+        const int W = d.W, H = d.H, TW = d.TW, C = d.C;
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
-            const int2 hc = a.hyps[a.survivors[s]];
+            const int2 hc = d.hyps[d.survivors[s]];
             uint32_t v[VPL];
             int sumb = 0;
 #pragma unroll
@@ -158,32 +196,32 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
                     const uint32_t o = offs[i];
                     const int ex = hc.x + (int)(short)(o & 0xffffu);
                     const int ey = hc.y + ((int)o >> 16);
-                    bv = ((unsigned)ex < (unsigned)a.W && (unsigned)ey < (unsigned)a.H)
-                             ? (uint32_t)__ldg(a.field + tile_index(ex, ey, a.TW))
-                             : (uint32_t)a.C;
+                    bv = ((unsigned)ex < (unsigned)W && (unsigned)ey < (unsigned)H)
+                             ? (uint32_t)__ldg(d.field + tile_index(ex, ey, TW))
+                             : (uint32_t)C;
                     sumb += (int)bv;
                 }
                 v[t] = bv;
             }
             // smallest b_k with #{b <= b_k} >= k
-            int lo = 0, hi = a.C;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
+            int blo = 0, bhi = C;
+            while (blo < bhi) {
+                const int mid = (blo + bhi) >> 1;
                 int c = 0;
 #pragma unroll
                 for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
                 c = __reduce_add_sync(kFull, c);
-                if (c >= k) hi = mid;
-                else lo = mid + 1;
+                if (c >= k) bhi = mid;
+                else blo = mid + 1;
             }
-            const uint32_t bk = (uint32_t)lo;
-            float sg = 0.0f, sl = 0.0f;
+            const uint32_t bk = (uint32_t)blo;
+            float sgs = 0.0f, sl = 0.0f;
             int clt = 0;
 #pragma unroll
             for (int t = 0; t < VPL; ++t) {
                 if (v[t] != kNoBeam) {
                     const float2 lg = lut[v[t]];
-                    sg += lg.y;
+                    sgs += lg.y;
                     if (v[t] < bk) {
                         sl += lg.x;
                         ++clt;
@@ -192,7 +230,7 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                sg += __shfl_xor_sync(kFull, sg, o);
+                sgs += __shfl_xor_sync(kFull, sgs, o);
                 sl += __shfl_xor_sync(kFull, sl, o);
             }
             clt = __reduce_add_sync(kFull, clt);
@@ -201,77 +239,127 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(TamArgs a) {
                 const float ltop = sl + (float)(k - clt) * lut[bk].x;
                 const float lbar = ltop / (float)k;
                 const float wp = expf(lbar);
-                const float dd = a.res * sg / Nf;   // d_max - dbar
-                const float dbar = a.d_max - dd;
-                const float span = a.d_max - a.d_min;
+                const float dd = d.res * sgs / Nf;   // d_max - dbar
+                const float dbar = d.d_max - dd;
+                const float span = d.d_max - d.d_min;
                 const float sd = fminf(dd, span) / span;
-                float var = a.res2 * ((float)sumb / Nf) - dbar * dbar;
+                float var = d.res2 * ((float)sumb / Nf) - dbar * dbar;
                 var = fmaxf(var, 0.0f);
-                const float c = expf(-0.5f * var);
-                const float T = cbrtf(wp * sd * c);
-                a.T[(size_t)s * a.n_orient + q] = T;
+                const float cc = expf(-0.5f * var);
+                const float T = cbrtf(wp * sd * cc);
+                d.T[(size_t)s * d.n_orient + q] = T;
                 const unsigned long long key =
                     ((unsigned long long)__float_as_uint(T) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
-                atomicMax(a.best_key + s, key);
+                atomicMax(d.best_key + s, key);
             }
         }
     }
-    (void)nb;
 }
 
 template <int VPL>
-cudaError_t run_tam(TamArgs a, int n_sm, cudaStream_t s, size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t run_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tam<VPL>, kTamWarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    // Pick the number of survivor chunks per orientation so that the tasks
-    // fill whole waves of resident CTAs and whole rounds of the CTA's warps.
-    const int nb = a.s_end - a.s_begin;
-    const int slots = n_sm * occ;
-    const int max_chunks = (nb + kTamWarps - 1) / kTamWarps;
-    int best_nc = 1;
-    double best_eff = -1.0;
-    for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
-        const int chunk = (nb + nc - 1) / nc;
-        const long long tasks = (long long)a.n_orient * ((nb + chunk - 1) / chunk);
-        const long long waves = (tasks + slots - 1) / slots;
-        const double eff = (double)tasks / (double)(waves * slots) *
-                           (double)chunk / (double)(((chunk + kTamWarps - 1) / kTamWarps) * kTamWarps);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best_nc = nc;
-        }
-    }
-    a.chunk = (nb + best_nc - 1) / best_nc;
-    a.n_chunks = (nb + a.chunk - 1) / a.chunk;
-    long long tasks = (long long)a.n_orient * a.n_chunks;
-    int grid = (int)(tasks < slots ? tasks : slots);
-    if (grid < 1) grid = 1;
-    k_tam<VPL><<<grid, kTamWarps * 32, smem, s>>>(a);
+    k_tam<VPL><<<tp.grid, kTamWarps * 32, tp.smem, s>>>(reqs, R, segs, tp.total_tasks);
     return cudaGetLastError();
+}
+
+template <int VPL>
+int tam_occupancy(size_t smem) {
+    int occ = 0;
+    if (cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tam<VPL>, kTamWarps * 32, smem) != cudaSuccess) return 0;
+    return occ;
+}
+
+#define RELO_TAM_VPLS(X) X(8) X(12) X(16) X(20) X(24) X(28) X(32) X(36) X(40) X(44) X(48) X(52) X(56) X(60) X(64)
+
+int vpl_bucket(int max_beams) {
+    const int need = (max_beams + 31) / 32;
+#define RELO_TAM_PICK(V) \
+    if (need <= V) return V;
+    RELO_TAM_VPLS(RELO_TAM_PICK)
+#undef RELO_TAM_PICK
+    return -1;
+}
+
+int occupancy_for(int vpl, size_t smem) {
+#define RELO_TAM_OCC(V) \
+    if (vpl == V) return tam_occupancy<V>(smem);
+    RELO_TAM_VPLS(RELO_TAM_OCC)
+#undef RELO_TAM_OCC
+    return 0;
 }
 
 }  // namespace
 
-cudaError_t launch_scan_prep(const float *ranges, int n, int skip, float max_range, double res, const int32_t *b,
-                             double a_mid, double a_low, int2 *vbR, ScanInfo *info, cudaStream_t s) {
-    k_scan_prep<<<1, 1024, 0, s>>>(ranges, n, skip, max_range, res, b, a_mid, a_low, vbR, info);
+cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s) {
+    k_scan_prep<<<R, 1024, 0, s>>>(reqs, bs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tam(const TamArgs &a, int n_beams_max, int n_sm, cudaStream_t s) {
-    if (a.s_end <= a.s_begin) return cudaSuccess;
-    size_t smem = (size_t)(a.C + 1) * sizeof(float2) + (size_t)n_beams_max * sizeof(uint32_t);
-    const int vpl = (n_beams_max + 31) / 32;
-#define RELO_TAM_CASE(V) \
-    if (vpl <= V) return run_tam<V>(a, n_sm, s, smem);
-    RELO_TAM_CASE(8) RELO_TAM_CASE(12) RELO_TAM_CASE(16) RELO_TAM_CASE(20) RELO_TAM_CASE(24) RELO_TAM_CASE(28)
-    RELO_TAM_CASE(32) RELO_TAM_CASE(36) RELO_TAM_CASE(40) RELO_TAM_CASE(44) RELO_TAM_CASE(48) RELO_TAM_CASE(52)
-    RELO_TAM_CASE(56) RELO_TAM_CASE(60) RELO_TAM_CASE(64)
-#undef RELO_TAM_CASE
+// Chooses, per request, the number of survivor chunks per orientation so that
+// the whole launch's tasks fill whole waves of resident CTAs and whole rounds
+// of a CTA's warps, and lays the requests' tasks out one after another.
+TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
+                 int max_C, int n_sm, TamSeg *segs) {
+    TamPlan tp{0, 0, vpl_bucket(max_beams), 0};
+    tp.smem = (size_t)(max_C + 1) * sizeof(float2) + (size_t)max_beams * sizeof(uint32_t);
+    if (tp.vpl < 0) return tp;
+    const int occ = occupancy_for(tp.vpl, tp.smem);
+    if (occ < 1) {
+        tp.vpl = -1;
+        return tp;
+    }
+    const int slots = n_sm * occ;
+    long long orient_total = 0;
+    for (int r = 0; r < R; ++r)
+        if (nb_per_req[r] > 0) orient_total += n_orient_per_req[r];
+    int task = 0;
+    for (int r = 0; r < R; ++r) {
+        const int nb = nb_per_req[r];
+        TamSeg &g = segs[r];
+        g.task_base = task;
+        g.s_begin = s_begin_per_req[r];
+        g.s_end = g.s_begin + (nb > 0 ? nb : 0);
+        if (nb <= 0) {
+            g.chunk = 1;
+            g.n_chunks = 0;
+            continue;
+        }
+        // this request's share of the slots, in proportion to its orientations
+        const double share = (double)slots * n_orient_per_req[r] / (double)(orient_total > 0 ? orient_total : 1);
+        const int max_chunks = (nb + kTamWarps - 1) / kTamWarps;
+        int best_nc = 1;
+        double best_eff = -1.0;
+        for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
+            const int chunk = (nb + nc - 1) / nc;
+            const double tasks = (double)n_orient_per_req[r] * ((nb + chunk - 1) / chunk);
+            const double waves = ceil(tasks / (share > 1.0 ? share : 1.0));
+            const double eff = tasks / (waves * (share > 1.0 ? share : 1.0)) * (double)chunk /
+                               (double)(((chunk + kTamWarps - 1) / kTamWarps) * kTamWarps);
+            if (eff > best_eff + 1e-9) {
+                best_eff = eff;
+                best_nc = nc;
+            }
+        }
+        g.chunk = (nb + best_nc - 1) / best_nc;
+        g.n_chunks = (nb + g.chunk - 1) / g.chunk;
+        task += n_orient_per_req[r] * g.n_chunks;
+    }
+    tp.total_tasks = task;
+    tp.grid = task < slots ? task : slots;
+    if (tp.grid < 1) tp.grid = 1;
+    return tp;
+}
+
+cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {
+    if (tp.total_tasks <= 0) return cudaSuccess;
+#define RELO_TAM_RUN(V) \
+    if (tp.vpl == V) return run_tam<V>(reqs, R, segs, tp, s);
+    RELO_TAM_VPLS(RELO_TAM_RUN)
+#undef RELO_TAM_RUN
     return cudaErrorInvalidValue;
 }
 

@@ -380,3 +380,81 @@ def test_profiling_then_blocking_call_then_close(relo, workload):
     out = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
     assert out.status == 0
     ctx.close()
+
+
+def mixed_batch_items(workload):
+    """Requests on different maps with different sensors, FoVs and hypothesis counts."""
+    items = []
+    wl0 = workload(0)
+    items.append((wl0.grid, wl0.res, wl0.hyps, wl0.ranges, wl0.angles, wl0.max_range, wl0.n_orient))
+    g = workloads.make_office(77, n=256)
+    hyps = np.argwhere(g == 0)[:, ::-1]
+    hyps = hyps[np.random.default_rng(4).choice(len(hyps), 700, replace=False)].astype(np.int32)
+    for n_beams, ns, seed in ((541, 720, 1), (720, 1080, 2), (361, 360, 3)):
+        ang = workloads.beam_angles(n_beams, ns)
+        h = hyps[seed * 5]
+        z = workloads.render_scan(g, 0.05, ((h[0] + 0.5) * 0.05, (h[1] + 0.5) * 0.05, 0.7 * seed), ang, 12.0)
+        z = workloads.add_noise(z, 12.0, seed)
+        items.append((g, 0.05, hyps[: 300 * seed], z, ang, 12.0, 72 if ns != 360 else 72))
+    wl = small_case(n_beams=100, ns=120)
+    keep = np.r_[0:30, 45:100]
+    items.append((wl.grid, wl.res, wl.hyps, wl.ranges[keep], wl.angles[keep], wl.max_range, 40))
+    return items
+
+
+def test_batch_equals_single_requests(relo, workload):
+    items = mixed_batch_items(workload)
+    # the orientation count is a context parameter: one context per count
+    groups = {}
+    for it in items:
+        groups.setdefault(it[6], []).append(it)
+    for n_orient, group in groups.items():
+        ctx = relo.Relo(n_orient=n_orient, topk=32, batch=12, local_topk=4, early_stop=1, tau=0.9)
+        reqs = []
+        for (g, res, hyps, z, ang, mr, _) in group:
+            mid = ctx.load_map(g, res)
+            ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
+            reqs.append((mid, z, ang, mr))
+        batch = ctx.relocalize_batch(reqs)
+        for (mid, z, ang, mr), got in zip(reqs, batch):
+            one = ctx.relocalize(mid, z, ang, mr)
+            assert got.as_dict() == one.as_dict()
+        ctx.close()
+
+
+def test_batch_dev_equals_host_and_oracle(relo, workload):
+    torch = torch_()
+    wl = workload(1)
+    g2 = workloads.make_office(91, n=512)
+    free = np.argwhere(g2 == 0)[:, ::-1]
+    h2 = free[np.random.default_rng(8).choice(len(free), 1500, replace=False)].astype(np.int32)
+    ang2 = workloads.beam_angles(1081, 1440)
+    z2 = workloads.add_noise(workloads.render_scan(g2, 0.05, ((h2[9, 0] + 0.5) * 0.05, (h2[9, 1] + 0.5) * 0.05, 1.0),
+                                                   ang2, 25.0), 25.0, 5)
+    ctx = relo.Relo(n_orient=360, topk=64, early_stop=0)
+    m1 = ctx.load_map(wl.grid, wl.res)
+    ctx.set_hypotheses(m1, workloads.cell_centres(wl.hyps, wl.res))
+    m2 = ctx.load_map(g2, 0.05)
+    ctx.set_hypotheses(m2, workloads.cell_centres(h2, 0.05))
+    items = [(m1, wl.ranges, wl.angles, wl.max_range), (m2, z2, ang2, 25.0), (m1, z2, ang2, 25.0)]
+    host = ctx.relocalize_batch(items)
+    res_t = torch.empty(len(items) * relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    dev_items = [(m, torch.tensor(z, device="cuda"), a, mr) for (m, z, a, mr) in items]
+    ctx.relocalize_batch_dev(dev_items, res_t)
+    torch.cuda.synchronize()
+    raw = bytes(res_t.cpu().numpy())
+    for i, h in enumerate(host):
+        d = relo.result_from_bytes(raw[i * relo.RESULT_BYTES:(i + 1) * relo.RESULT_BYTES])
+        assert d.as_dict() == h.as_dict()
+    # the second request against the oracle
+    prm = oracle.Params(n_orient=360, topk=64)
+    want = oracle.relocalize(g2, 0.05, h2, z2, ang2, 25.0, prm, early_stop=False)
+    pl = oracle.plan(z2, ang2, 25.0, 0.05, prm)
+    d2 = oracle.edt(g2)
+
+    def T_at(h, m):
+        return float(oracle.tam(g2, np.array([h2[h]]), np.array([m]), pl, prm, 0.05, d2)[0])
+    check_pose(host[1], want["hyp"], want["m"], T_at)
+    assert abs(host[1].tam - T_at(host[1].hyp, host[1].m)) <= RTOL * T_at(host[1].hyp, host[1].m)
+    assert host[1].smad_num == want["smad_nums"][host[1].hyp]
+    ctx.close()
