@@ -216,6 +216,9 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__r
         long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(ns_pad));
         if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
         const int2 hc = d.hyps[h];
+        const uint64_t *bits = d.bits;
+        const int2 *D = d.D;
+        const int W = d.W, H = d.H, TW = d.TW, lim = d.lim;
         for (;;) {
             int c = 0;
             if (lane == 0) c = atomicAdd(&s_next, 1);
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__r
             const int j = (c << 5) + lane;
             uint32_t r = 0u;
             int hit, steps = 0;
-            if (j < ns) r = cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, d.D[j], &hit, &steps);
+            if (j < ns) r = cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
             my_steps += (unsigned)steps;
             inner[j] = r;
         }

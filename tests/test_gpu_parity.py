@@ -390,7 +390,7 @@ def mixed_batch_items(workload):
     g = workloads.make_office(77, n=256)
     hyps = np.argwhere(g == 0)[:, ::-1]
     hyps = hyps[np.random.default_rng(4).choice(len(hyps), 700, replace=False)].astype(np.int32)
-    for n_beams, ns, seed in ((541, 720, 1), (720, 1080, 2), (361, 360, 3)):
+    for n_beams, ns, seed in ((541, 720, 1), (720, 1080, 2), (360, 360, 3)):
         ang = workloads.beam_angles(n_beams, ns)
         h = hyps[seed * 5]
         z = workloads.render_scan(g, 0.05, ((h[0] + 0.5) * 0.05, (h[1] + 0.5) * 0.05, 0.7 * seed), ang, 12.0)
