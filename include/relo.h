@@ -140,6 +140,26 @@ int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const fl
 int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles,
                         int32_t n_beams, float max_range, relo_result *result_dev);
 
+/* Served form (continuous batching).  relo_serve_start starts a worker thread
+ * that takes submitted requests in arrival order and runs them as batches
+ * (relo_relocalize_batch semantics): up to max_batch requests per batch and
+ * up to max_inflight batches on the device at once, each on its own stream,
+ * so requests arriving while others run are admitted as soon as a batch slot
+ * and memory free up and their work overlaps on the device.  A request is
+ * admitted only while the scratch of all requests in flight stays within
+ * hbm_budget bytes (0 = no limit); one that cannot fit even alone completes
+ * with RELO_E_OVER_BUDGET.  While serving, the calling thread may only use
+ * relo_submit, relo_poll and relo_serve_stop on this context.
+ * relo_submit copies the scan and returns a ticket; relo_poll returns
+ * RELO_PENDING until the request is done, then its status with the result and
+ * (optional) the latency from submit to completion in seconds, and forgets
+ * the ticket.  relo_serve_stop finishes the queued requests and stops. */
+int relo_serve_start(relo_ctx *ctx, int32_t max_batch, int32_t max_inflight, int64_t hbm_budget);
+int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                float max_range, int64_t *ticket);
+int relo_poll(relo_ctx *ctx, int64_t ticket, relo_result *out, double *latency_s);
+int relo_serve_stop(relo_ctx *ctx);
+
 /* A batch of independent relocalizations (configs with many requests, and
  * the served form): each request names a loaded map (with its hypotheses), a
  * scan and its sensor geometry; maps, beam counts, hypothesis counts and FoVs
@@ -152,6 +172,7 @@ typedef struct relo_request {
     const float *angles;   /* n_beams float32 radians, host memory */
     int32_t n_beams;
     float max_range;
+    int32_t topk;          /* SMAD survivors scored by TAM for this request; 0 = the context's topk */
 } relo_request;
 /* Blocking; out[i] receives request i's result.  Returns the first error. */
 int relo_relocalize_batch(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *out);

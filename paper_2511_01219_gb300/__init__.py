@@ -39,7 +39,8 @@ EXPORTED = [
     "relo_load_map_dev", "relo_update_map", "relo_update_map_dev", "relo_unload_map", "relo_map_tables_dev", "relo_set_hypotheses",
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
-    "relo_relocalize_batch", "relo_relocalize_batch_dev",
+    "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
+    "relo_serve_stop",
 ]
 STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
 
@@ -72,7 +73,7 @@ RESULT_BYTES = ctypes.sizeof(Result)
 
 class Request(ctypes.Structure):
     _fields_ = [("map_id", ctypes.c_int32), ("ranges", ctypes.c_void_p), ("angles", ctypes.c_void_p),
-                ("n_beams", ctypes.c_int32), ("max_range", ctypes.c_float)]
+                ("n_beams", ctypes.c_int32), ("max_range", ctypes.c_float), ("topk", ctypes.c_int32)]
 
 
 class ReloError(RuntimeError):
@@ -115,6 +116,10 @@ def lib() -> ctypes.CDLL:
             "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
             "relo_relocalize_batch": (ctypes.c_int, [P, P, I32, P]),
             "relo_relocalize_batch_dev": (ctypes.c_int, [P, P, I32, P]),
+            "relo_serve_start": (ctypes.c_int, [P, I32, I32, I64]),
+            "relo_submit": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
+            "relo_poll": (ctypes.c_int, [P, I64, P, P]),
+            "relo_serve_stop": (ctypes.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -294,29 +299,57 @@ class Relo:
         return k.value
 
     def relocalize_batch(self, items) -> list:
-        """items: [(map_id, ranges ndarray, angles ndarray, max_range)]; blocking; list of Result."""
+        """items: [(map_id, ranges ndarray, angles ndarray, max_range[, topk])]; blocking; list of Result."""
         keep = []
         arr = (Request * len(items))()
-        for i, (mid, z, a, mr) in enumerate(items):
+        for i, it in enumerate(items):
+            mid, z, a, mr = it[:4]
             z = np.ascontiguousarray(z, dtype=np.float32)
             a = np.ascontiguousarray(a, dtype=np.float32)
             keep += [z, a]
-            arr[i] = Request(mid, z.ctypes.data, a.ctypes.data, len(z), mr)
+            arr[i] = Request(mid, z.ctypes.data, a.ctypes.data, len(z), mr, it[4] if len(it) > 4 else 0)
         out = (Result * len(items))()
         self._check(self._L.relo_relocalize_batch(self._h, arr, len(items), out), "relocalize_batch")
         return list(out)
 
     def relocalize_batch_dev(self, items, results_t):
-        """items: [(map_id, ranges device tensor, angles ndarray, max_range)]; asynchronous;
+        """items: [(map_id, ranges device tensor, angles ndarray, max_range[, topk])]; asynchronous;
         results_t: device uint8 tensor of len(items) * RESULT_BYTES bytes."""
         keep = []
         arr = (Request * len(items))()
-        for i, (mid, zt, a, mr) in enumerate(items):
+        for i, it in enumerate(items):
+            mid, zt, a, mr = it[:4]
             a = np.ascontiguousarray(a, dtype=np.float32)
             keep.append(a)
-            arr[i] = Request(mid, zt.data_ptr(), a.ctypes.data, int(zt.numel()), mr)
+            arr[i] = Request(mid, zt.data_ptr(), a.ctypes.data, int(zt.numel()), mr, it[4] if len(it) > 4 else 0)
         self._check(self._L.relo_relocalize_batch_dev(self._h, arr, len(items), _t_ptr(results_t)),
                     "relocalize_batch_dev")
+
+    # ---- served form ------------------------------------------------------------------
+    def serve_start(self, max_batch: int = 64, max_inflight: int = 2, hbm_budget: int = 0):
+        self._check(self._L.relo_serve_start(self._h, max_batch, max_inflight, hbm_budget), "serve_start")
+
+    def submit(self, map_id: int, ranges: np.ndarray, angles: np.ndarray, max_range: float) -> int:
+        z = np.ascontiguousarray(ranges, dtype=np.float32)
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        t = ctypes.c_int64(0)
+        self._check(self._L.relo_submit(self._h, map_id, _np_ptr(z), _np_ptr(a), len(z), max_range, ctypes.byref(t)),
+                    "submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (status, Result, latency seconds)."""
+        out = Result()
+        lat = ctypes.c_double(0.0)
+        rc = self._L.relo_poll(self._h, ticket, ctypes.byref(out), ctypes.byref(lat))
+        if rc == PENDING:
+            return None
+        if rc == E_NOT_FOUND:
+            raise ReloError(rc, "unknown ticket")
+        return rc, out, lat.value
+
+    def serve_stop(self):
+        self._check(self._L.relo_serve_stop(self._h), "serve_stop")
 
     def stage(self, which: int, dst_t):
         self._check(self._L.relo_get_stage(self._h, which, _t_ptr(dst_t), dst_t.numel() * dst_t.element_size()),

@@ -8,8 +8,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/relo.h"
@@ -68,6 +74,24 @@ __global__ void k_upload(const __grid_constant__ Blob blob, unsigned char *dst) 
         dst[i] = blob.bytes[i];
 }
 
+// Device resources of one batch in flight: its stream, descriptors, TAM
+// segments, counters, results, scratch arena and uploaded scans.
+struct BatchSlot {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ReqDesc *reqs_dev = nullptr;          // [kMaxBatchRequests]
+    TamSeg *segs_dev = nullptr;           // [kMaxBatches * kMaxBatchRequests]
+    BatchState *bs = nullptr;
+    relo_result *results_dev = nullptr;   // [kMaxBatchRequests]
+    unsigned char *arena = nullptr;       // per-request scratch of the batch
+    size_t arena_cap = 0;
+    float *ranges_dev = nullptr;          // uploaded scans
+    size_t ranges_cap = 0;
+    cudaEvent_t done = nullptr;           // recorded after the batch's last kernel (served form)
+};
+
+struct Ticket;
+
 }  // namespace
 
 struct relo_ctx {
@@ -80,16 +104,11 @@ struct relo_ctx {
     unsigned long long plan_clock = 0;
     std::string err;
     long long held = 0;
-    // batch state
-    ReqDesc *reqs_dev = nullptr;          // [kMaxBatchRequests]
-    TamSeg *segs_dev = nullptr;           // [kMaxBatches * kMaxBatchRequests]
-    BatchState *bs = nullptr;
-    relo_result *results_dev = nullptr;   // [kMaxBatchRequests]
-    unsigned char *arena = nullptr;       // per-request scratch of the current batch
-    size_t arena_cap = 0;
-    float *ranges_dev = nullptr;          // host-scan uploads
-    size_t ranges_cap = 0;
+    // batches run by the calling thread use `main` (on the context stream)
+    BatchSlot main;
     int *bad = nullptr;
+    // served form
+    struct Server *server = nullptr;
     Blob *blob = nullptr;                 // host staging of one upload (heap)
     // stage timing
     bool profiling = false;
@@ -101,6 +120,7 @@ struct relo_ctx {
     long long kernels = 0;
     // the first request of the last batch (for relo_get_stage)
     ReqDesc last{};
+    BatchState *last_bs = nullptr;
     bool has_last = false;
 };
 
@@ -134,20 +154,25 @@ cudaEvent_t take_event(relo_ctx *ctx) {
 
 // Wraps one kernel launch: counts it and, with profiling on, brackets it with events.
 template <typename F>
-cudaError_t timed(relo_ctx *ctx, int stage, int n_kernels, F &&launch) {
+cudaError_t timed_on(relo_ctx *ctx, cudaStream_t st, int stage, int n_kernels, F &&launch) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (ctx->profiling) {
         a = take_event(ctx);
         b = take_event(ctx);
-        if (a) cudaEventRecord(a, ctx->stream);
+        if (a) cudaEventRecord(a, st);
     }
     cudaError_t e = launch();
     ctx->kernels += n_kernels;
     if (ctx->profiling && a && b) {
-        cudaEventRecord(b, ctx->stream);
+        cudaEventRecord(b, st);
         ctx->pending.push_back({stage, a, b});
     }
     return e;
+}
+
+template <typename F>
+cudaError_t timed(relo_ctx *ctx, int stage, int n_kernels, F &&launch) {
+    return timed_on(ctx, ctx->stream, stage, n_kernels, launch);
 }
 
 int dev_alloc(relo_ctx *ctx, void **p, size_t bytes, const char *what) {
@@ -468,14 +493,14 @@ int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, 
 
 // ---- batches ------------------------------------------------------------------------------------
 
-int upload(relo_ctx *ctx, void *dst, const void *src, size_t bytes) {
+int upload(relo_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
     const unsigned char *p = static_cast<const unsigned char *>(src);
     unsigned char *d = static_cast<unsigned char *>(dst);
     while (bytes > 0) {
         const size_t n = bytes < kBlobBytes ? bytes : kBlobBytes;
         ctx->blob->n = (unsigned int)n;
         memcpy(ctx->blob->bytes, p, n);
-        k_upload<<<(unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16), 256, 0, ctx->stream>>>(*ctx->blob, d);
+        k_upload<<<(unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16), 256, 0, st>>>(*ctx->blob, d);
         CK(cudaGetLastError(), "descriptor upload");
         ctx->kernels += 1;
         p += n;
@@ -489,7 +514,7 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Checks one request and resolves its map and sensor plan.
 int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float *angles, int32_t n_beams,
-            float max_range, void *result_dev, Prepared *out) {
+            float max_range, void *result_dev, Prepared *out, int topk = 0) {
     if (!ranges_dev || !angles || !result_dev || n_beams < 2)
         return fail(ctx, RELO_E_INVALID_ARG, "bad relocalize arguments");
     MapSlot *m = get_map(ctx, map_id);
@@ -512,7 +537,8 @@ int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float 
     out->result_dev = result_dev;
     out->max_range = max_range;
     out->lim = (int)((rmax_q16 * rmax_q16) >> 32);
-    out->K = std::min(p.topk, m->n_hyp);
+    if (topk < 0 || topk > kMaxTopk) return fail(ctx, RELO_E_INVALID_ARG, "topk must be in [0, 4096]");
+    out->K = std::min(topk > 0 ? topk : p.topk, m->n_hyp);
     out->B = std::min(p.batch, out->K);
     out->n_batches = (out->K + out->B - 1) / out->B;
     if (out->n_batches > kMaxBatches)
@@ -521,7 +547,7 @@ int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float 
 }
 
 // Lays out the batch's scratch, uploads its descriptors and launches every stage once.
-int run_batch(relo_ctx *ctx, const Prepared *pr, int R) {
+int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     if (R < 1 || R > kMaxBatchRequests) return fail(ctx, RELO_E_INVALID_ARG, "1 to 256 requests per batch");
     const relo_params &p = ctx->p;
     std::vector<ReqDesc> desc((size_t)R);
@@ -544,7 +570,7 @@ int run_batch(relo_ctx *ctx, const Prepared *pr, int R) {
         max_C = std::max(max_C, q.m->dev.C);
         max_batches = std::max(max_batches, q.n_batches);
     }
-    int rc = ensure(ctx, &ctx->arena, &ctx->arena_cap, total, "request scratch");
+    int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
     if (rc) return rc;
     for (int r = 0; r < R; ++r) {
         const Prepared &q = pr[r];
@@ -592,7 +618,7 @@ int run_batch(relo_ctx *ctx, const Prepared *pr, int R) {
         d.early_stop = p.early_stop;
         d.tau = p.tau;
         d.n_smad_evals = (long long)m.n_hyp * P.n_m;
-        unsigned char *a = ctx->arena + off[r];
+        unsigned char *a = sl.arena + off[r];
         auto take = [&a](size_t bytes) {
             unsigned char *x = a;
             a += align_up(bytes);
@@ -630,25 +656,279 @@ int run_batch(relo_ctx *ctx, const Prepared *pr, int R) {
         plans[bi] = plan_tam(nb.data(), no.data(), sb.data(), R, max_beams, max_C, ctx->n_sm, &segs[(size_t)bi * R]);
         if (plans[bi].vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
     }
-    if ((rc = upload(ctx, ctx->reqs_dev, desc.data(), sizeof(ReqDesc) * R)) ||
-        (rc = upload(ctx, ctx->segs_dev, segs.data(), sizeof(TamSeg) * segs.size())))
+    cudaStream_t st = sl.stream;
+    if ((rc = upload(ctx, st, sl.reqs_dev, desc.data(), sizeof(ReqDesc) * R)) ||
+        (rc = upload(ctx, st, sl.segs_dev, segs.data(), sizeof(TamSeg) * segs.size())))
         return rc;
-    cudaStream_t st = ctx->stream;
-    CK(timed(ctx, 1, 1, [&] { return launch_scan_prep(ctx->reqs_dev, R, ctx->bs, st); }), "scan preparation");
-    CK(timed(ctx, 2, 1, [&] { return launch_raycast_smad(ctx->reqs_dev, R, total_hyp, max_ns_pad, ctx->bs, ctx->n_sm, st); }),
+    ReqDesc *rq = sl.reqs_dev;
+    CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
+    CK(timed_on(ctx, st, 2, 1, [&] { return launch_raycast_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
        "ray cast + SMAD");
-    CK(timed(ctx, 3, 1, [&] { return launch_topk(ctx->reqs_dev, R, max_n_hyp, max_K, st); }), "SMAD top-K");
+    CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {
-        const TamSeg *sg = ctx->segs_dev + (size_t)bi * R;
-        CK(timed(ctx, 4, 1, [&] { return launch_tam(ctx->reqs_dev, R, sg, plans[bi], st); }), "TAM");
-        CK(timed(ctx, 5, 1, [&] { return launch_select_batch(ctx->reqs_dev, R, bi, st); }), "batch selection");
+        const TamSeg *sg = sl.segs_dev + (size_t)bi * R;
+        CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, plans[bi], st); }), "TAM");
+        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, st); }), "batch selection");
     }
-    CK(timed(ctx, 5, 1, [&] { return launch_finalize(ctx->reqs_dev, R, st); }), "finalize");
+    CK(timed_on(ctx, st, 5, 1, [&] { return launch_finalize(rq, R, st); }), "finalize");
     ctx->last = desc[0];
+    ctx->last_bs = sl.bs;
     ctx->has_last = true;
     return RELO_OK;
 }
 
+int slot_init(relo_ctx *ctx, BatchSlot &sl, cudaStream_t stream) {
+    int rc;
+    if (stream) {
+        sl.stream = stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "batch stream");
+        sl.own_stream = true;
+    }
+    if ((rc = dev_alloc(ctx, (void **)&sl.reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests, "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&sl.segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests,
+                        "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&sl.bs, sizeof(BatchState), "batch state")) ||
+        (rc = dev_alloc(ctx, (void **)&sl.results_dev, sizeof(relo_result) * kMaxBatchRequests, "batch state")))
+        return rc;
+    return RELO_OK;
+}
+
+void slot_free(relo_ctx *ctx, BatchSlot &sl) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    dev_free(ctx, sl.reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests);
+    dev_free(ctx, sl.segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests);
+    dev_free(ctx, sl.bs, sizeof(BatchState));
+    dev_free(ctx, sl.results_dev, sizeof(relo_result) * kMaxBatchRequests);
+    dev_free(ctx, sl.arena, sl.arena_cap);
+    dev_free(ctx, sl.ranges_dev, sizeof(float) * sl.ranges_cap);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.own_stream) cudaStreamDestroy(sl.stream);
+    sl = BatchSlot();
+}
+
+
+
+// ---- served form: continuous batching ------------------------------------------------------------
+
+using Clock = std::chrono::steady_clock;
+
+struct Ticket {
+    long long id = 0;
+    int map_id = -1;
+    std::vector<float> ranges, angles;
+    float max_range = 0;
+    relo_result result{};
+    int status = RELO_PENDING;
+    Clock::time_point t_submit, t_done;
+    size_t bytes = 0;
+};
+
+struct InFlight {
+    BatchSlot slot;
+    std::vector<Ticket *> tickets;
+    size_t bytes = 0;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct Server {
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Ticket *> queue;
+    std::unordered_map<long long, Ticket *> tickets;   // submitted and not yet polled
+    long long next_id = 1;
+    bool running = false;
+    int max_batch = 64, max_inflight = 2;
+    long long budget = 0;
+    size_t inflight_bytes = 0;
+    std::vector<InFlight> slots;
+};
+
+namespace {
+
+// device bytes a request occupies while in flight (scratch and its scan)
+size_t request_bytes(const relo_ctx *ctx, const Prepared &q) {
+    const size_t n = (size_t)q.P->n, nh = (size_t)q.m->n_hyp, K = (size_t)q.K;
+    return align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8 * nh) * 2 + align_up(4 * nh) +
+           align_up(4 * K) * 2 + align_up(4 * K * q.P->n_orient) + align_up(8 * K) +
+           align_up(4ull * q.n_batches * ctx->p.local_topk) + align_up(sizeof(SelectState)) +
+           align_up(sizeof(float) * q.P->n * ctx->p.n_skip_beam);
+}
+
+void finish(Server *S, Ticket *t, int status, const relo_result *r) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (r) t->result = *r;
+    t->result.status = status;
+    t->status = status;
+    t->t_done = Clock::now();
+}
+
+// Launches one batch of admitted tickets on a free slot (worker thread only).
+void launch_batch(relo_ctx *ctx, InFlight &f, std::vector<Ticket *> &batch, std::vector<Prepared> &pr) {
+    Server *S = ctx->server;
+    BatchSlot &sl = f.slot;
+    size_t total = 0;
+    for (Ticket *t : batch) total += t->ranges.size();
+    std::vector<float> host(total);
+    std::vector<size_t> off(batch.size());
+    size_t pos = 0;
+    for (size_t i = 0; i < batch.size(); ++i) {
+        off[i] = pos;
+        memcpy(host.data() + pos, batch[i]->ranges.data(), sizeof(float) * batch[i]->ranges.size());
+        pos += batch[i]->ranges.size();
+    }
+    int rc = ensure(ctx, &sl.ranges_dev, &sl.ranges_cap, total, "scan upload");
+    if (rc == RELO_OK && cudaMemcpyAsync(sl.ranges_dev, host.data(), sizeof(float) * total, cudaMemcpyHostToDevice,
+                                         sl.stream) != cudaSuccess)
+        rc = RELO_E_CUDA;
+    if (rc == RELO_OK) {
+        for (size_t i = 0; i < batch.size(); ++i) {
+            pr[i].ranges_dev = sl.ranges_dev + off[i];
+            pr[i].result_dev = sl.results_dev + i;
+        }
+        rc = run_batch(ctx, sl, pr.data(), (int)batch.size());
+    }
+    if (rc == RELO_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = RELO_E_CUDA;
+    if (rc != RELO_OK) {
+        cudaStreamSynchronize(sl.stream);
+        for (Ticket *t : batch) finish(S, t, rc, nullptr);
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Ticket *t : batch) S->inflight_bytes -= t->bytes;
+        return;
+    }
+    f.tickets = batch;
+    f.bytes = 0;
+    for (Ticket *t : batch) f.bytes += t->bytes;
+    f.busy = true;
+}
+
+// Copies the results of a finished slot back and completes its tickets.
+void retire(relo_ctx *ctx, InFlight &f, cudaError_t q) {
+    Server *S = ctx->server;
+    std::vector<relo_result> res(f.tickets.size());
+    cudaError_t e = q;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.data(), f.slot.results_dev, sizeof(relo_result) * res.size(), cudaMemcpyDeviceToHost,
+                            f.slot.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f.slot.stream);
+    const Clock::time_point now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (size_t i = 0; i < f.tickets.size(); ++i) {
+            Ticket *t = f.tickets[i];
+            if (e == cudaSuccess) t->result = res[i];
+            t->status = e == cudaSuccess ? res[i].status : RELO_E_CUDA;
+            t->result.status = t->status;
+            t->t_done = now;
+        }
+        S->inflight_bytes -= f.bytes;
+    }
+    f.tickets.clear();
+    f.bytes = 0;
+    f.busy = false;
+}
+
+void serve_loop(relo_ctx *ctx) {
+    Server *S = ctx->server;
+    for (;;) {
+        bool any_busy = false, progressed = false;
+        for (InFlight &f : S->slots) {
+            if (!f.busy) continue;
+            const cudaError_t q = cudaEventQuery(f.slot.done);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            retire(ctx, f, q);
+            progressed = true;
+        }
+        InFlight *free_slot = nullptr;
+        for (InFlight &f : S->slots)
+            if (!f.busy) {
+                free_slot = &f;
+                break;
+            }
+        std::vector<Ticket *> cand;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (!S->running && S->queue.empty() && !any_busy) break;
+            if (free_slot && !S->queue.empty()) {
+                while (!S->queue.empty() && (int)cand.size() < S->max_batch) {
+                    cand.push_back(S->queue.front());
+                    S->queue.pop_front();
+                }
+            } else if (!progressed) {
+                if (!any_busy)
+                    S->cv.wait_for(lk, std::chrono::milliseconds(2));
+                else {
+                    lk.unlock();
+                    std::this_thread::sleep_for(std::chrono::microseconds(20));
+                }
+                continue;
+            }
+        }
+        if (cand.empty()) continue;
+        // admission: prepare in FIFO order while the HBM budget allows
+        std::vector<Ticket *> batch;
+        std::vector<Prepared> pr;
+        std::vector<Ticket *> back;
+        for (Ticket *t : cand) {
+            if (!back.empty()) {
+                back.push_back(t);
+                continue;
+            }
+            Prepared q;
+            const int rc = prepare(ctx, t->map_id, t->ranges.data(), t->angles.data(), (int)t->ranges.size(),
+                                   t->max_range, (void *)1, &q);   // placeholder pointers, replaced at launch
+            if (rc != RELO_OK) {
+                finish(S, t, rc, nullptr);
+                continue;
+            }
+            t->bytes = request_bytes(ctx, q);
+            bool fits;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                fits = S->budget <= 0 || S->inflight_bytes + t->bytes <= (size_t)S->budget;
+                if (!fits && S->inflight_bytes == 0 && batch.empty()) {
+                    fits = false;
+                } else if (fits) {
+                    S->inflight_bytes += t->bytes;
+                }
+            }
+            if (fits) {
+                batch.push_back(t);
+                pr.push_back(q);
+            } else if (batch.empty() && !any_busy) {
+                finish(S, t, RELO_E_OVER_BUDGET, nullptr);   // can never fit
+            } else {
+                back.push_back(t);
+            }
+        }
+        if (!back.empty()) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (auto it = back.rbegin(); it != back.rend(); ++it) S->queue.push_front(*it);
+        }
+        if (!batch.empty()) launch_batch(ctx, *free_slot, batch, pr);
+    }
+}
+
+void serve_shutdown(relo_ctx *ctx) {
+    Server *S = ctx->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->running = false;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (InFlight &f : S->slots) slot_free(ctx, f.slot);
+    for (auto &kv : S->tickets) delete kv.second;
+    delete S;
+    ctx->server = nullptr;
+}
 
 }  // namespace
 
@@ -706,11 +986,7 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
         delete ctx;
         return RELO_E_CUDA;
     }
-    if ((rc = dev_alloc(ctx, (void **)&ctx->reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests, "batch state")) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests,
-                        "batch state")) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->bs, sizeof(BatchState), "batch state")) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->results_dev, sizeof(relo_result) * kMaxBatchRequests, "batch state")) ||
+    if ((rc = slot_init(ctx, ctx->main, ctx->stream)) ||
         (rc = dev_alloc(ctx, (void **)&ctx->bad, sizeof(int), "batch state"))) {
         relo_destroy(ctx);
         return rc;
@@ -721,14 +997,14 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
 
 int relo_destroy(relo_ctx *ctx) {
     if (!ctx) return RELO_E_INVALID_ARG;
+    serve_shutdown(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &m : ctx->maps)
         if (m.live) free_map(ctx, m);
     for (SensorPlan *P : ctx->plans) free_plan(ctx, P);
     ctx->plans.clear();
-    void *ptrs[] = {ctx->reqs_dev, ctx->segs_dev, ctx->bs, ctx->results_dev, ctx->arena, ctx->ranges_dev, ctx->bad};
-    for (void *q : ptrs)
-        if (q) cudaFree(q);
+    slot_free(ctx, ctx->main);
+    if (ctx->bad) cudaFree(ctx->bad);
     for (auto &pe : ctx->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -840,13 +1116,13 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
     Prepared pr;
     int rc = prepare(ctx, map_id, ranges_dev, angles, n_beams, max_range, result_dev, &pr);
     if (rc) return rc;
-    return run_batch(ctx, &pr, 1);
+    return run_batch(ctx, ctx->main, &pr, 1);
 }
 
 int relo_relocalize(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
                     float max_range, relo_result *out) {
     if (!ctx || !ranges || !angles || !out || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
-    relo_request rq = {map_id, ranges, angles, n_beams, max_range};
+    relo_request rq = {map_id, ranges, angles, n_beams, max_range, 0};
     return relo_relocalize_batch(ctx, &rq, 1, out);
 }
 
@@ -856,10 +1132,10 @@ int relo_relocalize_batch_dev(relo_ctx *ctx, const relo_request *reqs, int32_t n
     std::vector<Prepared> pr((size_t)n);
     for (int i = 0; i < n; ++i) {
         int rc = prepare(ctx, reqs[i].map_id, reqs[i].ranges, reqs[i].angles, reqs[i].n_beams, reqs[i].max_range,
-                         results_dev + i, &pr[i]);
+                         results_dev + i, &pr[i], reqs[i].topk);
         if (rc) return rc;
     }
-    return run_batch(ctx, pr.data(), n);
+    return run_batch(ctx, ctx->main, pr.data(), n);
 }
 
 int relo_relocalize_batch(relo_ctx *ctx, const relo_request *reqs, int32_t n, relo_result *out) {
@@ -872,23 +1148,24 @@ int relo_relocalize_batch(relo_ctx *ctx, const relo_request *reqs, int32_t n, re
         if (!reqs[i].ranges || reqs[i].n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad request");
         total += (size_t)reqs[i].n_beams;
     }
-    int rc = ensure(ctx, &ctx->ranges_dev, &ctx->ranges_cap, total, "scan upload");
+    BatchSlot &sl = ctx->main;
+    int rc = ensure(ctx, &sl.ranges_dev, &sl.ranges_cap, total, "scan upload");
     if (rc) return rc;
     std::vector<relo_request> dreq(reqs, reqs + n);
     size_t pos = 0;
     for (int i = 0; i < n; ++i) {
-        CK(cudaMemcpyAsync(ctx->ranges_dev + pos, reqs[i].ranges, sizeof(float) * reqs[i].n_beams,
+        CK(cudaMemcpyAsync(sl.ranges_dev + pos, reqs[i].ranges, sizeof(float) * reqs[i].n_beams,
                            cudaMemcpyHostToDevice, ctx->stream),
            "scan upload");
-        dreq[i].ranges = ctx->ranges_dev + pos;
+        dreq[i].ranges = sl.ranges_dev + pos;
         pos += (size_t)reqs[i].n_beams;
     }
-    rc = relo_relocalize_batch_dev(ctx, dreq.data(), n, ctx->results_dev);
+    rc = relo_relocalize_batch_dev(ctx, dreq.data(), n, sl.results_dev);
     if (rc) {
         cudaStreamSynchronize(ctx->stream);
         return rc;
     }
-    CK(cudaMemcpyAsync(out, ctx->results_dev, sizeof(relo_result) * n, cudaMemcpyDeviceToHost, ctx->stream),
+    CK(cudaMemcpyAsync(out, sl.results_dev, sizeof(relo_result) * n, cudaMemcpyDeviceToHost, ctx->stream),
        "result download");
     CK(cudaStreamSynchronize(ctx->stream), "relocalize");
     for (int i = 0; i < n; ++i)
@@ -915,7 +1192,7 @@ int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes) {
             BatchState bs;
             CK(cudaMemcpyAsync(&si, d.scan, sizeof si, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
             CK(cudaMemcpyAsync(&ss, d.state, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
-            CK(cudaMemcpyAsync(&bs, ctx->bs, sizeof bs, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
+            CK(cudaMemcpyAsync(&bs, ctx->last_bs, sizeof bs, cudaMemcpyDeviceToHost, ctx->stream), "stage read");
             CK(cudaStreamSynchronize(ctx->stream), "stage read");
             long long v[RELO_SCAN_INFO_LEN] = {d.ns, d.n_orient, d.n_enum, si.n_valid, si.k_ret, si.sum_real,
                                                d.K, ss.n_batches, (long long)bs.dda_steps, d.n_hyp};
@@ -960,6 +1237,82 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     ra.n_hyp = n;
     CK(launch_synth(ra, ranges_dev, hit_dev, ctx->stream), "synthesized scans");
     CK(cudaStreamSynchronize(ctx->stream), "synthesized scans");
+    return RELO_OK;
+}
+
+int relo_serve_start(relo_ctx *ctx, int32_t max_batch, int32_t max_inflight, int64_t hbm_budget) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    if (ctx->server) return fail(ctx, RELO_E_INVALID_ARG, "already serving");
+    if (max_batch < 1 || max_batch > kMaxBatchRequests || max_inflight < 1 || max_inflight > 8 || hbm_budget < 0)
+        return fail(ctx, RELO_E_INVALID_ARG, "max_batch in [1, 256], max_inflight in [1, 8], budget >= 0");
+    Server *S = new (std::nothrow) Server();
+    if (!S) return fail(ctx, RELO_E_INVALID_ARG, "out of host memory");
+    S->max_batch = max_batch;
+    S->max_inflight = max_inflight;
+    S->budget = hbm_budget;
+    S->slots.resize((size_t)max_inflight);
+    ctx->server = S;
+    for (InFlight &f : S->slots) {
+        int rc = slot_init(ctx, f.slot, nullptr);
+        if (rc == RELO_OK && cudaEventCreateWithFlags(&f.slot.done, cudaEventDisableTiming) != cudaSuccess)
+            rc = RELO_E_CUDA;
+        if (rc != RELO_OK) {
+            serve_shutdown(ctx);
+            return rc;
+        }
+    }
+    S->running = true;
+    S->worker = std::thread(serve_loop, ctx);
+    return RELO_OK;
+}
+
+int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                float max_range, int64_t *ticket) {
+    if (!ctx || !ranges || !angles || !ticket || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    Server *S = ctx->server;
+    if (!S) return fail(ctx, RELO_E_INVALID_ARG, "not serving: call relo_serve_start first");
+    Ticket *t = new (std::nothrow) Ticket();
+    if (!t) return fail(ctx, RELO_E_INVALID_ARG, "out of host memory");
+    t->map_id = map_id;
+    t->ranges.assign(ranges, ranges + n_beams);
+    t->angles.assign(angles, angles + n_beams);
+    t->max_range = max_range;
+    t->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!S->running) {
+            delete t;
+            return fail(ctx, RELO_E_INVALID_ARG, "server stopping");
+        }
+        t->id = S->next_id++;
+        S->tickets[t->id] = t;
+        S->queue.push_back(t);
+        *ticket = t->id;
+    }
+    S->cv.notify_one();
+    return RELO_OK;
+}
+
+int relo_poll(relo_ctx *ctx, int64_t ticket, relo_result *out, double *latency_s) {
+    if (!ctx || !out) return RELO_E_INVALID_ARG;
+    Server *S = ctx->server;
+    if (!S) return RELO_E_NOT_FOUND;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return RELO_E_NOT_FOUND;
+    Ticket *t = it->second;
+    if (t->status == RELO_PENDING) return RELO_PENDING;
+    *out = t->result;
+    if (latency_s) latency_s[0] = std::chrono::duration<double>(t->t_done - t->t_submit).count();
+    const int st = t->status;
+    S->tickets.erase(it);
+    delete t;
+    return st;
+}
+
+int relo_serve_stop(relo_ctx *ctx) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    serve_shutdown(ctx);
     return RELO_OK;
 }
 

@@ -458,3 +458,63 @@ def test_batch_dev_equals_host_and_oracle(relo, workload):
     assert abs(host[1].tam - T_at(host[1].hyp, host[1].m)) <= RTOL * T_at(host[1].hyp, host[1].m)
     assert host[1].smad_num == want["smad_nums"][host[1].hyp]
     ctx.close()
+
+
+def served_setup(relo, workload, **params):
+    items = [it for it in mixed_batch_items(workload) if it[6] == 72]
+    ctx = relo.Relo(n_orient=72, topk=32, batch=12, local_topk=4, early_stop=1, tau=0.9, **params)
+    reqs = []
+    for (g, res, hyps, z, ang, mr, _) in items:
+        mid = ctx.load_map(g, res)
+        ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
+        reqs.append((mid, z, ang, mr))
+    return ctx, reqs
+
+
+def poll_all(ctx, tickets, timeout_s=60.0):
+    import time
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = ctx.poll(t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < timeout_s, "served requests did not finish"
+        time.sleep(0.001)
+    return [out[t] for t in tickets]
+
+
+def test_served_results_equal_alone(relo, workload):
+    """Continuous batching: a mixed stream of requests, submitted in waves
+    while earlier ones run, gives every request the result it gets alone."""
+    ctx, reqs = served_setup(relo, workload)
+    alone = [ctx.relocalize(*r).as_dict() for r in reqs]
+    ctx.serve_start(max_batch=3, max_inflight=2)
+    order = [i % len(reqs) for i in range(17)]
+    tickets = [ctx.submit(*reqs[i]) for i in order[:9]]
+    tickets += [ctx.submit(*reqs[i]) for i in order[9:]]
+    done = poll_all(ctx, tickets)
+    ctx.serve_stop()
+    for i, (status, res, lat) in zip(order, done):
+        assert status == relo.OK and lat > 0
+        assert res.as_dict() == alone[i]
+    ctx.close()
+
+
+def test_served_admission_by_budget(relo, workload):
+    ctx, reqs = served_setup(relo, workload)
+    alone = [ctx.relocalize(*r).as_dict() for r in reqs]
+    ctx.serve_start(max_batch=8, max_inflight=2, hbm_budget=1024)      # smaller than any request's scratch
+    t = ctx.submit(*reqs[1])
+    (status, res, lat), = poll_all(ctx, [t])
+    assert status == relo.E_OVER_BUDGET
+    ctx.serve_stop()
+    ctx.serve_start(max_batch=8, max_inflight=2, hbm_budget=3 << 20)   # room for about one request at a time
+    tickets = [ctx.submit(*r) for r in reqs]
+    done = poll_all(ctx, tickets)
+    ctx.serve_stop()
+    for i, (status, res, lat) in enumerate(done):
+        assert status == relo.OK and res.as_dict() == alone[i]
+    ctx.close()

@@ -146,7 +146,7 @@ def make_office(seed: int, n: int = 1024, res: float = 0.05, corridor_m: float =
 
 
 def make_warehouse(seed: int, n: int = 4096, res: float = 0.05, shelf_m: float = 1.0, aisle_m: float = 3.0,
-                   shelf_len_m: float = 20.0, cross_m: float = 2.5, margin_m: float = 4.0) -> np.ndarray:
+                   shelf_len_m: float | None = None, cross_m: float = 2.5, margin_m: float = 4.0) -> np.ndarray:
     """Warehouse with perimeter walls and periodic, identical shelving rows.
 
     Shelf rows run along x, ``shelf_m`` deep, separated by ``aisle_m`` aisles,
@@ -156,6 +156,8 @@ def make_warehouse(seed: int, n: int = 4096, res: float = 0.05, shelf_m: float =
     rng = np.random.default_rng(seed)
     g = np.zeros((n, n), np.int8)
     g[0, :] = g[-1, :] = g[:, 0] = g[:, -1] = OCC
+    if shelf_len_m is None:   # 20 m runs, shorter on small maps so at least two fit across
+        shelf_len_m = min(20.0, (n * res - 2 * margin_m - cross_m) / 2.0)
     sh = int(round(shelf_m / res))
     ai = int(round(aisle_m / res))
     sl = int(round(shelf_len_m / res))
@@ -335,6 +337,92 @@ def rrt_hypotheses(grid: np.ndarray, res: float, n_hyp: int, seed: int, r_robot:
     cells = cells[:n_hyp]
     order = np.lexsort((cells[:, 0], cells[:, 1]))
     return cells[order].astype(np.int32), rho
+
+
+def free_hypotheses(grid: np.ndarray, res: float, n_hyp: int, seed: int, r_robot: float = 0.21,
+                    clr: np.ndarray | None = None) -> np.ndarray:
+    """n_hyp distinct seeded cells whose clearance is at least r_robot (int32 [n, 2], sorted).
+
+    A fast stand-in for Algorithm 1 where many large maps must be generated
+    (the batched and served workloads): uniform over the traversable cells
+    instead of the RRT's voxel representatives."""
+    clr = clearance_table(grid, res) if clr is None else clr
+    ok = np.argwhere(clr >= r_robot)[:, ::-1]
+    rng = np.random.default_rng(seed)
+    pick = ok[rng.choice(len(ok), size=min(n_hyp, len(ok)), replace=False)]
+    order = np.lexsort((pick[:, 0], pick[:, 1]))
+    return pick[order].astype(np.int32)
+
+
+def scan_for(grid: np.ndarray, res: float, hyps: np.ndarray, n_beams: int, n_s: int, n_orient: int,
+             max_range: float, seed: int, noisy: bool = True):
+    """(angles, ranges, ground-truth pose) of a seeded scan near a random hypothesis."""
+    return _scan_for(grid, res, hyps, n_beams, n_s, n_orient, max_range, seed, noisy)
+
+
+@dataclass
+class Instance:
+    grid: np.ndarray
+    res: float
+    hyps: np.ndarray
+    ranges: np.ndarray
+    angles: np.ndarray
+    max_range: float
+    topk: int
+    n_s: int
+
+
+BEAM_COUNTS = (541, 720, 1081, 1440)
+
+
+def batched_instances(seed: int = 1003, count: int = 64, n_orient: int = 360):
+    """The batched workload: `count` independent relocalizations.
+
+    Map sides uniform over {512, 576, ..., 2048} cells (office for even draws,
+    warehouse for odd), beam counts from {541, 720, 1081, 1440} with a FoV
+    drawn in [180, 360] deg (N_s a multiple of n_orient in [N, 2N]), 1k-20k
+    hypotheses, TAM on the top 256 (maps up to 1024^2) or 1024, 25 m range,
+    office noise model."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.integers(8, 33)) * 64
+        s_i = seed * 100 + i
+        grid = make_office(s_i, n=side) if i % 2 == 0 else make_warehouse(s_i, n=side)
+        n_beams = int(rng.choice(BEAM_COUNTS))
+        fov = float(rng.uniform(180.0, 360.0))
+        n_s = choose_ns(n_beams, fov, n_orient)
+        n_hyp = int(rng.integers(1000, 20001))
+        hyps = free_hypotheses(grid, 0.05, n_hyp, s_i)
+        angles, z, _ = _scan_for(grid, 0.05, hyps, n_beams, n_s, n_orient, 25.0, s_i, True)
+        out.append(Instance(grid, 0.05, hyps, z, angles, 25.0, 256 if side <= 1024 else 1024, n_s))
+    return out
+
+
+def served_maps(seed: int = 1004):
+    """The served workload's 8 resident maps: two each of 512^2, 1024^2, 2048^2
+    and 4096^2 (one office, one warehouse) with 1250 / 5000 / 10000 / 20000
+    hypotheses."""
+    out = []
+    for k, (side, n_hyp) in enumerate(((512, 1250), (1024, 5000), (2048, 10000), (4096, 20000))):
+        for j in range(2):
+            s_i = seed * 100 + 2 * k + j
+            grid = make_office(s_i, n=side) if j == 0 else make_warehouse(s_i, n=side)
+            out.append((grid, 0.05, free_hypotheses(grid, 0.05, n_hyp, s_i)))
+    return out
+
+
+def served_scans(maps, per_map: int = 6, seed: int = 1004, n_orient: int = 360):
+    """A pool of seeded scans per resident map (beam counts as the batched workload)."""
+    rng = np.random.default_rng(seed + 1)
+    pool = []
+    for mi, (grid, res, hyps) in enumerate(maps):
+        for j in range(per_map):
+            n_beams = int(rng.choice(BEAM_COUNTS))
+            n_s = choose_ns(n_beams, float(rng.uniform(180.0, 360.0)), n_orient)
+            angles, z, _ = _scan_for(grid, res, hyps, n_beams, n_s, n_orient, 25.0, seed * 1000 + mi * 10 + j, True)
+            pool.append((mi, z, angles, 25.0))
+    return pool
 
 
 def cell_centres(cells: np.ndarray, res: float) -> np.ndarray:
