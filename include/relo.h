@@ -66,6 +66,8 @@ typedef struct relo_params {
     int32_t n_skip_beam;                               /* Eq. 11 beam stride */
     int32_t early_stop;                                /* 1: stop after the first batch whose best >= tau */
     int64_t hbm_budget;                                /* bytes the context may hold; 0 = no limit */
+    double max_range;                                  /* metres: the longest scan range maps loaded from now on accept
+                                                          (sets the border of the TAM field; default 30) */
 } relo_params;
 
 /* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */

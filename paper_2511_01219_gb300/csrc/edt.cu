@@ -1,7 +1,11 @@
 // Map precompute: exact squared Euclidean distance transform (the EDT lookup
 // table of Sec. III-A item 3, used by the likelihood field of Eq. 23 and the
-// distance statistics of Eq. 29-30), its clamped tiled copy for TAM, and the
+// distance statistics of Eq. 29-30), its clamped padded copy for TAM, and the
 // tiled occupancy bitmap for ray casting (Eq. 13).
+//
+// The clamped field is stored row-major with a border of P cells holding C on
+// every side, P at least the longest beam in cells, so every beam endpoint of
+// TAM falls inside the array and needs no bounds test.
 //
 // d2(x, y) = min over occupied (x', y') of (x - x')^2 + (y - y')^2 separates
 // into a column term g2(x', y) = min over occupied y' in column x' of
@@ -74,7 +78,7 @@ __global__ void k_edt_col_final(const int8_t *__restrict__ grid, int W, int H, i
     }
 }
 
-__global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int TW, int32_t *__restrict__ d2,
+__global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int Wp, int32_t *__restrict__ d2,
                            uint16_t *__restrict__ field) {
     extern __shared__ int32_t row[];
     const int y = blockIdx.x;
@@ -97,14 +101,12 @@ __global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int 
             }
         }
         d2[(size_t)y * W + x] = best == kInf ? kD2None : best;
-        field[tile_index(x, y, TW)] = (uint16_t)(best > C ? C : best);
+        field[(size_t)y * Wp + x] = (uint16_t)(best > C ? C : best);
     }
 }
 
-// one thread per 8x8 tile: occupancy bits, and the clamp value in the parts of
-// edge tiles that lie outside the map
-__global__ void k_tiles(const int8_t *__restrict__ grid, int W, int H, int TW, int TH, int C,
-                        uint64_t *__restrict__ bits, uint16_t *__restrict__ field) {
+// one thread per 8x8 tile: occupancy bits (cells outside the map are free)
+__global__ void k_tiles(const int8_t *__restrict__ grid, int W, int H, int TW, int TH, uint64_t *__restrict__ bits) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= TW * TH) return;
     int tx = t % TW, ty = t / TW;
@@ -113,24 +115,29 @@ __global__ void k_tiles(const int8_t *__restrict__ grid, int W, int H, int TW, i
         int y = ty * 8 + r;
         for (int c = 0; c < 8; ++c) {
             int x = tx * 8 + c;
-            if (x < W && y < H) {
-                if (grid[(size_t)y * W + x] >= 65) w |= 1ull << (r * 8 + c);
-            } else {
-                field[(size_t)t * 64 + r * 8 + c] = (uint16_t)C;
-            }
+            if (x < W && y < H && grid[(size_t)y * W + x] >= 65) w |= 1ull << (r * 8 + c);
         }
     }
     bits[t] = w;
 }
 
+// the border of the padded field: every cell outside the map reads C (d = d_max)
+__global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int P, int Wp, int C) {
+    const size_t n = (size_t)(H + 2 * P) * Wp;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / Wp) - P, x = (int)(i % Wp) - P;
+        if (x < 0 || y < 0 || x >= W || y >= H) fieldp[i] = (uint16_t)C;
+    }
+}
+
 __global__ void k_map_tables(const int32_t *__restrict__ d2s, const uint16_t *__restrict__ fs,
-                             const uint64_t *__restrict__ bs, int W, int H, int TW, int32_t *d2, uint16_t *field,
+                             const uint64_t *__restrict__ bs, int W, int H, int TW, int Wp, int32_t *d2, uint16_t *field,
                              uint8_t *occ) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)W * H) return;
     int x = (int)(i % W), y = (int)(i / W);
     if (d2) d2[i] = d2s[i];
-    if (field) field[i] = fs[tile_index(x, y, TW)];
+    if (field) field[i] = fs[(size_t)y * Wp + x];
     if (occ) occ[i] = (uint8_t)((bs[(size_t)(y >> 3) * TW + (x >> 3)] >> (((y & 7) << 3) | (x & 7))) & 1ull);
 }
 
@@ -152,19 +159,23 @@ cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
     k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.summ);
     k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
     int nt = m.TW * m.TH;
-    k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.C, m.bits, m.field);
+    k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.bits);
+    uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
+    k_field_border<<<256, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.C);
     size_t smem = (size_t)m.W * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.TW, m.d2, m.field);
+    k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.Wp, m.d2, field00);
     return cudaGetLastError();
 }
 
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s) {
     size_t n = (size_t)m.W * m.H;
-    k_map_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.d2, m.field, m.bits, m.W, m.H, m.TW, d2, field, occ);
+    const uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
+    k_map_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.d2, field00, m.bits, m.W, m.H, m.TW, m.Wp, d2, field,
+                                                             occ);
     return cudaGetLastError();
 }
 

@@ -85,10 +85,15 @@ struct Ray {
             else if (ax == 0) xexit = false;
             else xexit = (long long)e + 2ll * (ny - 1) * ax - 2ll * (nx - 1) * ay >= 0;
             if (xexit) {
+                // j = smallest integer with j * 2|Dx| >= A (0 when A <= 0), A = 2(nx-1)|Dy| - e
                 const long long A = 2ll * (nx - 1) * ay - e;
                 const long long dd = 2ll * ax;
                 int j = 0;
-                while ((long long)j * dd < A) ++j;
+                if (A > 0) {
+                    j = (int)ceilf((float)A / (float)dd);
+                    if ((long long)(j - 1) * dd >= A) --j;
+                    if ((long long)j * dd < A) ++j;
+                }
                 e = (int)((long long)e - 2ll * nx * ay + 2ll * j * ax);
                 cx += sx * nx;
                 cy += sy * j;
@@ -96,12 +101,14 @@ struct Ray {
                 ady += j;
                 n += nx + j;
             } else {
+                // i = 0 if B < 0, else floor(B / (2|Dy|)) + 1, B = e + 2(ny-1)|Dx|
                 const long long B = (long long)e + 2ll * (ny - 1) * ax;
                 const long long dd = 2ll * ay;
                 int i = 0;
                 if (B >= 0) {
-                    i = 1;
-                    while ((long long)i * dd <= B) ++i;
+                    i = (int)floorf((float)B / (float)dd) + 1;
+                    if ((long long)(i - 1) * dd > B) --i;
+                    if ((long long)i * dd <= B) ++i;
                 }
                 e = (int)((long long)e + 2ll * ny * ax - 2ll * i * ay);
                 cx += sx * i;

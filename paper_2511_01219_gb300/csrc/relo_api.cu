@@ -218,7 +218,14 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
         return fail(ctx, RELO_E_INVALID_ARG, "local_topk must be in [1, batch]");
     if (p.n_skip_beam < 1) return fail(ctx, RELO_E_INVALID_ARG, "n_skip_beam must be >= 1");
     if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
+    if (!(p.max_range > 0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
     return RELO_OK;
+}
+
+// border of the padded TAM field: the longest beam in cells, plus one for rounding
+int pad_for(double max_range, double res) {
+    const double c = ceil(max_range / res) + 1.0;
+    return c < 32768.0 ? (int)c : -1;
 }
 
 // clamp C = (d_max / res)^2; d_max / res must be an integer
@@ -235,19 +242,20 @@ int clamp_for(relo_ctx *ctx, double d_max, double res, int *C) {
 int build_lut(relo_ctx *ctx, MapSlot &m) {
     const relo_params &p = ctx->p;
     const int C = m.dev.C;
-    std::vector<float2> h(C + 1);
+    std::vector<float2> h(C + 2);
     const double sc = sqrt((double)C);
     for (int b = 0; b <= C; ++b) {
         double d = m.res * sqrt((double)b);
         double l = log(p.z_hit * exp(-(d * d) / (2.0 * p.sigma_hit * p.sigma_hit)) + p.z_rand + p.eps);
         h[b] = make_float2((float)l, (float)(sc - sqrt((double)b)));
     }
+    h[C + 1] = make_float2(0.0f, 0.0f);   // "no beam": contributes nothing
     if (!m.lut) {
-        int rc = dev_alloc(ctx, (void **)&m.lut, sizeof(float2) * (kMaxClamp + 1), "likelihood table");
+        int rc = dev_alloc(ctx, (void **)&m.lut, sizeof(float2) * (kMaxClamp + 2), "likelihood table");
         if (rc) return rc;
-        m.bytes += sizeof(float2) * (kMaxClamp + 1);
+        m.bytes += sizeof(float2) * (kMaxClamp + 2);
     }
-    CK(cudaMemcpyAsync(m.lut, h.data(), sizeof(float2) * (C + 1), cudaMemcpyHostToDevice, ctx->stream), "lut upload");
+    CK(cudaMemcpyAsync(m.lut, h.data(), sizeof(float2) * (C + 2), cudaMemcpyHostToDevice, ctx->stream), "lut upload");
     return RELO_OK;
 }
 
@@ -388,10 +396,10 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
-    dev_free(ctx, m.dev.field, sizeof(uint16_t) * 64 * (size_t)m.dev.TW * m.dev.TH);
+    dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * (m.dev.H + 2 * m.dev.P));
     dev_free(ctx, m.dev.bits, sizeof(uint64_t) * (size_t)m.dev.TW * m.dev.TH);
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
-    dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 1));
+    dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
     m = MapSlot();
 }
 
@@ -410,10 +418,14 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     m.dev.TH = (h + 7) / 8;
     int rc = clamp_for(ctx, ctx->p.d_max, res, &m.dev.C);
     if (rc) return rc;
+    m.dev.P = pad_for(ctx->p.max_range, res);
+    if (m.dev.P < 1) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
+    m.dev.Wp = w + 2 * m.dev.P;
     const size_t cells = (size_t)w * h, tiles = (size_t)m.dev.TW * m.dev.TH;
+    const size_t fcells = (size_t)m.dev.Wp * (h + 2 * m.dev.P);
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
-        {(void **)&m.dev.field, tiles * 64 * 2}, {(void **)&m.dev.bits, tiles * 8},
+        {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, tiles * 8},
         {(void **)&m.dev.summ, sizeof(int2) * (size_t)w * edt_segments(h)}};
     for (auto &a : allocs) {
         rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
@@ -425,7 +437,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     }
     cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
-    if (e == cudaSuccess) e = timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = timed(ctx, 0, 5, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -530,6 +542,8 @@ int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float 
     const long long rmax_q16 = llrint(rq);
     if ((double)P->n * (double)rmax_q16 >= 8.0e12)
         return fail(ctx, RELO_E_INVALID_ARG, "beam count x max range too large for the SMAD key");
+    if ((double)max_range / m->res + 1.0 > (double)m->dev.P)
+        return fail(ctx, RELO_E_INVALID_ARG, "scan max_range exceeds the context's max_range (the map's field border)");
     const relo_params &p = ctx->p;
     out->m = m;
     out->P = P;
@@ -579,7 +593,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         ReqDesc &d = desc[r];
         memset(&d, 0, sizeof d);
         d.bits = m.dev.bits;
-        d.field = m.dev.field;
+        d.field = m.dev.field + (size_t)m.dev.P * m.dev.Wp + m.dev.P;
+        d.Wp = m.dev.Wp;
+        d.P = m.dev.P;
         d.lut = m.lut;
         d.W = m.dev.W;
         d.H = m.dev.H;
@@ -955,6 +971,7 @@ void relo_default_params(relo_params *p) {
     p->n_skip_beam = 1;
     p->early_stop = 1;
     p->hbm_budget = 0;
+    p->max_range = 30.0;
 }
 
 int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
@@ -1033,7 +1050,7 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             int C;
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
-            CK(timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
+            CK(timed(ctx, 0, 5, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -1057,7 +1074,7 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 5, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -1067,7 +1084,7 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 5, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 

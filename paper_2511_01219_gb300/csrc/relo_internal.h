@@ -5,7 +5,7 @@
 
 namespace relo {
 
-constexpr int kTile = 8;               // field and bitmap are stored in 8x8-cell tiles
+constexpr int kTile = 8;               // the occupancy bitmap is stored in 8x8-cell tiles
 constexpr int kMaxClamp = 8100;        // C = (d_max/res)^2 <= 90^2 so the TAM table fits shared memory
 constexpr int kMaxValidBeams = 2048;   // register-resident TAM selection holds <= 64 values per lane
 constexpr int kMaxNs = 8192;           // panoramic beam count
@@ -19,7 +19,8 @@ struct MapDev {
     int W = 0, H = 0, TW = 0, TH = 0;
     int C = 0;                  // clamp (d_max / res)^2 used by the TAM field
     int32_t *d2 = nullptr;      // [H*W] exact squared EDT, -1 = no obstacle
-    uint16_t *field = nullptr;  // [TH*TW*64] min(d2, C), 8x8 tiles
+    uint16_t *field = nullptr;  // [(H+2P) * (W+2P)] min(d2, C), row-major with a border of P cells holding C
+    int P = 0, Wp = 0;          // border width and padded row length
     uint64_t *bits = nullptr;   // [TH*TW] occupancy, bit (y&7)*8 + (x&7)
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
     int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
@@ -81,9 +82,9 @@ struct RayArgs {
 struct ReqDesc {
     // map tables
     const uint64_t *bits;
-    const uint16_t *field;
-    const float2 *lut;           // [C+1] (l(b), sqrt(C) - sqrt(b))
-    int W, H, TW, C;
+    const uint16_t *field;       // padded clamped field, pointer to cell (0, 0)
+    const float2 *lut;           // [C+2] (l(b), sqrt(C) - sqrt(b)); entry C+1 = (0, 0) marks "no beam"
+    int W, H, TW, C, Wp, P;
     float res, res2, d_max, d_min;
     double resd, ox, oy;
     // hypotheses

@@ -12,8 +12,9 @@
 //
 // k_tam: one warp per (survivor, orientation m).  For each valid beam i the
 // endpoint cell is hypothesis + round-half-up(R_i * D_{(b_i + m) mod N_s} /
-// 2^46); its clamped squared distance b = min(d2, C) is read from the tiled
-// field (off-map endpoints take C, i.e. d = d_max).  The likelihood l
+// 2^46); its clamped squared distance b = min(d2, C) is read from the padded
+// field, whose border holds C (off-map endpoints take d = d_max), so the read
+// needs no bounds test.  The likelihood l
 // (Eq. 23) falls strictly as b grows, so the descending sort of Eq. 24 is the
 // ascending order of b: the warp finds the k-th smallest b by bisection over
 // [0, C] with register-resident values, and the top-k sum of l is
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // orientation, beam).  The likelihood table is reloaded only when a CTA moves
 // to another request's task.
 template <int VPL>
-__global__ void __launch_bounds__(kTamWarps * 32) k_tam(const ReqDesc *__restrict__ reqs, int R,
+__global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__restrict__ reqs, int R,
                                                        const TamSeg *__restrict__ segs, int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
@@ -160,12 +161,12 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(const ReqDesc *__restric
         __syncthreads();   // the previous task's reads of offs / lut are done
         if (threadIdx.x == 0) s_skip = d.state->done || N <= 0;
         if (s_lut_r != r) {
-            for (int i = threadIdx.x; i <= d.C; i += blockDim.x) lut[i] = d.lut[i];
+            for (int i = threadIdx.x; i <= d.C + 1; i += blockDim.x) lut[i] = d.lut[i];
         }
         __syncthreads();
         if (threadIdx.x == 0) s_lut_r = r;
         if (s_skip) continue;
-        uint32_t *offs = reinterpret_cast<uint32_t *>(smem + (size_t)(d.C + 1) * sizeof(float2));
+        int *offs = reinterpret_cast<int *>(smem + (size_t)(d.C + 2) * sizeof(float2));
         const int local = task - sg.task_base;
         const int q = local % d.n_orient;
         const int chunk = local / d.n_orient;
@@ -177,28 +178,25 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(const ReqDesc *__restric
             const int2 dir = d.D[j];
             const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
             const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
-            offs[i] = ((uint32_t)ox & 0xffffu) | ((uint32_t)oy << 16);
+            offs[i] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
         }
         __syncthreads();
         const int s_lo = sg.s_begin + chunk * sg.chunk;
         const int s_hi = min(sg.s_end, s_lo + sg.chunk);
         const float Nf = (float)N;
-        const int W = d.W, H = d.H, TW = d.TW, C = d.C;
+        const int C = d.C;
+        const uint32_t none = (uint32_t)C + 1u;   // table entry with zero weight
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
             const int2 hc = d.hyps[d.survivors[s]];
+            const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
             uint32_t v[VPL];
             int sumb = 0;
 #pragma unroll
             for (int t = 0; t < VPL; ++t) {
                 const int i = (t << 5) + lane;
-                uint32_t bv = kNoBeam;
+                uint32_t bv = none;
                 if (i < N) {
-                    const uint32_t o = offs[i];
-                    const int ex = hc.x + (int)(short)(o & 0xffffu);
-                    const int ey = hc.y + ((int)o >> 16);
-                    bv = ((unsigned)ex < (unsigned)W && (unsigned)ey < (unsigned)H)
-                             ? (uint32_t)__ldg(d.field + tile_index(ex, ey, TW))
-                             : (uint32_t)C;
+                    bv = (uint32_t)__ldg(fh + offs[i]);
                     sumb += (int)bv;
                 }
                 v[t] = bv;
@@ -219,13 +217,11 @@ __global__ void __launch_bounds__(kTamWarps * 32) k_tam(const ReqDesc *__restric
             int clt = 0;
 #pragma unroll
             for (int t = 0; t < VPL; ++t) {
-                if (v[t] != kNoBeam) {
-                    const float2 lg = lut[v[t]];
-                    sgs += lg.y;
-                    if (v[t] < bk) {
-                        sl += lg.x;
-                        ++clt;
-                    }
+                const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
+                sgs += lg.y;
+                if (v[t] < bk) {
+                    sl += lg.x;
+                    ++clt;
                 }
             }
 #pragma unroll
@@ -305,7 +301,7 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStr
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
                  int max_C, int n_sm, TamSeg *segs) {
     TamPlan tp{0, 0, vpl_bucket(max_beams), 0};
-    tp.smem = (size_t)(max_C + 1) * sizeof(float2) + (size_t)max_beams * sizeof(uint32_t);
+    tp.smem = (size_t)(max_C + 2) * sizeof(float2) + (size_t)max_beams * sizeof(int);
     if (tp.vpl < 0) return tp;
     const int occ = occupancy_for(tp.vpl, tp.smem);
     if (occ < 1) {
