@@ -161,13 +161,17 @@ cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
     int nt = m.TW * m.TH;
     k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.bits);
     uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
-    k_field_border<<<256, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.C);
     size_t smem = (size_t)m.W * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.Wp, m.d2, field00);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_border(const MapDev &m, cudaStream_t s) {
+    k_field_border<<<1024, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.C);
     return cudaGetLastError();
 }
 

@@ -437,7 +437,9 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     }
     cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
-    if (e == cudaSuccess) e = timed(ctx, 0, 5, [&] { return launch_edt(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = launch_field_border(m.dev, ctx->stream);
+    if (e == cudaSuccess) ctx->kernels += 1;
+    if (e == cudaSuccess) e = timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -1050,7 +1052,8 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             int C;
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
-            CK(timed(ctx, 0, 5, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
+            CK(launch_field_border(m.dev, ctx->stream), "map rebuild");
+            CK(timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -1074,7 +1077,7 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 5, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -1084,7 +1087,7 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 5, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 

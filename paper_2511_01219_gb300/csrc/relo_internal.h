@@ -139,7 +139,8 @@ struct TamSeg {
 constexpr int kMaxBatchRequests = 256;
 constexpr int kMaxBatches = 64;      // ceil(K / batch) limit, bounds the TamSeg table
 
-cudaError_t launch_edt(const MapDev &m, cudaStream_t s);
+cudaError_t launch_edt(const MapDev &m, cudaStream_t s);          // interior of the field, d2, bitmap
+cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the field's constant border (once per map)
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);
 cudaError_t launch_synth(const RayArgs &a, uint32_t *ranges, int32_t *hit, cudaStream_t s);

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // orientation, beam).  The likelihood table is reloaded only when a CTA moves
 // to another request's task.
 template <int VPL>
-__global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__restrict__ reqs, int R,
+__global__ void __launch_bounds__(kTamWarps * 32, 3) k_tam(const ReqDesc *__restrict__ reqs, int R,
                                                        const TamSeg *__restrict__ segs, int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
