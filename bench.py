@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--workload", default="office", choices=["office", "batched", "served"],
                     help="office: one request (default); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
-    ap.add_argument("--rates", default="50,200,500,1000,2000", help="served: arrival rates per second")
+    ap.add_argument("--rates", default="100,200,300,400,600,800,1000,1500,2000,3000,4000,6000",
+                    help="served: arrival rates per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals per rate")
     return ap.parse_args()
 
@@ -481,9 +482,18 @@ def run_batched(args, world, rank, local, dist):
 
 
 def run_served(args, world, rank, local, dist):
-    """Poisson arrivals against 8 resident maps: the served form (continuous
-    batching) against the plain one-request-at-a-time GPU pipeline, at the
-    same arrival process, with p50 / p99 latency."""
+    """Poisson arrivals against 8 resident maps, p50 / p99 latency per arrival
+    rate, for four ways of serving the same requests:
+
+    plain           one request at a time (relo_relocalize), rays cast per request
+    plain_tables    one request at a time, synthesized scans read from the
+                    resident per-map tables (scan_cache_bytes)
+    served_cast     continuous batching (relo_serve_start / submit / poll), rays cast
+    served          continuous batching with the resident tables
+
+    Every mode first runs each pooled request once (sensor plans, kernels and,
+    with tables, the tables themselves are then resident: steady state).  A
+    mode's rate ladder stops once its p99 passes 1 s (it is saturated)."""
     import numpy as np
     import torch
 
@@ -495,32 +505,33 @@ def run_served(args, world, rank, local, dist):
     torch.cuda.set_device(local)
     maps = workloads.served_maps()
     pool = workloads.served_scans(maps)
-    ctx = relo.Relo(n_orient=360, topk=256, batch=200, local_topk=20, early_stop=1, tau=0.95, stream="private")
-    mids = []
-    for grid, res, hyps in maps:
-        mid = ctx.load_map(grid, res)
-        ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
-        mids.append(mid)
-    reqs = [(mids[mi], z, a, mr) for (mi, z, a, mr) in pool]
-    for r in reqs:                       # warm every sensor plan and kernel
-        ctx.relocalize(*r)
-    rng = np.random.default_rng(4242)
     rates = [float(x) for x in args.rates.split(",")]
+    table_bytes = 16 << 30
 
-    def arrivals(rate):
+    def make_ctx(tables):
+        ctx = relo.Relo(n_orient=360, topk=256, batch=200, local_topk=20, early_stop=1, tau=0.95, stream="private",
+                        scan_cache_bytes=table_bytes if tables else 0)
+        mids = []
+        for grid, res, hyps in maps:
+            mid = ctx.load_map(grid, res)
+            ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
+            mids.append(mid)
+        reqs = [(mids[mi], z, a, mr) for (mi, z, a, mr) in pool]
+        results = [ctx.relocalize(*r).as_dict() for r in reqs]   # warm plans, kernels, tables
+        return ctx, reqs, results
+
+    def arrivals(rate, seed):
+        rng = np.random.default_rng(seed)
         n = max(1, int(rate * args.duration))
-        t = np.cumsum(rng.exponential(1.0 / rate, size=n))
-        return t, rng.integers(len(reqs), size=n)
+        return np.cumsum(rng.exponential(1.0 / rate, size=n)), rng.integers(len(pool), size=n)
 
     def stats(lat, span):
         lat = np.sort(np.asarray(lat))
         return {"throughput": len(lat) / span, "p50_ms": float(1e3 * lat[len(lat) // 2]),
                 "p99_ms": float(1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]), "n": int(len(lat))}
 
-    plain, served = {}, {}
-    for rate in rates:
-        t_arr, which = arrivals(rate)
-        # plain: one request at a time, in arrival order, each waiting for the previous
+    def run_plain(ctx, reqs, rate, seed):
+        t_arr, which = arrivals(rate, seed)
         lat = []
         t0 = time.perf_counter()
         for ta, w in zip(t_arr, which):
@@ -529,49 +540,81 @@ def run_served(args, world, rank, local, dist):
                 time.sleep(ta - now)
             ctx.relocalize(*reqs[w])
             lat.append(time.perf_counter() - t0 - ta)
-        plain[rate] = stats(lat, time.perf_counter() - t0)
-    ctx.serve_start(max_batch=64, max_inflight=3, hbm_budget=8 << 30)
-    for rate in rates:
-        t_arr, which = arrivals(rate)
+        return stats(lat, time.perf_counter() - t0)
+
+    def run_srv(ctx, reqs, rate, seed, agree):
+        t_arr, which = arrivals(rate, seed)
         lat, pending = [], []
         t0 = time.perf_counter()
         i = 0
         while i < len(t_arr) or pending:
             now = time.perf_counter() - t0
             while i < len(t_arr) and t_arr[i] <= now:
-                pending.append(ctx.submit(*reqs[which[i]]))
+                pending.append((ctx.submit(*reqs[which[i]]), which[i]))
                 i += 1
             still = []
-            for tk in pending:
+            for tk, w in pending:
                 r = ctx.poll(tk)
                 if r is None:
-                    still.append(tk)
+                    still.append((tk, w))
                 else:
                     assert r[0] == relo.OK, r[0]
                     lat.append(r[2])
+                    agree.append(r[1].as_dict() == alone[w])
             pending = still
             if i < len(t_arr) and not pending:
                 time.sleep(max(0.0, min(t_arr[i] - (time.perf_counter() - t0), 0.0005)))
-        served[rate] = stats(lat, time.perf_counter() - t0)
-    ctx.serve_stop()
-    ctx.close()
+        return stats(lat, time.perf_counter() - t0)
 
-    def best(tab):
-        ok = [v["throughput"] for v in tab.values() if v["p99_ms"] <= 50.0]
+    out = {}
+    alone = None
+    tables_info = None
+    for mode in ("plain", "plain_tables", "served_cast", "served"):
+        tables = mode.endswith("tables") or mode == "served"
+        ctx, reqs, results = make_ctx(tables)
+        if alone is None:
+            alone = results
+        assert results == alone, "resident tables changed a result"
+        agree = []
+        tab = {}
+        if mode.startswith("served"):
+            ctx.serve_start(max_batch=64, max_inflight=3, hbm_budget=8 << 30)
+        for k, rate in enumerate(rates):
+            tab[rate] = (run_srv(ctx, reqs, rate, 4242 + k, agree) if mode.startswith("served")
+                         else run_plain(ctx, reqs, rate, 4242 + k))
+            if tab[rate]["p99_ms"] > 1000.0:
+                break
+        if mode.startswith("served"):
+            ctx.serve_stop()
+            out[mode + "_pose_agreement"] = float(np.mean(agree)) if agree else None
+        if tables:
+            tables_info = ctx.scan_cache_stats()
+        out[mode] = {str(k): v for k, v in tab.items()}
+        ctx.close()
+        torch.cuda.synchronize()
+
+    def best(tab, cap=None):
+        ok = [v["throughput"] for k, v in tab.items() if v["p99_ms"] <= 50.0 and (cap is None or float(k) <= cap)]
         return max(ok) if ok else 0.0
-    b_srv, b_pln = best(served), best(plain)
+    bests = {m: best(out[m]) for m in ("plain", "plain_tables", "served_cast", "served")}
+    bests_cfg = {m: best(out[m], 2000.0) for m in bests}
+    b_srv, b_pln = bests["served"], bests["plain"]
     return {
         "metric": METRIC, "value": b_srv, "unit": "relocalizations/s", "n_gpus": world, "steps": len(rates),
-        "warmup": len(reqs), "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "warmup": len(pool), "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32/i64+f32", "data": "synthetic (8 resident maps 512^2..4096^2, pooled noisy scans, Poisson arrivals)",
         "config": {"workload": "served: 8 resident maps (two each of 512^2, 1024^2, 2048^2, 4096^2; 1250/5000/10000/"
                                "20000 hypotheses), Poisson arrivals, beams 541/720/1081/1440, 360 orientations, TAM "
                                "in batches of 200 of the top 256 with tau 0.95; continuous batching (64 per batch, 3 "
-                               "batches in flight, 8 GiB budget) vs one request at a time",
+                               "batches in flight, 8 GiB admission budget, 16 GiB of resident synthesized scans) vs "
+                               "one request at a time",
                    "rates_per_s": rates, "seconds_per_rate": args.duration, "parallelism": "1 GPU"},
-        "served": {str(k): v for k, v in served.items()}, "plain": {str(k): v for k, v in plain.items()},
-        "best_rate_p99_le_50ms": {"served": b_srv, "plain": b_pln,
-                                  "ratio": (b_srv / b_pln) if b_pln > 0 else None},
+        **out,
+        "scan_tables": tables_info,
+        "best_rate_p99_le_50ms": {**bests, "ratio_served_vs_plain": (b_srv / b_pln) if b_pln > 0 else None,
+                                  "ratio_served_vs_plain_tables": (b_srv / bests["plain_tables"])
+                                  if bests["plain_tables"] > 0 else None},
+        "best_rate_p99_le_50ms_rates_le_2000": bests_cfg,
     }
 
 

@@ -68,6 +68,8 @@ typedef struct relo_params {
     int64_t hbm_budget;                                /* bytes the context may hold; 0 = no limit */
     double max_range;                                  /* metres: the longest scan range maps loaded from now on accept
                                                           (sets the border of the TAM field; default 30) */
+    int64_t scan_cache_bytes;                          /* device bytes for resident synthesized scans; 0 = none
+                                                          (see relo_scan_cache_stats) */
 } relo_params;
 
 /* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */
@@ -211,6 +213,23 @@ int relo_get_stage(relo_ctx *ctx, int32_t which, void *dst_dev, int64_t bytes);
 int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n, const float *angles,
                          int32_t n_beams, float max_range, uint32_t *ranges_dev, int32_t *hit_dev, int64_t capacity,
                          int32_t *ns_out);
+
+/* Resident synthesized scans.  The panoramic synthesized scan of a
+ * hypothesis (Eq. 13) depends on the map, the hypothesis, the beam grid N_s
+ * and the range limit only, never on the real scan, so with
+ * scan_cache_bytes > 0 the context keeps, per loaded map, one table of
+ * N_h x N_s uint32 Q16 ranges for each (N_s, max_range) it has served: the
+ * first request with that sensor geometry casts its rays and stores them,
+ * later ones read the table instead of casting (the SMAD, TAM and selection
+ * results are identical either way).  Tables count against hbm_budget too;
+ * beyond scan_cache_bytes the least recently used ones are freed (after the
+ * device finishes its queued work).  Loading a new grid into a map
+ * (relo_update_map*), setting its hypotheses, unloading it or changing the
+ * parameters frees its tables.
+ * relo_scan_cache_stats writes min(n, 5) counters to out: tables held, bytes
+ * held, requests that read a table, requests that cast their rays (and
+ * stored them when the budget allowed), tables evicted. */
+int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
 
 /* Stage timing (tracing).  With profiling on, the context records a CUDA
  * event pair on its stream around every kernel it launches and sums the

@@ -40,7 +40,7 @@ EXPORTED = [
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
-    "relo_serve_stop",
+    "relo_serve_stop", "relo_scan_cache_stats",
 ]
 STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
 
@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("panoramic_ratio", ctypes.c_double), ("n_orient", ctypes.c_int32),
         ("topk", ctypes.c_int32), ("batch", ctypes.c_int32), ("local_topk", ctypes.c_int32),
         ("n_skip_beam", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-        ("max_range", ctypes.c_double),
+        ("max_range", ctypes.c_double), ("scan_cache_bytes", ctypes.c_int64),
     ]
 
 
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
             "relo_submit": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
             "relo_poll": (ctypes.c_int, [P, I64, P, P]),
             "relo_serve_stop": (ctypes.c_int, [P]),
+            "relo_scan_cache_stats": (ctypes.c_int, [P, P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -293,6 +294,12 @@ class Relo:
 
     def dda_steps(self) -> int:
         return int(self.scan_info()[8])
+
+    def scan_cache_stats(self) -> dict:
+        """Resident synthesized scans: tables and bytes held, requests that read a table, requests that cast, evictions."""
+        v = (ctypes.c_int64 * 5)()
+        self._check(self._L.relo_scan_cache_stats(self._h, v, 5), "scan_cache_stats")
+        return dict(zip(["tables", "bytes", "hits", "misses", "evictions"], list(v)))
 
     def kernels_launched(self) -> int:
         k = ctypes.c_int64(0)

@@ -19,6 +19,13 @@
 // a hit is floor(sqrt(|d|^2 * 2^32)) (cells, Q16), else 0 (the placeholder of
 // the invalid beam).  Occupancy comes from the 8x8-tile bitmap; the current
 // tile's 64-bit word stays in a register until the ray leaves the tile.
+//
+// A panoramic synthesized scan depends only on the map, the hypothesis, the
+// beam grid N_s and the range limit, not on the real scan.  A request may
+// therefore store its ranges into a resident table (kScanStore) or, when an
+// earlier launch stored them for the same map, hypotheses, N_s and limit,
+// read them from it (kScanRead) instead of casting; the SMAD arithmetic is
+// the same in all three modes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -222,21 +229,32 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__r
         uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
         long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(ns_pad));
         if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
-        const int2 hc = d.hyps[h];
-        const uint64_t *bits = d.bits;
-        const int2 *D = d.D;
-        const int W = d.W, H = d.H, TW = d.TW, lim = d.lim;
-        for (;;) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&s_next, 1);
-            c = __shfl_sync(kFull, c, 0);
-            if (c >= nch) break;
-            const int j = (c << 5) + lane;
-            uint32_t r = 0u;
-            int hit, steps = 0;
-            if (j < ns) r = cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
-            my_steps += (unsigned)steps;
-            inner[j] = r;
+        const int mode = d.scan_mode;
+        if (mode == kScanRead) {
+            // resident ranges: one coalesced pass over the hypothesis's row
+            const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
+            for (int j = threadIdx.x; j < ns_pad; j += blockDim.x) inner[j] = j < ns ? __ldg(row + j) : 0u;
+        } else {
+            uint32_t *row = mode == kScanStore ? d.scan_table + (size_t)h * ns : nullptr;
+            const int2 hc = d.hyps[h];
+            const uint64_t *bits = d.bits;
+            const int2 *D = d.D;
+            const int W = d.W, H = d.H, TW = d.TW, lim = d.lim;
+            for (;;) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&s_next, 1);
+                c = __shfl_sync(kFull, c, 0);
+                if (c >= nch) break;
+                const int j = (c << 5) + lane;
+                uint32_t r = 0u;
+                int hit, steps = 0;
+                if (j < ns) {
+                    r = cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
+                    if (row) row[j] = r;
+                }
+                my_steps += (unsigned)steps;
+                inner[j] = r;
+            }
         }
         __syncthreads();
         for (int c = warp; c < nch; c += nwarps) {

@@ -39,6 +39,17 @@ struct SensorPlan {
     unsigned long long last_use = 0;
 };
 
+// Resident synthesized scans of one map and hypothesis set for one beam grid
+// N_s and range limit: [n_hyp * ns] uint32 Q16 ranges, row per hypothesis.
+struct ScanTable {
+    int ns = 0, lim = 0;
+    uint32_t *data = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t written = nullptr;    // recorded after the ray-cast launch that stores the table
+    unsigned long long last_use = 0;
+    unsigned long long pin = 0;       // batch sequence number of the last batch that used it
+};
+
 struct MapSlot {
     bool live = false;
     MapDev dev;
@@ -47,6 +58,7 @@ struct MapSlot {
     int n_hyp = 0, hyp_cap = 0;
     float2 *lut = nullptr;
     size_t bytes = 0;
+    std::vector<ScanTable *> tables;
 };
 
 // One request prepared for a batch.
@@ -122,6 +134,9 @@ struct relo_ctx {
     ReqDesc last{};
     BatchState *last_bs = nullptr;
     bool has_last = false;
+    // resident synthesized scans
+    long long table_bytes = 0, cache_hits = 0, cache_misses = 0, cache_evictions = 0;
+    unsigned long long table_clock = 0, batch_seq = 0;
 };
 
 namespace {
@@ -219,6 +234,7 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
     if (p.n_skip_beam < 1) return fail(ctx, RELO_E_INVALID_ARG, "n_skip_beam must be >= 1");
     if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
     if (!(p.max_range > 0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
+    if (p.scan_cache_bytes < 0) return fail(ctx, RELO_E_INVALID_ARG, "scan_cache_bytes must be >= 0");
     return RELO_OK;
 }
 
@@ -391,7 +407,87 @@ MapSlot *get_map(relo_ctx *ctx, int id) {
     return &ctx->maps[id];
 }
 
+// ---- resident synthesized scans ------------------------------------------------------------------
+
+void free_table(relo_ctx *ctx, ScanTable *t) {
+    dev_free(ctx, t->data, t->bytes);
+    ctx->table_bytes -= (long long)t->bytes;
+    if (t->written) cudaEventDestroy(t->written);
+    delete t;
+}
+
+// Frees every table of the map, once the device has finished the work that may read them.
+void drop_tables(relo_ctx *ctx, MapSlot &m) {
+    if (m.tables.empty()) return;
+    cudaDeviceSynchronize();
+    for (ScanTable *t : m.tables) free_table(ctx, t);
+    m.tables.clear();
+}
+
+ScanTable *find_table(MapSlot &m, int ns, int lim) {
+    for (ScanTable *t : m.tables)
+        if (t->ns == ns && t->lim == lim) return t;
+    return nullptr;
+}
+
+// Evicts least recently used tables not used by the batch being built until
+// `need` more bytes fit the scan-cache budget; false when they cannot.
+bool make_room(relo_ctx *ctx, size_t need) {
+    const long long cap = ctx->p.scan_cache_bytes;
+    if ((long long)need > cap) return false;
+    bool synced = false;
+    while (ctx->table_bytes + (long long)need > cap) {
+        ScanTable *victim = nullptr;
+        MapSlot *owner = nullptr;
+        for (MapSlot &m : ctx->maps) {
+            if (!m.live) continue;
+            for (ScanTable *t : m.tables)
+                if (t->pin != ctx->batch_seq && (!victim || t->last_use < victim->last_use)) {
+                    victim = t;
+                    owner = &m;
+                }
+        }
+        if (!victim) return false;
+        if (!synced) {
+            cudaDeviceSynchronize();   // queued batches may still read it
+            synced = true;
+        }
+        owner->tables.erase(std::find(owner->tables.begin(), owner->tables.end(), victim));
+        free_table(ctx, victim);
+        ++ctx->cache_evictions;
+    }
+    return true;
+}
+
+// A new, unwritten table for (m, ns, lim), or nullptr when the budget (or
+// the context's HBM budget) cannot hold it; failing here is not an error.
+ScanTable *new_table(relo_ctx *ctx, MapSlot &m, int ns, int lim) {
+    const size_t bytes = sizeof(uint32_t) * (size_t)m.n_hyp * (size_t)ns;
+    if (!make_room(ctx, bytes)) return nullptr;
+    ScanTable *t = new (std::nothrow) ScanTable();
+    if (!t) return nullptr;
+    const std::string saved = ctx->err;
+    if (dev_alloc(ctx, (void **)&t->data, bytes, "scan table") != RELO_OK) {
+        ctx->err = saved;
+        delete t;
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&t->written, cudaEventDisableTiming) != cudaSuccess) {
+        t->written = nullptr;
+        dev_free(ctx, t->data, bytes);
+        delete t;
+        return nullptr;
+    }
+    t->ns = ns;
+    t->lim = lim;
+    t->bytes = bytes;
+    ctx->table_bytes += (long long)bytes;
+    m.tables.push_back(t);
+    return t;
+}
+
 void free_map(relo_ctx *ctx, MapSlot &m) {
+    drop_tables(ctx, m);
     dev_free(ctx, m.dev.d2, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
@@ -480,6 +576,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
 int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, int n) {
     int rc = RELO_OK;
     if (n > (1 << kHypBits)) return fail(ctx, RELO_E_INVALID_ARG, "too many hypotheses (max 2^21)");
+    drop_tables(ctx, m);
     if (n > m.hyp_cap) {
         dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
         m.hyps = nullptr;
@@ -588,6 +685,52 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     }
     int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
     if (rc) return rc;
+    // Resident synthesized scans: read a table stored by an earlier launch, or
+    // store a new one (one writer per table; other requests of this batch
+    // with the same geometry cast).  Tables this batch creates are freed again
+    // if the batch fails to launch.
+    ++ctx->batch_seq;
+    std::vector<ScanTable *> tab((size_t)R, nullptr);
+    std::vector<int> mode((size_t)R, kScanCast);
+    struct Created {
+        relo_ctx *ctx;
+        std::vector<std::pair<MapSlot *, ScanTable *>> list;
+        bool keep = false;
+        ~Created() {
+            if (keep || list.empty()) return;
+            cudaDeviceSynchronize();
+            for (auto &x : list) {
+                auto &v = x.first->tables;
+                v.erase(std::find(v.begin(), v.end(), x.second));
+                free_table(ctx, x.second);
+            }
+        }
+    } created{ctx, {}, false};
+    if (p.scan_cache_bytes > 0) {
+        for (int r = 0; r < R; ++r) {
+            MapSlot &m = *pr[r].m;
+            ScanTable *t = find_table(m, pr[r].P->ns, pr[r].lim);
+            bool fresh = false;
+            for (auto &x : created.list) fresh = fresh || x.second == t;
+            if (t && !fresh) {
+                mode[r] = kScanRead;
+                ++ctx->cache_hits;
+            } else {
+                ++ctx->cache_misses;
+                if (!t && (t = new_table(ctx, m, pr[r].P->ns, pr[r].lim))) {
+                    mode[r] = kScanStore;
+                    created.list.push_back({&m, t});
+                } else {
+                    t = nullptr;
+                }
+            }
+            if (t) {
+                t->last_use = ++ctx->table_clock;
+                t->pin = ctx->batch_seq;
+                tab[r] = t;
+            }
+        }
+    }
     for (int r = 0; r < R; ++r) {
         const Prepared &q = pr[r];
         const MapSlot &m = *q.m;
@@ -654,6 +797,8 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.local = (int32_t *)take(4ull * q.n_batches * p.local_topk);
         d.state = (SelectState *)take(sizeof(SelectState));
         d.result = q.result_dev;
+        d.scan_table = tab[r] ? tab[r]->data : nullptr;
+        d.scan_mode = mode[r];
     }
     int base = 0;
     for (int r = 0; r < R; ++r) {
@@ -680,8 +825,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         return rc;
     ReqDesc *rq = sl.reqs_dev;
     CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
+    for (int r = 0; r < R; ++r)
+        if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
     CK(timed_on(ctx, st, 2, 1, [&] { return launch_raycast_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
        "ray cast + SMAD");
+    for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {
         const TamSeg *sg = sl.segs_dev + (size_t)bi * R;
@@ -689,6 +837,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, st); }), "batch selection");
     }
     CK(timed_on(ctx, st, 5, 1, [&] { return launch_finalize(rq, R, st); }), "finalize");
+    created.keep = true;
     ctx->last = desc[0];
     ctx->last_bs = sl.bs;
     ctx->has_last = true;
@@ -1044,6 +1193,8 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
     const bool lut_changed = p->z_hit != ctx->p.z_hit || p->sigma_hit != ctx->p.sigma_hit ||
                              p->z_rand != ctx->p.z_rand || p->eps != ctx->p.eps || p->d_max != ctx->p.d_max;
     ctx->p = *p;
+    for (auto &m : ctx->maps)
+        if (m.live) drop_tables(ctx, m);
     for (SensorPlan *P : ctx->plans) free_plan(ctx, P);   // plans depend on n_orient, n_skip and Eq. 25
     ctx->plans.clear();
     if (lut_changed) {
@@ -1075,6 +1226,7 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     if (!ctx || !grid_dev) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    drop_tables(ctx, *m);
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
     CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
@@ -1085,6 +1237,7 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     if (!ctx || !grid) return fail(ctx, RELO_E_INVALID_ARG, "null argument");
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    drop_tables(ctx, *m);
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
     CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
@@ -1333,6 +1486,16 @@ int relo_poll(relo_ctx *ctx, int64_t ticket, relo_result *out, double *latency_s
 int relo_serve_stop(relo_ctx *ctx) {
     if (!ctx) return RELO_E_INVALID_ARG;
     serve_shutdown(ctx);
+    return RELO_OK;
+}
+
+int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {
+    if (!ctx || (!out && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    long long tables = 0;
+    for (const MapSlot &m : ctx->maps)
+        if (m.live) tables += (long long)m.tables.size();
+    const long long v[5] = {tables, ctx->table_bytes, ctx->cache_hits, ctx->cache_misses, ctx->cache_evictions};
+    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
     return RELO_OK;
 }
 

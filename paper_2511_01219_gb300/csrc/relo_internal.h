@@ -120,7 +120,15 @@ struct ReqDesc {
     void *result;                // relo_result in device memory
     // work lists
     int hyp_base;                // first slot of this request in the batch's hypothesis list
+    // resident synthesized scans of (map, hypotheses, N_s, lim): [n_hyp * ns] Q16 ranges
+    uint32_t *scan_table;
+    int scan_mode;               // kScanCast, kScanStore or kScanRead
 };
+
+// How the ray-cast stage obtains a request's synthesized ranges.
+constexpr int kScanCast = 0;     // cast every ray
+constexpr int kScanStore = 1;    // cast every ray and store the ranges into scan_table
+constexpr int kScanRead = 2;     // read the ranges from scan_table (written by an earlier launch)
 
 // Counters shared by the whole batch.
 struct BatchState {

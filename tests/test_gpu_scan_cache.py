@@ -1,0 +1,217 @@
+"""Resident synthesized scans: reading a stored table gives the same results as casting.
+
+The synthesized panoramic scan of a hypothesis (Eq. 13) depends on the map,
+the hypothesis, N_s and the range limit only, so a table stored by one
+request and read by a later one must reproduce every integer stage output
+bit for bit and every TAM score exactly (the same arithmetic runs on the same
+ranges).  The path that casts is itself checked against the oracle in
+test_gpu_parity.py; here every comparison is against a context without the
+cache.  Also covered: invalidation when the map or the hypotheses change,
+LRU eviction under a small budget, two requests of one geometry in one batch,
+and the served form.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+GIB = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def relo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    return relo
+
+
+def stage_arrays(relo, ctx, n_hyp, K, n_orient):
+    import torch
+    out = {}
+    for name, which, n, dt in (("num", relo.STAGE_SMAD_NUM, n_hyp, torch.int64),
+                               ("m", relo.STAGE_SMAD_M, n_hyp, torch.int32),
+                               ("surv", relo.STAGE_SURVIVORS, K, torch.int32),
+                               ("T", relo.STAGE_TAM, K * n_orient, torch.float32),
+                               ("best_m", relo.STAGE_BEST_M, K, torch.int32)):
+        out[name] = ctx.stage(which, torch.empty(n, dtype=dt, device="cuda")).cpu().numpy()
+    out["T"] = out["T"].view(np.uint32)   # bitwise, NaN (unscored) included
+    return out
+
+
+def assert_same(a, b):
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def fresh_result(relo, grid, res, hyps, z, ang, mr, **params):
+    ctx = relo.Relo(**params)
+    mid = ctx.load_map(grid, res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, res))
+    out = ctx.relocalize(mid, z, ang, mr).as_dict()
+    ctx.close()
+    return out
+
+
+def test_office_table_read_equals_cast(relo, workload):
+    wl = workload(1)
+    K, n_orient = 256, wl.n_orient
+    plain = relo.Relo(n_orient=n_orient, topk=K, early_stop=0)
+    cached = relo.Relo(n_orient=n_orient, topk=K, early_stop=0, scan_cache_bytes=GIB)
+    ids = []
+    for ctx in (plain, cached):
+        mid = ctx.load_map(wl.grid, wl.res)
+        ctx.set_hypotheses(mid, workloads.cell_centres(wl.hyps, wl.res))
+        ids.append(mid)
+    want = plain.relocalize(ids[0], wl.ranges, wl.angles, wl.max_range).as_dict()
+    want_st = stage_arrays(relo, plain, len(wl.hyps), K, n_orient)
+    for rep in range(3):
+        got = cached.relocalize(ids[1], wl.ranges, wl.angles, wl.max_range).as_dict()
+        assert got == want
+        assert_same(stage_arrays(relo, cached, len(wl.hyps), K, n_orient), want_st)
+        st = cached.scan_cache_stats()
+        assert st["tables"] == 1 and st["misses"] == 1 and st["hits"] == rep
+        assert st["bytes"] == 4 * len(wl.hyps) * 1440
+        info = cached.scan_info()
+        assert (info[8] == 0) == (rep > 0)   # no ray is cast once the table is stored
+    plain.close()
+    cached.close()
+
+
+def small_map(seed=5, n=128, n_hyp=400):
+    g = workloads.make_office(seed, n=n)
+    free = np.argwhere(g == 0)[:, ::-1]
+    hyps = free[np.random.default_rng(seed).choice(len(free), n_hyp, replace=False)].astype(np.int32)
+    return g, hyps
+
+
+def scan_from(g, hyps, idx, n_beams, ns, theta, mr=4.0, seed=0):
+    ang = workloads.beam_angles(n_beams, ns)
+    h = hyps[idx]
+    z = workloads.render_scan(g, 0.05, ((h[0] + 0.5) * 0.05, (h[1] + 0.5) * 0.05, theta), ang, mr)
+    return workloads.add_noise(z, mr, seed), ang
+
+
+def test_tables_dropped_on_map_and_hypothesis_change(relo):
+    g, hyps = small_map()
+    z, ang = scan_from(g, hyps, 17, 90, 120, 0.4)
+    prm = dict(n_orient=40, topk=24, batch=8, local_topk=4, early_stop=0, max_range=5.0)
+    ctx = relo.Relo(scan_cache_bytes=GIB, **prm)
+    mid = ctx.load_map(g, 0.05)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == fresh_result(relo, g, 0.05, hyps, z, ang, 4.0, **prm)
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == fresh_result(relo, g, 0.05, hyps, z, ang, 4.0, **prm)
+    assert ctx.scan_cache_stats()["hits"] == 1
+    # a new obstacle changes the synthesized scans: the stored table must not be read
+    g2 = g.copy()
+    free = np.argwhere(g2 == 0)
+    occupied = set()
+    for (y, x) in free[np.random.default_rng(1).choice(len(free), 300, replace=False)]:
+        g2[y, x] = 100
+        occupied.add((x, y))
+    keep = np.array([(int(h[0]), int(h[1])) not in occupied for h in hyps])
+    ctx.update_map(mid, g2)
+    assert ctx.scan_cache_stats()["tables"] == 0
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps[keep], 0.05))
+    want = fresh_result(relo, g2, 0.05, hyps[keep], z, ang, 4.0, **prm)
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    # another hypothesis set on the same map
+    sub = hyps[keep][::3]
+    ctx.set_hypotheses(mid, workloads.cell_centres(sub, 0.05))
+    assert ctx.scan_cache_stats()["tables"] == 0
+    want = fresh_result(relo, g2, 0.05, sub, z, ang, 4.0, **prm)
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    st = ctx.scan_cache_stats()
+    assert st["hits"] == 3 and st["misses"] == 3
+    ctx.close()
+
+
+def test_small_budget_evicts_least_recently_used(relo):
+    g, hyps = small_map(seed=6)
+    za, anga = scan_from(g, hyps, 3, 90, 120, 1.0, seed=1)     # N_s 120: 192000-byte table
+    zb, angb = scan_from(g, hyps, 9, 100, 160, -2.0, seed=2)   # N_s 160: 256000-byte table
+    prm = dict(n_orient=40, topk=16, batch=8, local_topk=4, early_stop=1, tau=0.9, max_range=5.0)
+    want_a = fresh_result(relo, g, 0.05, hyps, za, anga, 4.0, **prm)
+    want_b = fresh_result(relo, g, 0.05, hyps, zb, angb, 4.0, **prm)
+    ctx = relo.Relo(scan_cache_bytes=300000, **prm)
+    mid = ctx.load_map(g, 0.05)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+    for which in "ababaa":
+        z, ang, want = (za, anga, want_a) if which == "a" else (zb, angb, want_b)
+        assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    st = ctx.scan_cache_stats()
+    assert st == {"tables": 1, "bytes": 192000, "hits": 1, "misses": 5, "evictions": 4}
+    ctx.close()
+    # a table larger than the whole budget is never stored
+    ctx = relo.Relo(scan_cache_bytes=1000, **prm)
+    mid = ctx.load_map(g, 0.05)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+    for _ in range(2):
+        assert ctx.relocalize(mid, za, anga, 4.0).as_dict() == want_a
+    assert ctx.scan_cache_stats() == {"tables": 0, "bytes": 0, "hits": 0, "misses": 2, "evictions": 0}
+    ctx.close()
+
+
+def test_one_geometry_twice_in_one_batch(relo):
+    g, hyps = small_map(seed=7)
+    z1, ang = scan_from(g, hyps, 5, 90, 120, 0.3, seed=3)
+    z2, _ = scan_from(g, hyps, 50, 90, 120, 2.5, seed=4)
+    prm = dict(n_orient=40, topk=16, batch=8, local_topk=4, early_stop=0, max_range=5.0)
+    want = [fresh_result(relo, g, 0.05, hyps, z, ang, 4.0, **prm) for z in (z1, z2)]
+    ctx = relo.Relo(scan_cache_bytes=GIB, **prm)
+    mid = ctx.load_map(g, 0.05)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+    items = [(mid, z1, ang, 4.0), (mid, z2, ang, 4.0)]
+    # first batch: request 0 stores the table, request 1 casts; second batch: both read
+    for _ in range(2):
+        assert [r.as_dict() for r in ctx.relocalize_batch(items)] == want
+    assert ctx.scan_cache_stats() == {"tables": 1, "bytes": 4 * len(hyps) * 120, "hits": 2, "misses": 2,
+                                      "evictions": 0}
+    ctx.close()
+
+
+def test_served_stream_with_tables_equals_alone(relo):
+    """Served form with resident scans: requests on several maps and sensors,
+    in waves while others run, each give their alone (uncached) result."""
+    prm = dict(n_orient=40, topk=16, batch=8, local_topk=4, early_stop=1, tau=0.9, max_range=5.0)
+    plain = relo.Relo(**prm)
+    served = relo.Relo(scan_cache_bytes=GIB, **prm)
+    reqs_plain, reqs_served = [], []
+    for seed in (11, 12):
+        g, hyps = small_map(seed=seed, n=96 + 32 * (seed - 11), n_hyp=300 + 100 * (seed - 11))
+        for ctx, reqs in ((plain, reqs_plain), (served, reqs_served)):
+            mid = ctx.load_map(g, 0.05)
+            ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+            for k, (nb, ns) in enumerate(((90, 120), (100, 160), (120, 120))):
+                z, ang = scan_from(g, hyps, 7 * k + seed, nb, ns, 0.5 * k - 1.0, seed=seed + k)
+                reqs.append((mid, z, ang, 4.0))
+    alone = [plain.relocalize(*r).as_dict() for r in reqs_plain]
+    served.serve_start(max_batch=3, max_inflight=2)
+    order = [(5 * i) % len(reqs_served) for i in range(24)]
+    tickets = [served.submit(*reqs_served[i]) for i in order[:10]]
+    tickets += [served.submit(*reqs_served[i]) for i in order[10:]]
+    import time
+    got, t0 = {}, time.time()
+    while len(got) < len(tickets):
+        for t in tickets:
+            if t not in got:
+                r = served.poll(t)
+                if r is not None:
+                    got[t] = r
+        assert time.time() - t0 < 60.0
+        time.sleep(0.001)
+    served.serve_stop()
+    for i, t in zip(order, tickets):
+        status, res, lat = got[t]
+        assert status == relo.OK and res.as_dict() == alone[i]
+    st = served.scan_cache_stats()
+    assert st["tables"] == 4 and st["hits"] > 0 and st["hits"] + st["misses"] == len(tickets)
+    plain.close()
+    served.close()
