@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--workload", default="office", choices=["office", "batched", "served"],
                     help="office: one request (default); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
-    ap.add_argument("--rates", default="100,200,300,400,600,800,1000,1500,2000,3000,4000,6000",
+    ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,2200,2400,2600,2800,3000,3500,4000,5000,6000",
                     help="served: arrival rates per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals per rate")
     return ap.parse_args()
@@ -589,6 +589,15 @@ def run_served(args, world, rank, local, dist):
             out[mode + "_pose_agreement"] = float(np.mean(agree)) if agree else None
         if tables:
             tables_info = ctx.scan_cache_stats()
+        if not mode.startswith("served"):
+            # device time per stage for one pass over the pool, one request at a time
+            ctx.stage_times(reset=True)
+            ctx.set_profiling(True)
+            for r in reqs:
+                ctx.relocalize(*r)
+            ms, _, _ = ctx.stage_times(reset=True)
+            ctx.set_profiling(False)
+            out[mode + "_stage_ms_per_request"] = {k: round(v / len(reqs), 5) for k, v in ms.items()}
         out[mode] = {str(k): v for k, v in tab.items()}
         ctx.close()
         torch.cuda.synchronize()
@@ -611,6 +620,9 @@ def run_served(args, world, rank, local, dist):
                    "rates_per_s": rates, "seconds_per_rate": args.duration, "parallelism": "1 GPU"},
         **out,
         "scan_tables": tables_info,
+        "pool": {"requests": len(pool),
+                 "tam_batches_mean": float(np.mean([r["n_batches"] for r in alone])),
+                 "early_stopped_fraction": float(np.mean([r["n_batches"] < -(-256 // 200) for r in alone]))},
         "best_rate_p99_le_50ms": {**bests, "ratio_served_vs_plain": (b_srv / b_pln) if b_pln > 0 else None,
                                   "ratio_served_vs_plain_tables": (b_srv / bests["plain_tables"])
                                   if bests["plain_tables"] > 0 else None},

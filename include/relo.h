@@ -70,6 +70,9 @@ typedef struct relo_params {
                                                           (sets the border of the TAM field; default 30) */
     int64_t scan_cache_bytes;                          /* device bytes for resident synthesized scans; 0 = none
                                                           (see relo_scan_cache_stats) */
+    int32_t ray_tables;                                /* 1 (default): trace rays tile by tile with per-direction
+                                                          tables built once per (N_s, max_range); 0: step cell by
+                                                          cell.  Same cells and ranges either way. */
 } relo_params;
 
 /* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */

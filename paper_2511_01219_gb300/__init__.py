@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("panoramic_ratio", ctypes.c_double), ("n_orient", ctypes.c_int32),
         ("topk", ctypes.c_int32), ("batch", ctypes.c_int32), ("local_topk", ctypes.c_int32),
         ("n_skip_beam", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-        ("max_range", ctypes.c_double), ("scan_cache_bytes", ctypes.c_int64),
+        ("max_range", ctypes.c_double), ("scan_cache_bytes", ctypes.c_int64), ("ray_tables", ctypes.c_int32),
     ]
 
 

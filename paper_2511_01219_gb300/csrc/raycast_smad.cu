@@ -169,6 +169,113 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
     return r;
 }
 
+// Tile walk with the per-direction tables (RayTables).  The ray moves from
+// tile to tile: in a tile whose occupancy word is not zero, the table's bit
+// board of the cells still ahead (anchored at the current cell) is shifted
+// onto the tile and ANDed with the word; the first set bit in the ray's
+// order (rows in the y direction of travel, then columns in the x direction,
+// which is the order of the cells along any monotone staircase) is the hit.
+// Otherwise the ray leaves the tile at the cell of step
+// min(selx[|dx| + nx], sely[|dy| + ny]), nx and ny being the x- and y-steps to
+// the tile's far edges.  Same cells, same hit, same range as cast_ray.
+__device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, int W, int H, int TW,
+                                             const RayTables &t, int ns, int j, int hx, int hy, int2 d, int *hit,
+                                             int *steps) {
+    const bool xneg = d.x <= 0, yneg = d.y <= 0;
+    int adx = 0, ady = 0, cx = hx, cy = hy;
+    for (;;) {
+        const uint64_t word = __ldg(bits + (size_t)(cy >> 3) * TW + (cx >> 3));
+        const int lx = cx & 7, ly = cy & 7;
+        if (word) {
+            const uint64_t R = __ldg(t.mask + (size_t)(adx + ady) * ns + j);
+            const uint32_t kb = xneg ? ((0xffu << (7 - lx)) & 0xffu) : (0xffu >> lx);
+            const int A = (xneg ? 0 : lx) + (yneg ? 0 : 8 * ly);
+            const int B = (xneg ? 7 - lx : 0) + (yneg ? 8 * (7 - ly) : 0);
+            const uint64_t hm = (((R & (0x0101010101010101ull * kb)) << A) >> B) & word;
+            if (hm) {
+                const int r = yneg ? (63 - __clzll((long long)hm)) >> 3 : (__ffsll((long long)hm) - 1) >> 3;
+                const uint32_t row = (uint32_t)(hm >> (8 * r)) & 0xffu;
+                const int c = xneg ? 31 - __clz((int)row) : __ffs((int)row) - 1;
+                adx += c > lx ? c - lx : lx - c;
+                ady += r > ly ? r - ly : ly - r;
+                cx += c - lx;
+                cy += r - ly;
+                *hit = cy * W + cx;
+                *steps = adx + ady;
+                return isqrt_q16(adx * adx + ady * ady);
+            }
+        }
+        const int nx = xneg ? lx + 1 : 8 - lx, ny = yneg ? ly + 1 : 8 - ly;
+        const uint32_t kx = __ldg(t.selx + (size_t)(adx + nx) * ns + j);
+        const uint32_t ky = __ldg(t.sely + (size_t)(ady + ny) * ns + j);
+        if (kx == kSelNone && ky == kSelNone) {   // the next cell lies beyond the range limit
+            *hit = -1;
+            *steps = __ldg(t.kmax + j) + 1;
+            return 0u;
+        }
+        if (kx < ky) {
+            adx += nx;
+            ady = (int)kx - adx;
+        } else {
+            ady += ny;
+            adx = (int)ky - ady;
+        }
+        cx = xneg ? hx - adx : hx + adx;
+        cy = yneg ? hy - ady : hy + ady;
+        if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {   // left the map
+            *hit = -1;
+            *steps = adx + ady;
+            return 0u;
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    return ((uint64_t)__byte_perm(lo, 0u, 0x0123u) << 32) | (uint64_t)__byte_perm(hi, 0u, 0x0123u);
+}
+
+// One thread per direction: the DDA of cast_ray from (0, 0), recorded.  The
+// forward pass writes the step indexes into selx / sely and, as scratch, the
+// kind of step k + 1 into mask row k; the backward pass turns those into the
+// bit boards, mask(k) = cell k plus mask(k + 1) moved one cell back along
+// step k + 1 (cells that fall off the 8x8 board are dropped), mirrored for
+// storage as RayTables describes.  mask rows must start at 0 and selx / sely
+// at kSelNone.
+__global__ void k_ray_tables(const int2 *__restrict__ D, int ns, int lim, uint64_t *mask, uint16_t *selx,
+                             uint16_t *sely, int32_t *kmax) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    const int2 d = D[j];
+    const int ax = d.x < 0 ? -d.x : d.x, ay = d.y < 0 ? -d.y : d.y;
+    const bool xneg = d.x <= 0, yneg = d.y <= 0;
+    int e = ax - ay, adx = 0, ady = 0, k = 0;
+    for (;;) {
+        const bool xs = e >= 0;
+        const long long nx = adx + (xs ? 1 : 0), ny = ady + (xs ? 0 : 1);
+        if (nx * nx + ny * ny > (long long)lim) break;
+        mask[(size_t)k * ns + j] = xs ? 1ull : 0ull;
+        e = xs ? (int)((uint32_t)e - 2u * (uint32_t)ay) : (int)((uint32_t)e + 2u * (uint32_t)ax);
+        adx = (int)nx;
+        ady = (int)ny;
+        ++k;
+        if (xs) selx[(size_t)adx * ns + j] = (uint16_t)k;
+        else sely[(size_t)ady * ns + j] = (uint16_t)k;
+    }
+    kmax[j] = k;
+    uint64_t R = 1ull;
+    for (int kk = k; kk >= 0; --kk) {
+        if (kk < k) {
+            const bool xs = mask[(size_t)kk * ns + j] != 0ull;
+            R = 1ull | (xs ? ((R & ~0x8080808080808080ull) << 1) : (R << 8));
+        }
+        uint64_t v = kk == 0 ? (R & ~1ull) : R;   // the start cell itself is never tested
+        if (xneg) v = bswap64(__brevll(v));        // mirror x: reverse the bits of every row
+        if (yneg) v = bswap64(v);                  // mirror y: reverse the rows
+        mask[(size_t)kk * ns + j] = v;
+    }
+}
+
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -249,7 +356,8 @@ __global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__r
                 uint32_t r = 0u;
                 int hit, steps = 0;
                 if (j < ns) {
-                    r = cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
+                    r = d.rt.mask ? walk_ray(bits, W, H, TW, d.rt, ns, j, hc.x, hc.y, D[j], &hit, &steps)
+                                  : cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
                     if (row) row[j] = r;
                 }
                 my_steps += (unsigned)steps;
@@ -334,7 +442,8 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
     const int2 hc = a.hyps[warp];
     for (int j = lane; j < a.ns; j += 32) {
         int hit, steps;
-        uint32_t r = cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
+        uint32_t r = a.tab.mask ? walk_ray(a.bits, a.W, a.H, a.TW, a.tab, a.ns, j, hc.x, hc.y, a.D[j], &hit, &steps)
+                                : cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
         ranges[(size_t)warp * a.ns + j] = r;
         if (hits) hits[(size_t)warp * a.ns + j] = hit;
     }
@@ -356,6 +465,17 @@ cudaError_t launch_raycast_smad(const ReqDesc *reqs, int R, int total_hyp, int m
     if (grid > total_hyp) grid = total_hyp;
     if (grid < 1) grid = 1;
     k_raycast_smad<<<grid, kRayThreads, smem, s>>>(reqs, R, total_hyp, bs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, uint16_t *selx, uint16_t *sely,
+                              int32_t *kmax, cudaStream_t s) {
+    const size_t rows_m = (size_t)ray_mask_rows(lim), rows_s = (size_t)ray_sel_rows(lim);
+    cudaError_t e = cudaMemsetAsync(mask, 0, sizeof(uint64_t) * rows_m * ns, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(selx, 0xff, sizeof(uint16_t) * rows_s * ns, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sely, 0xff, sizeof(uint16_t) * rows_s * ns, s);
+    if (e != cudaSuccess) return e;
+    k_ray_tables<<<(ns + 127) / 128, 128, 0, s>>>(D, ns, lim, mask, selx, sely, kmax);
     return cudaGetLastError();
 }
 

@@ -50,6 +50,21 @@ struct ScanTable {
     unsigned long long pin = 0;       // batch sequence number of the last batch that used it
 };
 
+// Per-direction traversal tables of one (N_s, range limit); see RayTables.
+struct RayTab {
+    int ns = 0, lim = 0;
+    uint64_t *mask = nullptr;
+    uint16_t *selx = nullptr, *sely = nullptr;
+    int32_t *kmax = nullptr;
+    size_t bytes_mask = 0, bytes_sel = 0;
+    cudaEvent_t built = nullptr;      // recorded after the build kernel
+    unsigned long long last_use = 0;
+    unsigned long long pin = 0;       // batch sequence number of the last batch that used it
+};
+
+constexpr int kMaxRayTabs = 16;
+constexpr size_t kMaxRayTabBytes = size_t(1) << 29;   // larger tables fall back to cell-by-cell stepping
+
 struct MapSlot {
     bool live = false;
     MapDev dev;
@@ -134,6 +149,8 @@ struct relo_ctx {
     ReqDesc last{};
     BatchState *last_bs = nullptr;
     bool has_last = false;
+    // per-direction traversal tables
+    std::vector<RayTab *> raytabs;
     // resident synthesized scans
     long long table_bytes = 0, cache_hits = 0, cache_misses = 0, cache_evictions = 0;
     unsigned long long table_clock = 0, batch_seq = 0;
@@ -486,6 +503,77 @@ ScanTable *new_table(relo_ctx *ctx, MapSlot &m, int ns, int lim) {
     return t;
 }
 
+// ---- per-direction traversal tables ---------------------------------------------------------------
+
+void free_raytab(relo_ctx *ctx, RayTab *t) {
+    dev_free(ctx, t->mask, t->bytes_mask);
+    dev_free(ctx, t->selx, t->bytes_sel);
+    dev_free(ctx, t->sely, t->bytes_sel);
+    dev_free(ctx, t->kmax, sizeof(int32_t) * (size_t)t->ns);
+    if (t->built) cudaEventDestroy(t->built);
+    delete t;
+}
+
+// The traversal tables of (P's directions, lim), from the cache or built on
+// stream st (the caller's stream must wait for t->built before using them);
+// nullptr when disabled or too large, in which case rays step cell by cell.
+RayTab *ray_tables_for(relo_ctx *ctx, const SensorPlan &P, int lim, cudaStream_t st) {
+    if (!ctx->p.ray_tables) return nullptr;
+    for (RayTab *t : ctx->raytabs)
+        if (t->ns == P.ns && t->lim == lim) {
+            t->last_use = ++ctx->table_clock;
+            t->pin = ctx->batch_seq;
+            return t;
+        }
+    const size_t bm = sizeof(uint64_t) * (size_t)ray_mask_rows(lim) * P.ns;
+    const size_t bs = sizeof(uint16_t) * (size_t)ray_sel_rows(lim) * P.ns;
+    if (bm + 2 * bs > kMaxRayTabBytes) return nullptr;
+    if ((int)ctx->raytabs.size() >= kMaxRayTabs) {
+        auto it = ctx->raytabs.end();
+        for (auto i = ctx->raytabs.begin(); i != ctx->raytabs.end(); ++i)
+            if ((*i)->pin != ctx->batch_seq && (it == ctx->raytabs.end() || (*i)->last_use < (*it)->last_use)) it = i;
+        if (it == ctx->raytabs.end()) return nullptr;
+        cudaDeviceSynchronize();   // queued work may still read it
+        free_raytab(ctx, *it);
+        ctx->raytabs.erase(it);
+    }
+    RayTab *t = new (std::nothrow) RayTab();
+    if (!t) return nullptr;
+    t->ns = P.ns;
+    t->lim = lim;
+    t->bytes_mask = bm;   // free_raytab releases whatever was allocated
+    t->bytes_sel = bs;
+    const std::string saved = ctx->err;
+    bool ok = dev_alloc(ctx, (void **)&t->mask, bm, "ray tables") == RELO_OK &&
+              dev_alloc(ctx, (void **)&t->selx, bs, "ray tables") == RELO_OK &&
+              dev_alloc(ctx, (void **)&t->sely, bs, "ray tables") == RELO_OK &&
+              dev_alloc(ctx, (void **)&t->kmax, sizeof(int32_t) * (size_t)P.ns, "ray tables") == RELO_OK &&
+              cudaEventCreateWithFlags(&t->built, cudaEventDisableTiming) == cudaSuccess &&
+              launch_ray_tables(P.D_dev, P.ns, lim, t->mask, t->selx, t->sely, t->kmax, st) == cudaSuccess &&
+              cudaEventRecord(t->built, st) == cudaSuccess;
+    if (!ok) {
+        ctx->err = saved;
+        free_raytab(ctx, t);
+        return nullptr;
+    }
+    ctx->kernels += 1;
+    t->last_use = ++ctx->table_clock;
+    t->pin = ctx->batch_seq;
+    ctx->raytabs.push_back(t);
+    return t;
+}
+
+RayTables ray_tables_view(const RayTab *t) {
+    RayTables v{nullptr, nullptr, nullptr, nullptr};
+    if (t) {
+        v.mask = t->mask;
+        v.selx = t->selx;
+        v.sely = t->sely;
+        v.kmax = t->kmax;
+    }
+    return v;
+}
+
 void free_map(relo_ctx *ctx, MapSlot &m) {
     drop_tables(ctx, m);
     dev_free(ctx, m.dev.d2, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
@@ -690,6 +778,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     // with the same geometry cast).  Tables this batch creates are freed again
     // if the batch fails to launch.
     ++ctx->batch_seq;
+    cudaStream_t st = sl.stream;
+    std::vector<RayTab *> rtab((size_t)R, nullptr);
+    for (int r = 0; r < R; ++r) rtab[r] = ray_tables_for(ctx, *pr[r].P, pr[r].lim, st);
     std::vector<ScanTable *> tab((size_t)R, nullptr);
     std::vector<int> mode((size_t)R, kScanCast);
     struct Created {
@@ -766,6 +857,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.n_enum = P.n_enum;
         d.n_m = P.n_m;
         d.lim = q.lim;
+        d.rt = ray_tables_view(rtab[r]);
         d.a_mid = P.a_mid;
         d.a_low = P.a_low;
         d.fov = (double)P.fov;
@@ -819,14 +911,15 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         plans[bi] = plan_tam(nb.data(), no.data(), sb.data(), R, max_beams, max_C, ctx->n_sm, &segs[(size_t)bi * R]);
         if (plans[bi].vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
     }
-    cudaStream_t st = sl.stream;
     if ((rc = upload(ctx, st, sl.reqs_dev, desc.data(), sizeof(ReqDesc) * R)) ||
         (rc = upload(ctx, st, sl.segs_dev, segs.data(), sizeof(TamSeg) * segs.size())))
         return rc;
     ReqDesc *rq = sl.reqs_dev;
     CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
+        if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
+    }
     CK(timed_on(ctx, st, 2, 1, [&] { return launch_raycast_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
        "ray cast + SMAD");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
@@ -1123,6 +1216,7 @@ void relo_default_params(relo_params *p) {
     p->early_stop = 1;
     p->hbm_budget = 0;
     p->max_range = 30.0;
+    p->ray_tables = 1;
 }
 
 int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
@@ -1171,6 +1265,8 @@ int relo_destroy(relo_ctx *ctx) {
         if (m.live) free_map(ctx, m);
     for (SensorPlan *P : ctx->plans) free_plan(ctx, P);
     ctx->plans.clear();
+    for (RayTab *t : ctx->raytabs) free_raytab(ctx, t);
+    ctx->raytabs.clear();
     slot_free(ctx, ctx->main);
     if (ctx->bad) cudaFree(ctx->bad);
     for (auto &pe : ctx->pending) {
@@ -1406,6 +1502,8 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     ra.ns = P->ns;
     ra.ns_pad = (P->ns + 31) & ~31;
     ra.lim = (int)((rmax_q16 * rmax_q16) >> 32);
+    ++ctx->batch_seq;
+    ra.tab = ray_tables_view(ray_tables_for(ctx, *P, ra.lim, ctx->stream));
     ra.hyps = reinterpret_cast<const int2 *>(cells_dev);
     ra.n_hyp = n;
     CK(launch_synth(ra, ranges_dev, hit_dev, ctx->stream), "synthesized scans");

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's CUDA and host sources.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace relo {
@@ -55,6 +56,44 @@ struct SelectState {
     int done;                  // early termination reached
 };
 
+// Per-direction traversal tables of one beam grid N_s and range limit lim.
+// Every ray starts at a cell centre and follows the integer DDA of its
+// direction, so the sequence of x- and y-steps of direction j is the same for
+// every hypothesis; the tables describe it once.  Layout [row][j] (row-major,
+// N_s entries per row) so the lanes of a warp, which trace neighbouring
+// directions, read neighbouring entries.
+//   selx[n][j]: index k of the step that makes the n-th x-step (k counts
+//               the cells entered, k = |dx| + |dy|); 0xffff when that cell
+//               lies beyond the range limit.  sely likewise for y-steps.
+//   mask[k][j]: the cells the ray enters after entering cell k (cell k
+//               included for k > 0), up to 7 cells further in x and in y
+//               and within the range limit, as an 8x8 bit board anchored at
+//               cell k: bit 8 dy + dx for offsets (dx, dy) in the ray's
+//               direction, stored mirrored in x when D_x <= 0 and in y when
+//               D_y <= 0 so that placing it on a tile is two shifts.
+//   kmax[j]:   the last cell index within the range limit.
+struct RayTables {
+    const uint64_t *mask;
+    const uint16_t *selx, *sely;
+    const int32_t *kmax;
+};
+constexpr uint32_t kSelNone = 0xffffu;
+
+// rows of the tables for a range limit lim (cells^2)
+__host__ __device__ inline int ray_mask_rows(int lim) {
+    // a cell k steps out has |d|^2 >= k^2 / 2, so k <= sqrt(2 lim)
+    int k = (int)sqrt(2.0 * (double)lim);
+    while ((long long)(k + 1) * (k + 1) <= 2ll * lim) ++k;
+    while ((long long)k * k > 2ll * lim) --k;
+    return k + 1;
+}
+__host__ __device__ inline int ray_sel_rows(int lim) {
+    int r = (int)sqrt((double)lim);
+    while ((long long)(r + 1) * (r + 1) <= (long long)lim) ++r;
+    while ((long long)r * r > (long long)lim) --r;
+    return r + 9;   // a cell in range has |dx| <= sqrt(lim); a tile exit adds at most 8
+}
+
 // single-request arguments of the synthesized-scan export (relo_synth_scans_dev)
 struct RayArgs {
     const uint64_t *bits;
@@ -62,6 +101,7 @@ struct RayArgs {
     const int2 *D;          // [ns] Q30 directions
     int ns, ns_pad;         // ns_pad = ns rounded up to 32
     int lim;                // floor(rmax_q16^2 / 2^32): max squared cell distance of an entered cell
+    RayTables tab;          // per-direction tables, or tab.mask == nullptr to step cell by cell
     const int2 *hyps;
     int n_hyp;
     const int2 *iv;         // [n_iv] (u, len) FoV intervals
@@ -96,6 +136,7 @@ struct ReqDesc {
     const int2 *iv;              // [n_iv] (u, len) FoV intervals
     int ns, ns_pad, n_iv, n_beams, n_orient, n_enum, n_m;
     int lim;                     // floor(rmax_q16^2 / 2^32)
+    RayTables rt;                // per-direction traversal tables, or rt.mask == nullptr
     double a_mid, a_low, fov;
     // scan input
     const float *ranges;
@@ -152,6 +193,9 @@ cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the field's
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);
 cudaError_t launch_synth(const RayArgs &a, uint32_t *ranges, int32_t *hit, cudaStream_t s);
+// fills the traversal tables of directions D[0, ns) for range limit lim (buffers sized by ray_*_rows)
+cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, uint16_t *selx, uint16_t *sely,
+                              int32_t *kmax, cudaStream_t s);
 
 // batched stages; R requests, descriptors in device memory
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s);
