@@ -184,8 +184,12 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     const bool xneg = d.x <= 0, yneg = d.y <= 0;
     int adx = 0, ady = 0, cx = hx, cy = hy;
     for (;;) {
-        const uint64_t word = __ldg(bits + (size_t)(cy >> 3) * TW + (cx >> 3));
         const int lx = cx & 7, ly = cy & 7;
+        const int nx = xneg ? lx + 1 : 8 - lx, ny = yneg ? ly + 1 : 8 - ly;
+        // the tile's word and the exit steps are loaded together: one memory round trip per tile
+        const uint64_t word = __ldg(bits + (size_t)(cy >> 3) * TW + (cx >> 3));
+        const uint32_t kx = __ldg(t.selx + (size_t)(adx + nx) * ns + j);
+        const uint32_t ky = __ldg(t.sely + (size_t)(ady + ny) * ns + j);
         if (word) {
             const uint64_t R = __ldg(t.mask + (size_t)(adx + ady) * ns + j);
             const uint32_t kb = xneg ? ((0xffu << (7 - lx)) & 0xffu) : (0xffu >> lx);
@@ -205,9 +209,6 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
                 return isqrt_q16(adx * adx + ady * ady);
             }
         }
-        const int nx = xneg ? lx + 1 : 8 - lx, ny = yneg ? ly + 1 : 8 - ly;
-        const uint32_t kx = __ldg(t.selx + (size_t)(adx + nx) * ns + j);
-        const uint32_t ky = __ldg(t.sely + (size_t)(ady + ny) * ns + j);
         if (kx == kSelNone && ky == kSelNone) {   // the next cell lies beyond the range limit
             *hit = -1;
             *steps = __ldg(t.kmax + j) + 1;
@@ -304,7 +305,7 @@ __host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
 // is the cyclic prefix sum of Eq. 17 for t in [0, N_s].  The threads then
 // split the orientations, evaluate Eq. 18-19 per m and reduce the minimum
 // (Eq. 20).
-__global__ void __launch_bounds__(kRayThreads) k_raycast_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
+__global__ void __launch_bounds__(kRayThreads, 5) k_raycast_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
                                                               BatchState *bs) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kRayThreads / 32];

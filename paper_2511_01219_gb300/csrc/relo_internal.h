@@ -206,6 +206,7 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cu
 struct TamPlan {
     int total_tasks, grid, vpl;
     size_t smem;
+    bool h2;   // selection counts on packed fp16 (C + 1 <= 2048)
 };
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
                  int max_beams, int max_C, int n_sm, TamSeg *segs);

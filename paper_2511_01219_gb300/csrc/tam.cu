@@ -29,6 +29,7 @@
 // accurate when dbar is close to d_max.  Each score is written out and folded
 // into a per-survivor 64-bit key (T bits, then smaller m) with atomicMax:
 // that is the orientation argmax of Eq. 22.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -42,6 +43,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTamWarps = 8;
 constexpr uint32_t kNoBeam = 0xffffu;
+constexpr int kHalfExact = 2048;   // fp16 holds every integer in [0, 2048] exactly
+
+// exact float of an integer 0 <= v < 2^23 (the float 2^23 + v, less 2^23)
+__device__ __forceinline__ float int_float(uint32_t v) { return __uint_as_float(0x4b000000u | v) - 8388608.0f; }
+// the integer of an integral float 0 <= f < 2^23
+__device__ __forceinline__ uint32_t float_int(float f) { return __float_as_uint(f + 8388608.0f) & 0x7fffffu; }
 
 // One CTA per request: the scan preparation above, plus the reset of the
 // request's selection buffers (argmax keys 0, shifts and local top-k -1, TAM
@@ -132,7 +139,11 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // is paid once per (orientation, beam) instead of once per (survivor,
 // orientation, beam).  The likelihood table is reloaded only when a CTA moves
 // to another request's task.
-template <int VPL>
+// H2: the selection counts run on packed fp16 (every launch has C + 1 <=
+// 2048, so the values, the thresholds and the per-lane counts are exact
+// integers in fp16): a value v <= mid adds sat(mid + 1 - v) = 1, a larger one
+// 0, two values per instruction.  Otherwise 32-bit integer compares.
+template <int VPL, bool H2>
 __global__ void __launch_bounds__(kTamWarps * 32, 3) k_tam(const ReqDesc *__restrict__ reqs, int R,
                                                        const TamSeg *__restrict__ segs, int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -189,39 +200,87 @@ __global__ void __launch_bounds__(kTamWarps * 32, 3) k_tam(const ReqDesc *__rest
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
             const int2 hc = d.hyps[d.survivors[s]];
             const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
-            uint32_t v[VPL];
             int sumb = 0;
-#pragma unroll
-            for (int t = 0; t < VPL; ++t) {
-                const int i = (t << 5) + lane;
-                uint32_t bv = none;
-                if (i < N) {
-                    bv = (uint32_t)__ldg(fh + offs[i]);
-                    sumb += (int)bv;
-                }
-                v[t] = bv;
-            }
-            // smallest b_k with #{b <= b_k} >= k
-            int blo = 0, bhi = C;
-            while (blo < bhi) {
-                const int mid = (blo + bhi) >> 1;
-                int c = 0;
-#pragma unroll
-                for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
-                c = __reduce_add_sync(kFull, c);
-                if (c >= k) bhi = mid;
-                else blo = mid + 1;
-            }
-            const uint32_t bk = (uint32_t)blo;
             float sgs = 0.0f, sl = 0.0f;
             int clt = 0;
+            uint32_t bk;
+            if constexpr (H2) {
+                __half2 hv[VPL / 2];
 #pragma unroll
-            for (int t = 0; t < VPL; ++t) {
-                const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
-                sgs += lg.y;
-                if (v[t] < bk) {
-                    sl += lg.x;
-                    ++clt;
+                for (int t = 0; t < VPL / 2; ++t) {
+                    const int i0 = (t << 6) + lane, i1 = i0 + 32;
+                    uint32_t b0 = none, b1 = none;
+                    if (i0 < N) {
+                        b0 = (uint32_t)__ldg(fh + offs[i0]);
+                        sumb += (int)b0;
+                    }
+                    if (i1 < N) {
+                        b1 = (uint32_t)__ldg(fh + offs[i1]);
+                        sumb += (int)b1;
+                    }
+                    hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
+                }
+                // smallest b_k with #{b <= b_k} >= k
+                int blo = 0, bhi = C;
+                while (blo < bhi) {
+                    const int mid = (blo + bhi) >> 1;
+                    const __half2 m1 = __float2half2_rn(int_float((uint32_t)mid + 1u));
+                    __half2 acc = __float2half2_rn(0.0f);
+#pragma unroll
+                    for (int t = 0; t < VPL / 2; ++t) acc = __hadd2(acc, __hsub2_sat(m1, hv[t]));
+                    const float2 af = __half22float2(acc);
+                    const int c = __reduce_add_sync(kFull, (int)float_int(af.x + af.y));
+                    if (c >= k) bhi = mid;
+                    else blo = mid + 1;
+                }
+                bk = (uint32_t)blo;
+#pragma unroll
+                for (int t = 0; t < VPL / 2; ++t) {
+                    const float2 f = __half22float2(hv[t]);
+                    const uint32_t v0 = float_int(f.x), v1 = float_int(f.y);
+                    const float2 g0 = lut[v0], g1 = lut[v1];   // entry C+1 (no beam) adds zero
+                    sgs += g0.y + g1.y;
+                    if (v0 < bk) {
+                        sl += g0.x;
+                        ++clt;
+                    }
+                    if (v1 < bk) {
+                        sl += g1.x;
+                        ++clt;
+                    }
+                }
+            } else {
+                uint32_t v[VPL];
+#pragma unroll
+                for (int t = 0; t < VPL; ++t) {
+                    const int i = (t << 5) + lane;
+                    uint32_t bv = none;
+                    if (i < N) {
+                        bv = (uint32_t)__ldg(fh + offs[i]);
+                        sumb += (int)bv;
+                    }
+                    v[t] = bv;
+                }
+                // smallest b_k with #{b <= b_k} >= k
+                int blo = 0, bhi = C;
+                while (blo < bhi) {
+                    const int mid = (blo + bhi) >> 1;
+                    int c = 0;
+#pragma unroll
+                    for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
+                    c = __reduce_add_sync(kFull, c);
+                    if (c >= k) bhi = mid;
+                    else blo = mid + 1;
+                }
+                bk = (uint32_t)blo;
+#pragma unroll
+                for (int t = 0; t < VPL; ++t) {
+                    const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
+                    sgs += lg.y;
+                    if (v[t] < bk) {
+                        sl += lg.x;
+                        ++clt;
+                    }
                 }
             }
 #pragma unroll
@@ -252,20 +311,21 @@ __global__ void __launch_bounds__(kTamWarps * 32, 3) k_tam(const ReqDesc *__rest
     }
 }
 
-template <int VPL>
+template <int VPL, bool H2>
 cudaError_t run_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tam<VPL, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
     if (e != cudaSuccess) return e;
-    k_tam<VPL><<<tp.grid, kTamWarps * 32, tp.smem, s>>>(reqs, R, segs, tp.total_tasks);
+    k_tam<VPL, H2><<<tp.grid, kTamWarps * 32, tp.smem, s>>>(reqs, R, segs, tp.total_tasks);
     return cudaGetLastError();
 }
 
-template <int VPL>
+template <int VPL, bool H2>
 int tam_occupancy(size_t smem) {
     int occ = 0;
-    if (cudaFuncSetAttribute(k_tam<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_tam<VPL, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tam<VPL>, kTamWarps * 32, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tam<VPL, H2>, kTamWarps * 32, smem) != cudaSuccess)
+        return 0;
     return occ;
 }
 
@@ -280,9 +340,9 @@ int vpl_bucket(int max_beams) {
     return -1;
 }
 
-int occupancy_for(int vpl, size_t smem) {
+int occupancy_for(int vpl, bool h2, size_t smem) {
 #define RELO_TAM_OCC(V) \
-    if (vpl == V) return tam_occupancy<V>(smem);
+    if (vpl == V) return h2 ? tam_occupancy<V, true>(smem) : tam_occupancy<V, false>(smem);
     RELO_TAM_VPLS(RELO_TAM_OCC)
 #undef RELO_TAM_OCC
     return 0;
@@ -300,10 +360,10 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStr
 // of a CTA's warps, and lays the requests' tasks out one after another.
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
                  int max_C, int n_sm, TamSeg *segs) {
-    TamPlan tp{0, 0, vpl_bucket(max_beams), 0};
+    TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfExact};
     tp.smem = (size_t)(max_C + 2) * sizeof(float2) + (size_t)max_beams * sizeof(int);
     if (tp.vpl < 0) return tp;
-    const int occ = occupancy_for(tp.vpl, tp.smem);
+    const int occ = occupancy_for(tp.vpl, tp.h2, tp.smem);
     if (occ < 1) {
         tp.vpl = -1;
         return tp;
@@ -353,7 +413,7 @@ TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {
     if (tp.total_tasks <= 0) return cudaSuccess;
 #define RELO_TAM_RUN(V) \
-    if (tp.vpl == V) return run_tam<V>(reqs, R, segs, tp, s);
+    if (tp.vpl == V) return tp.h2 ? run_tam<V, true>(reqs, R, segs, tp, s) : run_tam<V, false>(reqs, R, segs, tp, s);
     RELO_TAM_VPLS(RELO_TAM_RUN)
 #undef RELO_TAM_RUN
     return cudaErrorInvalidValue;

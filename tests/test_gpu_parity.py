@@ -149,12 +149,13 @@ def test_synth_scans_bit_exact(relo, workload, cfg, n_check):
 # the whole path
 # ------------------------------------------------------------------------------------------
 
-def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95, n_skip=1, sample_tam=None):
+def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95, n_skip=1, sample_tam=None,
+              d_max=2.0):
     prm = oracle.Params(n_orient=wl.n_orient, topk=K, batch=batch, local_topk=local_topk, tau=tau,
-                        n_skip_beam=n_skip)
+                        n_skip_beam=n_skip, d_max=d_max)
     ctx, mid, got = run(relo, wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, n_orient=wl.n_orient,
                         topk=K, batch=batch, local_topk=local_topk, tau=tau, early_stop=int(early_stop),
-                        n_skip_beam=n_skip)
+                        n_skip_beam=n_skip, d_max=d_max)
     pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
     Kc = min(K, len(wl.hyps))
     B = min(batch, Kc)
@@ -206,6 +207,22 @@ def test_full_path_matches_oracle(relo, workload, cfg):
     assert math.isclose(got.x, (wl.hyps[got.hyp, 0] + 0.5) * wl.res) and got.smad_num == st["num"][got.hyp]
     th = got.m * 2 * math.pi / pl["ns"]
     assert math.isclose(got.theta, th - 2 * math.pi if th >= math.pi else th, abs_tol=1e-12)
+    ctx.close()
+
+
+@pytest.mark.parametrize("d_max", [2.25, 2.3, 4.5])
+def test_selection_counts_either_side_of_fp16_range(relo, workload, d_max):
+    """The TAM selection counts run in packed fp16 while C + 1 <= 2048
+    (d_max / res = 45 gives C = 2025) and in 32-bit integers above (46^2 =
+    2116, 90^2 = 8100, the largest clamp): both match the oracle."""
+    wl = workload(0)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, d_max=d_max)
+    want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
+                             early_stop=False)
+
+    def T_at(h, m):
+        return float(oracle.tam(wl.grid, np.array([wl.hyps[h]]), np.array([m]), pl, prm, wl.res, d2)[0])
+    check_pose(got, want["hyp"], want["m"], T_at)
     ctx.close()
 
 

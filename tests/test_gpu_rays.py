@@ -28,18 +28,18 @@ def relo():
     return relo
 
 
-def synth(relo, grid, cells, angles, max_range, ns, **params):
+def synth(relo, grid, cells, angles, scan_range, ns, **params):
     import torch
     ctx = relo.Relo(**params)
     mid = ctx.load_map(grid, 0.05)
     c = torch.tensor(cells, dtype=torch.int32, device="cuda")
-    r, h = ctx.synth_scans(mid, c, angles, max_range, ns)
+    r, h = ctx.synth_scans(mid, c, angles, scan_range, ns)
     ctx.close()
     return r.cpu().numpy().view(np.uint32).astype(np.int64), h.cpu().numpy()
 
 
 @pytest.mark.parametrize("shape,density,max_range,n_beams,ns", [
-    ((197, 203), 0.0, 6.0, 120, 120),       # office cut to odd sides, panoramic, 4/8 of directions axis-aligned
+    ((197, 203), 0.0, 6.0, 120, 120),       # office cut to odd sides, panoramic (the four axis directions included)
     ((61, 45), 0.04, 3.0, 64, 96),          # random obstacles, short range
     ((64, 64), 0.002, 30.0, 72, 72),        # nearly empty: rays leave the map
     ((130, 9), 0.01, 2.0, 50, 100),         # thin map, range limit inside the first tiles
