@@ -1,31 +1,34 @@
-// Ray-cast panoramic synthesized scans (Eq. 13) fused with SMAD (Eq. 16-20).
+// Ray-cast panoramic synthesized scans (Eq. 13) and SMAD (Eq. 16-20).
 //
-// Rays are cast 32 at a time (lane = ray within a chunk, so neighbouring
-// lanes trace neighbouring directions of similar length); chunk prefixes give
-// the cyclic prefix sum S of Eq. 17 at any index; the orientations m of
-// Eq. 15 then each need two lookups per FoV interval for the window sum of
-// Eq. 18, and the integer SMAD numerator |sum R_real - W_m| of Eq. 19 (the
-// shared denominator of the two means cancels from every comparison) is
-// minimised over m (Eq. 20; ties keep the smaller m).
+// Two kernels per batch.  k_cast casts every ray of every hypothesis, 32
+// neighbouring directions per warp (lane = ray, so the lanes of a warp trace
+// rays of similar length), into a per-request table of Q16 ranges.  k_smad
+// then reads a hypothesis's row, forms chunk prefixes that
+// give the cyclic prefix sum S of Eq. 17 at any index, evaluates the window
+// sums of Eq. 18 for the orientations m of Eq. 15 with two lookups per FoV
+// interval, and minimises the integer SMAD numerator |sum R_real - W_m| of
+// Eq. 19 over m (Eq. 20; ties keep the smaller m; the shared denominator of
+// the two means cancels from every comparison).
 //
 // Ray traversal.  From the hypothesis cell centre along the Q30 direction D,
 // cells are entered in the order of the ray's grid-line crossings: with k x-
 // and l y-crossings so far, x is stepped when (2k+1)|Dy| <= (2l+1)|Dx| (a
-// corner tie steps x).  The kernel tracks the difference e = (2l+1)|Dx| -
+// corner tie steps x).  The recurrence tracks the difference e = (2l+1)|Dx| -
 // (2k+1)|Dy| incrementally (e -= 2|Dy| after an x step, e += 2|Dx| after a y
 // step); it always lies in [-2^31, 2^31), so a 32-bit integer holds it
 // exactly.  The ray stops on leaving the map, on entering a cell whose centre
 // lies beyond the maximum range, or on entering an occupied cell; the range of
 // a hit is floor(sqrt(|d|^2 * 2^32)) (cells, Q16), else 0 (the placeholder of
-// the invalid beam).  Occupancy comes from the 8x8-tile bitmap; the current
-// tile's 64-bit word stays in a register until the ray leaves the tile.
+// the invalid beam).  Occupancy comes from the 8x8-tile bitmap.  The default
+// traversal (walk_ray) moves tile by tile with per-direction tables built
+// once per (N_s, range limit); cast_ray steps cell by cell with the same
+// recurrence.
 //
 // A panoramic synthesized scan depends only on the map, the hypothesis, the
-// beam grid N_s and the range limit, not on the real scan.  A request may
-// therefore store its ranges into a resident table (kScanStore) or, when an
-// earlier launch stored them for the same map, hypotheses, N_s and limit,
-// read them from it (kScanRead) instead of casting; the SMAD arithmetic is
-// the same in all three modes.
+// beam grid N_s and the range limit, not on the real scan.  The table a
+// request casts into is either its scratch (kScanCast) or a resident table
+// (kScanStore) that later requests with the same map, hypotheses, N_s and
+// limit read without casting (kScanRead).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -293,35 +296,75 @@ __host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
     return inner_bytes(ns_pad) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
-// One CTA per hypothesis.  A batch's hypotheses form one list (request r owns
-// slots [hyp_base_r, hyp_base_r + n_hyp_r)); CTAs take slots from a device
-// work counter, so costly hypotheses (long rays) and uneven requests do not
-// leave CTAs idle at the end.  Inside the CTA the warps take 32-ray chunks
-// from a shared counter (lane = ray, so the lanes of a warp trace
-// neighbouring directions of similar length) until the hypothesis's N_s rays
-// are cast; ranges land in shared memory by ray index.  Each chunk is then
-// scanned by a warp into exclusive in-chunk prefixes and one warp turns the
+// Casting.  The batch's rays form one list of 32-ray chunks (request r owns
+// chunks [chunk_base_r, chunk_base_r + n_hyp_r * N_s_pad / 32), hypothesis
+// by hypothesis); every warp takes chunks from a device counter until none is
+// left, casts its 32 neighbouring directions (lane = ray) and writes their
+// ranges into the request's scan table, 128 contiguous bytes per chunk.  No
+// warp waits for another, so long and short rays, hypotheses and requests
+// mix freely across the GPU.
+constexpr int kCastThreads = 256;
+
+__global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
+                                                       BatchState *bs) {
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].chunk_base;
+    if (threadIdx.x == 0) s_base[R] = total_chunks;
+    __syncthreads();
+    unsigned long long my_steps = 0;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&bs->cast_work, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= total_chunks) break;
+        int lo = 0, hi = R - 1;   // last request whose chunk_base <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_base[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDesc &d = reqs[lo];
+        const int nch = d.ns_pad >> 5;
+        const int local = g - s_base[lo];
+        const int h = local / nch;
+        const int j = ((local - h * nch) << 5) + lane;
+        if (j < d.ns) {
+            const int2 hc = d.hyps[h];
+            const int2 dir = d.D[j];
+            int hit, steps = 0;
+            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.W, d.H, d.TW, d.rt, d.ns, j, hc.x, hc.y, dir, &hit, &steps)
+                                         : cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, dir, &hit, &steps);
+            d.scan_table[(size_t)h * d.ns + j] = r;
+            my_steps += (unsigned)steps;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, o);
+    if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
+}
+
+// SMAD.  One CTA per hypothesis, taken from a device counter over the
+// batch's hypothesis list (request r owns slots [hyp_base_r, hyp_base_r +
+// n_hyp_r)).  The CTA reads the hypothesis's N_s ranges, each warp scans
+// 32-range chunks into exclusive in-chunk prefixes and one warp turns the
 // chunk totals into 64-bit chunk prefixes; P(t) = chunkP[t / 32] + inner[t]
 // is the cyclic prefix sum of Eq. 17 for t in [0, N_s].  The threads then
 // split the orientations, evaluate Eq. 18-19 per m and reduce the minimum
 // (Eq. 20).
-__global__ void __launch_bounds__(kRayThreads, 5) k_raycast_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
+__global__ void __launch_bounds__(kRayThreads) k_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
                                                               BatchState *bs) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kRayThreads / 32];
     __shared__ int s_base[kMaxBatchRequests + 1];
-    __shared__ int s_g, s_next;
+    __shared__ int s_g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nwarps = kRayThreads / 32;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].hyp_base;
     if (threadIdx.x == 0) s_base[R] = total_hyp;
-    unsigned long long my_steps = 0;
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_g = (int)atomicAdd(&bs->ray_work, 1u);
-            s_next = 0;
-        }
+        if (threadIdx.x == 0) s_g = (int)atomicAdd(&bs->ray_work, 1u);
         __syncthreads();
         const int g = s_g;
         if (g >= total_hyp) break;
@@ -337,38 +380,10 @@ __global__ void __launch_bounds__(kRayThreads, 5) k_raycast_smad(const ReqDesc *
         uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
         long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(ns_pad));
         if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
-        const int mode = d.scan_mode;
-        if (mode == kScanRead) {
-            // resident ranges: one coalesced pass over the hypothesis's row
-            const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
-            for (int j = threadIdx.x; j < ns_pad; j += blockDim.x) inner[j] = j < ns ? __ldg(row + j) : 0u;
-        } else {
-            uint32_t *row = mode == kScanStore ? d.scan_table + (size_t)h * ns : nullptr;
-            const int2 hc = d.hyps[h];
-            const uint64_t *bits = d.bits;
-            const int2 *D = d.D;
-            const int W = d.W, H = d.H, TW = d.TW, lim = d.lim;
-            for (;;) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&s_next, 1);
-                c = __shfl_sync(kFull, c, 0);
-                if (c >= nch) break;
-                const int j = (c << 5) + lane;
-                uint32_t r = 0u;
-                int hit, steps = 0;
-                if (j < ns) {
-                    r = d.rt.mask ? walk_ray(bits, W, H, TW, d.rt, ns, j, hc.x, hc.y, D[j], &hit, &steps)
-                                  : cast_ray(bits, W, H, TW, lim, hc.x, hc.y, D[j], &hit, &steps);
-                    if (row) row[j] = r;
-                }
-                my_steps += (unsigned)steps;
-                inner[j] = r;
-            }
-        }
-        __syncthreads();
+        const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
         for (int c = warp; c < nch; c += nwarps) {
             const int jj = (c << 5) + lane;
-            const uint32_t r = jj < ns ? inner[jj] : 0u;
+            const uint32_t r = jj < ns ? __ldg(row + jj) : 0u;
             uint32_t sc = r;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -432,9 +447,6 @@ __global__ void __launch_bounds__(kRayThreads, 5) k_raycast_smad(const ReqDesc *
         }
         // the next iteration's first __syncthreads orders these reads before inner/chunkP are rewritten
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, o);
-    if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
 }
 
 __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__ ranges, int32_t *__restrict__ hits) {
@@ -452,20 +464,34 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
 
 }  // namespace
 
-cudaError_t launch_raycast_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s) {
+    if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
+    if (total_chunks <= 0) return cudaSuccess;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cast, kCastThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const long long warps = (long long)total_chunks;
+    long long grid = (long long)n_sm * occ;
+    if (grid * (kCastThreads / 32) > warps) grid = (warps + kCastThreads / 32 - 1) / (kCastThreads / 32);
+    k_cast<<<(int)grid, kCastThreads, 0, s>>>(reqs, R, total_chunks, bs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
                                 cudaStream_t s) {
     if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
     size_t smem = cta_smem_bytes(max_ns_pad);
-    cudaError_t e = cudaFuncSetAttribute(k_raycast_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raycast_smad, kRayThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smad, kRayThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int grid = n_sm * occ;
     if (grid > total_hyp) grid = total_hyp;
     if (grid < 1) grid = 1;
-    k_raycast_smad<<<grid, kRayThreads, smem, s>>>(reqs, R, total_hyp, bs);
+    k_smad<<<grid, kRayThreads, smem, s>>>(reqs, R, total_hyp, bs);
     return cudaGetLastError();
 }
 

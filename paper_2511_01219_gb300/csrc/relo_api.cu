@@ -751,36 +751,14 @@ int prepare(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, const float 
 int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     if (R < 1 || R > kMaxBatchRequests) return fail(ctx, RELO_E_INVALID_ARG, "1 to 256 requests per batch");
     const relo_params &p = ctx->p;
-    std::vector<ReqDesc> desc((size_t)R);
-    std::vector<size_t> off((size_t)R);
-    size_t total = 0;
-    int total_hyp = 0, max_ns_pad = 32, max_n_hyp = 1, max_K = 1, max_beams = 1, max_C = 0, max_batches = 0;
-    for (int r = 0; r < R; ++r) {
-        const Prepared &q = pr[r];
-        const int n = q.P->n, nh = q.m->n_hyp, K = q.K;
-        off[r] = total;
-        total += align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
-                 align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
-                 align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
-        if ((long long)total_hyp + nh > (1ll << 30)) return fail(ctx, RELO_E_INVALID_ARG, "batch too large");
-        total_hyp += nh;
-        max_ns_pad = std::max(max_ns_pad, (q.P->ns + 31) & ~31);
-        max_n_hyp = std::max(max_n_hyp, nh);
-        max_K = std::max(max_K, K);
-        max_beams = std::max(max_beams, n);
-        max_C = std::max(max_C, q.m->dev.C);
-        max_batches = std::max(max_batches, q.n_batches);
-    }
-    int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
-    if (rc) return rc;
-    // Resident synthesized scans: read a table stored by an earlier launch, or
-    // store a new one (one writer per table; other requests of this batch
-    // with the same geometry cast).  Tables this batch creates are freed again
-    // if the batch fails to launch.
     ++ctx->batch_seq;
     cudaStream_t st = sl.stream;
     std::vector<RayTab *> rtab((size_t)R, nullptr);
     for (int r = 0; r < R; ++r) rtab[r] = ray_tables_for(ctx, *pr[r].P, pr[r].lim, st);
+    // Resident synthesized scans: read a table stored by an earlier launch, or
+    // store a new one (one writer per table; other requests of this batch
+    // with the same geometry cast into their scratch).  Tables this batch
+    // creates are freed again if the batch fails to launch.
     std::vector<ScanTable *> tab((size_t)R, nullptr);
     std::vector<int> mode((size_t)R, kScanCast);
     struct Created {
@@ -822,6 +800,32 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             }
         }
     }
+    std::vector<ReqDesc> desc((size_t)R);
+    std::vector<size_t> off((size_t)R);
+    size_t total = 0;
+    int total_hyp = 0, max_ns_pad = 32, max_n_hyp = 1, max_K = 1, max_beams = 1, max_C = 0, max_batches = 0;
+    long long total_chunks = 0;
+    for (int r = 0; r < R; ++r) {
+        const Prepared &q = pr[r];
+        const int n = q.P->n, nh = q.m->n_hyp, K = q.K;
+        off[r] = total;
+        total += align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
+                 align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
+                 align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
+        if (mode[r] == kScanCast) total += align_up(4ull * nh * q.P->ns);   // the request's synthesized ranges
+        if (mode[r] != kScanRead) total_chunks += (long long)nh * (((q.P->ns + 31) & ~31) >> 5);
+        if ((long long)total_hyp + nh > (1ll << 30) || total_chunks > (1ll << 31) - 1)
+            return fail(ctx, RELO_E_INVALID_ARG, "batch too large");
+        total_hyp += nh;
+        max_ns_pad = std::max(max_ns_pad, (q.P->ns + 31) & ~31);
+        max_n_hyp = std::max(max_n_hyp, nh);
+        max_K = std::max(max_K, K);
+        max_beams = std::max(max_beams, n);
+        max_C = std::max(max_C, q.m->dev.C);
+        max_batches = std::max(max_batches, q.n_batches);
+    }
+    int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
+    if (rc) return rc;
     for (int r = 0; r < R; ++r) {
         const Prepared &q = pr[r];
         const MapSlot &m = *q.m;
@@ -889,13 +893,15 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.local = (int32_t *)take(4ull * q.n_batches * p.local_topk);
         d.state = (SelectState *)take(sizeof(SelectState));
         d.result = q.result_dev;
-        d.scan_table = tab[r] ? tab[r]->data : nullptr;
+        d.scan_table = mode[r] == kScanCast ? (uint32_t *)take(4ull * m.n_hyp * P.ns) : tab[r]->data;
         d.scan_mode = mode[r];
     }
-    int base = 0;
+    int base = 0, cbase = 0;
     for (int r = 0; r < R; ++r) {
         desc[r].hyp_base = base;
         base += desc[r].n_hyp;
+        desc[r].chunk_base = cbase;
+        if (desc[r].scan_mode != kScanRead) cbase += desc[r].n_hyp * (desc[r].ns_pad >> 5);
     }
     // TAM work of every batch index
     std::vector<TamSeg> segs((size_t)max_batches * R);
@@ -920,7 +926,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
         if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
     }
-    CK(timed_on(ctx, st, 2, 1, [&] { return launch_raycast_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
+    CK(timed_on(ctx, st, 2, total_chunks > 0 ? 2 : 1,
+                [&] {
+                    cudaError_t e = launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st);
+                    return e != cudaSuccess ? e : launch_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st);
+                }),
        "ray cast + SMAD");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
@@ -1012,10 +1022,11 @@ namespace {
 // device bytes a request occupies while in flight (scratch and its scan)
 size_t request_bytes(const relo_ctx *ctx, const Prepared &q) {
     const size_t n = (size_t)q.P->n, nh = (size_t)q.m->n_hyp, K = (size_t)q.K;
+    const bool resident = ctx->p.scan_cache_bytes > 0 && find_table(*q.m, q.P->ns, q.lim) != nullptr;
     return align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8 * nh) * 2 + align_up(4 * nh) +
            align_up(4 * K) * 2 + align_up(4 * K * q.P->n_orient) + align_up(8 * K) +
            align_up(4ull * q.n_batches * ctx->p.local_topk) + align_up(sizeof(SelectState)) +
-           align_up(sizeof(float) * q.P->n * ctx->p.n_skip_beam);
+           align_up(sizeof(float) * q.P->n * ctx->p.n_skip_beam) + (resident ? 0 : align_up(4 * nh * q.P->ns));
 }
 
 void finish(Server *S, Ticket *t, int status, const relo_result *r) {

@@ -161,20 +161,24 @@ struct ReqDesc {
     void *result;                // relo_result in device memory
     // work lists
     int hyp_base;                // first slot of this request in the batch's hypothesis list
-    // resident synthesized scans of (map, hypotheses, N_s, lim): [n_hyp * ns] Q16 ranges
+    // synthesized scans of (map, hypotheses, N_s, lim): [n_hyp * ns] Q16 ranges, row per hypothesis
     uint32_t *scan_table;
     int scan_mode;               // kScanCast, kScanStore or kScanRead
+    int chunk_base;              // first 32-ray chunk of this request in the batch's cast list
 };
 
-// How the ray-cast stage obtains a request's synthesized ranges.
-constexpr int kScanCast = 0;     // cast every ray
-constexpr int kScanStore = 1;    // cast every ray and store the ranges into scan_table
-constexpr int kScanRead = 2;     // read the ranges from scan_table (written by an earlier launch)
+// Where a request's synthesized ranges come from.  The cast kernel writes
+// them into scan_table (request scratch for kScanCast, a resident table for
+// kScanStore); kScanRead requests have no chunks, their table was written by
+// an earlier launch.  The SMAD kernel reads scan_table in every mode.
+constexpr int kScanCast = 0;
+constexpr int kScanStore = 1;
+constexpr int kScanRead = 2;
 
 // Counters shared by the whole batch.
 struct BatchState {
-    unsigned int ray_work;          // next global hypothesis slot for the ray-cast CTAs
-    unsigned int pad;
+    unsigned int ray_work;          // next global hypothesis slot for the SMAD CTAs
+    unsigned int cast_work;         // next global 32-ray chunk for the cast warps
     unsigned long long dda_steps;   // cells entered by all rays of the batch
 };
 
@@ -199,7 +203,10 @@ cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, ui
 
 // batched stages; R requests, descriptors in device memory
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s);
-cudaError_t launch_raycast_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
+// casts the total_chunks 32-ray chunks of the batch into the requests' scan tables
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s);
+// SMAD of every hypothesis of the batch from the requests' scan tables
+cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
                                 cudaStream_t s);
 cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s);
 // plans the TAM launch of one batch index: fills segs[R] and returns the task count and grid size

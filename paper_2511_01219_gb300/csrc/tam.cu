@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
     if (threadIdx.x == 0) s_base = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bs->ray_work = 0u;
+        bs->cast_work = 0u;
         bs->dda_steps = 0ull;
     }
     for (int i = threadIdx.x; i < d.K; i += blockDim.x) {
