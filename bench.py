@@ -259,18 +259,24 @@ def run_ours(args, world, rank, local, dist):
                        "peak_source": f"{peak_kind} hbm_gbs",
                        "avg_launch_ms": round(stage_ms["tam"] / max(stage_n["tam"], 1), 4)}
     dda = info[8]
-    if stage_ms["raycast_smad"] > 0 and dda:
+    if stage_ms["raycast"] > 0 and dda:
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         peak_tops = 128 * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ops = dda * OPS_PER_DDA_STEP * args.steps
-        tops = ops / (stage_ms["raycast_smad"] / 1e3) / 1e12
-        roof["raycast_smad"] = {"bound": "alu", "achieved": round(tops, 3), "peak": round(peak_tops, 2),
-                                "unit": "Tops/s", "frac": round(tops / peak_tops, 4),
-                                "traffic": committed_traffic("raycast_smad"),
-                                "peak_source": f"128 int32 lanes x {sm_count} SMs x {peaks.get('sm_max_mhz')} MHz",
-                                "dda_steps_per_step": dda,
-                                "avg_launch_ms": round(stage_ms["raycast_smad"] / max(stage_n["raycast_smad"], 1),
-                                                       4)}
+        tops = ops / (stage_ms["raycast"] / 1e3) / 1e12
+        roof["raycast"] = {"bound": "alu", "achieved": round(tops, 3), "peak": round(peak_tops, 2),
+                           "unit": "Tops/s", "frac": round(tops / peak_tops, 4),
+                           "traffic": committed_traffic("raycast"),
+                           "peak_source": f"128 int32 lanes x {sm_count} SMs x {peaks.get('sm_max_mhz')} MHz",
+                           "dda_steps_per_step": dda,
+                           "avg_launch_ms": round(stage_ms["raycast"] / max(stage_n["raycast"], 1), 4)}
+    if stage_ms["smad"] > 0:
+        smad_bytes = 4.0 * info[0] * info[9] * args.steps          # one Q16 range per (hypothesis, direction)
+        gbs = smad_bytes / (stage_ms["smad"] / 1e3) / 1e9
+        roof["smad"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": committed_traffic("smad"),
+                        "peak_source": f"{peak_kind} hbm_gbs",
+                        "avg_launch_ms": round(stage_ms["smad"] / max(stage_n["smad"], 1), 4)}
     main_roof = roof.get(dominant) or roof.get("tam")
     pct = sorted(per_step)
     line = {

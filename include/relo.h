@@ -237,14 +237,14 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
 /* Stage timing (tracing).  With profiling on, the context records a CUDA
  * event pair on its stream around every kernel it launches and sums the
  * elapsed device time per stage:
- *   0 EDT map precompute, 1 scan preparation, 2 ray cast + SMAD,
- *   3 SMAD top-K, 4 TAM, 5 batch selection and finalize.
+ *   0 EDT map precompute, 1 scan preparation, 2 ray cast (Eq. 13),
+ *   3 SMAD top-K, 4 TAM, 5 batch selection and finalize, 6 SMAD (Eq. 16-20).
  * relo_stage_times synchronises the stream, writes min(n, RELO_N_STAGES)
  * totals in milliseconds to ms_out and launch counts to launches_out (either
  * may be NULL), and with reset != 0 clears the totals.  Independently of
  * profiling, *kernels_out (optional) receives the number of kernels the
  * context has launched since it was created. */
-#define RELO_N_STAGES 6
+#define RELO_N_STAGES 7
 int relo_set_profiling(relo_ctx *ctx, int32_t enable);
 int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
                      int64_t *kernels_out);

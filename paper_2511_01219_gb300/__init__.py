@@ -42,7 +42,7 @@ EXPORTED = [
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
     "relo_serve_stop", "relo_scan_cache_stats",
 ]
-STAGES = ["edt", "scan_prep", "raycast_smad", "topk", "tam", "select"]
+STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
 
 class Params(ctypes.Structure):

@@ -172,41 +172,49 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
     return r;
 }
 
+__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    return ((uint64_t)__byte_perm(lo, 0u, 0x0123u) << 32) | (uint64_t)__byte_perm(hi, 0u, 0x0123u);
+}
+
 // Tile walk with the per-direction tables (RayTables).  The ray moves from
-// tile to tile: in a tile whose occupancy word is not zero, the table's bit
-// board of the cells still ahead (anchored at the current cell) is shifted
-// onto the tile and ANDed with the word; the first set bit in the ray's
-// order (rows in the y direction of travel, then columns in the x direction,
-// which is the order of the cells along any monotone staircase) is the hit.
-// Otherwise the ray leaves the tile at the cell of step
-// min(selx[|dx| + nx], sely[|dy| + ny]), nx and ny being the x- and y-steps to
-// the tile's far edges.  Same cells, same hit, same range as cast_ray.
+// tile to tile in its own frame, the tile mirrored in x when D_x <= 0 and in
+// y when D_y <= 0, so that it always travels towards +x and +y.  In a tile
+// whose occupancy word is not zero, the table's bit board of the cells still
+// ahead (anchored at the current cell) is shifted onto the mirrored word; on
+// a staircase that only moves +x and +y the cell order along the ray is the
+// row-major bit order, so the lowest common bit is the hit.  Otherwise the
+// ray leaves the tile at the cell of step min(selx[|dx| + nx], sely[|dy| +
+// ny]), nx and ny being the x- and y-steps to the tile's far edges.  Same
+// cells, same hit, same range as cast_ray.
 __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, int W, int H, int TW,
                                              const RayTables &t, int ns, int j, int hx, int hy, int2 d, int *hit,
                                              int *steps) {
     const bool xneg = d.x <= 0, yneg = d.y <= 0;
+    const int xm = xneg ? 7 : 0, ym = yneg ? 7 : 0;
+    const int sx = xneg ? -1 : 1, sy = yneg ? -1 : 1;
+    const uint16_t *__restrict__ selx = t.selx + j;
+    const uint16_t *__restrict__ sely = t.sely + j;
+    const uint64_t *__restrict__ mk = t.mask + j;
     int adx = 0, ady = 0, cx = hx, cy = hy;
     for (;;) {
-        const int lx = cx & 7, ly = cy & 7;
-        const int nx = xneg ? lx + 1 : 8 - lx, ny = yneg ? ly + 1 : 8 - ly;
+        const int lx = (cx & 7) ^ xm, ly = (cy & 7) ^ ym;   // the cell inside the tile, in the ray's frame
         // the tile's word and the exit steps are loaded together: one memory round trip per tile
         const uint64_t word = __ldg(bits + (size_t)(cy >> 3) * TW + (cx >> 3));
-        const uint32_t kx = __ldg(t.selx + (size_t)(adx + nx) * ns + j);
-        const uint32_t ky = __ldg(t.sely + (size_t)(ady + ny) * ns + j);
+        const uint32_t kx = __ldg(selx + (size_t)(adx + 8 - lx) * ns);
+        const uint32_t ky = __ldg(sely + (size_t)(ady + 8 - ly) * ns);
         if (word) {
-            const uint64_t R = __ldg(t.mask + (size_t)(adx + ady) * ns + j);
-            const uint32_t kb = xneg ? ((0xffu << (7 - lx)) & 0xffu) : (0xffu >> lx);
-            const int A = (xneg ? 0 : lx) + (yneg ? 0 : 8 * ly);
-            const int B = (xneg ? 7 - lx : 0) + (yneg ? 8 * (7 - ly) : 0);
-            const uint64_t hm = (((R & (0x0101010101010101ull * kb)) << A) >> B) & word;
+            uint64_t w = word;
+            if (xneg) w = bswap64(__brevll(w));   // reverse the bits of every row
+            if (yneg) w = bswap64(w);             // reverse the rows
+            const uint64_t R = __ldg(mk + (size_t)(adx + ady) * ns);
+            const uint64_t hm = ((R & (0x0101010101010101ull * (0xffu >> lx))) << (lx + 8 * ly)) & w;
             if (hm) {
-                const int r = yneg ? (63 - __clzll((long long)hm)) >> 3 : (__ffsll((long long)hm) - 1) >> 3;
-                const uint32_t row = (uint32_t)(hm >> (8 * r)) & 0xffu;
-                const int c = xneg ? 31 - __clz((int)row) : __ffs((int)row) - 1;
-                adx += c > lx ? c - lx : lx - c;
-                ady += r > ly ? r - ly : ly - r;
-                cx += c - lx;
-                cy += r - ly;
+                const int b = __ffsll((long long)hm) - 1;
+                adx += (b & 7) - lx;
+                ady += (b >> 3) - ly;
+                cx = hx + sx * adx;
+                cy = hy + sy * ady;
                 *hit = cy * W + cx;
                 *steps = adx + ady;
                 return isqrt_q16(adx * adx + ady * ady);
@@ -218,14 +226,14 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
             return 0u;
         }
         if (kx < ky) {
-            adx += nx;
+            adx += 8 - lx;
             ady = (int)kx - adx;
         } else {
-            ady += ny;
+            ady += 8 - ly;
             adx = (int)ky - ady;
         }
-        cx = xneg ? hx - adx : hx + adx;
-        cy = yneg ? hy - ady : hy + ady;
+        cx = hx + sx * adx;
+        cy = hy + sy * ady;
         if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {   // left the map
             *hit = -1;
             *steps = adx + ady;
@@ -234,25 +242,18 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     }
 }
 
-__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
-    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
-    return ((uint64_t)__byte_perm(lo, 0u, 0x0123u) << 32) | (uint64_t)__byte_perm(hi, 0u, 0x0123u);
-}
-
 // One thread per direction: the DDA of cast_ray from (0, 0), recorded.  The
 // forward pass writes the step indexes into selx / sely and, as scratch, the
 // kind of step k + 1 into mask row k; the backward pass turns those into the
 // bit boards, mask(k) = cell k plus mask(k + 1) moved one cell back along
-// step k + 1 (cells that fall off the 8x8 board are dropped), mirrored for
-// storage as RayTables describes.  mask rows must start at 0 and selx / sely
-// at kSelNone.
+// step k + 1 (cells that fall off the 8x8 board are dropped).  mask rows must
+// start at 0 and selx / sely at kSelNone.
 __global__ void k_ray_tables(const int2 *__restrict__ D, int ns, int lim, uint64_t *mask, uint16_t *selx,
                              uint16_t *sely, int32_t *kmax) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ns) return;
     const int2 d = D[j];
     const int ax = d.x < 0 ? -d.x : d.x, ay = d.y < 0 ? -d.y : d.y;
-    const bool xneg = d.x <= 0, yneg = d.y <= 0;
     int e = ax - ay, adx = 0, ady = 0, k = 0;
     for (;;) {
         const bool xs = e >= 0;
@@ -273,10 +274,7 @@ __global__ void k_ray_tables(const int2 *__restrict__ D, int ns, int lim, uint64
             const bool xs = mask[(size_t)kk * ns + j] != 0ull;
             R = 1ull | (xs ? ((R & ~0x8080808080808080ull) << 1) : (R << 8));
         }
-        uint64_t v = kk == 0 ? (R & ~1ull) : R;   // the start cell itself is never tested
-        if (xneg) v = bswap64(__brevll(v));        // mirror x: reverse the bits of every row
-        if (yneg) v = bswap64(v);                  // mirror y: reverse the rows
-        mask[(size_t)kk * ns + j] = v;
+        mask[(size_t)kk * ns + j] = kk == 0 ? (R & ~1ull) : R;   // the start cell itself is never tested
     }
 }
 

@@ -926,12 +926,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
         if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
     }
-    CK(timed_on(ctx, st, 2, total_chunks > 0 ? 2 : 1,
-                [&] {
-                    cudaError_t e = launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st);
-                    return e != cudaSuccess ? e : launch_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st);
-                }),
-       "ray cast + SMAD");
+    if (total_chunks > 0)
+        CK(timed_on(ctx, st, 2, 1, [&] { return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st); }),
+           "ray cast");
+    CK(timed_on(ctx, st, 6, 1, [&] { return launch_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
+       "SMAD");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {

@@ -68,9 +68,7 @@ struct SelectState {
 //   mask[k][j]: the cells the ray enters after entering cell k (cell k
 //               included for k > 0), up to 7 cells further in x and in y
 //               and within the range limit, as an 8x8 bit board anchored at
-//               cell k: bit 8 dy + dx for offsets (dx, dy) in the ray's
-//               direction, stored mirrored in x when D_x <= 0 and in y when
-//               D_y <= 0 so that placing it on a tile is two shifts.
+//               cell k: bit 8 |dy| + |dx| for the offsets (dx, dy).
 //   kmax[j]:   the last cell index within the range limit.
 struct RayTables {
     const uint64_t *mask;

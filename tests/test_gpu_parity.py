@@ -393,7 +393,7 @@ def test_profiling_then_blocking_call_then_close(relo, workload):
         ctx.relocalize_dev(mid, z, wl.angles, wl.max_range, res)
     ms, n, k = ctx.stage_times(reset=True)
     ctx.set_profiling(False)
-    assert n["raycast_smad"] == 3 and n["edt"] == 3 and all(v >= 0 for v in ms.values()) and k > 0
+    assert n["raycast"] == 3 and n["smad"] == 3 and n["edt"] == 3 and all(v >= 0 for v in ms.values()) and k > 0
     out = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
     assert out.status == 0
     ctx.close()
