@@ -46,7 +46,7 @@ __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     const unsigned long long N = (unsigned long long)(unsigned)c2 << 32;
     unsigned long long r = (unsigned long long)(sqrtf((float)c2) * 65536.0f);
     long long err = (long long)(N - r * r);
-    r = (unsigned long long)((long long)r + (long long)((float)err / (2.0f * (float)r + 1.0f)));
+    r = (unsigned long long)((long long)r + (long long)__fdividef((float)err, 2.0f * (float)r + 1.0f));
     while (r * r > N) --r;
     while ((r + 1) * (r + 1) <= N) ++r;
     return (uint32_t)r;
@@ -196,7 +196,10 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     const uint16_t *__restrict__ selx = t.selx + j;
     const uint16_t *__restrict__ sely = t.sely + j;
     const uint64_t *__restrict__ mk = t.mask + j;
+    // The loop only finds where the ray stops; the range is computed after it,
+    // once for the whole warp, rather than in a divergent branch per lane.
     int adx = 0, ady = 0, cx = hx, cy = hy;
+    int stop;   // 1 hit, 2 range limit, 3 left the map
     for (;;) {
         const int lx = (cx & 7) ^ xm, ly = (cy & 7) ^ ym;   // the cell inside the tile, in the ray's frame
         // the tile's word and the exit steps are loaded together: one memory round trip per tile
@@ -213,17 +216,13 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
                 const int b = __ffsll((long long)hm) - 1;
                 adx += (b & 7) - lx;
                 ady += (b >> 3) - ly;
-                cx = hx + sx * adx;
-                cy = hy + sy * ady;
-                *hit = cy * W + cx;
-                *steps = adx + ady;
-                return isqrt_q16(adx * adx + ady * ady);
+                stop = 1;
+                break;
             }
         }
         if (kx == kSelNone && ky == kSelNone) {   // the next cell lies beyond the range limit
-            *hit = -1;
-            *steps = __ldg(t.kmax + j) + 1;
-            return 0u;
+            stop = 2;
+            break;
         }
         if (kx < ky) {
             adx += 8 - lx;
@@ -235,11 +234,16 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
         cx = hx + sx * adx;
         cy = hy + sy * ady;
         if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {   // left the map
-            *hit = -1;
-            *steps = adx + ady;
-            return 0u;
+            stop = 3;
+            break;
         }
     }
+    cx = hx + sx * adx;
+    cy = hy + sy * ady;
+    *hit = stop == 1 ? cy * W + cx : -1;
+    *steps = stop == 2 ? __ldg(t.kmax + j) + 1 : adx + ady;
+    const uint32_t r = isqrt_q16(stop == 1 ? adx * adx + ady * ady : 0);   // a hit lies within the range limit
+    return stop == 1 ? r : 0u;
 }
 
 // One thread per direction: the DDA of cast_ray from (0, 0), recorded.  The

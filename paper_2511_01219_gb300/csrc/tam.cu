@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // integers in fp16): a value v <= mid adds sat(mid + 1 - v) = 1, a larger one
 // 0, two values per instruction.  Otherwise 32-bit integer compares.
 template <int VPL, bool H2>
-__global__ void __launch_bounds__(kTamWarps * 32, 3) k_tam(const ReqDesc *__restrict__ reqs, int R,
+__global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__restrict__ reqs, int R,
                                                        const TamSeg *__restrict__ segs, int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
