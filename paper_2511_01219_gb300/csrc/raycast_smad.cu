@@ -196,31 +196,37 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     const uint16_t *__restrict__ selx = t.selx + j;
     const uint16_t *__restrict__ sely = t.sely + j;
     const uint64_t *__restrict__ mk = t.mask + j;
+    const unsigned uns = (unsigned)ns;
     // The loop only finds where the ray stops; the range is computed after it,
     // once for the whole warp, rather than in a divergent branch per lane.
+    // Indexes are unsigned 32-bit (every table and map index fits).
     int adx = 0, ady = 0, cx = hx, cy = hy;
     int stop;   // 1 hit, 2 range limit, 3 left the map
     for (;;) {
         const int lx = (cx & 7) ^ xm, ly = (cy & 7) ^ ym;   // the cell inside the tile, in the ray's frame
         // the tile's word and the exit steps are loaded together: one memory round trip per tile
-        const uint64_t word = __ldg(bits + (size_t)(cy >> 3) * TW + (cx >> 3));
-        const uint32_t kx = __ldg(selx + (size_t)(adx + 8 - lx) * ns);
-        const uint32_t ky = __ldg(sely + (size_t)(ady + 8 - ly) * ns);
+        const uint64_t word = __ldg(bits + ((unsigned)(cy >> 3) * (unsigned)TW + (unsigned)(cx >> 3)));
+        const uint32_t kx = __ldg(selx + (unsigned)(adx + 8 - lx) * uns);
+        const uint32_t ky = __ldg(sely + (unsigned)(ady + 8 - ly) * uns);
         if (word) {
             uint64_t w = word;
             if (xneg) w = bswap64(__brevll(w));   // reverse the bits of every row
             if (yneg) w = bswap64(w);             // reverse the rows
-            const uint64_t R = __ldg(mk + (size_t)(adx + ady) * ns);
-            const uint64_t hm = ((R & (0x0101010101010101ull * (0xffu >> lx))) << (lx + 8 * ly)) & w;
+            // move the current cell to bit 0; bits that wrap into the row below
+            // sit in columns the board's column mask removes
+            w >>= lx + 8 * ly;
+            const uint32_t cm = 0x01010101u * (0xffu >> lx);   // board columns dx <= 7 - lx, every row
+            const uint64_t R = __ldg(mk + (unsigned)(adx + ady) * uns) & (((uint64_t)cm << 32) | cm);
+            const uint64_t hm = R & w;
             if (hm) {
                 const int b = __ffsll((long long)hm) - 1;
-                adx += (b & 7) - lx;
-                ady += (b >> 3) - ly;
+                adx += b & 7;
+                ady += b >> 3;
                 stop = 1;
                 break;
             }
         }
-        if (kx == kSelNone && ky == kSelNone) {   // the next cell lies beyond the range limit
+        if (min(kx, ky) == kSelNone) {   // the next cell lies beyond the range limit
             stop = 2;
             break;
         }
