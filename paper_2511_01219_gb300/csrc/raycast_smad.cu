@@ -39,7 +39,6 @@ namespace relo {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRayThreads = 256;
 
 __device__ __forceinline__ uint32_t isqrt_q16(int c2) {
     // floor(sqrt(c2 * 2^32)): float estimate, one Newton correction, exact fix-up
@@ -297,11 +296,9 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-__host__ __device__ __forceinline__ size_t inner_bytes(int ns_pad) {
-    return ((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7;
-}
-__host__ __device__ __forceinline__ size_t cta_smem_bytes(int ns_pad) {
-    return inner_bytes(ns_pad) + (size_t)(ns_pad / 32 + 1) * 8;
+// shared memory of one SMAD warp: in-chunk prefixes [ns_pad + 32] and chunk prefixes [ns_pad / 32 + 1]
+__host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
+    return (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
 // Casting.  The batch's rays form one list of 32-ray chunks (request r owns
@@ -352,29 +349,27 @@ __global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict
     if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
 }
 
-// SMAD.  One CTA per hypothesis, taken from a device counter over the
+// SMAD.  One warp per hypothesis, taken from a device counter over the
 // batch's hypothesis list (request r owns slots [hyp_base_r, hyp_base_r +
-// n_hyp_r)).  The CTA reads the hypothesis's N_s ranges, each warp scans
-// 32-range chunks into exclusive in-chunk prefixes and one warp turns the
-// chunk totals into 64-bit chunk prefixes; P(t) = chunkP[t / 32] + inner[t]
-// is the cyclic prefix sum of Eq. 17 for t in [0, N_s].  The threads then
-// split the orientations, evaluate Eq. 18-19 per m and reduce the minimum
-// (Eq. 20).
-__global__ void __launch_bounds__(kRayThreads) k_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
-                                                              BatchState *bs) {
+// n_hyp_r)).  The warp reads the hypothesis's N_s ranges 32 at a time,
+// scans each chunk with shuffles into exclusive in-chunk prefixes and carries
+// the 64-bit chunk prefix; P(t) = chunkP[t / 32] + inner[t] is then the cyclic
+// prefix sum of Eq. 17 for t in [0, N_s].  The lanes split the orientations,
+// evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).  No CTA barrier:
+// each warp owns its slice of shared memory.
+__global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
+                                              BatchState *bs, int warp_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_best[kRayThreads / 32];
     __shared__ int s_base[kMaxBatchRequests + 1];
-    __shared__ int s_g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int nwarps = kRayThreads / 32;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].hyp_base;
     if (threadIdx.x == 0) s_base[R] = total_hyp;
-
+    __syncthreads();
+    unsigned char *mine = smem + (size_t)warp * warp_bytes;
     for (;;) {
-        if (threadIdx.x == 0) s_g = (int)atomicAdd(&bs->ray_work, 1u);
-        __syncthreads();
-        const int g = s_g;
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&bs->ray_work, 1u);
+        g = __shfl_sync(kFull, g, 0);
         if (g >= total_hyp) break;
         int lo = 0, hi = R - 1;   // last request whose base <= g
         while (lo < hi) {
@@ -385,42 +380,37 @@ __global__ void __launch_bounds__(kRayThreads) k_smad(const ReqDesc *__restrict_
         const ReqDesc &d = reqs[lo];
         const int h = g - s_base[lo];
         const int ns = d.ns, ns_pad = d.ns_pad, nch = ns_pad >> 5;
-        uint32_t *inner = reinterpret_cast<uint32_t *>(smem);
-        long long *chunkP = reinterpret_cast<long long *>(smem + inner_bytes(ns_pad));
-        if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
+        uint32_t *inner = reinterpret_cast<uint32_t *>(mine);
+        long long *chunkP = reinterpret_cast<long long *>(mine + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
         const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
-        for (int c = warp; c < nch; c += nwarps) {
-            const int jj = (c << 5) + lane;
-            const uint32_t r = jj < ns ? __ldg(row + jj) : 0u;
-            uint32_t sc = r;
+        long long carry = 0;
+        for (int c0 = 0; c0 < nch; c0 += 4) {
+            uint32_t r[4];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(kFull, sc, o);
-                if (lane >= o) sc += t;
+            for (int u = 0; u < 4; ++u) {   // four loads in flight
+                const int jj = ((c0 + u) << 5) + lane;
+                r[u] = (c0 + u < nch && jj < ns) ? __ldg(row + jj) : 0u;
             }
-            inner[jj] = sc - r;
-            if (lane == 31) chunkP[c + 1] = (long long)sc;   // chunk total, turned into a prefix below
-        }
-        __syncthreads();
-        if (warp == 0) {
-            long long carry = 0;
-            for (int c0 = 0; c0 < nch; c0 += 32) {
-                const int c = c0 + lane;
-                long long v = c < nch ? chunkP[c + 1] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= nch) break;
+                uint32_t sc = r[u];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    long long t = __shfl_up_sync(kFull, v, o);
-                    if (lane >= o) v += t;
+                    const uint32_t t = __shfl_up_sync(kFull, sc, o);
+                    if (lane >= o) sc += t;
                 }
-                if (c < nch) chunkP[c + 1] = carry + v;
-                carry += __shfl_sync(kFull, v, 31);
+                inner[((c0 + u) << 5) + lane] = sc - r[u];
+                if (lane == 0) chunkP[c0 + u] = carry;
+                carry += __shfl_sync(kFull, sc, 31);
             }
-            if (lane == 0) chunkP[0] = 0;
         }
-        __syncthreads();
+        inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
+        if (lane == 0) chunkP[nch] = carry;
+        __syncwarp();
         const long long sum_real = d.scan->sum_real;
         unsigned long long best = ~0ull;
-        for (int q = threadIdx.x; q < d.n_m; q += kRayThreads) {
+        for (int q = lane; q < d.n_m; q += 32) {
             const int m = q * d.n_enum;
             long long Wm = 0;
             for (int k = 0; k < d.n_iv; ++k) {
@@ -442,18 +432,14 @@ __global__ void __launch_bounds__(kRayThreads) k_smad(const ReqDesc *__restrict_
             best = key < best ? key : best;
         }
         best = warp_min_u64(best);
-        if (lane == 0) s_best[warp] = best;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long b = s_best[0];
-            for (int w = 1; w < nwarps; ++w) b = s_best[w] < b ? s_best[w] : b;
-            const unsigned long long num = b >> 20;
-            const int q = (int)(b & 0xfffffu);
+        if (lane == 0) {
+            const unsigned long long num = best >> 20;
+            const int q = (int)(best & 0xfffffu);
             d.keys[h] = (num << kHypBits) | (unsigned long long)h;
             d.smad_num[h] = (long long)num;
             d.smad_m[h] = q * d.n_enum;
         }
-        // the next iteration's first __syncthreads orders these reads before inner/chunkP are rewritten
+        __syncwarp();   // the orientation reads are done before the next hypothesis rewrites the prefixes
     }
 }
 
@@ -487,19 +473,23 @@ cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState
 }
 
 cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
-                                cudaStream_t s) {
+                        cudaStream_t s) {
     if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
-    size_t smem = cta_smem_bytes(max_ns_pad);
+    const size_t wb = smad_warp_bytes(max_ns_pad);
+    int wpc = 8;   // warps per CTA, within 200 KiB of shared memory
+    while (wpc > 1 && (size_t)wpc * wb > (size_t)200 * 1024) --wpc;
+    const size_t smem = (size_t)wpc * wb;
     cudaError_t e = cudaFuncSetAttribute(k_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smad, kRayThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smad, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    int grid = n_sm * occ;
-    if (grid > total_hyp) grid = total_hyp;
+    long long grid = (long long)n_sm * occ;
+    const long long need = ((long long)total_hyp + wpc - 1) / wpc;
+    if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_smad<<<grid, kRayThreads, smem, s>>>(reqs, R, total_hyp, bs);
+    k_smad<<<(int)grid, wpc * 32, smem, s>>>(reqs, R, total_hyp, bs, (int)wb);
     return cudaGetLastError();
 }
 

@@ -9,9 +9,9 @@
 //
 // k_select_batch: after TAM has scored one batch, the per-hypothesis
 // orientation argmax of Eq. 22 (already reduced by TAM into one 64-bit key per
-// survivor), the batch's local top-k by TAM (ties to the earlier survivor),
-// the running best over batches, and the early-termination flag once a
-// batch's best reaches tau (Remark 2).
+// survivor), the batch's local top-k by TAM (ties to the earlier survivor) by
+// rank counting, the running best over batches, and the early-termination
+// flag once a batch's best reaches tau (Remark 2).
 //
 // k_finalize: the selected pose and counters into a relo_result.
 #include <cuda_runtime.h>
@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
 }
 
 // one CTA per request: selection of batch `batch_idx` (skipped when the
-// request has fewer batches or already terminated early)
+// request has fewer batches or already terminated early).  Keys (TAM
+// descending, then survivor position) are unique, so each survivor's rank is
+// the number of smaller keys; ranks below L fill the local top-k directly.
 __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_idx) {
     __shared__ unsigned long long v[kMaxBatch];
     __shared__ int s_skip;
@@ -140,35 +142,32 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
     const int s_begin = batch_idx * d.B;
     const int s_end = min(d.K, s_begin + d.B);
     const int nb = s_end - s_begin;
-    int np2 = 1;
-    while (np2 < nb) np2 <<= 1;
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-        if (i < nb) {
-            const int s = s_begin + i;
-            const unsigned long long k = d.best_key[s];
-            const unsigned tb = (unsigned)(k >> 32);
-            const unsigned q = 0xffffffffu - (unsigned)(k & 0xffffffffu);
-            d.best_m[s] = (int)q * d.n_enum;
-            v[i] = ((unsigned long long)(~tb) << 32) | (unsigned)s;   // ascending = TAM desc, survivor asc
-        } else {
-            v[i] = ~0ull;
-        }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const int s = s_begin + i;
+        const unsigned long long k = d.best_key[s];
+        const unsigned tb = (unsigned)(k >> 32);
+        const unsigned q = 0xffffffffu - (unsigned)(k & 0xffffffffu);
+        d.best_m[s] = (int)q * d.n_enum;
+        v[i] = ((unsigned long long)(~tb) << 32) | (unsigned)s;   // ascending = TAM desc, survivor asc
     }
     __syncthreads();
-    bitonic_sort(v, np2);
     const int L = d.L;
-    const int Lb = L < nb ? L : nb;
-    for (int r = threadIdx.x; r < L; r += blockDim.x)
-        d.local[(size_t)batch_idx * L + r] = r < Lb ? (int)(v[r] & 0xffffffffu) : -1;
-    if (threadIdx.x == 0) {
-        const unsigned tb = ~(unsigned)(v[0] >> 32);
-        const unsigned s = (unsigned)(v[0] & 0xffffffffu);
-        const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
-        if (cand > st->best) st->best = cand;
-        st->n_batches += 1;
-        st->n_tam_evals += (long long)nb * d.n_orient;
-        if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const unsigned long long me = v[i];
+        int rank = 0;
+        for (int k = 0; k < nb; ++k) rank += v[k] < me ? 1 : 0;
+        if (rank < L) d.local[(size_t)batch_idx * L + rank] = (int)(me & 0xffffffffu);
+        if (rank == 0) {
+            const unsigned tb = ~(unsigned)(me >> 32);
+            const unsigned s = (unsigned)(me & 0xffffffffu);
+            const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
+            if (cand > st->best) st->best = cand;
+            st->n_batches += 1;
+            st->n_tam_evals += (long long)nb * d.n_orient;
+            if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
+        }
     }
+    for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;
 }
 
 __global__ void k_finalize(const ReqDesc *__restrict__ reqs, int R) {

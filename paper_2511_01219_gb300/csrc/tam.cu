@@ -50,9 +50,10 @@ __device__ __forceinline__ float int_float(uint32_t v) { return __uint_as_float(
 // the integer of an integral float 0 <= f < 2^23
 __device__ __forceinline__ uint32_t float_int(float f) { return __float_as_uint(f + 8388608.0f) & 0x7fffffu; }
 
-// One CTA per request: the scan preparation above, plus the reset of the
-// request's selection buffers (argmax keys 0, shifts and local top-k -1, TAM
-// scores NaN, selection state 0), so a batch needs no separate memsets.
+// CTA (request, 0) does the scan preparation above and resets the request's
+// selection buffers (argmax keys 0, shifts and local top-k -1, selection
+// state 0); all CTAs (request, y) share the fill of its TAM scores with NaN
+// (unscored), so a batch needs no separate memsets.
 __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ reqs, BatchState *bs) {
     __shared__ int warp_cnt[32];
     __shared__ long long warp_sum[32];
@@ -60,8 +61,13 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
     const ReqDesc &d = reqs[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = d.n_beams;
+    // every CTA of the request (blockIdx.y) fills its share of the TAM scores
+    const int nT = d.K * d.n_orient;
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < nT; i += gridDim.y * blockDim.x)
+        d.T[i] = __int_as_float(0x7fffffff);
+    if (blockIdx.y != 0) return;
     if (threadIdx.x == 0) s_base = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         bs->ray_work = 0u;
         bs->cast_work = 0u;
         bs->dda_steps = 0ull;
@@ -70,8 +76,6 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
         d.best_key[i] = 0ull;
         d.best_m[i] = -1;
     }
-    const int nT = d.K * d.n_orient;
-    for (int i = threadIdx.x; i < nT; i += blockDim.x) d.T[i] = __int_as_float(0x7fffffff);
     for (int i = threadIdx.x; i < d.n_batches * d.L; i += blockDim.x) d.local[i] = -1;
     if (threadIdx.x == 0) {
         d.state->best = 0ull;
@@ -352,7 +356,7 @@ int occupancy_for(int vpl, bool h2, size_t smem) {
 }  // namespace
 
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s) {
-    k_scan_prep<<<R, 1024, 0, s>>>(reqs, bs);
+    k_scan_prep<<<dim3(R, 8), 1024, 0, s>>>(reqs, bs);
     return cudaGetLastError();
 }
 
