@@ -148,12 +148,17 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // 2048, so the values, the thresholds and the per-lane counts are exact
 // integers in fp16): a value v <= mid adds sat(mid + 1 - v) = 1, a larger one
 // 0, two values per instruction.  Otherwise 32-bit integer compares.
+// resident CTAs per SM the register budget is sized for
+__host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 4 : 2) : (vpl <= 24 ? 3 : 2); }
+
 template <int VPL, bool H2>
-__global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__restrict__ reqs, int R,
-                                                       const TamSeg *__restrict__ segs, int total_tasks) {
+__global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam(const ReqDesc *__restrict__ reqs,
+                                                                             int R, const TamSeg *__restrict__ segs,
+                                                                             int total_tasks) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
     __shared__ int s_skip, s_lut_r;
+    __shared__ float s_ep[5];   // per-task constants of the epilogue (lane 0 reads them)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
     if (threadIdx.x == 0) {
@@ -175,7 +180,14 @@ __global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__rest
         const int N = d.scan->n_valid;
         const int k = d.scan->k_ret;
         __syncthreads();   // the previous task's reads of offs / lut are done
-        if (threadIdx.x == 0) s_skip = d.state->done || N <= 0;
+        if (threadIdx.x == 0) {
+            s_skip = d.state->done || N <= 0;
+            s_ep[0] = 1.0f / (float)k;                // 1 / k
+            s_ep[1] = d.res / (float)N;               // res / N
+            s_ep[2] = d.d_max - d.d_min;              // span of Eq. 29
+            s_ep[3] = 1.0f / (d.d_max - d.d_min);
+            s_ep[4] = d.res2 / (float)N;              // res^2 / N
+        }
         if (s_lut_r != r) {
             for (int i = threadIdx.x; i <= d.C + 1; i += blockDim.x) lut[i] = d.lut[i];
         }
@@ -199,7 +211,6 @@ __global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__rest
         __syncthreads();
         const int s_lo = sg.s_begin + chunk * sg.chunk;
         const int s_hi = min(sg.s_end, s_lo + sg.chunk);
-        const float Nf = (float)N;
         const int C = d.C;
         const uint32_t none = (uint32_t)C + 1u;   // table entry with zero weight
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
@@ -296,17 +307,13 @@ __global__ void __launch_bounds__(kTamWarps * 32, 4) k_tam(const ReqDesc *__rest
             clt = __reduce_add_sync(kFull, clt);
             sumb = __reduce_add_sync(kFull, sumb);
             if (lane == 0) {
-                const float ltop = sl + (float)(k - clt) * lut[bk].x;
-                const float lbar = ltop / (float)k;
-                const float wp = expf(lbar);
-                const float dd = d.res * sgs / Nf;   // d_max - dbar
+                // Eq. 27-31; exp(Lbar) * exp(-var / 2) as one exponential
+                const float lbar = (sl + (float)(k - clt) * lut[bk].x) * s_ep[0];
+                const float dd = s_ep[1] * sgs;   // d_max - dbar
                 const float dbar = d.d_max - dd;
-                const float span = d.d_max - d.d_min;
-                const float sd = fminf(dd, span) / span;
-                float var = d.res2 * ((float)sumb / Nf) - dbar * dbar;
-                var = fmaxf(var, 0.0f);
-                const float cc = expf(-0.5f * var);
-                const float T = cbrtf(wp * sd * cc);
+                const float sd = fminf(dd, s_ep[2]) * s_ep[3];
+                const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
+                const float T = cbrtf(expf(lbar - 0.5f * var) * sd);
                 d.T[(size_t)s * d.n_orient + q] = T;
                 const unsigned long long key =
                     ((unsigned long long)__float_as_uint(T) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
@@ -334,7 +341,9 @@ int tam_occupancy(size_t smem) {
     return occ;
 }
 
-#define RELO_TAM_VPLS(X) X(8) X(12) X(16) X(20) X(24) X(28) X(32) X(36) X(40) X(44) X(48) X(52) X(56) X(60) X(64)
+#define RELO_TAM_VPLS(X)                                                                                       \
+    X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32) X(34) X(36) X(38) X(40) X(42) X(44) \
+        X(46) X(48) X(50) X(52) X(54) X(56) X(58) X(60) X(62) X(64)
 
 int vpl_bucket(int max_beams) {
     const int need = (max_beams + 31) / 32;
