@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // integers in fp16): a value v <= mid adds sat(mid + 1 - v) = 1, a larger one
 // 0, two values per instruction.  Otherwise 32-bit integer compares.
 // resident CTAs per SM the register budget is sized for
-__host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 4 : 2) : (vpl <= 24 ? 3 : 2); }
+__host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 6 : 2) : (vpl <= 24 ? 3 : 2); }
 
 template <int VPL, bool H2>
 __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam(const ReqDesc *__restrict__ reqs,
@@ -241,10 +241,13 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                 while (blo < bhi) {
                     const int mid = (blo + bhi) >> 1;
                     const __half2 m1 = __float2half2_rn(int_float((uint32_t)mid + 1u));
-                    __half2 acc = __float2half2_rn(0.0f);
+                    __half2 acc0 = __float2half2_rn(0.0f), acc1 = acc0;   // two chains: half the add latency
 #pragma unroll
-                    for (int t = 0; t < VPL / 2; ++t) acc = __hadd2(acc, __hsub2_sat(m1, hv[t]));
-                    const float2 af = __half22float2(acc);
+                    for (int t = 0; t < VPL / 2; t += 2) {
+                        acc0 = __hadd2(acc0, __hsub2_sat(m1, hv[t]));
+                        if (t + 1 < VPL / 2) acc1 = __hadd2(acc1, __hsub2_sat(m1, hv[t + 1]));
+                    }
+                    const float2 af = __half22float2(__hadd2(acc0, acc1));
                     const int c = __reduce_add_sync(kFull, (int)float_int(af.x + af.y));
                     if (c >= k) bhi = mid;
                     else blo = mid + 1;
