@@ -296,28 +296,9 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-// shared memory of one SMAD warp: two row buffers of [ns_pad + 32] words (one
-// being scanned in place into in-chunk prefixes, the next hypothesis's row
-// arriving in the other) and the chunk prefixes [ns_pad / 32 + 1]
-__host__ __device__ __forceinline__ size_t smad_row_words(int ns_pad) { return (size_t)((ns_pad + 32 + 3) & ~3); }
-__host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {   // a multiple of 16: 16-byte copies
-    return (2 * smad_row_words(ns_pad) * 4 + (size_t)(ns_pad / 32 + 1) * 8 + 15) & ~(size_t)15;
-}
-
-// Asynchronous copy of one hypothesis's N_s ranges into shared memory by the
-// 32 lanes of a warp (16-byte copies when source and size allow, else 4-byte);
-// the words past N_s up to ns_pad + 32 are zeroed with plain stores.
-__device__ __forceinline__ void smad_fetch_row(uint32_t *dst, const uint32_t *src, int ns, int ns_pad, int lane) {
-    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
-    if (((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (ns & 3) == 0) {
-        for (int i = lane; i < (ns >> 2); i += 32)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16u * (unsigned)i), "l"(src + 4 * i));
-    } else {
-        for (int i = lane; i < ns; i += 32)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sdst + 4u * (unsigned)i), "l"(src + i));
-    }
-    for (int i = ns + lane; i < ns_pad + 32; i += 32) dst[i] = 0u;
-    asm volatile("cp.async.commit_group;\n" ::);
+// shared memory of one SMAD warp: in-chunk prefixes [ns_pad + 32] and chunk prefixes [ns_pad / 32 + 1]
+__host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
+    return (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
 // Casting.  The batch's rays form one list of 32-ray chunks (request r owns
@@ -370,78 +351,63 @@ __global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict
 
 // SMAD.  One warp per hypothesis, taken from a device counter over the
 // batch's hypothesis list (request r owns slots [hyp_base_r, hyp_base_r +
-// n_hyp_r)).  While the warp works on one hypothesis, the row of the next one
-// it has taken is already being copied into its other buffer.  The warp scans
-// the row in place, chunk by chunk, into exclusive in-chunk prefixes and
-// carries the 64-bit chunk prefix; P(t) = chunkP[t / 32] + inner[t] is then
-// the cyclic prefix sum of Eq. 17 for t in [0, N_s].  The lanes split the
-// orientations, evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).  No
-// CTA barrier: each warp owns its slice of shared memory.
+// n_hyp_r)).  The warp reads the hypothesis's N_s ranges 32 at a time,
+// scans each chunk with shuffles into exclusive in-chunk prefixes and carries
+// the 64-bit chunk prefix; P(t) = chunkP[t / 32] + inner[t] is then the cyclic
+// prefix sum of Eq. 17 for t in [0, N_s].  The lanes split the orientations,
+// evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).  No CTA barrier:
+// each warp owns its slice of shared memory.
 __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
-                                              BatchState *bs, int row_words, int warp_bytes) {
+                                              BatchState *bs, int warp_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].hyp_base;
     if (threadIdx.x == 0) s_base[R] = total_hyp;
     __syncthreads();
-    uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem + (size_t)warp * warp_bytes);
-    uint32_t *buf1 = buf0 + row_words;
-    long long *chunkP = reinterpret_cast<long long *>(buf1 + row_words);
-
-    auto take = [&]() {
+    unsigned char *mine = smem + (size_t)warp * warp_bytes;
+    for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&bs->ray_work, 1u);
-        return __shfl_sync(kFull, g, 0);
-    };
-    auto locate = [&](int g, int *h) {   // request of slot g and the hypothesis index inside it
-        int lo = 0, hi = R - 1;
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= total_hyp) break;
+        int lo = 0, hi = R - 1;   // last request whose base <= g
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_base[mid] <= g) lo = mid;
             else hi = mid - 1;
         }
-        *h = g - s_base[lo];
-        return lo;
-    };
-    int g = take();
-    if (g < total_hyp) {
-        int h;
-        const ReqDesc &d = reqs[locate(g, &h)];
-        smad_fetch_row(buf0, d.scan_table + (size_t)h * d.ns, d.ns, d.ns_pad, lane);
-    }
-    uint32_t *cur = buf0, *nxt = buf1;
-    while (g < total_hyp) {
-        const int gn = take();
-        if (gn < total_hyp) {
-            int hn;
-            const ReqDesc &dn = reqs[locate(gn, &hn)];
-            smad_fetch_row(nxt, dn.scan_table + (size_t)hn * dn.ns, dn.ns, dn.ns_pad, lane);
-            asm volatile("cp.async.wait_group 1;\n" ::);
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-        }
-        __syncwarp();
-        int h;
-        const ReqDesc &d = reqs[locate(g, &h)];
-        const int ns = d.ns, nch = d.ns_pad >> 5;
+        const ReqDesc &d = reqs[lo];
+        const int h = g - s_base[lo];
+        const int ns = d.ns, ns_pad = d.ns_pad, nch = ns_pad >> 5;
+        uint32_t *inner = reinterpret_cast<uint32_t *>(mine);
+        long long *chunkP = reinterpret_cast<long long *>(mine + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
+        const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
         long long carry = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int jj = (c << 5) + lane;
-            const uint32_t r = cur[jj];
-            uint32_t sc = r;
+        for (int c0 = 0; c0 < nch; c0 += 4) {
+            uint32_t r[4];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, sc, o);
-                if (lane >= o) sc += t;
+            for (int u = 0; u < 4; ++u) {   // four loads in flight
+                const int jj = ((c0 + u) << 5) + lane;
+                r[u] = (c0 + u < nch && jj < ns) ? __ldg(row + jj) : 0u;
             }
-            cur[jj] = sc - r;
-            if (lane == 0) chunkP[c] = carry;
-            carry += __shfl_sync(kFull, sc, 31);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= nch) break;
+                uint32_t sc = r[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, sc, o);
+                    if (lane >= o) sc += t;
+                }
+                inner[((c0 + u) << 5) + lane] = sc - r[u];
+                if (lane == 0) chunkP[c0 + u] = carry;
+                carry += __shfl_sync(kFull, sc, 31);
+            }
         }
+        inner[ns_pad + lane] = 0u;   // P(t) for t in [ns_pad, ns_pad + 32) adds nothing
         if (lane == 0) chunkP[nch] = carry;
         __syncwarp();
-        const uint32_t *inner = cur;
         const long long sum_real = d.scan->sum_real;
         unsigned long long best = ~0ull;
         for (int q = lane; q < d.n_m; q += 32) {
@@ -473,11 +439,7 @@ __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, 
             d.smad_num[h] = (long long)num;
             d.smad_m[h] = q * d.n_enum;
         }
-        __syncwarp();   // every lane is done with this buffer before it receives the row after next
-        uint32_t *t = cur;
-        cur = nxt;
-        nxt = t;
-        g = gn;
+        __syncwarp();   // the orientation reads are done before the next hypothesis rewrites the prefixes
     }
 }
 
@@ -527,7 +489,7 @@ cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pa
     const long long need = ((long long)total_hyp + wpc - 1) / wpc;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_smad<<<(int)grid, wpc * 32, smem, s>>>(reqs, R, total_hyp, bs, (int)smad_row_words(max_ns_pad), (int)wb);
+    k_smad<<<(int)grid, wpc * 32, smem, s>>>(reqs, R, total_hyp, bs, (int)wb);
     return cudaGetLastError();
 }
 
