@@ -229,9 +229,15 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
  * device finishes its queued work).  Loading a new grid into a map
  * (relo_update_map*), setting its hypotheses, unloading it or changing the
  * parameters frees its tables.
- * relo_scan_cache_stats writes min(n, 5) counters to out: tables held, bytes
- * held, requests that read a table, requests that cast their rays (and
- * stored them when the budget allowed), tables evicted. */
+ * For each stored table and sensor plan (FoV intervals, Theta) the context
+ * also keeps, within the same budget, the window sums W_m of Eq. 18 of every
+ * hypothesis sorted ascending: they do not depend on the real scan either, so
+ * the SMAD minimum of Eq. 19-20 becomes a nearest-value search around
+ * sum R_real (the same numerator and the same m, ties to the smaller m).
+ * relo_scan_cache_stats writes min(n, 7) counters to out: tables held, bytes
+ * held (scan and window tables), requests that read a table, requests that
+ * cast their rays (and stored them when the budget allowed), tables evicted,
+ * window tables held, requests whose SMAD read a window table. */
 int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
 
 /* Stage timing (tracing).  With profiling on, the context records a CUDA

@@ -296,10 +296,11 @@ class Relo:
         return int(self.scan_info()[8])
 
     def scan_cache_stats(self) -> dict:
-        """Resident synthesized scans: tables and bytes held, requests that read a table, requests that cast, evictions."""
-        v = (ctypes.c_int64 * 5)()
-        self._check(self._L.relo_scan_cache_stats(self._h, v, 5), "scan_cache_stats")
-        return dict(zip(["tables", "bytes", "hits", "misses", "evictions"], list(v)))
+        """Resident synthesized scans: tables and bytes held, requests that read a table, requests that cast,
+        evictions, window tables held, requests whose SMAD read a window table."""
+        v = (ctypes.c_int64 * 7)()
+        self._check(self._L.relo_scan_cache_stats(self._h, v, 7), "scan_cache_stats")
+        return dict(zip(["tables", "bytes", "hits", "misses", "evictions", "win_tables", "win_hits"], list(v)))
 
     def kernels_launched(self) -> int:
         k = ctypes.c_int64(0)

@@ -443,6 +443,186 @@ __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, 
     }
 }
 
+// Window tables.  k_win_build: one CTA per hypothesis of the build list.
+// It scans the hypothesis's row into prefixes (as k_smad), evaluates W_m of
+// Eq. 18 for every m of Theta, takes the SMAD minimum as k_smad does, and
+// sorts the keys W_m << 13 | q ascending (bitonic, in shared memory) into the
+// request's window table.
+__device__ __forceinline__ int list_request(const int *s_base, int R, int g) {   // last request whose base <= g
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_base[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_win_build(const ReqDesc *__restrict__ reqs, int R, int total, int nm_pad_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    __shared__ unsigned long long s_best[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].wbuild_base;
+    if (threadIdx.x == 0) s_base[R] = total;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem);   // [nm_pad_max]
+    unsigned char *rest = smem + (size_t)nm_pad_max * 8;
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        __syncthreads();   // s_base ready; the previous hypothesis is done with shared memory
+        const int r = list_request(s_base, R, g);
+        const ReqDesc &d = reqs[r];
+        const int h = g - s_base[r];
+        const int ns = d.ns, ns_pad = d.ns_pad, nch = ns_pad >> 5, n_m = d.n_m;
+        uint32_t *inner = reinterpret_cast<uint32_t *>(rest);
+        long long *chunkP = reinterpret_cast<long long *>(rest + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
+        if (threadIdx.x < 32) inner[ns_pad + lane] = 0u;
+        const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
+        for (int c = warp; c < nch; c += nwarps) {
+            const int jj = (c << 5) + lane;
+            const uint32_t rv = jj < ns ? __ldg(row + jj) : 0u;
+            uint32_t sc = rv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, sc, o);
+                if (lane >= o) sc += t;
+            }
+            inner[jj] = sc - rv;
+            if (lane == 31) chunkP[c + 1] = (long long)sc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            long long carry = 0;
+            for (int c0 = 0; c0 < nch; c0 += 32) {
+                const int c = c0 + lane;
+                long long v = c < nch ? chunkP[c + 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long t = __shfl_up_sync(kFull, v, o);
+                    if (lane >= o) v += t;
+                }
+                if (c < nch) chunkP[c + 1] = carry + v;
+                carry += __shfl_sync(kFull, v, 31);
+            }
+            if (lane == 0) chunkP[0] = 0;
+        }
+        __syncthreads();
+        int nm_pad = 1;
+        while (nm_pad < n_m) nm_pad <<= 1;
+        const long long sum_real = d.scan->sum_real;
+        unsigned long long best = ~0ull;
+        for (int q = threadIdx.x; q < nm_pad; q += blockDim.x) {
+            if (q >= n_m) {
+                keys[q] = ~0ull;
+                continue;
+            }
+            const int m = q * d.n_enum;
+            long long Wm = 0;
+            for (int k = 0; k < d.n_iv; ++k) {
+                const int2 iv = d.iv[k];
+                int s0 = iv.x + m;
+                if (s0 >= ns) s0 -= ns;
+                const int e = s0 + iv.y;
+                const long long p0 = chunkP[s0 >> 5] + inner[s0];
+                if (e <= ns) {
+                    Wm += chunkP[e >> 5] + inner[e] - p0;
+                } else {
+                    const int e2 = e - ns;
+                    Wm += (chunkP[ns >> 5] + inner[ns] - p0) + (chunkP[e2 >> 5] + inner[e2]);
+                }
+            }
+            keys[q] = ((unsigned long long)Wm << kWinQBits) | (unsigned)q;
+            long long dnum = sum_real - Wm;
+            if (dnum < 0) dnum = -dnum;
+            const unsigned long long key = ((unsigned long long)dnum << 20) | (unsigned)q;
+            best = key < best ? key : best;
+        }
+        best = warp_min_u64(best);
+        if (lane == 0) s_best[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = s_best[0];
+            for (int w = 1; w < nwarps; ++w) b = s_best[w] < b ? s_best[w] : b;
+            const unsigned long long num = b >> 20;
+            const int q = (int)(b & 0xfffffu);
+            d.keys[h] = (num << kHypBits) | (unsigned long long)h;
+            d.smad_num[h] = (long long)num;
+            d.smad_m[h] = q * d.n_enum;
+        }
+        // bitonic sort of the keys, ascending
+        for (int k = 2; k <= nm_pad; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < nm_pad; i += blockDim.x) {
+                    const int p = i ^ j;
+                    if (p > i) {
+                        const unsigned long long a = keys[i], b = keys[p];
+                        if ((a > b) == ((i & k) == 0)) {
+                            keys[i] = b;
+                            keys[p] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        unsigned long long *out = d.win + (size_t)h * n_m;
+        for (int i = threadIdx.x; i < n_m; i += blockDim.x) out[i] = keys[i];
+    }
+}
+
+// k_win_read: one thread per hypothesis of the read list.  With S = sum
+// R_real, the nearest W_m at or above S is the first key >= S << 13, and the
+// nearest below is the key before it; each run of equal W_m starts with its
+// smallest q, so the run start found by a second search is the smaller m of
+// that value.  The closer of the two wins and a tie goes to the smaller m:
+// exactly the minimum k_smad takes (Eq. 20).
+__device__ __forceinline__ int lower_bound_u64(const unsigned long long *__restrict__ a, int n, unsigned long long x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_win_read(const ReqDesc *__restrict__ reqs, int R, int total) {
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].wread_base;
+    if (threadIdx.x == 0) s_base[R] = total;
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const int r = list_request(s_base, R, g);
+        const ReqDesc &d = reqs[r];
+        const int h = g - s_base[r];
+        const int n_m = d.n_m;
+        const unsigned long long *keys = d.win + (size_t)h * n_m;
+        const long long S = d.scan->sum_real;
+        const unsigned long long qmask = (1ull << kWinQBits) - 1ull;
+        const int pa = lower_bound_u64(keys, n_m, (unsigned long long)S << kWinQBits);
+        long long dist = -1;
+        unsigned q = 0;
+        if (pa < n_m) {
+            const unsigned long long ka = __ldg(keys + pa);
+            dist = (long long)(ka >> kWinQBits) - S;
+            q = (unsigned)(ka & qmask);
+        }
+        if (pa > 0) {
+            const unsigned long long wb = __ldg(keys + pa - 1) >> kWinQBits;
+            const long long db = S - (long long)wb;
+            if (dist < 0 || db <= dist) {
+                const int pb = lower_bound_u64(keys, pa - 1, wb << kWinQBits);   // start of the run of wb
+                const unsigned qb = (unsigned)(__ldg(keys + pb) & qmask);
+                if (dist < 0 || db < dist || qb < q) q = qb;
+                dist = db;
+            }
+        }
+        d.keys[h] = ((unsigned long long)dist << kHypBits) | (unsigned long long)h;
+        d.smad_num[h] = dist;
+        d.smad_m[h] = (int)q * d.n_enum;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__ ranges, int32_t *__restrict__ hits) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= a.n_hyp) return;
@@ -490,6 +670,33 @@ cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pa
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     k_smad<<<(int)grid, wpc * 32, smem, s>>>(reqs, R, total_hyp, bs, (int)wb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_win_build(const ReqDesc *reqs, int R, int total, int max_ns_pad, int max_nm, cudaStream_t s) {
+    if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
+    if (total <= 0) return cudaSuccess;
+    int nm_pad = 1;
+    while (nm_pad < max_nm) nm_pad <<= 1;
+    const size_t smem = (size_t)nm_pad * 8 + (((size_t)(max_ns_pad + 32) * 4 + 7) & ~(size_t)7) +
+                        (size_t)(max_ns_pad / 32 + 1) * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_win_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, n_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_win_build, 256, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int grid = total < n_sm * occ ? total : n_sm * occ;
+    k_win_build<<<grid, 256, smem, s>>>(reqs, R, total, nm_pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_win_read(const ReqDesc *reqs, int R, int total, cudaStream_t s) {
+    if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
+    if (total <= 0) return cudaSuccess;
+    k_win_read<<<(total + 255) / 256, 256, 0, s>>>(reqs, R, total);
     return cudaGetLastError();
 }
 

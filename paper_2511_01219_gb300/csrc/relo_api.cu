@@ -41,6 +41,15 @@ struct SensorPlan {
 
 // Resident synthesized scans of one map and hypothesis set for one beam grid
 // N_s and range limit: [n_hyp * ns] uint32 Q16 ranges, row per hypothesis.
+// Sorted window sums of one scan table for one sensor plan (intervals, Theta).
+struct WinTable {
+    int n_enum = 0, n_m = 0;
+    std::vector<int2> iv;
+    unsigned long long *keys = nullptr;   // [n_hyp][n_m] W_m << 13 | q, ascending per hypothesis
+    size_t bytes = 0;
+    cudaEvent_t built = nullptr;          // recorded after the kernel that builds it
+};
+
 struct ScanTable {
     int ns = 0, lim = 0;
     uint32_t *data = nullptr;
@@ -48,6 +57,7 @@ struct ScanTable {
     cudaEvent_t written = nullptr;    // recorded after the ray-cast launch that stores the table
     unsigned long long last_use = 0;
     unsigned long long pin = 0;       // batch sequence number of the last batch that used it
+    std::vector<WinTable *> wins;     // derived window tables (freed with the scan table)
 };
 
 // Per-direction traversal tables of one (N_s, range limit); see RayTables.
@@ -152,7 +162,7 @@ struct relo_ctx {
     // per-direction traversal tables
     std::vector<RayTab *> raytabs;
     // resident synthesized scans
-    long long table_bytes = 0, cache_hits = 0, cache_misses = 0, cache_evictions = 0;
+    long long table_bytes = 0, cache_hits = 0, cache_misses = 0, cache_evictions = 0, win_hits = 0;
     unsigned long long table_clock = 0, batch_seq = 0;
 };
 
@@ -426,7 +436,16 @@ MapSlot *get_map(relo_ctx *ctx, int id) {
 
 // ---- resident synthesized scans ------------------------------------------------------------------
 
+void free_win(relo_ctx *ctx, WinTable *w) {
+    dev_free(ctx, w->keys, w->bytes);
+    ctx->table_bytes -= (long long)w->bytes;
+    if (w->built) cudaEventDestroy(w->built);
+    delete w;
+}
+
 void free_table(relo_ctx *ctx, ScanTable *t) {
+    for (WinTable *w : t->wins) free_win(ctx, w);
+    t->wins.clear();
     dev_free(ctx, t->data, t->bytes);
     ctx->table_bytes -= (long long)t->bytes;
     if (t->written) cudaEventDestroy(t->written);
@@ -439,6 +458,15 @@ void drop_tables(relo_ctx *ctx, MapSlot &m) {
     cudaDeviceSynchronize();
     for (ScanTable *t : m.tables) free_table(ctx, t);
     m.tables.clear();
+}
+
+WinTable *find_win(ScanTable *t, const SensorPlan &P) {
+    for (WinTable *w : t->wins)
+        if (w->n_enum == P.n_enum && w->n_m == P.n_m && w->iv.size() == P.iv.size() &&
+            std::equal(w->iv.begin(), w->iv.end(), P.iv.begin(),
+                       [](const int2 &a, const int2 &b) { return a.x == b.x && a.y == b.y; }))
+            return w;
+    return nullptr;
 }
 
 ScanTable *find_table(MapSlot &m, int ns, int lim) {
@@ -572,6 +600,34 @@ RayTables ray_tables_view(const RayTab *t) {
         v.kmax = t->kmax;
     }
     return v;
+}
+
+// A new, unbuilt window table of scan table t for plan P, or nullptr when the
+// budget cannot hold it (not an error: the request then takes SMAD from the ranges).
+WinTable *new_win(relo_ctx *ctx, ScanTable *t, const SensorPlan &P, int n_hyp) {
+    const size_t bytes = 8 * (size_t)n_hyp * (size_t)P.n_m;
+    if (!make_room(ctx, bytes)) return nullptr;
+    WinTable *w = new (std::nothrow) WinTable();
+    if (!w) return nullptr;
+    const std::string saved = ctx->err;
+    if (dev_alloc(ctx, (void **)&w->keys, bytes, "window table") != RELO_OK) {
+        ctx->err = saved;
+        delete w;
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&w->built, cudaEventDisableTiming) != cudaSuccess) {
+        w->built = nullptr;
+        dev_free(ctx, w->keys, bytes);
+        delete w;
+        return nullptr;
+    }
+    w->n_enum = P.n_enum;
+    w->n_m = P.n_m;
+    w->iv = P.iv;
+    w->bytes = bytes;
+    ctx->table_bytes += (long long)bytes;
+    t->wins.push_back(w);
+    return w;
 }
 
 void free_map(relo_ctx *ctx, MapSlot &m) {
@@ -800,6 +856,43 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             }
         }
     }
+    // Window tables of the requests with a scan table: read one built by an
+    // earlier launch, or build it now (one builder per table).
+    std::vector<WinTable *> win((size_t)R, nullptr);
+    std::vector<int> wmode((size_t)R, kWinNone);
+    struct NewWins {   // window tables this batch builds; freed again if the batch fails to launch
+        relo_ctx *ctx;
+        std::vector<std::pair<ScanTable *, WinTable *>> list;
+        bool keep = false;
+        bool has(const WinTable *w) const {
+            for (auto &x : list)
+                if (x.second == w) return true;
+            return false;
+        }
+        ~NewWins() {
+            if (keep || list.empty()) return;
+            cudaDeviceSynchronize();
+            for (auto &x : list) {
+                auto &v = x.first->wins;
+                v.erase(std::find(v.begin(), v.end(), x.second));
+                free_win(ctx, x.second);
+            }
+        }
+    } wnew{ctx, {}, false};
+    for (int r = 0; r < R; ++r) {
+        if (!tab[r]) continue;
+        WinTable *w = find_win(tab[r], *pr[r].P);
+        if (w && !wnew.has(w)) {
+            wmode[r] = kWinRead;
+            ++ctx->win_hits;
+        } else if (!w && (w = new_win(ctx, tab[r], *pr[r].P, pr[r].m->n_hyp))) {
+            wmode[r] = kWinBuild;
+            wnew.list.push_back({tab[r], w});
+        } else {
+            w = nullptr;
+        }
+        win[r] = w;
+    }
     std::vector<ReqDesc> desc((size_t)R);
     std::vector<size_t> off((size_t)R);
     size_t total = 0;
@@ -895,14 +988,24 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.result = q.result_dev;
         d.scan_table = mode[r] == kScanCast ? (uint32_t *)take(4ull * m.n_hyp * P.ns) : tab[r]->data;
         d.scan_mode = mode[r];
+        d.win = win[r] ? win[r]->keys : nullptr;
+        d.win_mode = wmode[r];
     }
-    int base = 0, cbase = 0;
+    // work lists: each kernel sees only its requests (the others take the running base, length 0)
+    int base = 0, cbase = 0, bbase = 0, rbase = 0, max_nm = 1;
     for (int r = 0; r < R; ++r) {
-        desc[r].hyp_base = base;
-        base += desc[r].n_hyp;
-        desc[r].chunk_base = cbase;
-        if (desc[r].scan_mode != kScanRead) cbase += desc[r].n_hyp * (desc[r].ns_pad >> 5);
+        ReqDesc &d = desc[r];
+        d.hyp_base = base;
+        d.wbuild_base = bbase;
+        d.wread_base = rbase;
+        d.chunk_base = cbase;
+        if (d.win_mode == kWinNone) base += d.n_hyp;
+        if (d.win_mode == kWinBuild) bbase += d.n_hyp;
+        if (d.win_mode == kWinRead) rbase += d.n_hyp;
+        if (d.scan_mode != kScanRead) cbase += d.n_hyp * (d.ns_pad >> 5);
+        if (d.win_mode == kWinBuild) max_nm = std::max(max_nm, d.n_m);
     }
+    const int total_smad = base, total_build = bbase, total_read = rbase;
     // TAM work of every batch index
     std::vector<TamSeg> segs((size_t)max_batches * R);
     std::vector<TamPlan> plans((size_t)max_batches);
@@ -924,13 +1027,22 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
     for (int r = 0; r < R; ++r) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
+        if (wmode[r] == kWinRead) CK(cudaStreamWaitEvent(st, win[r]->built, 0), "window table");
         if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
     }
     if (total_chunks > 0)
         CK(timed_on(ctx, st, 2, 1, [&] { return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st); }),
            "ray cast");
-    CK(timed_on(ctx, st, 6, 1, [&] { return launch_smad(rq, R, total_hyp, max_ns_pad, sl.bs, ctx->n_sm, st); }),
-       "SMAD");
+    if (total_smad > 0)
+        CK(timed_on(ctx, st, 6, 1, [&] { return launch_smad(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st); }),
+           "SMAD");
+    if (total_build > 0) {
+        CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_build(rq, R, total_build, max_ns_pad, max_nm, st); }),
+           "SMAD window tables");
+        for (auto &x : wnew.list) CK(cudaEventRecord(x.second->built, st), "window table");
+    }
+    if (total_read > 0)
+        CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_read(rq, R, total_read, st); }), "SMAD by window tables");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {
@@ -940,6 +1052,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     }
     CK(timed_on(ctx, st, 5, 1, [&] { return launch_finalize(rq, R, st); }), "finalize");
     created.keep = true;
+    wnew.keep = true;
     ctx->last = desc[0];
     ctx->last_bs = sl.bs;
     ctx->has_last = true;
@@ -1602,8 +1715,13 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {
     long long tables = 0;
     for (const MapSlot &m : ctx->maps)
         if (m.live) tables += (long long)m.tables.size();
-    const long long v[5] = {tables, ctx->table_bytes, ctx->cache_hits, ctx->cache_misses, ctx->cache_evictions};
-    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    long long wins = 0;
+    for (const MapSlot &m : ctx->maps)
+        if (m.live)
+            for (const ScanTable *t : m.tables) wins += (long long)t->wins.size();
+    const long long v[7] = {tables, ctx->table_bytes, ctx->cache_hits, ctx->cache_misses, ctx->cache_evictions,
+                            wins, ctx->win_hits};
+    for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
     return RELO_OK;
 }
 

@@ -163,7 +163,20 @@ struct ReqDesc {
     uint32_t *scan_table;
     int scan_mode;               // kScanCast, kScanStore or kScanRead
     int chunk_base;              // first 32-ray chunk of this request in the batch's cast list
+    // resident window sums of (map, hypotheses, N_s, lim, intervals, Theta): per hypothesis the n_m keys
+    // W_m << 13 | q (W_m the window sum of Eq. 18 at m = q n_enum), ascending
+    unsigned long long *win;
+    int win_mode;                // kWinNone (SMAD from the ranges), kWinBuild or kWinRead
+    int wbuild_base, wread_base; // first slot of this request in the window-build / window-read lists
 };
+
+// SMAD by window tables.  W_m depends on the map, the hypothesis and the
+// sensor plan, never on the real scan, so min over m of |sum R_real - W_m|
+// (Eq. 19-20) is a nearest-value search in the sorted W_m.
+constexpr int kWinNone = 0;
+constexpr int kWinBuild = 1;     // SMAD from the ranges, and the sorted keys stored into win
+constexpr int kWinRead = 2;      // SMAD by binary search in win
+constexpr int kWinQBits = 13;    // q < 8192 = kMaxNs
 
 // Where a request's synthesized ranges come from.  The cast kernel writes
 // them into scan_table (request scratch for kScanCast, a resident table for
@@ -205,7 +218,11 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStr
 cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s);
 // SMAD of every hypothesis of the batch from the requests' scan tables
 cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
-                                cudaStream_t s);
+                        cudaStream_t s);
+// SMAD of the window-build requests' hypotheses, storing their sorted window keys
+cudaError_t launch_win_build(const ReqDesc *reqs, int R, int total, int max_ns_pad, int max_nm, cudaStream_t s);
+// SMAD of the window-read requests' hypotheses by search in their window keys
+cudaError_t launch_win_read(const ReqDesc *reqs, int R, int total, cudaStream_t s);
 cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s);
 // plans the TAM launch of one batch index: fills segs[R] and returns the task count and grid size
 struct TamPlan {

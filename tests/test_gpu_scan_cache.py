@@ -71,12 +71,14 @@ def test_office_table_read_equals_cast(relo, workload):
     want = plain.relocalize(ids[0], wl.ranges, wl.angles, wl.max_range).as_dict()
     want_st = stage_arrays(relo, plain, len(wl.hyps), K, n_orient)
     for rep in range(3):
+        # call 0 casts, stores the ranges and builds the window table; calls 1 and 2 read the windows
         got = cached.relocalize(ids[1], wl.ranges, wl.angles, wl.max_range).as_dict()
         assert got == want
         assert_same(stage_arrays(relo, cached, len(wl.hyps), K, n_orient), want_st)
         st = cached.scan_cache_stats()
         assert st["tables"] == 1 and st["misses"] == 1 and st["hits"] == rep
-        assert st["bytes"] == 4 * len(wl.hyps) * 1440
+        assert st["win_tables"] == 1 and st["win_hits"] == rep
+        assert st["bytes"] == 4 * len(wl.hyps) * 1440 + 8 * len(wl.hyps) * n_orient
         info = cached.scan_info()
         assert (info[8] == 0) == (rep > 0)   # no ray is cast once the table is stored
     plain.close()
@@ -147,7 +149,9 @@ def test_small_budget_evicts_least_recently_used(relo):
         z, ang, want = (za, anga, want_a) if which == "a" else (zb, angb, want_b)
         assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
     st = ctx.scan_cache_stats()
-    assert st == {"tables": 1, "bytes": 192000, "hits": 1, "misses": 5, "evictions": 4}
+    # a window table (400 x 40 x 8 B) never fits beside its scan table in this budget
+    assert st == {"tables": 1, "bytes": 192000, "hits": 1, "misses": 5, "evictions": 4, "win_tables": 0,
+                  "win_hits": 0}
     ctx.close()
     # a table larger than the whole budget is never stored
     ctx = relo.Relo(scan_cache_bytes=1000, **prm)
@@ -155,7 +159,8 @@ def test_small_budget_evicts_least_recently_used(relo):
     ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
     for _ in range(2):
         assert ctx.relocalize(mid, za, anga, 4.0).as_dict() == want_a
-    assert ctx.scan_cache_stats() == {"tables": 0, "bytes": 0, "hits": 0, "misses": 2, "evictions": 0}
+    assert ctx.scan_cache_stats() == {"tables": 0, "bytes": 0, "hits": 0, "misses": 2, "evictions": 0,
+                                      "win_tables": 0, "win_hits": 0}
     ctx.close()
 
 
@@ -169,11 +174,12 @@ def test_one_geometry_twice_in_one_batch(relo):
     mid = ctx.load_map(g, 0.05)
     ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
     items = [(mid, z1, ang, 4.0), (mid, z2, ang, 4.0)]
-    # first batch: request 0 stores the table, request 1 casts; second batch: both read
+    # first batch: request 0 stores the table and builds its window table, request 1 casts into its
+    # scratch; second batch: both read the window table
     for _ in range(2):
         assert [r.as_dict() for r in ctx.relocalize_batch(items)] == want
-    assert ctx.scan_cache_stats() == {"tables": 1, "bytes": 4 * len(hyps) * 120, "hits": 2, "misses": 2,
-                                      "evictions": 0}
+    assert ctx.scan_cache_stats() == {"tables": 1, "bytes": 4 * len(hyps) * 120 + 8 * len(hyps) * 40, "hits": 2,
+                                      "misses": 2, "evictions": 0, "win_tables": 1, "win_hits": 2}
     ctx.close()
 
 
@@ -213,5 +219,39 @@ def test_served_stream_with_tables_equals_alone(relo):
         assert status == relo.OK and res.as_dict() == alone[i]
     st = served.scan_cache_stats()
     assert st["tables"] == 4 and st["hits"] > 0 and st["hits"] + st["misses"] == len(tickets)
+    assert st["win_tables"] == 6 and st["win_hits"] > 0   # three plans per map, two sharing N_s = 120
     plain.close()
     served.close()
+
+
+def test_window_search_keeps_the_smaller_m_on_ties(relo):
+    """A square room seen from points on its axes of symmetry: many orientations
+    give the same window sum, and pairs of orientations lie at the same distance
+    on either side of sum R_real.  SMAD by window search must pick the same
+    (numerator, m) as the direct minimum, smaller m on every tie."""
+    import torch
+    n = 96
+    g = np.zeros((n, n), np.int8)
+    g[0, :] = g[-1, :] = g[:, 0] = g[:, -1] = 100
+    c = n // 2
+    cells = np.array([[c, c], [c, c - 20], [c - 20, c], [c + 13, c + 13], [c - 7, c + 7], [c, 9]], np.int32)
+    prm = dict(n_orient=40, topk=6, batch=6, local_topk=3, early_stop=0, max_range=6.0)
+    for n_beams, ns, theta in ((90, 120, 0.0), (60, 120, np.pi / 2), (100, 160, 0.3)):
+        ang = workloads.beam_angles(n_beams, ns)
+        for h in range(len(cells)):
+            z = workloads.render_scan(g, 0.05, ((cells[h, 0] + 0.5) * 0.05, (cells[h, 1] + 0.5) * 0.05, theta), ang, 5.0)
+            out = []
+            for cache in (0, GIB):
+                ctx = relo.Relo(scan_cache_bytes=cache, **prm)
+                mid = ctx.load_map(g, 0.05)
+                ctx.set_hypotheses(mid, workloads.cell_centres(cells, 0.05))
+                for _ in range(2 if cache else 1):   # with the cache, the second call reads the window table
+                    res = ctx.relocalize(mid, z, ang, 5.0).as_dict()
+                num = ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(len(cells), dtype=torch.int64, device="cuda")).cpu()
+                mm = ctx.stage(relo.STAGE_SMAD_M, torch.empty(len(cells), dtype=torch.int32, device="cuda")).cpu()
+                if cache:
+                    assert ctx.scan_cache_stats()["win_hits"] == 1
+                out.append((res, num.numpy(), mm.numpy()))
+                ctx.close()
+            assert out[0][0] == out[1][0]
+            assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
