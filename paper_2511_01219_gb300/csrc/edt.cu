@@ -26,21 +26,35 @@ namespace {
 constexpr int kInf = 0x7fffffff;
 
 // Column term, step 1: for every (column, segment of L rows) the first and the
-// last occupied row inside the segment (-1 if none).
-__global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H, int L,
-                                  int2 *__restrict__ summ) {
+// last occupied row inside the segment (-1 if none).  The same pass builds the
+// occupancy bitmap: a warp covers 32 consecutive columns (four 8x8 tiles) and
+// L is a multiple of 8, so the ballot of each row gives four tile rows, which
+// lanes 0-3 collect into their tile's word (cells outside the map are free).
+__global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H, int L, int TW, int TH,
+                                  int2 *__restrict__ summ, uint64_t *__restrict__ bits) {
+    const int lane = threadIdx.x & 31;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = x - lane;
     const int sgm = blockIdx.y;
-    if (x >= W) return;
-    const int y0 = sgm * L, y1 = min(H, y0 + L);
+    if (x0 >= W) return;   // the whole warp lies right of the map
+    const int y0 = sgm * L;
     int first = -1, last = -1;
-    for (int y = y0; y < y1; ++y) {
-        if (grid[(size_t)y * W + x] >= 65) {
+    uint64_t word = 0ull;
+    for (int y = y0; y < y0 + L; ++y) {
+        const bool occ = x < W && y < H && grid[(size_t)y * W + x] >= 65;
+        if (occ) {
             if (first < 0) first = y;
             last = y;
         }
+        const unsigned b = __ballot_sync(0xffffffffu, occ);
+        word |= (uint64_t)((b >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
+        if ((y & 7) == 7) {
+            const int tx = (x0 >> 3) + lane, ty = y >> 3;
+            if (lane < 4 && tx < TW && ty < TH) bits[(size_t)ty * TW + tx] = word;
+            word = 0ull;
+        }
     }
-    summ[(size_t)sgm * W + x] = make_int2(first, last);
+    if (x < W) summ[(size_t)sgm * W + x] = make_int2(first, last);
 }
 
 // Column term, step 2: the nearest occupied rows above and below the segment
@@ -105,22 +119,6 @@ __global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int 
     }
 }
 
-// one thread per 8x8 tile: occupancy bits (cells outside the map are free)
-__global__ void k_tiles(const int8_t *__restrict__ grid, int W, int H, int TW, int TH, uint64_t *__restrict__ bits) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= TW * TH) return;
-    int tx = t % TW, ty = t / TW;
-    uint64_t w = 0;
-    for (int r = 0; r < 8; ++r) {
-        int y = ty * 8 + r;
-        for (int c = 0; c < 8; ++c) {
-            int x = tx * 8 + c;
-            if (x < W && y < H && grid[(size_t)y * W + x] >= 65) w |= 1ull << (r * 8 + c);
-        }
-    }
-    bits[t] = w;
-}
-
 // the border of the padded field: every cell outside the map reads C (d = d_max)
 __global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int P, int Wp, int C) {
     const size_t n = (size_t)(H + 2 * P) * Wp;
@@ -156,10 +154,8 @@ __global__ void k_check_cells(const int2 *__restrict__ cells, int n, const uint6
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
     const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;
     const dim3 cgrid((m.W + 127) / 128, S);
-    k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.summ);
+    k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.TW, m.TH, m.summ, m.bits);
     k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
-    int nt = m.TW * m.TH;
-    k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(m.grid, m.W, m.H, m.TW, m.TH, m.bits);
     uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
     size_t smem = (size_t)m.W * sizeof(int32_t);
     if (smem > 48 * 1024) {

@@ -116,8 +116,7 @@ __global__ void k_upload(const __grid_constant__ Blob blob, unsigned char *dst) 
 struct BatchSlot {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    ReqDesc *reqs_dev = nullptr;          // [kMaxBatchRequests]
-    TamSeg *segs_dev = nullptr;           // [kMaxBatches * kMaxBatchRequests]
+    ReqDesc *reqs_dev = nullptr;          // descriptors [R], then the TAM segments [batches * R] (one upload)
     BatchState *bs = nullptr;
     relo_result *results_dev = nullptr;   // [kMaxBatchRequests]
     unsigned char *arena = nullptr;       // per-request scratch of the batch
@@ -679,7 +678,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
                                     ctx->stream);
     if (e == cudaSuccess) e = launch_field_border(m.dev, ctx->stream);
     if (e == cudaSuccess) ctx->kernels += 1;
-    if (e == cudaSuccess) e = timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -1020,10 +1019,14 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         plans[bi] = plan_tam(nb.data(), no.data(), sb.data(), R, max_beams, max_C, ctx->n_sm, &segs[(size_t)bi * R]);
         if (plans[bi].vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
     }
-    if ((rc = upload(ctx, st, sl.reqs_dev, desc.data(), sizeof(ReqDesc) * R)) ||
-        (rc = upload(ctx, st, sl.segs_dev, segs.data(), sizeof(TamSeg) * segs.size())))
-        return rc;
+    // descriptors and TAM segments travel together in one upload
+    const size_t seg_off = align_up(sizeof(ReqDesc) * R);
+    std::vector<unsigned char> blob(seg_off + sizeof(TamSeg) * segs.size(), 0);
+    memcpy(blob.data(), desc.data(), sizeof(ReqDesc) * R);
+    memcpy(blob.data() + seg_off, segs.data(), sizeof(TamSeg) * segs.size());
+    if ((rc = upload(ctx, st, sl.reqs_dev, blob.data(), blob.size()))) return rc;
     ReqDesc *rq = sl.reqs_dev;
+    const TamSeg *segs_dev = reinterpret_cast<const TamSeg *>(reinterpret_cast<unsigned char *>(sl.reqs_dev) + seg_off);
     CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
     for (int r = 0; r < R; ++r) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
@@ -1046,17 +1049,22 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {
-        const TamSeg *sg = sl.segs_dev + (size_t)bi * R;
+        const TamSeg *sg = segs_dev + (size_t)bi * R;
         CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, plans[bi], st); }), "TAM");
-        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, st); }), "batch selection");
+        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, bi == max_batches - 1, st); }),
+           "batch selection");
     }
-    CK(timed_on(ctx, st, 5, 1, [&] { return launch_finalize(rq, R, st); }), "finalize");
     created.keep = true;
     wnew.keep = true;
     ctx->last = desc[0];
     ctx->last_bs = sl.bs;
     ctx->has_last = true;
     return RELO_OK;
+}
+
+// device bytes of a slot's descriptor region: descriptors, then TAM segments
+size_t slot_desc_bytes() {
+    return align_up(sizeof(ReqDesc) * kMaxBatchRequests) + sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests;
 }
 
 int slot_init(relo_ctx *ctx, BatchSlot &sl, cudaStream_t stream) {
@@ -1067,9 +1075,7 @@ int slot_init(relo_ctx *ctx, BatchSlot &sl, cudaStream_t stream) {
         CK(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "batch stream");
         sl.own_stream = true;
     }
-    if ((rc = dev_alloc(ctx, (void **)&sl.reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests, "batch state")) ||
-        (rc = dev_alloc(ctx, (void **)&sl.segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests,
-                        "batch state")) ||
+    if ((rc = dev_alloc(ctx, (void **)&sl.reqs_dev, slot_desc_bytes(), "batch state")) ||
         (rc = dev_alloc(ctx, (void **)&sl.bs, sizeof(BatchState), "batch state")) ||
         (rc = dev_alloc(ctx, (void **)&sl.results_dev, sizeof(relo_result) * kMaxBatchRequests, "batch state")))
         return rc;
@@ -1078,8 +1084,7 @@ int slot_init(relo_ctx *ctx, BatchSlot &sl, cudaStream_t stream) {
 
 void slot_free(relo_ctx *ctx, BatchSlot &sl) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
-    dev_free(ctx, sl.reqs_dev, sizeof(ReqDesc) * kMaxBatchRequests);
-    dev_free(ctx, sl.segs_dev, sizeof(TamSeg) * kMaxBatches * kMaxBatchRequests);
+    dev_free(ctx, sl.reqs_dev, slot_desc_bytes());
     dev_free(ctx, sl.bs, sizeof(BatchState));
     dev_free(ctx, sl.results_dev, sizeof(relo_result) * kMaxBatchRequests);
     dev_free(ctx, sl.arena, sl.arena_cap);
@@ -1423,7 +1428,7 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
             CK(launch_field_border(m.dev, ctx->stream), "map rebuild");
-            CK(timed(ctx, 0, 4, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
+            CK(timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -1448,7 +1453,7 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     drop_tables(ctx, *m);
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 
@@ -1459,7 +1464,7 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     drop_tables(ctx, *m);
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 4, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
     return RELO_OK;
 }
 

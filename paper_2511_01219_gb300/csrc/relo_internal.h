@@ -28,10 +28,12 @@ struct MapDev {
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
 };
 
-// rows per column segment of the EDT column pass: at least 16, at most 64 segments
+// rows per column segment of the EDT column pass: at least 16, at most 64
+// segments, a multiple of 8 (the segment pass also builds the 8x8 tiles)
 __host__ __device__ inline int edt_segment_rows(int H) {
     int L = (H + 63) / 64;
-    return L < 16 ? 16 : L;
+    L = L < 16 ? 16 : L;
+    return (L + 7) & ~7;
 }
 
 __host__ __device__ inline size_t tile_index(int x, int y, int TW) {
@@ -233,7 +235,7 @@ struct TamPlan {
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
                  int max_beams, int max_C, int n_sm, TamSeg *segs);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, cudaStream_t s);
-cudaError_t launch_finalize(const ReqDesc *reqs, int R, cudaStream_t s);
+// selection of batch index batch_idx; with last, also every request's result
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, bool last, cudaStream_t s);
 
 }  // namespace relo

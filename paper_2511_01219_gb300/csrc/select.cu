@@ -13,7 +13,8 @@
 // rank counting, the running best over batches, and the early-termination
 // flag once a batch's best reaches tau (Remark 2).
 //
-// k_finalize: the selected pose and counters into a relo_result.
+// The last selection launch also writes the selected pose and counters into
+// each request's relo_result.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -77,12 +78,20 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     int top = s_or ? 63 - __clzll((long long)s_or) : 0;
     unsigned long long prefix = 0, mask = 0;
     int remaining = K;
+    const int lane = threadIdx.x & 31;
+    const int n_round = (n + blockDim.x - 1) / blockDim.x * blockDim.x;   // whole warps in every round
     for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            unsigned long long k = keys[i];
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        for (int i = threadIdx.x; i < n_round; i += blockDim.x) {
+            // keys share their leading digits, so count per warp first: one atomic per distinct digit
+            unsigned dig = 256u;
+            if (i < n) {
+                const unsigned long long k = keys[i];
+                if ((k & mask) == prefix) dig = (unsigned)(k >> shift) & 255u;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, dig);
+            if (dig < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -115,10 +124,15 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         remaining -= s_below;
         __syncthreads();
     }
-    // prefix is now the K-th smallest key
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        unsigned long long k = keys[i];
-        if (k <= prefix) sortbuf[atomicAdd(&s_cnt, 1)] = k;
+    // prefix is now the K-th smallest key; one slot reservation per warp
+    for (int i = threadIdx.x; i < n_round; i += blockDim.x) {
+        const unsigned long long k = i < n ? keys[i] : ~0ull;
+        const bool take = i < n && k <= prefix;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_cnt, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) sortbuf[base + __popc(bal & ((1u << lane) - 1u))] = k;
     }
     for (int i = K + threadIdx.x; i < Kp; i += blockDim.x) sortbuf[i] = ~0ull;
     __syncthreads();
@@ -127,53 +141,8 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         d.survivors[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
 }
 
-// one CTA per request: selection of batch `batch_idx` (skipped when the
-// request has fewer batches or already terminated early).  Keys (TAM
-// descending, then survivor position) are unique, so each survivor's rank is
-// the number of smaller keys; ranks below L fill the local top-k directly.
-__global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_idx) {
-    __shared__ unsigned long long v[kMaxBatch];
-    __shared__ int s_skip;
-    const ReqDesc &d = reqs[blockIdx.x];
-    if (threadIdx.x == 0) s_skip = batch_idx >= d.n_batches || d.state->done || d.scan->n_valid <= 0;
-    __syncthreads();
-    if (s_skip) return;
-    SelectState *st = d.state;
-    const int s_begin = batch_idx * d.B;
-    const int s_end = min(d.K, s_begin + d.B);
-    const int nb = s_end - s_begin;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        const int s = s_begin + i;
-        const unsigned long long k = d.best_key[s];
-        const unsigned tb = (unsigned)(k >> 32);
-        const unsigned q = 0xffffffffu - (unsigned)(k & 0xffffffffu);
-        d.best_m[s] = (int)q * d.n_enum;
-        v[i] = ((unsigned long long)(~tb) << 32) | (unsigned)s;   // ascending = TAM desc, survivor asc
-    }
-    __syncthreads();
-    const int L = d.L;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        const unsigned long long me = v[i];
-        int rank = 0;
-        for (int k = 0; k < nb; ++k) rank += v[k] < me ? 1 : 0;
-        if (rank < L) d.local[(size_t)batch_idx * L + rank] = (int)(me & 0xffffffffu);
-        if (rank == 0) {
-            const unsigned tb = ~(unsigned)(me >> 32);
-            const unsigned s = (unsigned)(me & 0xffffffffu);
-            const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
-            if (cand > st->best) st->best = cand;
-            st->n_batches += 1;
-            st->n_tam_evals += (long long)nb * d.n_orient;
-            if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
-        }
-    }
-    for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;
-}
-
-__global__ void k_finalize(const ReqDesc *__restrict__ reqs, int R) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R) return;
-    const ReqDesc &d = reqs[i];
+// The request's pose, score and counters into its relo_result (one thread).
+__device__ void finalize_request(const ReqDesc &d) {
     relo_result r;
     const SelectState st = *d.state;
     const unsigned tb = (unsigned)(st.best >> 32);
@@ -207,6 +176,55 @@ __global__ void k_finalize(const ReqDesc *__restrict__ reqs, int R) {
     *reinterpret_cast<relo_result *>(d.result) = r;
 }
 
+// one CTA per request: selection of batch `batch_idx` (skipped when the
+// request has fewer batches or already terminated early).  Keys (TAM
+// descending, then survivor position) are unique, so each survivor's rank is
+// the number of smaller keys; ranks below L fill the local top-k directly.
+// The launch of the last batch index also writes every request's result.
+__global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_idx, int last) {
+    __shared__ unsigned long long v[kMaxBatch];
+    __shared__ int s_skip;
+    const ReqDesc &d = reqs[blockIdx.x];
+    if (threadIdx.x == 0) s_skip = batch_idx >= d.n_batches || d.state->done || d.scan->n_valid <= 0;
+    __syncthreads();
+    if (!s_skip) {
+        SelectState *st = d.state;
+        const int s_begin = batch_idx * d.B;
+        const int s_end = min(d.K, s_begin + d.B);
+        const int nb = s_end - s_begin;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const int s = s_begin + i;
+            const unsigned long long k = d.best_key[s];
+            const unsigned tb = (unsigned)(k >> 32);
+            const unsigned q = 0xffffffffu - (unsigned)(k & 0xffffffffu);
+            d.best_m[s] = (int)q * d.n_enum;
+            v[i] = ((unsigned long long)(~tb) << 32) | (unsigned)s;   // ascending = TAM desc, survivor asc
+        }
+        __syncthreads();
+        const int L = d.L;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const unsigned long long me = v[i];
+            int rank = 0;
+            for (int k = 0; k < nb; ++k) rank += v[k] < me ? 1 : 0;
+            if (rank < L) d.local[(size_t)batch_idx * L + rank] = (int)(me & 0xffffffffu);
+            if (rank == 0) {
+                const unsigned tb = ~(unsigned)(me >> 32);
+                const unsigned s = (unsigned)(me & 0xffffffffu);
+                const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
+                if (cand > st->best) st->best = cand;
+                st->n_batches += 1;
+                st->n_tam_evals += (long long)nb * d.n_orient;
+                if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
+            }
+        }
+        for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;
+    }
+    if (last) {
+        __syncthreads();   // the selection state of this launch is complete
+        if (threadIdx.x == 0) finalize_request(d);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s) {
@@ -220,13 +238,8 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, cudaStream_t s) {
-    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_idx);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const ReqDesc *reqs, int R, cudaStream_t s) {
-    k_finalize<<<(R + 127) / 128, 128, 0, s>>>(reqs, R);
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, bool last, cudaStream_t s) {
+    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_idx, last ? 1 : 0);
     return cudaGetLastError();
 }
 
