@@ -1005,19 +1005,44 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (d.win_mode == kWinBuild) max_nm = std::max(max_nm, d.n_m);
     }
     const int total_smad = base, total_build = bbase, total_read = rbase;
-    // TAM work of every batch index
-    std::vector<TamSeg> segs((size_t)max_batches * R);
-    std::vector<TamPlan> plans((size_t)max_batches);
+    // TAM work of every batch index, one launch per class of requests with the
+    // same register-resident values per lane (a 541-beam request does not run
+    // at the width of a 1440-beam one); one class if the segment table would
+    // not fit the slot
+    std::vector<int> vcls((size_t)R);
+    for (int r = 0; r < R; ++r) {
+        vcls[r] = tam_vpl_for(pr[r].P->n);
+        if (vcls[r] < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
+    }
+    std::vector<int> classes(vcls);
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    if ((size_t)max_batches * classes.size() * R > (size_t)kMaxBatches * kMaxBatchRequests) {
+        std::fill(vcls.begin(), vcls.end(), classes.back());
+        classes.assign(1, classes.back());
+    }
+    const int NC = (int)classes.size();
+    std::vector<TamSeg> segs((size_t)max_batches * NC * R);
+    std::vector<TamPlan> plans((size_t)max_batches * NC);
     std::vector<int> nb((size_t)R), no((size_t)R), sb((size_t)R);
     for (int bi = 0; bi < max_batches; ++bi) {
-        for (int r = 0; r < R; ++r) {
-            const int s0 = bi * desc[r].B;
-            nb[r] = bi < desc[r].n_batches ? std::min(desc[r].K, s0 + desc[r].B) - s0 : 0;
-            no[r] = desc[r].n_orient;
-            sb[r] = s0;
+        for (int c = 0; c < NC; ++c) {
+            int beams_c = 1, C_c = 0;
+            for (int r = 0; r < R; ++r) {
+                const int s0 = bi * desc[r].B;
+                const bool in = vcls[r] == classes[c] && bi < desc[r].n_batches;
+                nb[r] = in ? std::min(desc[r].K, s0 + desc[r].B) - s0 : 0;
+                no[r] = desc[r].n_orient;
+                sb[r] = s0;
+                if (vcls[r] == classes[c]) {
+                    beams_c = std::max(beams_c, pr[r].P->n);
+                    C_c = std::max(C_c, pr[r].m->dev.C);
+                }
+            }
+            TamPlan &tp = plans[(size_t)bi * NC + c];
+            tp = plan_tam(nb.data(), no.data(), sb.data(), R, beams_c, C_c, ctx->n_sm, &segs[((size_t)bi * NC + c) * R]);
+            if (tp.vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
         }
-        plans[bi] = plan_tam(nb.data(), no.data(), sb.data(), R, max_beams, max_C, ctx->n_sm, &segs[(size_t)bi * R]);
-        if (plans[bi].vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
     }
     // descriptors and TAM segments travel together in one upload
     const size_t seg_off = align_up(sizeof(ReqDesc) * R);
@@ -1049,8 +1074,12 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     for (int bi = 0; bi < max_batches; ++bi) {
-        const TamSeg *sg = segs_dev + (size_t)bi * R;
-        CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, plans[bi], st); }), "TAM");
+        for (int c = 0; c < NC; ++c) {
+            const TamPlan &tp = plans[(size_t)bi * NC + c];
+            if (tp.total_tasks <= 0) continue;
+            const TamSeg *sg = segs_dev + ((size_t)bi * NC + c) * R;
+            CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, tp, st); }), "TAM");
+        }
         CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, bi == max_batches - 1, st); }),
            "batch selection");
     }

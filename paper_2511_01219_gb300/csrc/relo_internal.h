@@ -232,6 +232,8 @@ struct TamPlan {
     size_t smem;
     bool h2;   // selection counts on packed fp16 (C + 1 <= 2048)
 };
+// values per lane the TAM kernel holds for max_beams valid beams (-1 if too many)
+int tam_vpl_for(int max_beams);
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
                  int max_beams, int max_C, int n_sm, TamSeg *segs);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);

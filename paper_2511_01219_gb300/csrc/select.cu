@@ -83,15 +83,9 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < n_round; i += blockDim.x) {
-            // keys share their leading digits, so count per warp first: one atomic per distinct digit
-            unsigned dig = 256u;
-            if (i < n) {
-                const unsigned long long k = keys[i];
-                if ((k & mask) == prefix) dig = (unsigned)(k >> shift) & 255u;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, dig);
-            if (dig < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long k = keys[i];
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
         }
         __syncthreads();
         if (threadIdx.x < 32) {

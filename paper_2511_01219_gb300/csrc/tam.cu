@@ -367,6 +367,8 @@ int occupancy_for(int vpl, bool h2, size_t smem) {
 
 }  // namespace
 
+int tam_vpl_for(int max_beams) { return vpl_bucket(max_beams); }
+
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s) {
     k_scan_prep<<<dim3(R, 8), 1024, 0, s>>>(reqs, bs);
     return cudaGetLastError();
