@@ -45,6 +45,14 @@ constexpr int kTamWarps = 8;
 constexpr uint32_t kNoBeam = 0xffffu;
 constexpr int kHalfExact = 2048;   // fp16 holds every integer in [0, 2048] exactly
 
+// Per-lane stride of the endpoint offsets in shared memory: slot s of lane l
+// (beam 32 s + l) sits at l * stride + s, so a lane reads four offsets with one
+// 16-byte load; stride / 4 odd keeps the eight lanes of each load phase on
+// distinct banks.
+__host__ __device__ constexpr int tam_offs_stride(int vpl) {
+    return ((vpl + 3) & ~3) + ((((vpl + 3) & ~3) / 4) % 2 == 0 ? 4 : 0);
+}
+
 // exact float of an integer 0 <= v < 2^23 (the float 2^23 + v, less 2^23)
 __device__ __forceinline__ float int_float(uint32_t v) { return __uint_as_float(0x4b000000u | v) - 8388608.0f; }
 // the integer of an integral float 0 <= f < 2^23
@@ -194,7 +202,8 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         __syncthreads();
         if (threadIdx.x == 0) s_lut_r = r;
         if (s_skip) continue;
-        int *offs = reinterpret_cast<int *>(smem + (size_t)(d.C + 2) * sizeof(float2));
+        constexpr int kS = tam_offs_stride(VPL);
+        int *offs = reinterpret_cast<int *>(smem + (((size_t)(d.C + 2) * sizeof(float2) + 15) & ~(size_t)15));
         const int local = task - sg.task_base;
         const int q = local % d.n_orient;
         const int chunk = local / d.n_orient;
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
             const int2 dir = d.D[j];
             const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
             const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
-            offs[i] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
+            offs[(i & 31) * kS + (i >> 5)] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
         }
         __syncthreads();
         const int s_lo = sg.s_begin + chunk * sg.chunk;
@@ -220,35 +229,48 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
             float sgs = 0.0f, sl = 0.0f;
             int clt = 0;
             uint32_t bk;
+            const int *ol = offs + lane * kS;   // this lane's offsets, slot s = beam 32 s + lane
             if constexpr (H2) {
                 __half2 hv[VPL / 2];
 #pragma unroll
-                for (int t = 0; t < VPL / 2; ++t) {
-                    const int i0 = (t << 6) + lane, i1 = i0 + 32;
-                    uint32_t b0 = none, b1 = none;
-                    if (i0 < N) {
-                        b0 = (uint32_t)__ldg(fh + offs[i0]);
-                        sumb += (int)b0;
+                for (int u = 0; u < (VPL + 3) / 4; ++u) {
+                    const int4 o4 = *reinterpret_cast<const int4 *>(ol + 4 * u);
+                    const int oo[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e += 2) {
+                        const int t = 2 * u + e / 2;   // pair of slots 2t, 2t + 1
+                        if (t < VPL / 2) {
+                            const int i0 = (t << 6) + lane, i1 = i0 + 32;
+                            uint32_t b0 = none, b1 = none;
+                            if (i0 < N) {
+                                b0 = (uint32_t)__ldg(fh + oo[e]);
+                                sumb += (int)b0;
+                            }
+                            if (i1 < N) {
+                                b1 = (uint32_t)__ldg(fh + oo[e + 1]);
+                                sumb += (int)b1;
+                            }
+                            hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
+                        }
                     }
-                    if (i1 < N) {
-                        b1 = (uint32_t)__ldg(fh + offs[i1]);
-                        sumb += (int)b1;
-                    }
-                    hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
                 }
                 // smallest b_k with #{b <= b_k} >= k
                 int blo = 0, bhi = C;
                 while (blo < bhi) {
                     const int mid = (blo + bhi) >> 1;
                     const __half2 m1 = __float2half2_rn(int_float((uint32_t)mid + 1u));
-                    __half2 acc0 = __float2half2_rn(0.0f), acc1 = acc0;   // two chains: half the add latency
+                    // two chains (half the add latency); the low half starts at 1024, so the
+                    // total 1024 + c (c <= 64) has the fp16 bits 0x6400 + c
+                    __half2 acc0 = __halves2half2(__float2half(1024.0f), __float2half(0.0f));
+                    __half2 acc1 = __float2half2_rn(0.0f);
 #pragma unroll
                     for (int t = 0; t < VPL / 2; t += 2) {
                         acc0 = __hadd2(acc0, __hsub2_sat(m1, hv[t]));
                         if (t + 1 < VPL / 2) acc1 = __hadd2(acc1, __hsub2_sat(m1, hv[t + 1]));
                     }
-                    const float2 af = __half22float2(__hadd2(acc0, acc1));
-                    const int c = __reduce_add_sync(kFull, (int)float_int(af.x + af.y));
+                    const __half2 sum = __hadd2(acc0, acc1);
+                    const __half2 tot = __hadd2(sum, __lowhigh2highlow(sum));
+                    const int c = __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
                     if (c >= k) bhi = mid;
                     else blo = mid + 1;
                 }
@@ -275,7 +297,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                     const int i = (t << 5) + lane;
                     uint32_t bv = none;
                     if (i < N) {
-                        bv = (uint32_t)__ldg(fh + offs[i]);
+                        bv = (uint32_t)__ldg(fh + ol[t]);
                         sumb += (int)bv;
                     }
                     v[t] = bv;
@@ -380,8 +402,9 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStr
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
                  int max_C, int n_sm, TamSeg *segs) {
     TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfExact};
-    tp.smem = (size_t)(max_C + 2) * sizeof(float2) + (size_t)max_beams * sizeof(int);
     if (tp.vpl < 0) return tp;
+    tp.smem = (((size_t)(max_C + 2) * sizeof(float2) + 15) & ~(size_t)15) +
+              (size_t)32 * tam_offs_stride(tp.vpl) * sizeof(int);
     const int occ = occupancy_for(tp.vpl, tp.h2, tp.smem);
     if (occ < 1) {
         tp.vpl = -1;
