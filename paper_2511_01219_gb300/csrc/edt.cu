@@ -27,9 +27,13 @@ constexpr int kInf = 0x7fffffff;
 
 // Column term, step 1: for every (column, segment of L rows) the first and the
 // last occupied row inside the segment (-1 if none).  The same pass builds the
-// occupancy bitmap: a warp covers 32 consecutive columns (four 8x8 tiles) and
+// occupancy bitmaps: a warp covers 32 consecutive columns (four 8x8 tiles) and
 // L is a multiple of 8, so the ballot of each row gives four tile rows, which
 // lanes 0-3 collect into their tile's word (cells outside the map are free).
+// Each word is stored four times: as is, and for the frames mirrored in x
+// (x' = 8 TW - 1 - x: tile TW - 1 - tx, bits reversed within each row), in y
+// (rows reversed) and in both (all 64 bits reversed), which the ray cast uses
+// so that every ray travels towards +x and +y.
 __global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H, int L, int TW, int TH,
                                   int2 *__restrict__ summ, uint64_t *__restrict__ bits) {
     const int lane = threadIdx.x & 31;
@@ -50,7 +54,18 @@ __global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H,
         word |= (uint64_t)((b >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
         if ((y & 7) == 7) {
             const int tx = (x0 >> 3) + lane, ty = y >> 3;
-            if (lane < 4 && tx < TW && ty < TH) bits[(size_t)ty * TW + tx] = word;
+            if (lane < 4 && tx < TW && ty < TH) {
+                const size_t n = (size_t)TW * TH;
+                const uint64_t rev = __brevll(word);   // both mirrors
+                const uint64_t ymir = ((uint64_t)__byte_perm((uint32_t)word, 0u, 0x0123u) << 32) |
+                                      (uint64_t)__byte_perm((uint32_t)(word >> 32), 0u, 0x0123u);
+                const uint64_t xmir = ((uint64_t)__byte_perm((uint32_t)rev, 0u, 0x0123u) << 32) |
+                                      (uint64_t)__byte_perm((uint32_t)(rev >> 32), 0u, 0x0123u);
+                bits[(size_t)ty * TW + tx] = word;
+                bits[n + (size_t)ty * TW + (TW - 1 - tx)] = xmir;
+                bits[2 * n + (size_t)(TH - 1 - ty) * TW + tx] = ymir;
+                bits[3 * n + (size_t)(TH - 1 - ty) * TW + (TW - 1 - tx)] = rev;
+            }
             word = 0ull;
         }
     }

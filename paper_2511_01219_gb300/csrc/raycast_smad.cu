@@ -171,27 +171,24 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
     return r;
 }
 
-__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
-    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
-    return ((uint64_t)__byte_perm(lo, 0u, 0x0123u) << 32) | (uint64_t)__byte_perm(hi, 0u, 0x0123u);
-}
-
 // Tile walk with the per-direction tables (RayTables).  The ray moves from
-// tile to tile in its own frame, the tile mirrored in x when D_x <= 0 and in
-// y when D_y <= 0, so that it always travels towards +x and +y.  In a tile
-// whose occupancy word is not zero, the table's bit board of the cells still
-// ahead (anchored at the current cell) is shifted onto the mirrored word; on
-// a staircase that only moves +x and +y the cell order along the ray is the
+// tile to tile in its own frame, the map mirrored in x when D_x <= 0 (x' =
+// 8 TW - 1 - x) and in y when D_y <= 0, so that it always travels towards +x
+// and +y; the occupancy of each mirrored frame is stored beside the native
+// one.  In a tile whose word is not zero, the word moved to the current cell
+// is ANDed with the table's bit board of the cells still ahead; on a
+// staircase that only moves +x and +y the cell order along the ray is the
 // row-major bit order, so the lowest common bit is the hit.  Otherwise the
 // ray leaves the tile at the cell of step min(selx[|dx| + nx], sely[|dy| +
 // ny]), nx and ny being the x- and y-steps to the tile's far edges.  Same
 // cells, same hit, same range as cast_ray.
-__device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, int W, int H, int TW,
+__device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int TH,
                                              const RayTables &t, int ns, int j, int hx, int hy, int2 d, int *hit,
                                              int *steps) {
     const bool xneg = d.x <= 0, yneg = d.y <= 0;
-    const int xm = xneg ? 7 : 0, ym = yneg ? 7 : 0;
-    const int sx = xneg ? -1 : 1, sy = yneg ? -1 : 1;
+    const uint64_t *__restrict__ bq = bits + (size_t)((xneg ? 1 : 0) + (yneg ? 2 : 0)) * TW * TH;
+    const int xlo = xneg ? 8 * TW - W : 0, ylo = yneg ? 8 * TH - H : 0;   // the map in the ray's frame
+    const int fx = xneg ? 8 * TW - 1 - hx : hx, fy = yneg ? 8 * TH - 1 - hy : hy;
     const uint16_t *__restrict__ selx = t.selx + j;
     const uint16_t *__restrict__ sely = t.sely + j;
     const uint64_t *__restrict__ mk = t.mask + j;
@@ -199,21 +196,18 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     // The loop only finds where the ray stops; the range is computed after it,
     // once for the whole warp, rather than in a divergent branch per lane.
     // Indexes are unsigned 32-bit (every table and map index fits).
-    int adx = 0, ady = 0, cx = hx, cy = hy;
+    int adx = 0, ady = 0, cx = fx, cy = fy;
     int stop;   // 1 hit, 2 range limit, 3 left the map
     for (;;) {
-        const int lx = (cx & 7) ^ xm, ly = (cy & 7) ^ ym;   // the cell inside the tile, in the ray's frame
+        const int lx = cx & 7, ly = cy & 7;
         // the tile's word and the exit steps are loaded together: one memory round trip per tile
-        const uint64_t word = __ldg(bits + ((unsigned)(cy >> 3) * (unsigned)TW + (unsigned)(cx >> 3)));
+        const uint64_t word = __ldg(bq + ((unsigned)(cy >> 3) * (unsigned)TW + (unsigned)(cx >> 3)));
         const uint32_t kx = __ldg(selx + (unsigned)(adx + 8 - lx) * uns);
         const uint32_t ky = __ldg(sely + (unsigned)(ady + 8 - ly) * uns);
         if (word) {
-            uint64_t w = word;
-            if (xneg) w = bswap64(__brevll(w));   // reverse the bits of every row
-            if (yneg) w = bswap64(w);             // reverse the rows
             // move the current cell to bit 0; bits that wrap into the row below
             // sit in columns the board's column mask removes
-            w >>= lx + 8 * ly;
+            const uint64_t w = word >> (lx + 8 * ly);
             const uint32_t cm = 0x01010101u * (0xffu >> lx);   // board columns dx <= 7 - lx, every row
             const uint64_t R = __ldg(mk + (unsigned)(adx + ady) * uns) & (((uint64_t)cm << 32) | cm);
             const uint64_t hm = R & w;
@@ -236,13 +230,14 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
             ady += 8 - ly;
             adx = (int)ky - ady;
         }
-        cx = hx + sx * adx;
-        cy = hy + sy * ady;
-        if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {   // left the map
+        cx = fx + adx;
+        cy = fy + ady;
+        if ((unsigned)(cx - xlo) >= (unsigned)W || (unsigned)(cy - ylo) >= (unsigned)H) {   // left the map
             stop = 3;
             break;
         }
     }
+    const int sx = xneg ? -1 : 1, sy = yneg ? -1 : 1;
     cx = hx + sx * adx;
     cy = hy + sy * ady;
     *hit = stop == 1 ? cy * W + cx : -1;
@@ -338,7 +333,7 @@ __global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict
             const int2 hc = d.hyps[h];
             const int2 dir = d.D[j];
             int hit, steps = 0;
-            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.W, d.H, d.TW, d.rt, d.ns, j, hc.x, hc.y, dir, &hit, &steps)
+            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.W, d.H, d.TW, d.TH, d.rt, d.ns, j, hc.x, hc.y, dir, &hit, &steps)
                                          : cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, dir, &hit, &steps);
             d.scan_table[(size_t)h * d.ns + j] = r;
             my_steps += (unsigned)steps;
@@ -629,7 +624,7 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
     const int2 hc = a.hyps[warp];
     for (int j = lane; j < a.ns; j += 32) {
         int hit, steps;
-        uint32_t r = a.tab.mask ? walk_ray(a.bits, a.W, a.H, a.TW, a.tab, a.ns, j, hc.x, hc.y, a.D[j], &hit, &steps)
+        uint32_t r = a.tab.mask ? walk_ray(a.bits, a.W, a.H, a.TW, a.TH, a.tab, a.ns, j, hc.x, hc.y, a.D[j], &hit, &steps)
                                 : cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
         ranges[(size_t)warp * a.ns + j] = r;
         if (hits) hits[(size_t)warp * a.ns + j] = hit;

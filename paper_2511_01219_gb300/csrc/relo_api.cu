@@ -636,7 +636,7 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * (m.dev.H + 2 * m.dev.P));
-    dev_free(ctx, m.dev.bits, sizeof(uint64_t) * (size_t)m.dev.TW * m.dev.TH);
+    dev_free(ctx, m.dev.bits, sizeof(uint64_t) * 4 * (size_t)m.dev.TW * m.dev.TH);
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
     dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
     m = MapSlot();
@@ -664,7 +664,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     const size_t fcells = (size_t)m.dev.Wp * (h + 2 * m.dev.P);
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
-        {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, tiles * 8},
+        {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, tiles * 8 * 4},
         {(void **)&m.dev.summ, sizeof(int2) * (size_t)w * edt_segments(h)}};
     for (auto &a : allocs) {
         rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
@@ -932,6 +932,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.W = m.dev.W;
         d.H = m.dev.H;
         d.TW = m.dev.TW;
+        d.TH = m.dev.TH;
         d.C = m.dev.C;
         d.res = (float)m.res;
         d.res2 = (float)(m.res * m.res);
@@ -1655,6 +1656,7 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     ra.W = m->dev.W;
     ra.H = m->dev.H;
     ra.TW = m->dev.TW;
+    ra.TH = m->dev.TH;
     ra.D = P->D_dev;
     ra.ns = P->ns;
     ra.ns_pad = (P->ns + 31) & ~31;

@@ -22,7 +22,7 @@ struct MapDev {
     int32_t *d2 = nullptr;      // [H*W] exact squared EDT, -1 = no obstacle
     uint16_t *field = nullptr;  // [(H+2P) * (W+2P)] min(d2, C), row-major with a border of P cells holding C
     int P = 0, Wp = 0;          // border width and padded row length
-    uint64_t *bits = nullptr;   // [TH*TW] occupancy, bit (y&7)*8 + (x&7)
+    uint64_t *bits = nullptr;   // [4][TH*TW] occupancy, bit (y&7)*8 + (x&7); [1..3] the x-, y- and xy-mirrored frames
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
     int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
@@ -96,8 +96,8 @@ __host__ __device__ inline int ray_sel_rows(int lim) {
 
 // single-request arguments of the synthesized-scan export (relo_synth_scans_dev)
 struct RayArgs {
-    const uint64_t *bits;
-    int W, H, TW;
+    const uint64_t *bits;   // the map's four occupancy frames (MapDev::bits)
+    int W, H, TW, TH;
     const int2 *D;          // [ns] Q30 directions
     int ns, ns_pad;         // ns_pad = ns rounded up to 32
     int lim;                // floor(rmax_q16^2 / 2^32): max squared cell distance of an entered cell
@@ -124,7 +124,7 @@ struct ReqDesc {
     const uint64_t *bits;
     const uint16_t *field;       // padded clamped field, pointer to cell (0, 0)
     const float2 *lut;           // [C+2] (l(b), sqrt(C) - sqrt(b)); entry C+1 = (0, 0) marks "no beam"
-    int W, H, TW, C, Wp, P;
+    int W, H, TW, TH, C, Wp, P;
     float res, res2, d_max, d_min;
     double resd, ox, oy;
     // hypotheses
