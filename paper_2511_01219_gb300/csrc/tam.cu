@@ -42,8 +42,55 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTamWarps = 8;
-constexpr uint32_t kNoBeam = 0xffffu;
 constexpr int kHalfExact = 2048;   // fp16 holds every integer in [0, 2048] exactly
+
+// The smallest b in [0, C] with count_le(b) >= k, given count_le(C) >= k (every
+// valid beam is <= C).  hint < 0: bisection over [0, C].  Otherwise the search
+// starts at hint: two counts confirm an unchanged answer; else it gallops
+// away from hint in doubling steps to a bracket [lo, hi] with count_le(lo - 1)
+// < k <= count_le(hi) and bisects it.
+template <typename F>
+__device__ __forceinline__ int kth_smallest(F &&count_le, int k, int C, int hint) {
+    int lo = 0, hi = C;
+    if (hint >= 0) {
+        if (count_le(hint) >= k) {
+            if (hint == 0 || count_le(hint - 1) < k) return hint;
+            hi = hint - 1;   // count_le(hi) >= k
+            for (int step = 1;; step <<= 1) {
+                const int p = hi - step;
+                if (p < 0) {
+                    lo = 0;
+                    break;
+                }
+                if (count_le(p) < k) {
+                    lo = p + 1;
+                    break;
+                }
+                hi = p;
+            }
+        } else {
+            lo = hint + 1;   // count_le(lo - 1) < k
+            for (int step = 1;; step <<= 1) {
+                const int p = lo + step - 1;
+                if (p >= C) {
+                    hi = C;
+                    break;
+                }
+                if (count_le(p) >= k) {
+                    hi = p;
+                    break;
+                }
+                lo = p + 1;
+            }
+        }
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (count_le(mid) >= k) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
 
 // Per-lane stride of the endpoint offsets in shared memory: slot s of lane l
 // (beam 32 s + l) sits at l * stride + s, so a lane reads four offsets with one
@@ -144,18 +191,25 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
     }
 }
 
-// Work is split into tasks (request, orientation q, chunk of survivors).  A
-// CTA first computes the endpoint offsets of its task's orientation for every
-// valid beam of the request, round-half-up(R_i * D_{(b_i + m) mod N_s} /
-// 2^46) per axis, packed as two int16 in shared memory; each warp then scores
-// one survivor at a time with those offsets, so the 64-bit offset arithmetic
-// is paid once per (orientation, beam) instead of once per (survivor,
-// orientation, beam).  The likelihood table is reloaded only when a CTA moves
-// to another request's task.
-// H2: the selection counts run on packed fp16 (every launch has C + 1 <=
-// 2048, so the values, the thresholds and the per-lane counts are exact
-// integers in fp16): a value v <= mid adds sat(mid + 1 - v) = 1, a larger one
-// 0, two values per instruction.  Otherwise 32-bit integer compares.
+// Work is split into tasks (request, block of kTamQ consecutive orientations,
+// chunk of survivors).  A CTA first computes the endpoint offsets of its
+// block's orientations for every valid beam of the request,
+// round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis, as one linear
+// offset into the padded field, in shared memory; each warp then scores one
+// survivor at a time over the block's orientations, so the 64-bit offset
+// arithmetic is paid once per (orientation, beam) instead of once per
+// (survivor, orientation, beam).
+//
+// Selection.  The k-th smallest clamped d2 of a survivor rarely changes from
+// one orientation to the next (neighbouring orientations see nearly the same
+// contour), so each orientation after the block's first starts from the
+// previous answer h: two counts confirm it (#{b <= h} >= k and #{b <= h-1} <
+// k); otherwise the search gallops away from h in doubling steps and bisects
+// the bracket.  Every step is a warp-wide count, and the result is the same
+// smallest b with #{b' <= b} >= k as a bisection over [0, C].  The likelihood
+// table is reloaded only when a CTA moves to another request's task.
+constexpr int kTamQ = 4;
+
 // resident CTAs per SM the register budget is sized for
 __host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 6 : 2) : (vpl <= 24 ? 3 : 2); }
 
@@ -205,17 +259,23 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         constexpr int kS = tam_offs_stride(VPL);
         int *offs = reinterpret_cast<int *>(smem + (((size_t)(d.C + 2) * sizeof(float2) + 15) & ~(size_t)15));
         const int local = task - sg.task_base;
-        const int q = local % d.n_orient;
-        const int chunk = local / d.n_orient;
-        const int m = q * d.n_enum;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const int2 bR = d.vbR[i];
-            int j = bR.x + m;
-            if (j >= d.ns) j -= d.ns;
-            const int2 dir = d.D[j];
-            const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
-            const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
-            offs[(i & 31) * kS + (i >> 5)] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
+        const int nblk = (d.n_orient + kTamQ - 1) / kTamQ;
+        const int qb = local % nblk;
+        const int chunk = local / nblk;
+        const int q0 = qb * kTamQ;
+        const int nq = min(kTamQ, d.n_orient - q0);
+        for (int qi = 0; qi < nq; ++qi) {
+            const int m = (q0 + qi) * d.n_enum;
+            int *oq = offs + qi * 32 * kS;
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int2 bR = d.vbR[i];
+                int j = bR.x + m;
+                if (j >= d.ns) j -= d.ns;
+                const int2 dir = d.D[j];
+                const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
+                const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
+                oq[(i & 31) * kS + (i >> 5)] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
+            }
         }
         __syncthreads();
         const int s_lo = sg.s_begin + chunk * sg.chunk;
@@ -225,124 +285,120 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
             const int2 hc = d.hyps[d.survivors[s]];
             const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
-            int sumb = 0;
-            float sgs = 0.0f, sl = 0.0f;
-            int clt = 0;
-            uint32_t bk;
-            const int *ol = offs + lane * kS;   // this lane's offsets, slot s = beam 32 s + lane
-            if constexpr (H2) {
-                __half2 hv[VPL / 2];
+            int hint = -1;   // the previous orientation's k-th smallest value
+            for (int qi = 0; qi < nq; ++qi) {
+                const int q = q0 + qi;
+                const int *ol = offs + (qi * 32 + lane) * kS;   // this lane's offsets, slot s = beam 32 s + lane
+                int sumb = 0;
+                float sgs = 0.0f, sl = 0.0f;
+                int clt = 0;
+                int bk;
+                if constexpr (H2) {
+                    __half2 hv[VPL / 2];
 #pragma unroll
-                for (int u = 0; u < (VPL + 3) / 4; ++u) {
-                    const int4 o4 = *reinterpret_cast<const int4 *>(ol + 4 * u);
-                    const int oo[4] = {o4.x, o4.y, o4.z, o4.w};
+                    for (int u = 0; u < (VPL + 3) / 4; ++u) {
+                        const int4 o4 = *reinterpret_cast<const int4 *>(ol + 4 * u);
+                        const int oo[4] = {o4.x, o4.y, o4.z, o4.w};
 #pragma unroll
-                    for (int e = 0; e < 4; e += 2) {
-                        const int t = 2 * u + e / 2;   // pair of slots 2t, 2t + 1
-                        if (t < VPL / 2) {
-                            const int i0 = (t << 6) + lane, i1 = i0 + 32;
-                            uint32_t b0 = none, b1 = none;
-                            if (i0 < N) {
-                                b0 = (uint32_t)__ldg(fh + oo[e]);
-                                sumb += (int)b0;
+                        for (int e = 0; e < 4; e += 2) {
+                            const int t = 2 * u + e / 2;   // pair of slots 2t, 2t + 1
+                            if (t < VPL / 2) {
+                                const int i0 = (t << 6) + lane, i1 = i0 + 32;
+                                uint32_t b0 = none, b1 = none;
+                                if (i0 < N) {
+                                    b0 = (uint32_t)__ldg(fh + oo[e]);
+                                    sumb += (int)b0;
+                                }
+                                if (i1 < N) {
+                                    b1 = (uint32_t)__ldg(fh + oo[e + 1]);
+                                    sumb += (int)b1;
+                                }
+                                hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
                             }
-                            if (i1 < N) {
-                                b1 = (uint32_t)__ldg(fh + oo[e + 1]);
-                                sumb += (int)b1;
-                            }
-                            hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
+                        }
+                    }
+                    // #{b <= x} over the warp: x + 1 - b saturated to [0, 1] is 1 exactly when b <= x
+                    auto count_le = [&](int x) -> int {
+                        const __half2 m1 = __float2half2_rn(int_float((uint32_t)x + 1u));
+                        // two chains (half the add latency); the low half starts at 1024, so the
+                        // total 1024 + c (c <= 64) has the fp16 bits 0x6400 + c
+                        __half2 acc0 = __halves2half2(__float2half(1024.0f), __float2half(0.0f));
+                        __half2 acc1 = __float2half2_rn(0.0f);
+#pragma unroll
+                        for (int t = 0; t < VPL / 2; t += 2) {
+                            acc0 = __hadd2(acc0, __hsub2_sat(m1, hv[t]));
+                            if (t + 1 < VPL / 2) acc1 = __hadd2(acc1, __hsub2_sat(m1, hv[t + 1]));
+                        }
+                        const __half2 sum = __hadd2(acc0, acc1);
+                        const __half2 tot = __hadd2(sum, __lowhigh2highlow(sum));
+                        return __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
+                    };
+                    bk = kth_smallest(count_le, k, C, hint);
+#pragma unroll
+                    for (int t = 0; t < VPL / 2; ++t) {
+                        const float2 f = __half22float2(hv[t]);
+                        const uint32_t v0 = float_int(f.x), v1 = float_int(f.y);
+                        const float2 g0 = lut[v0], g1 = lut[v1];   // entry C+1 (no beam) adds zero
+                        sgs += g0.y + g1.y;
+                        if (v0 < (uint32_t)bk) {
+                            sl += g0.x;
+                            ++clt;
+                        }
+                        if (v1 < (uint32_t)bk) {
+                            sl += g1.x;
+                            ++clt;
+                        }
+                    }
+                } else {
+                    uint32_t v[VPL];
+#pragma unroll
+                    for (int t = 0; t < VPL; ++t) {
+                        const int i = (t << 5) + lane;
+                        uint32_t bv = none;
+                        if (i < N) {
+                            bv = (uint32_t)__ldg(fh + ol[t]);
+                            sumb += (int)bv;
+                        }
+                        v[t] = bv;
+                    }
+                    auto count_le = [&](int x) -> int {
+                        int c = 0;
+#pragma unroll
+                        for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)x) ? 1 : 0;
+                        return __reduce_add_sync(kFull, c);
+                    };
+                    bk = kth_smallest(count_le, k, C, hint);
+#pragma unroll
+                    for (int t = 0; t < VPL; ++t) {
+                        const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
+                        sgs += lg.y;
+                        if (v[t] < (uint32_t)bk) {
+                            sl += lg.x;
+                            ++clt;
                         }
                     }
                 }
-                // smallest b_k with #{b <= b_k} >= k
-                int blo = 0, bhi = C;
-                while (blo < bhi) {
-                    const int mid = (blo + bhi) >> 1;
-                    const __half2 m1 = __float2half2_rn(int_float((uint32_t)mid + 1u));
-                    // two chains (half the add latency); the low half starts at 1024, so the
-                    // total 1024 + c (c <= 64) has the fp16 bits 0x6400 + c
-                    __half2 acc0 = __halves2half2(__float2half(1024.0f), __float2half(0.0f));
-                    __half2 acc1 = __float2half2_rn(0.0f);
+                hint = bk;
 #pragma unroll
-                    for (int t = 0; t < VPL / 2; t += 2) {
-                        acc0 = __hadd2(acc0, __hsub2_sat(m1, hv[t]));
-                        if (t + 1 < VPL / 2) acc1 = __hadd2(acc1, __hsub2_sat(m1, hv[t + 1]));
-                    }
-                    const __half2 sum = __hadd2(acc0, acc1);
-                    const __half2 tot = __hadd2(sum, __lowhigh2highlow(sum));
-                    const int c = __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
-                    if (c >= k) bhi = mid;
-                    else blo = mid + 1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    sgs += __shfl_xor_sync(kFull, sgs, o);
+                    sl += __shfl_xor_sync(kFull, sl, o);
                 }
-                bk = (uint32_t)blo;
-#pragma unroll
-                for (int t = 0; t < VPL / 2; ++t) {
-                    const float2 f = __half22float2(hv[t]);
-                    const uint32_t v0 = float_int(f.x), v1 = float_int(f.y);
-                    const float2 g0 = lut[v0], g1 = lut[v1];   // entry C+1 (no beam) adds zero
-                    sgs += g0.y + g1.y;
-                    if (v0 < bk) {
-                        sl += g0.x;
-                        ++clt;
-                    }
-                    if (v1 < bk) {
-                        sl += g1.x;
-                        ++clt;
-                    }
+                clt = __reduce_add_sync(kFull, clt);
+                sumb = __reduce_add_sync(kFull, sumb);
+                if (lane == 0) {
+                    // Eq. 27-31; exp(Lbar) * exp(-var / 2) as one exponential
+                    const float lbar = (sl + (float)(k - clt) * lut[bk].x) * s_ep[0];
+                    const float dd = s_ep[1] * sgs;   // d_max - dbar
+                    const float dbar = d.d_max - dd;
+                    const float sd = fminf(dd, s_ep[2]) * s_ep[3];
+                    const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
+                    const float T = cbrtf(expf(lbar - 0.5f * var) * sd);
+                    d.T[(size_t)s * d.n_orient + q] = T;
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) |
+                                                   (unsigned long long)(0xffffffffu - (unsigned)q);
+                    atomicMax(d.best_key + s, key);
                 }
-            } else {
-                uint32_t v[VPL];
-#pragma unroll
-                for (int t = 0; t < VPL; ++t) {
-                    const int i = (t << 5) + lane;
-                    uint32_t bv = none;
-                    if (i < N) {
-                        bv = (uint32_t)__ldg(fh + ol[t]);
-                        sumb += (int)bv;
-                    }
-                    v[t] = bv;
-                }
-                // smallest b_k with #{b <= b_k} >= k
-                int blo = 0, bhi = C;
-                while (blo < bhi) {
-                    const int mid = (blo + bhi) >> 1;
-                    int c = 0;
-#pragma unroll
-                    for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)mid) ? 1 : 0;
-                    c = __reduce_add_sync(kFull, c);
-                    if (c >= k) bhi = mid;
-                    else blo = mid + 1;
-                }
-                bk = (uint32_t)blo;
-#pragma unroll
-                for (int t = 0; t < VPL; ++t) {
-                    const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
-                    sgs += lg.y;
-                    if (v[t] < bk) {
-                        sl += lg.x;
-                        ++clt;
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sgs += __shfl_xor_sync(kFull, sgs, o);
-                sl += __shfl_xor_sync(kFull, sl, o);
-            }
-            clt = __reduce_add_sync(kFull, clt);
-            sumb = __reduce_add_sync(kFull, sumb);
-            if (lane == 0) {
-                // Eq. 27-31; exp(Lbar) * exp(-var / 2) as one exponential
-                const float lbar = (sl + (float)(k - clt) * lut[bk].x) * s_ep[0];
-                const float dd = s_ep[1] * sgs;   // d_max - dbar
-                const float dbar = d.d_max - dd;
-                const float sd = fminf(dd, s_ep[2]) * s_ep[3];
-                const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
-                const float T = cbrtf(expf(lbar - 0.5f * var) * sd);
-                d.T[(size_t)s * d.n_orient + q] = T;
-                const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(T) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
-                atomicMax(d.best_key + s, key);
             }
         }
     }
@@ -404,7 +460,7 @@ TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *
     TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfExact};
     if (tp.vpl < 0) return tp;
     tp.smem = (((size_t)(max_C + 2) * sizeof(float2) + 15) & ~(size_t)15) +
-              (size_t)32 * tam_offs_stride(tp.vpl) * sizeof(int);
+              (size_t)kTamQ * 32 * tam_offs_stride(tp.vpl) * sizeof(int);
     const int occ = occupancy_for(tp.vpl, tp.h2, tp.smem);
     if (occ < 1) {
         tp.vpl = -1;
@@ -433,7 +489,7 @@ TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *
         double best_eff = -1.0;
         for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
             const int chunk = (nb + nc - 1) / nc;
-            const double tasks = (double)n_orient_per_req[r] * ((nb + chunk - 1) / chunk);
+            const double tasks = (double)((n_orient_per_req[r] + kTamQ - 1) / kTamQ) * ((nb + chunk - 1) / chunk);
             const double waves = ceil(tasks / (share > 1.0 ? share : 1.0));
             const double eff = tasks / (waves * (share > 1.0 ? share : 1.0)) * (double)chunk /
                                (double)(((chunk + kTamWarps - 1) / kTamWarps) * kTamWarps);
@@ -444,7 +500,7 @@ TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *
         }
         g.chunk = (nb + best_nc - 1) / best_nc;
         g.n_chunks = (nb + g.chunk - 1) / g.chunk;
-        task += n_orient_per_req[r] * g.n_chunks;
+        task += (n_orient_per_req[r] + kTamQ - 1) / kTamQ * g.n_chunks;
     }
     tp.total_tasks = task;
     tp.grid = task < slots ? task : slots;
