@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--workload", default="office", choices=["office", "batched", "served"],
                     help="office: one request (default); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
-    ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,2200,2400,2600,2800,3000,3500,4000,5000,6000",
+    ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,3000,4000,5000,6000,7000,8000,10000,12000",
                     help="served: arrival rates per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals per rate")
     ap.add_argument("--serve-configs", default="8x2,16x3,64x3",
