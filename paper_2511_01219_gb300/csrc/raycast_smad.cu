@@ -344,6 +344,8 @@ __global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict
     if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
 }
 
+constexpr int kSmadLoads = 4;   // 32-range chunks a SMAD warp has in flight
+
 // SMAD.  One warp per hypothesis, taken from a device counter over the
 // batch's hypothesis list (request r owns slots [hyp_base_r, hyp_base_r +
 // n_hyp_r)).  The warp reads the hypothesis's N_s ranges 32 at a time,
@@ -379,15 +381,15 @@ __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, 
         long long *chunkP = reinterpret_cast<long long *>(mine + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
         const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
         long long carry = 0;
-        for (int c0 = 0; c0 < nch; c0 += 4) {
-            uint32_t r[4];
+        for (int c0 = 0; c0 < nch; c0 += kSmadLoads) {
+            uint32_t r[kSmadLoads];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {   // four loads in flight
+            for (int u = 0; u < kSmadLoads; ++u) {   // kSmadLoads loads in flight
                 const int jj = ((c0 + u) << 5) + lane;
                 r[u] = (c0 + u < nch && jj < ns) ? __ldg(row + jj) : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kSmadLoads; ++u) {
                 if (c0 + u >= nch) break;
                 uint32_t sc = r[u];
 #pragma unroll
