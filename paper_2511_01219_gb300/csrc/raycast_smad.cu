@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict
     if (lane == 0 && my_steps) atomicAdd(&bs->dda_steps, my_steps);
 }
 
-constexpr int kSmadLoads = 4;   // 32-range chunks a SMAD warp has in flight
+constexpr int kSmadLoads = 16;   // 32-range chunks a SMAD warp has in flight
 
 // SMAD.  One warp per hypothesis, taken from a device counter over the
 // batch's hypothesis list (request r owns slots [hyp_base_r, hyp_base_r +

@@ -3,9 +3,11 @@
 // k_topk: the K hypotheses with the smallest SMAD (Sec. III intro: SMAD orders
 // all positions, the ordered set is cut into batches).  Keys are
 // numerator << 21 | index, so they are unique and ascending key order is
-// (SMAD, index) order.  One CTA finds the K-th smallest key by MSB-first radix
-// select over 8-bit digits (only the digits below the highest set bit), keeps
-// the K keys not above it, and sorts them with a bitonic network.
+// (SMAD, index) order.  One CTA histograms the 11 bits below the keys' highest
+// set bit, finds the digit holding the K-th smallest key, and sorts the keys
+// up to that digit with a bitonic network, keeping the first K; when too many
+// keys share that digit it falls back to an MSB-first radix select over 8-bit
+// digits.
 //
 // k_select_batch: after TAM has scored one batch, the per-hypothesis
 // orientation argmax of Eq. 22 (already reduced by TAM into one 64-bit key per
@@ -48,6 +50,8 @@ __device__ void bitonic_sort(unsigned long long *v, int n_pow2) {
     }
 }
 
+constexpr int kTopkBins = 2048;   // first pass: the 11 bits below the keys' highest set bit
+
 // one CTA per request
 __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap) {
     extern __shared__ __align__(16) unsigned long long sm[];
@@ -56,15 +60,19 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     const int n = d.n_hyp, K = d.K;
     int Kp = 1;
     while (Kp < K) Kp <<= 1;
-    unsigned long long *sortbuf = sm;                                        // [Kp_cap]
-    unsigned int *hist = reinterpret_cast<unsigned int *>(sm + Kp_cap);      // [256]
-    unsigned long long *keys_s = sm + Kp_cap + 128;                          // [stage_cap]
+    unsigned long long *sortbuf = sm;                                          // [2 * Kp_cap]
+    unsigned int *hist = reinterpret_cast<unsigned int *>(sm + 2 * Kp_cap);    // [kTopkBins]
+    unsigned long long *keys_s = sm + 2 * Kp_cap + kTopkBins / 2;              // [stage_cap]
     __shared__ unsigned long long s_or;
     __shared__ int s_digit, s_below, s_cnt;
+    __shared__ unsigned int s_warp[32];
     const bool staged = n <= stage_cap;
     const unsigned long long *keys = staged ? keys_s : keys_g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_round = (n + blockDim.x - 1) / blockDim.x * blockDim.x;   // whole warps in every round
 
     if (threadIdx.x == 0) { s_or = 0; s_cnt = 0; }
+    for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     unsigned long long orv = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -73,14 +81,75 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         orv |= k;
     }
     for (int o = 16; o > 0; o >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, o);
-    if ((threadIdx.x & 31) == 0) atomicOr(&s_or, orv);
+    if (lane == 0) atomicOr(&s_or, orv);
     __syncthreads();
-    int top = s_or ? 63 - __clzll((long long)s_or) : 0;
+    const int top = s_or ? 63 - __clzll((long long)s_or) : 0;
+
+    // One pass over 11-bit digits finds the digit b* of the K-th smallest key;
+    // the keys with digit < b* are all in, those with digit b* are sorted with
+    // them and the first K kept.
+    const int sh = top >= 10 ? top - 10 : 0;   // every key is < 2^(top + 1), so key >> sh < 2^11
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[keys[i] >> sh], 1u);
+    __syncthreads();
+    {
+        const unsigned a = hist[2 * threadIdx.x], b = hist[2 * threadIdx.x + 1];   // 1024 threads x 2 bins
+        unsigned incl = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned v = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            s_warp[lane] = v - s_warp[lane];   // exclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const unsigned excl = s_warp[warp] + incl - (a + b);
+        if (excl < (unsigned)K && excl + a + b >= (unsigned)K) {
+            if (excl + a >= (unsigned)K) {
+                s_digit = 2 * threadIdx.x;
+                s_below = (int)excl;
+            } else {
+                s_digit = 2 * threadIdx.x + 1;
+                s_below = (int)(excl + a);
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long dstar = (unsigned long long)s_digit;
+    const int n_sel = s_below + (int)hist[s_digit];   // keys with digit <= b*
+    if (n_sel <= 2 * Kp_cap) {
+        for (int i = threadIdx.x; i < n_round; i += blockDim.x) {   // one slot reservation per warp
+            const unsigned long long k = i < n ? keys[i] : ~0ull;
+            const bool take = i < n && (k >> sh) <= dstar;
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&s_cnt, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) sortbuf[base + __popc(bal & ((1u << lane) - 1u))] = k;
+        }
+        int P = 1;
+        while (P < n_sel) P <<= 1;
+        for (int i = n_sel + threadIdx.x; i < P; i += blockDim.x) sortbuf[i] = ~0ull;
+        __syncthreads();
+        bitonic_sort(sortbuf, P);
+        for (int i = threadIdx.x; i < K; i += blockDim.x)
+            d.survivors[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
+        return;
+    }
+
+    // Many keys share the digit b*: MSB-first radix select over 8-bit digits.
     unsigned long long prefix = 0, mask = 0;
     int remaining = K;
-    const int lane = threadIdx.x & 31;
-    const int n_round = (n + blockDim.x - 1) / blockDim.x * blockDim.x;   // whole warps in every round
     for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
+        __syncthreads();
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -89,7 +158,6 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         }
         __syncthreads();
         if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
             unsigned int local = 0;
             for (int dg = 0; dg < 8; ++dg) local += hist[lane * 8 + dg];
             unsigned int incl = local;
@@ -116,7 +184,6 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         prefix |= (unsigned long long)s_digit << shift;
         mask |= 255ull << shift;
         remaining -= s_below;
-        __syncthreads();
     }
     // prefix is now the K-th smallest key; one slot reservation per warp
     for (int i = threadIdx.x; i < n_round; i += blockDim.x) {
@@ -224,8 +291,10 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
 cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s) {
     int Kp = 1;
     while (Kp < max_K) Kp <<= 1;
-    const int stage_cap = max_n_hyp <= kStageMax ? max_n_hyp : 0;
-    size_t smem = (size_t)Kp * 8 + 256 * 4 + (size_t)stage_cap * 8;
+    const size_t fixed = (size_t)2 * Kp * 8 + (size_t)kTopkBins * 4;
+    const size_t smem_max = 227 * 1024;
+    const int stage_cap = (max_n_hyp <= kStageMax && fixed + (size_t)max_n_hyp * 8 <= smem_max) ? max_n_hyp : 0;
+    const size_t smem = fixed + (size_t)stage_cap * 8;
     cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_topk<<<R, kTopkThreads, smem, s>>>(reqs, Kp, stage_cap);

@@ -535,3 +535,29 @@ def test_served_admission_by_budget(relo, workload):
     for i, (status, res, lat) in enumerate(done):
         assert status == relo.OK and res.as_dict() == alone[i]
     ctx.close()
+
+
+def test_survivors_when_every_smad_ties(relo):
+    """A map without obstacles: every synthesized scan is empty, every SMAD
+    numerator is the same, and the survivor keys differ only in the hypothesis
+    index.  The top-K's first 11-bit histogram then puts every key in one bin
+    (the radix-select path); the survivors must be the K lowest indices."""
+    torch = torch_()
+    g = np.zeros((80, 96), np.int8)
+    rng = np.random.default_rng(12)
+    cells = np.stack([rng.integers(0, 96, 300), rng.integers(0, 80, 300)], 1).astype(np.int32)
+    cells = np.unique(cells, axis=0)
+    ang = workloads.beam_angles(90, 120)
+    z = np.full(90, 3.0, np.float32)
+    for K in (16, 100):
+        ctx = relo.Relo(n_orient=40, topk=K, batch=K, local_topk=4, early_stop=0, max_range=5.0)
+        mid = ctx.load_map(g, 0.05)
+        ctx.set_hypotheses(mid, workloads.cell_centres(cells, 0.05))
+        res = ctx.relocalize(mid, z, ang, 4.0)
+        assert res.status == relo.OK
+        num = ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(len(cells), dtype=torch.int64, device="cuda")).cpu().numpy()
+        surv = ctx.stage(relo.STAGE_SURVIVORS, torch.empty(K, dtype=torch.int32, device="cuda")).cpu().numpy()
+        assert (num == num[0]).all()
+        assert np.array_equal(surv, np.arange(K))
+        assert np.array_equal(surv, oracle.rank(num, K))
+        ctx.close()
