@@ -209,7 +209,6 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // smallest b with #{b' <= b} >= k as a bisection over [0, C].  The likelihood
 // table is reloaded only when a CTA moves to another request's task.
 constexpr int kTamQ = 4;
-constexpr int kTamMaxSlots = 32;   // survivors a warp keeps hints for within one chunk
 
 // resident CTAs per SM the register budget is sized for
 __host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 6 : 2) : (vpl <= 24 ? 3 : 2); }
@@ -222,8 +221,6 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
     __shared__ int s_base[kMaxBatchRequests + 1];
     __shared__ int s_skip, s_lut_r;
     __shared__ float s_ep[5];   // per-task constants of the epilogue (lane 0 reads them)
-    // each warp's last k-th smallest value per survivor slot, carried to the next orientation block
-    __shared__ int s_hint[kTamWarps][kTamMaxSlots];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
     if (threadIdx.x == 0) {
@@ -232,12 +229,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
     }
     __syncthreads();
     float2 *lut = reinterpret_cast<float2 *>(smem);
-    // A CTA takes a contiguous run of tasks: consecutive tasks are the next
-    // orientation blocks of the same survivors, so the hints carry over.
-    const int per = (total_tasks + gridDim.x - 1) / gridDim.x;
-    const int t_end = min(total_tasks, (int)(blockIdx.x + 1) * per);
-    int prev_r = -1, prev_chunk = -1, prev_qb = -1;
-    for (int task = blockIdx.x * per; task < t_end; ++task) {
+    for (int task = blockIdx.x; task < total_tasks; task += gridDim.x) {
         int lo = 0, hi = R - 1;   // last request whose task_base <= task
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -272,10 +264,6 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         const int chunk = local / nblk;
         const int q0 = qb * kTamQ;
         const int nq = min(kTamQ, d.n_orient - q0);
-        const bool chained = r == prev_r && chunk == prev_chunk && qb == prev_qb + 1;
-        prev_r = r;
-        prev_chunk = chunk;
-        prev_qb = qb;
         for (int qi = 0; qi < nq; ++qi) {
             const int m = (q0 + qi) * d.n_enum;
             int *oq = offs + qi * 32 * kS;
@@ -294,11 +282,10 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         const int s_hi = min(sg.s_end, s_lo + sg.chunk);
         const int C = d.C;
         const uint32_t none = (uint32_t)C + 1u;   // table entry with zero weight
-        for (int s = s_lo + warp, slot = 0; s < s_hi; s += kTamWarps, ++slot) {
+        for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
             const int2 hc = d.hyps[d.survivors[s]];
             const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
-            // the previous orientation's k-th smallest value (from the previous block when chained)
-            int hint = chained && slot < kTamMaxSlots ? s_hint[warp][slot] : -1;
+            int hint = -1;   // the previous orientation's k-th smallest value
             for (int qi = 0; qi < nq; ++qi) {
                 const int q = q0 + qi;
                 const int *ol = offs + (qi * 32 + lane) * kS;   // this lane's offsets, slot s = beam 32 s + lane
@@ -413,8 +400,6 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                     atomicMax(d.best_key + s, key);
                 }
             }
-            if (lane == 0 && slot < kTamMaxSlots) s_hint[warp][slot] = hint;
-            __syncwarp();
         }
     }
 }
