@@ -252,6 +252,10 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
  * context has launched since it was created. */
 #define RELO_N_STAGES 7
 int relo_set_profiling(relo_ctx *ctx, int32_t enable);
+/* Profiles only the stages whose bit is set in stage_mask (bit s = stage s
+ * above; 0 = off).  Each event pair costs the launch stream a little time, so
+ * a caller timing the whole path can bracket only the kernels it needs. */
+int relo_set_profiling_mask(relo_ctx *ctx, uint32_t stage_mask);
 int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
                      int64_t *kernels_out);
 

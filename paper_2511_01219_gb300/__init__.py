@@ -40,7 +40,7 @@ EXPORTED = [
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
-    "relo_serve_stop", "relo_scan_cache_stats",
+    "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
             "relo_get_stage": (ctypes.c_int, [P, I32, P, I64]),
             "relo_synth_scans_dev": (ctypes.c_int, [P, I32, P, I32, P, I32, F, P, P, I64, P]),
             "relo_set_profiling": (ctypes.c_int, [P, I32]),
+            "relo_set_profiling_mask": (ctypes.c_int, [P, ctypes.c_uint32]),
             "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
             "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
             "relo_relocalize_batch": (ctypes.c_int, [P, P, I32, P]),
@@ -276,6 +277,13 @@ class Relo:
 
     def set_profiling(self, on: bool):
         self._check(self._L.relo_set_profiling(self._h, int(bool(on))), "set_profiling")
+
+    def set_profiling_stages(self, stages):
+        """Profile only the named stages (names from STAGES); an empty list turns profiling off."""
+        mask = 0
+        for name in stages:
+            mask |= 1 << STAGES.index(name)
+        self._check(self._L.relo_set_profiling_mask(self._h, mask), "set_profiling_mask")
 
     def stage_times(self, reset: bool = False):
         """({stage: ms}, {stage: launches}, kernels launched since creation)."""

@@ -147,7 +147,7 @@ struct relo_ctx {
     struct Server *server = nullptr;
     Blob *blob = nullptr;                 // host staging of one upload (heap)
     // stage timing
-    bool profiling = false;
+    unsigned profile_mask = 0;   // stages whose launches are bracketed with events
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
@@ -193,18 +193,19 @@ cudaEvent_t take_event(relo_ctx *ctx) {
     return e;
 }
 
-// Wraps one kernel launch: counts it and, with profiling on, brackets it with events.
+// Wraps one kernel launch: counts it and, when its stage is profiled, brackets it with events.
 template <typename F>
 cudaError_t timed_on(relo_ctx *ctx, cudaStream_t st, int stage, int n_kernels, F &&launch) {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (ctx->profiling) {
+    const bool prof = (ctx->profile_mask >> stage) & 1u;
+    if (prof) {
         a = take_event(ctx);
         b = take_event(ctx);
         if (a) cudaEventRecord(a, st);
     }
     cudaError_t e = launch();
     ctx->kernels += n_kernels;
-    if (ctx->profiling && a && b) {
+    if (prof && a && b) {
         cudaEventRecord(b, st);
         ctx->pending.push_back({stage, a, b});
     }
@@ -1763,7 +1764,13 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {
 
 int relo_set_profiling(relo_ctx *ctx, int32_t enable) {
     if (!ctx) return RELO_E_INVALID_ARG;
-    ctx->profiling = enable != 0;
+    ctx->profile_mask = enable ? (1u << RELO_N_STAGES) - 1u : 0u;
+    return RELO_OK;
+}
+
+int relo_set_profiling_mask(relo_ctx *ctx, uint32_t stage_mask) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    ctx->profile_mask = stage_mask & ((1u << RELO_N_STAGES) - 1u);
     return RELO_OK;
 }
 
