@@ -305,7 +305,7 @@ __host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
 // mix freely across the GPU.
 constexpr int kCastThreads = 256;
 
-__global__ void __launch_bounds__(kCastThreads) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
+__global__ void __launch_bounds__(kCastThreads, 6) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
                                                        BatchState *bs) {
     __shared__ int s_base[kMaxBatchRequests + 1];
     const int lane = threadIdx.x & 31;
