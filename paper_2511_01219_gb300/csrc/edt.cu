@@ -107,29 +107,33 @@ __global__ void k_edt_col_final(const int8_t *__restrict__ grid, int W, int H, i
     }
 }
 
+// The row is staged with W cells of sentinel on each side and "no obstacle in
+// this column" as the same sentinel, a value larger than any squared distance
+// that still leaves room for dx^2, so the outward scan needs no bounds or
+// sentinel tests: a sentinel never improves the minimum.
+constexpr int kRowSentinel = 0x3fffffff;
+
 __global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int Wp, int32_t *__restrict__ d2,
                            uint16_t *__restrict__ field) {
-    extern __shared__ int32_t row[];
+    extern __shared__ int32_t rowbuf[];   // [3W]: sentinels, the row, sentinels
+    int32_t *row = rowbuf + W;
     const int y = blockIdx.x;
     const int32_t *src = colsq + (size_t)y * W;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) row[x] = src[x];
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const int v = src[x];
+        row[x] = v == kInf ? kRowSentinel : v;
+        rowbuf[x] = kRowSentinel;
+        row[W + x] = kRowSentinel;
+    }
     __syncthreads();
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         int best = row[x];
-        for (int dx = 1; (long long)dx * dx < best; ++dx) {
-            const int dx2 = dx * dx;
-            const int xl = x - dx, xr = x + dx;
-            if (xl < 0 && xr >= W) break;
-            if (xl >= 0) {
-                int v = row[xl];
-                if (v != kInf && v + dx2 < best) best = v + dx2;
-            }
-            if (xr < W) {
-                int v = row[xr];
-                if (v != kInf && v + dx2 < best) best = v + dx2;
-            }
+        const int reach = x > W - 1 - x ? x : W - 1 - x;   // past this both sides are sentinels
+        for (int dx = 1; dx <= reach && dx * dx < best; ++dx) {
+            const int v = min(row[x - dx], row[x + dx]) + dx * dx;
+            best = v < best ? v : best;
         }
-        d2[(size_t)y * W + x] = best == kInf ? kD2None : best;
+        d2[(size_t)y * W + x] = best >= kRowSentinel ? kD2None : best;
         field[(size_t)y * Wp + x] = (uint16_t)(best > C ? C : best);
     }
 }
@@ -172,7 +176,7 @@ cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
     k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.TW, m.TH, m.summ, m.bits);
     k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
     uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
-    size_t smem = (size_t)m.W * sizeof(int32_t);
+    size_t smem = (size_t)3 * m.W * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
