@@ -18,9 +18,11 @@
 // (Eq. 23) falls strictly as b grows, so the descending sort of Eq. 24 is the
 // ascending order of b: the warp finds the k-th smallest b by bisection over
 // [0, C] with register-resident values, and the top-k sum of l is
-// sum_{b < b_k} l(b) + (k - #{b < b_k}) l(b_k).  A shared-memory table holds
+// sum_{b <= b_k} l(b) - (#{b <= b_k} - k) l(b_k), the count being the one the
+// search ends on.  The counts run on fp16 patterns 0x6400 + b, two beams per
+// instruction, while C + 1 <= 6143.  A shared-memory table holds
 // l(b) and sqrt(C) - sqrt(b) for every b in [0, C]; with those and the exact
-// integer sum of b, lane 0 evaluates Eq. 27-31:
+// integer sum of b, one lane per orientation evaluates Eq. 27-31:
 //     wp = exp(Lbar),  d_max - dbar = res * sum(sqrt(C) - sqrt(b)) / N,
 //     s_d = min(d_max - dbar, d_max - d_min) / (d_max - d_min),
 //     var = res^2 * sum(b) / N - dbar^2,  c = exp(-var / 2),
@@ -42,42 +44,55 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTamWarps = 8;
-constexpr int kHalfExact = 2048;   // fp16 holds every integer in [0, 2048] exactly
+// Selection values as fp16 bit patterns 0x6400 + b.  Positive fp16 numbers
+// order like their bit patterns, so this is an increasing map of b onto fp16
+// numbers >= 1024, consecutive ones at least 1 apart; it stays finite while
+// 0x6400 + b <= 0x7bff, i.e. b <= 6143.
+constexpr uint32_t kHalfBias = 0x6400u;
+constexpr int kHalfMaxB = 0x7bff - 0x6400;
 
-// The smallest b in [0, C] with count_le(b) >= k, given count_le(C) >= k (every
-// valid beam is <= C).  hint < 0: bisection over [0, C].  Otherwise the search
-// starts at hint: two counts confirm an unchanged answer; else it gallops
-// away from hint in doubling steps to a bracket [lo, hi] with count_le(lo - 1)
-// < k <= count_le(hi) and bisects it.
+// The smallest b in [0, C] with count_le(b) >= k, given count_le(C) = n_C >= k
+// (every valid beam is <= C); cnt receives count_le(b).  hint < 0: bisection
+// over [0, C].  Otherwise the search starts at hint: two counts confirm an
+// unchanged answer; else it gallops away from hint in doubling steps to a
+// bracket [lo, hi] with count_le(lo - 1) < k <= count_le(hi) and bisects it.
+// The count at hi is carried along, so the answer's count costs nothing.
 template <typename F>
-__device__ __forceinline__ int kth_smallest(F &&count_le, int k, int C, int hint) {
-    int lo = 0, hi = C;
+__device__ __forceinline__ int kth_smallest(F &&count_le, int k, int C, int n_C, int hint, int &cnt) {
+    int lo = 0, hi = C, c_hi = n_C;
     if (hint >= 0) {
-        if (count_le(hint) >= k) {
-            if (hint == 0 || count_le(hint - 1) < k) return hint;
-            hi = hint - 1;   // count_le(hi) >= k
+        const int ch = count_le(hint);
+        if (ch >= k) {
+            const int cm = hint == 0 ? 0 : count_le(hint - 1);
+            if (cm < k) {
+                cnt = ch;
+                return hint;
+            }
+            hi = hint - 1;
+            c_hi = cm;
             for (int step = 1;; step <<= 1) {
                 const int p = hi - step;
                 if (p < 0) {
                     lo = 0;
                     break;
                 }
-                if (count_le(p) < k) {
+                const int cp = count_le(p);
+                if (cp < k) {
                     lo = p + 1;
                     break;
                 }
                 hi = p;
+                c_hi = cp;
             }
         } else {
             lo = hint + 1;   // count_le(lo - 1) < k
             for (int step = 1;; step <<= 1) {
                 const int p = lo + step - 1;
-                if (p >= C) {
-                    hi = C;
-                    break;
-                }
-                if (count_le(p) >= k) {
+                if (p >= C) break;   // hi = C
+                const int cp = count_le(p);
+                if (cp >= k) {
                     hi = p;
+                    c_hi = cp;
                     break;
                 }
                 lo = p + 1;
@@ -86,9 +101,15 @@ __device__ __forceinline__ int kth_smallest(F &&count_le, int k, int C, int hint
     }
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (count_le(mid) >= k) hi = mid;
-        else lo = mid + 1;
+        const int cm = count_le(mid);
+        if (cm >= k) {
+            hi = mid;
+            c_hi = cm;
+        } else {
+            lo = mid + 1;
+        }
     }
+    cnt = c_hi;
     return lo;
 }
 
@@ -220,7 +241,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_base[kMaxBatchRequests + 1];
     __shared__ int s_skip, s_lut_r;
-    __shared__ float s_ep[5];   // per-task constants of the epilogue (lane 0 reads them)
+    __shared__ float s_ep[5];   // per-task constants of the epilogue
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
     if (threadIdx.x == 0) {
@@ -282,19 +303,19 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         const int s_hi = min(sg.s_end, s_lo + sg.chunk);
         const int C = d.C;
         const uint32_t none = (uint32_t)C + 1u;   // table entry with zero weight
+        const float d_max = d.d_max;
         for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
             const int2 hc = d.hyps[d.survivors[s]];
             const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
             int hint = -1;   // the previous orientation's k-th smallest value
             for (int qi = 0; qi < nq; ++qi) {
-                const int q = q0 + qi;
                 const int *ol = offs + (qi * 32 + lane) * kS;   // this lane's offsets, slot s = beam 32 s + lane
                 int sumb = 0;
                 float sgs = 0.0f, sl = 0.0f;
-                int clt = 0;
                 int bk;
+                int cle;   // #{b <= bk} over the valid beams
                 if constexpr (H2) {
-                    __half2 hv[VPL / 2];
+                    uint32_t hv[VPL / 2];   // fp16 patterns 0x6400 + b of slots 2t (low half) and 2t + 1
 #pragma unroll
                     for (int u = 0; u < (VPL + 3) / 4; ++u) {
                         const int4 o4 = *reinterpret_cast<const int4 *>(ol + 4 * u);
@@ -313,41 +334,40 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                                     b1 = (uint32_t)__ldg(fh + oo[e + 1]);
                                     sumb += (int)b1;
                                 }
-                                hv[t] = __floats2half2_rn(int_float(b0), int_float(b1));
+                                hv[t] = (b0 | (b1 << 16)) + (kHalfBias | (kHalfBias << 16));   // b <= C + 1: no carry
                             }
                         }
                     }
-                    // #{b <= x} over the warp: x + 1 - b saturated to [0, 1] is 1 exactly when b <= x
+                    // #{b > x} on a lane: f(b) - f(x) saturated to [0, 1] is 1 exactly when b > x (the
+                    // exact difference is then >= 1, else <= 0, and rounding keeps both); then
+                    // #{b <= x} over the warp is the 32 VPL slots less those (no-beam slots are > C)
                     auto count_le = [&](int x) -> int {
-                        const __half2 m1 = __float2half2_rn(int_float((uint32_t)x + 1u));
+                        const __half2 fx = __halves2half2(__ushort_as_half((unsigned short)(kHalfBias + x)),
+                                                          __ushort_as_half((unsigned short)(kHalfBias + x)));
                         // two chains (half the add latency); the low half starts at 1024, so the
                         // total 1024 + c (c <= 64) has the fp16 bits 0x6400 + c
-                        __half2 acc0 = __halves2half2(__float2half(1024.0f), __float2half(0.0f));
+                        __half2 acc0 = __halves2half2(__ushort_as_half((unsigned short)kHalfBias), __float2half(0.0f));
                         __half2 acc1 = __float2half2_rn(0.0f);
 #pragma unroll
                         for (int t = 0; t < VPL / 2; t += 2) {
-                            acc0 = __hadd2(acc0, __hsub2_sat(m1, hv[t]));
-                            if (t + 1 < VPL / 2) acc1 = __hadd2(acc1, __hsub2_sat(m1, hv[t + 1]));
+                            acc0 = __hadd2(acc0, __hsub2_sat(*reinterpret_cast<const __half2 *>(&hv[t]), fx));
+                            if (t + 1 < VPL / 2)
+                                acc1 = __hadd2(acc1, __hsub2_sat(*reinterpret_cast<const __half2 *>(&hv[t + 1]), fx));
                         }
                         const __half2 sum = __hadd2(acc0, acc1);
                         const __half2 tot = __hadd2(sum, __lowhigh2highlow(sum));
-                        return __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
+                        const int gt = __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
+                        return 32 * VPL - gt;
                     };
-                    bk = kth_smallest(count_le, k, C, hint);
+                    bk = kth_smallest(count_le, k, C, N, hint, cle);
+                    const uint32_t bkb = kHalfBias + (uint32_t)bk;
 #pragma unroll
                     for (int t = 0; t < VPL / 2; ++t) {
-                        const float2 f = __half22float2(hv[t]);
-                        const uint32_t v0 = float_int(f.x), v1 = float_int(f.y);
-                        const float2 g0 = lut[v0], g1 = lut[v1];   // entry C+1 (no beam) adds zero
+                        const uint32_t p0 = hv[t] & 0xffffu, p1 = hv[t] >> 16;
+                        const float2 g0 = lut[p0 - kHalfBias], g1 = lut[p1 - kHalfBias];   // C+1 (no beam) adds zero
                         sgs += g0.y + g1.y;
-                        if (v0 < (uint32_t)bk) {
-                            sl += g0.x;
-                            ++clt;
-                        }
-                        if (v1 < (uint32_t)bk) {
-                            sl += g1.x;
-                            ++clt;
-                        }
+                        if (p0 <= bkb) sl += g0.x;
+                        if (p1 <= bkb) sl += g1.x;
                     }
                 } else {
                     uint32_t v[VPL];
@@ -367,15 +387,12 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                         for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)x) ? 1 : 0;
                         return __reduce_add_sync(kFull, c);
                     };
-                    bk = kth_smallest(count_le, k, C, hint);
+                    bk = kth_smallest(count_le, k, C, N, hint, cle);
 #pragma unroll
                     for (int t = 0; t < VPL; ++t) {
                         const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
                         sgs += lg.y;
-                        if (v[t] < (uint32_t)bk) {
-                            sl += lg.x;
-                            ++clt;
-                        }
+                        if (v[t] <= (uint32_t)bk) sl += lg.x;
                     }
                 }
                 hint = bk;
@@ -384,20 +401,20 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                     sgs += __shfl_xor_sync(kFull, sgs, o);
                     sl += __shfl_xor_sync(kFull, sl, o);
                 }
-                clt = __reduce_add_sync(kFull, clt);
                 sumb = __reduce_add_sync(kFull, sumb);
                 if (lane == 0) {
-                    // Eq. 27-31; exp(Lbar) * exp(-var / 2) as one exponential
-                    const float lbar = (sl + (float)(k - clt) * lut[bk].x) * s_ep[0];
+                    const int q = q0 + qi;
+                    // top-k sum of l: every b <= bk, less the cle - k ties at bk beyond the k-th
+                    const float lbar = (sl - (float)(cle - k) * lut[bk].x) * s_ep[0];
                     const float dd = s_ep[1] * sgs;   // d_max - dbar
-                    const float dbar = d.d_max - dd;
+                    const float dbar = d_max - dd;
                     const float sd = fminf(dd, s_ep[2]) * s_ep[3];
                     const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
                     const float T = cbrtf(expf(lbar - 0.5f * var) * sd);
-                    d.T[(size_t)s * d.n_orient + q] = T;
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) |
-                                                   (unsigned long long)(0xffffffffu - (unsigned)q);
-                    atomicMax(d.best_key + s, key);
+                d.T[(size_t)s * d.n_orient + q] = T;
+                const unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) |
+                                               (unsigned long long)(0xffffffffu - (unsigned)q);
+                atomicMax(d.best_key + s, key);
                 }
             }
         }
@@ -457,7 +474,7 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStr
 // of a CTA's warps, and lays the requests' tasks out one after another.
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
                  int max_C, int n_sm, TamSeg *segs) {
-    TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfExact};
+    TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfMaxB};
     if (tp.vpl < 0) return tp;
     tp.smem = (((size_t)(max_C + 2) * sizeof(float2) + 15) & ~(size_t)15) +
               (size_t)kTamQ * 32 * tam_offs_stride(tp.vpl) * sizeof(int);

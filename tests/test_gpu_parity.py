@@ -210,11 +210,12 @@ def test_full_path_matches_oracle(relo, workload, cfg):
     ctx.close()
 
 
-@pytest.mark.parametrize("d_max", [2.25, 2.3, 4.5])
+@pytest.mark.parametrize("d_max", [2.25, 2.3, 3.9, 3.95, 4.5])
 def test_selection_counts_either_side_of_fp16_range(relo, workload, d_max):
-    """The TAM selection counts run in packed fp16 while C + 1 <= 2048
-    (d_max / res = 45 gives C = 2025) and in 32-bit integers above (46^2 =
-    2116, 90^2 = 8100, the largest clamp): both match the oracle."""
+    """The TAM selection counts run on packed fp16 patterns 0x6400 + b while
+    C + 1 <= 6143 (d_max / res = 78 gives C = 6084; 45 and 46 straddle the
+    2048 where fp16 stops holding every integer) and in 32-bit integers above
+    (79^2 = 6241, 90^2 = 8100, the largest clamp): all match the oracle."""
     wl = workload(0)
     ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, d_max=d_max)
     want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
