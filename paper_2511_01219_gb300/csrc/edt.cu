@@ -30,10 +30,11 @@ constexpr int kInf = 0x7fffffff;
 // occupancy bitmaps: a warp covers 32 consecutive columns (four 8x8 tiles) and
 // L is a multiple of 8, so the ballot of each row gives four tile rows, which
 // lanes 0-3 collect into their tile's word (cells outside the map are free).
-// Each word is stored four times: as is, and for the frames mirrored in x
-// (x' = 8 TW - 1 - x: tile TW - 1 - tx, bits reversed within each row), in y
-// (rows reversed) and in both (all 64 bits reversed), which the ray cast uses
-// so that every ray travels towards +x and +y.
+// The word is stored as is, and, with the cells outside the map set, into the
+// four walk frames: as is, and mirrored in x (x' = 8 TW - 1 - x: tile TW - 1 -
+// tx, bits reversed within each row), in y (rows reversed) and in both (all 64
+// bits reversed), which the ray cast uses so that every ray travels towards +x
+// and +y.
 __global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H, int L, int TW, int TH,
                                   int2 *__restrict__ summ, uint64_t *__restrict__ bits) {
     const int lane = threadIdx.x & 31;
@@ -43,30 +44,36 @@ __global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H,
     if (x0 >= W) return;   // the whole warp lies right of the map
     const int y0 = sgm * L;
     int first = -1, last = -1;
-    uint64_t word = 0ull;
+    uint64_t word = 0ull, wword = 0ull;   // the map's word; the walk frames' word (outside cells set)
     for (int y = y0; y < y0 + L; ++y) {
-        const bool occ = x < W && y < H && grid[(size_t)y * W + x] >= 65;
+        const bool inside = x < W && y < H;
+        const bool occ = inside && grid[(size_t)y * W + x] >= 65;
         if (occ) {
             if (first < 0) first = y;
             last = y;
         }
         const unsigned b = __ballot_sync(0xffffffffu, occ);
+        const unsigned bw = __ballot_sync(0xffffffffu, occ || !inside);
         word |= (uint64_t)((b >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
+        wword |= (uint64_t)((bw >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
         if ((y & 7) == 7) {
             const int tx = (x0 >> 3) + lane, ty = y >> 3;
             if (lane < 4 && tx < TW && ty < TH) {
-                const size_t n = (size_t)TW * TH;
-                const uint64_t rev = __brevll(word);   // both mirrors
-                const uint64_t ymir = ((uint64_t)__byte_perm((uint32_t)word, 0u, 0x0123u) << 32) |
-                                      (uint64_t)__byte_perm((uint32_t)(word >> 32), 0u, 0x0123u);
+                const size_t WB = (size_t)TW + 1, n = walk_frame_words(TW, TH);
+                uint64_t *wf = bits + (size_t)TW * TH;
+                const uint64_t rev = __brevll(wword);   // both mirrors
+                const uint64_t ymir = ((uint64_t)__byte_perm((uint32_t)wword, 0u, 0x0123u) << 32) |
+                                      (uint64_t)__byte_perm((uint32_t)(wword >> 32), 0u, 0x0123u);
                 const uint64_t xmir = ((uint64_t)__byte_perm((uint32_t)rev, 0u, 0x0123u) << 32) |
                                       (uint64_t)__byte_perm((uint32_t)(rev >> 32), 0u, 0x0123u);
                 bits[(size_t)ty * TW + tx] = word;
-                bits[n + (size_t)ty * TW + (TW - 1 - tx)] = xmir;
-                bits[2 * n + (size_t)(TH - 1 - ty) * TW + tx] = ymir;
-                bits[3 * n + (size_t)(TH - 1 - ty) * TW + (TW - 1 - tx)] = rev;
+                wf[(size_t)ty * WB + tx] = wword;
+                wf[n + (size_t)ty * WB + (TW - 1 - tx)] = xmir;
+                wf[2 * n + (size_t)(TH - 1 - ty) * WB + tx] = ymir;
+                wf[3 * n + (size_t)(TH - 1 - ty) * WB + (TW - 1 - tx)] = rev;
             }
             word = 0ull;
+            wword = 0ull;
         }
     }
     if (x < W) summ[(size_t)sgm * W + x] = make_int2(first, last);
@@ -147,6 +154,14 @@ __global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int 
     }
 }
 
+// the last column and row of tiles of each walk frame: every bit set
+__global__ void k_walk_border(uint64_t *__restrict__ wf, int TW, int TH) {
+    uint64_t *f = wf + (size_t)blockIdx.x * walk_frame_words(TW, TH);
+    const int WB = TW + 1;
+    for (int i = threadIdx.x; i <= TH; i += blockDim.x) f[(size_t)i * WB + TW] = ~0ull;
+    for (int i = threadIdx.x; i < TW; i += blockDim.x) f[(size_t)TH * WB + i] = ~0ull;
+}
+
 __global__ void k_map_tables(const int32_t *__restrict__ d2s, const uint16_t *__restrict__ fs,
                              const uint64_t *__restrict__ bs, int W, int H, int TW, int Wp, int32_t *d2, uint16_t *field,
                              uint8_t *occ) {
@@ -187,6 +202,7 @@ cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
 
 cudaError_t launch_field_border(const MapDev &m, cudaStream_t s) {
     k_field_border<<<1024, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.C);
+    k_walk_border<<<4, 256, 0, s>>>(m.bits + (size_t)m.TW * m.TH, m.TW, m.TH);
     return cudaGetLastError();
 }
 

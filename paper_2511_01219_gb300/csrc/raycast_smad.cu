@@ -174,8 +174,11 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
 // Tile walk with the per-direction tables (RayTables).  The ray moves from
 // tile to tile in its own frame, the map mirrored in x when D_x <= 0 (x' =
 // 8 TW - 1 - x) and in y when D_y <= 0, so that it always travels towards +x
-// and +y; the occupancy of each mirrored frame is stored beside the native
-// one.  In a tile whose word is not zero, the word moved to the current cell
+// and +y.  Each of the four frames is stored as a walk frame: cells outside
+// the map are set and a last column and row of full tiles follow the map, so
+// the first cell outside the map stops the ray like an occupied one and is
+// recognised after the loop, which needs no bounds test per tile.  In a tile
+// whose word is not zero, the word moved to the current cell
 // is ANDed with the table's bit board of the cells still ahead; on a
 // staircase that only moves +x and +y the cell order along the ray is the
 // row-major bit order, so the lowest common bit is the hit.  Otherwise the
@@ -186,7 +189,9 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
                                              const RayTables &t, int ns, int j, int hx, int hy, int2 d, int *hit,
                                              int *steps) {
     const bool xneg = d.x <= 0, yneg = d.y <= 0;
-    const uint64_t *__restrict__ bq = bits + (size_t)((xneg ? 1 : 0) + (yneg ? 2 : 0)) * TW * TH;
+    const unsigned WB = (unsigned)TW + 1u;   // walk frame row, with the border column
+    const uint64_t *__restrict__ bq =
+        bits + (size_t)TW * TH + (size_t)((xneg ? 1 : 0) + (yneg ? 2 : 0)) * walk_frame_words(TW, TH);
     const int xlo = xneg ? 8 * TW - W : 0, ylo = yneg ? 8 * TH - H : 0;   // the map in the ray's frame
     const int fx = xneg ? 8 * TW - 1 - hx : hx, fy = yneg ? 8 * TH - 1 - hy : hy;
     const uint16_t *__restrict__ selx = t.selx + j;
@@ -195,13 +200,15 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     const unsigned uns = (unsigned)ns;
     // The loop only finds where the ray stops; the range is computed after it,
     // once for the whole warp, rather than in a divergent branch per lane.
-    // Indexes are unsigned 32-bit (every table and map index fits).
+    // Cells outside the map are set in the walk frames, so leaving the map
+    // ends the loop as a hit and is told apart afterwards.  Indexes are
+    // unsigned 32-bit (every table and map index fits).
     int adx = 0, ady = 0, cx = fx, cy = fy;
-    int stop;   // 1 hit, 2 range limit, 3 left the map
+    int stop;   // 1 hit (or left the map), 2 range limit
     for (;;) {
         const int lx = cx & 7, ly = cy & 7;
         // the tile's word and the exit steps are loaded together: one memory round trip per tile
-        const uint64_t word = __ldg(bq + ((unsigned)(cy >> 3) * (unsigned)TW + (unsigned)(cx >> 3)));
+        const uint64_t word = __ldg(bq + ((unsigned)(cy >> 3) * WB + (unsigned)(cx >> 3)));
         const uint32_t kx = __ldg(selx + (unsigned)(adx + 8 - lx) * uns);
         const uint32_t ky = __ldg(sely + (unsigned)(ady + 8 - ly) * uns);
         if (word) {
@@ -232,11 +239,9 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
         }
         cx = fx + adx;
         cy = fy + ady;
-        if ((unsigned)(cx - xlo) >= (unsigned)W || (unsigned)(cy - ylo) >= (unsigned)H) {   // left the map
-            stop = 3;
-            break;
-        }
     }
+    if (stop == 1 && ((unsigned)(fx + adx - xlo) >= (unsigned)W || (unsigned)(fy + ady - ylo) >= (unsigned)H))
+        stop = 3;   // the first cell outside the map
     const int sx = xneg ? -1 : 1, sy = yneg ? -1 : 1;
     cx = hx + sx * adx;
     cy = hy + sy * ady;

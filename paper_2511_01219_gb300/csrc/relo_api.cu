@@ -637,7 +637,7 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * (m.dev.H + 2 * m.dev.P));
-    dev_free(ctx, m.dev.bits, sizeof(uint64_t) * 4 * (size_t)m.dev.TW * m.dev.TH);
+    dev_free(ctx, m.dev.bits, sizeof(uint64_t) * occupancy_words(m.dev.TW, m.dev.TH));
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
     dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
     m = MapSlot();
@@ -661,11 +661,11 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     m.dev.P = pad_for(ctx->p.max_range, res);
     if (m.dev.P < 1) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
     m.dev.Wp = w + 2 * m.dev.P;
-    const size_t cells = (size_t)w * h, tiles = (size_t)m.dev.TW * m.dev.TH;
+    const size_t cells = (size_t)w * h;
     const size_t fcells = (size_t)m.dev.Wp * (h + 2 * m.dev.P);
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
-        {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, tiles * 8 * 4},
+        {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, occupancy_words(m.dev.TW, m.dev.TH) * 8},
         {(void **)&m.dev.summ, sizeof(int2) * (size_t)w * edt_segments(h)}};
     for (auto &a : allocs) {
         rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
@@ -678,7 +678,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
     if (e == cudaSuccess) e = launch_field_border(m.dev, ctx->stream);
-    if (e == cudaSuccess) ctx->kernels += 1;
+    if (e == cudaSuccess) ctx->kernels += 2;
     if (e == cudaSuccess) e = timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); });
     if (e != cudaSuccess) {
         free_map(ctx, m);

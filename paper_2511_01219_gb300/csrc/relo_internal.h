@@ -22,7 +22,8 @@ struct MapDev {
     int32_t *d2 = nullptr;      // [H*W] exact squared EDT, -1 = no obstacle
     uint16_t *field = nullptr;  // [(H+2P) * (W+2P)] min(d2, C), row-major with a border of P cells holding C
     int P = 0, Wp = 0;          // border width and padded row length
-    uint64_t *bits = nullptr;   // [4][TH*TW] occupancy, bit (y&7)*8 + (x&7); [1..3] the x-, y- and xy-mirrored frames
+    uint64_t *bits = nullptr;   // occupancy, bit (y&7)*8 + (x&7): [TH*TW] the map (cells outside free), then the
+                                // four walk frames (walk_frame_words each: native, mirrored in x, y and both)
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
     int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
@@ -34,6 +35,15 @@ __host__ __device__ inline int edt_segment_rows(int H) {
     int L = (H + 63) / 64;
     L = L < 16 ? 16 : L;
     return (L + 7) & ~7;
+}
+
+// A walk frame holds TW+1 x TH+1 tiles: the map's tiles with every cell
+// outside the map set, plus a last column and row of tiles with every bit set,
+// so a ray that leaves the map (always towards +x, +y in its frame) meets a set
+// bit at its first cell outside.
+__host__ __device__ inline size_t walk_frame_words(int TW, int TH) { return (size_t)(TW + 1) * (TH + 1); }
+__host__ __device__ inline size_t occupancy_words(int TW, int TH) {
+    return (size_t)TW * TH + 4 * walk_frame_words(TW, TH);
 }
 
 __host__ __device__ inline size_t tile_index(int x, int y, int TW) {
@@ -206,7 +216,7 @@ constexpr int kMaxBatchRequests = 256;
 constexpr int kMaxBatches = 64;      // ceil(K / batch) limit, bounds the TamSeg table
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s);          // interior of the field, d2, bitmap
-cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the field's constant border (once per map)
+cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the constant borders of the field and walk frames (once per map)
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);
 cudaError_t launch_synth(const RayArgs &a, uint32_t *ranges, int32_t *hit, cudaStream_t s);
