@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include "relo_internal.h"
+#include "scan_prep.cuh"
 
 namespace relo {
 
@@ -314,6 +315,10 @@ __global__ void __launch_bounds__(kCastThreads, 6) k_cast(const ReqDesc *__restr
                                                        BatchState *bs) {
     __shared__ int s_base[kMaxBatchRequests + 1];
     const int lane = threadIdx.x & 31;
+    // first the scan preparation, which the later stages need and the cast does
+    // not: every CTA fills its share of the TAM scores, CTA r prepares request r
+    for (int r = 0; r < R; ++r) scan_prep_fill(reqs[r], blockIdx.x, gridDim.x);
+    if ((int)blockIdx.x < R) scan_prep_request(reqs[blockIdx.x]);
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].chunk_base;
     if (threadIdx.x == 0) s_base[R] = total_chunks;
     __syncthreads();
@@ -650,6 +655,7 @@ cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState
     const long long warps = (long long)total_chunks;
     long long grid = (long long)n_sm * occ;
     if (grid * (kCastThreads / 32) > warps) grid = (warps + kCastThreads / 32 - 1) / (kCastThreads / 32);
+    if (grid < R) grid = R;   // one CTA per request for the scan preparation
     k_cast<<<(int)grid, kCastThreads, 0, s>>>(reqs, R, total_chunks, bs);
     return cudaGetLastError();
 }

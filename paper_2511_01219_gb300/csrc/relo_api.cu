@@ -106,9 +106,15 @@ struct Blob {
     unsigned char bytes[kBlobBytes];
 };
 
-__global__ void k_upload(const __grid_constant__ Blob blob, unsigned char *dst) {
+// copies the blob; with bs, also zeroes the batch's work counters
+__global__ void k_upload(const __grid_constant__ Blob blob, unsigned char *dst, BatchState *bs) {
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < blob.n; i += gridDim.x * blockDim.x)
         dst[i] = blob.bytes[i];
+    if (bs && blockIdx.x == 0 && threadIdx.x == 0) {
+        bs->ray_work = 0u;
+        bs->cast_work = 0u;
+        bs->dda_steps = 0ull;
+    }
 }
 
 // Device resources of one batch in flight: its stream, descriptors, TAM
@@ -748,14 +754,15 @@ int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, 
 
 // ---- batches ------------------------------------------------------------------------------------
 
-int upload(relo_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
+int upload(relo_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes, BatchState *bs) {
     const unsigned char *p = static_cast<const unsigned char *>(src);
     unsigned char *d = static_cast<unsigned char *>(dst);
     while (bytes > 0) {
         const size_t n = bytes < kBlobBytes ? bytes : kBlobBytes;
         ctx->blob->n = (unsigned int)n;
         memcpy(ctx->blob->bytes, p, n);
-        k_upload<<<(unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16), 256, 0, st>>>(*ctx->blob, d);
+        k_upload<<<(unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16), 256, 0, st>>>(*ctx->blob, d, bs);
+        bs = nullptr;
         CK(cudaGetLastError(), "descriptor upload");
         ctx->kernels += 1;
         p += n;
@@ -1024,16 +1031,22 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         classes.assign(1, classes.back());
     }
     const int NC = (int)classes.size();
+    // Without early termination no batch waits on another's outcome: one TAM
+    // round scores every batch's survivors and one selection launch takes the
+    // batches in order (Remark 2's termination test is then never made).
+    bool any_early = false;
+    for (int r = 0; r < R; ++r) any_early = any_early || desc[r].early_stop;
+    const int tam_rounds = any_early ? max_batches : std::min(max_batches, 1);
     std::vector<TamSeg> segs((size_t)max_batches * NC * R);
     std::vector<TamPlan> plans((size_t)max_batches * NC);
     std::vector<int> nb((size_t)R), no((size_t)R), sb((size_t)R);
-    for (int bi = 0; bi < max_batches; ++bi) {
+    for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {
             int beams_c = 1, C_c = 0;
             for (int r = 0; r < R; ++r) {
-                const int s0 = bi * desc[r].B;
+                const int s0 = any_early ? bi * desc[r].B : 0;
                 const bool in = vcls[r] == classes[c] && bi < desc[r].n_batches;
-                nb[r] = in ? std::min(desc[r].K, s0 + desc[r].B) - s0 : 0;
+                nb[r] = in ? (any_early ? std::min(desc[r].K, s0 + desc[r].B) - s0 : desc[r].K) : 0;
                 no[r] = desc[r].n_orient;
                 sb[r] = s0;
                 if (vcls[r] == classes[c]) {
@@ -1051,10 +1064,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     std::vector<unsigned char> blob(seg_off + sizeof(TamSeg) * segs.size(), 0);
     memcpy(blob.data(), desc.data(), sizeof(ReqDesc) * R);
     memcpy(blob.data() + seg_off, segs.data(), sizeof(TamSeg) * segs.size());
-    if ((rc = upload(ctx, st, sl.reqs_dev, blob.data(), blob.size()))) return rc;
+    if ((rc = upload(ctx, st, sl.reqs_dev, blob.data(), blob.size(), sl.bs))) return rc;
     ReqDesc *rq = sl.reqs_dev;
     const TamSeg *segs_dev = reinterpret_cast<const TamSeg *>(reinterpret_cast<unsigned char *>(sl.reqs_dev) + seg_off);
-    CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, sl.bs, st); }), "scan preparation");
+    // the ray-cast launch prepares the scans first; a batch without rays to cast prepares them alone
+    if (total_chunks <= 0) CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, st); }), "scan preparation");
     for (int r = 0; r < R; ++r) {
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
         if (wmode[r] == kWinRead) CK(cudaStreamWaitEvent(st, win[r]->built, 0), "window table");
@@ -1075,14 +1089,15 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_read(rq, R, total_read, st); }), "SMAD by window tables");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
-    for (int bi = 0; bi < max_batches; ++bi) {
+    for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {
             const TamPlan &tp = plans[(size_t)bi * NC + c];
             if (tp.total_tasks <= 0) continue;
             const TamSeg *sg = segs_dev + ((size_t)bi * NC + c) * R;
             CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, tp, st); }), "TAM");
         }
-        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, bi, bi == max_batches - 1, st); }),
+        const int lo = any_early ? bi : 0, hi = any_early ? bi + 1 : max_batches;
+        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, lo, hi, bi == tam_rounds - 1, st); }),
            "batch selection");
     }
     created.keep = true;

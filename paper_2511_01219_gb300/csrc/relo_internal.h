@@ -225,7 +225,8 @@ cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, ui
                               int32_t *kmax, cudaStream_t s);
 
 // batched stages; R requests, descriptors in device memory
-cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s);
+// scan preparation alone, for a batch that casts no rays (launch_cast does it otherwise)
+cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s);
 // casts the total_chunks 32-ray chunks of the batch into the requests' scan tables
 cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s);
 // SMAD of every hypothesis of the batch from the requests' scan tables
@@ -247,7 +248,7 @@ int tam_vpl_for(int max_beams);
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
                  int max_beams, int max_C, int n_sm, TamSeg *segs);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
-// selection of batch index batch_idx; with last, also every request's result
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, bool last, cudaStream_t s);
+// selection of batch indexes batch_lo .. batch_hi - 1 in order; with last, also every request's result
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s);
 
 }  // namespace relo

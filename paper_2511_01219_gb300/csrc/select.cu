@@ -237,15 +237,19 @@ __device__ void finalize_request(const ReqDesc &d) {
     *reinterpret_cast<relo_result *>(d.result) = r;
 }
 
-// one CTA per request: selection of batch `batch_idx` (skipped when the
-// request has fewer batches or already terminated early).  Keys (TAM
-// descending, then survivor position) are unique, so each survivor's rank is
-// the number of smaller keys; ranks below L fill the local top-k directly.
-// The launch of the last batch index also writes every request's result.
-__global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_idx, int last) {
+// one CTA per request: selection of batches batch_lo .. batch_hi - 1 in
+// order (each skipped when the request has fewer batches or already
+// terminated early).  Keys (TAM descending, then survivor position) are
+// unique, so each survivor's rank is the number of smaller keys; ranks below
+// L fill the local top-k directly.  With last, the launch also writes every
+// request's result.
+__global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_lo, int batch_hi,
+                                                       int last) {
     __shared__ unsigned long long v[kMaxBatch];
     __shared__ int s_skip;
     const ReqDesc &d = reqs[blockIdx.x];
+    for (int batch_idx = batch_lo; batch_idx < batch_hi; ++batch_idx) {
+    __syncthreads();   // the previous batch's ranks and state updates are done
     if (threadIdx.x == 0) s_skip = batch_idx >= d.n_batches || d.state->done || d.scan->n_valid <= 0;
     __syncthreads();
     if (!s_skip) {
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
         }
         for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;
     }
+    }
     if (last) {
         __syncthreads();   // the selection state of this launch is complete
         if (threadIdx.x == 0) finalize_request(d);
@@ -301,8 +306,8 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_idx, bool last, cudaStream_t s) {
-    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_idx, last ? 1 : 0);
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s) {
+    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_lo, batch_hi, last ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -1,14 +1,5 @@
-// Scan preparation (Eq. 11, 16, 26) and TAM scoring (Eq. 22-31).
-//
-// k_scan_prep (one CTA): converts the float32 ranges of the (n_skip-strided)
-// beams to Q16 cell ranges R_i = llrint(z_i * 65536 / res) for valid beams
-// (finite, 0 < z < max_range; invalid beams count 0, Eq. 16 and the
-// placeholder rule after Eq. 20), sums them, compacts the valid beams in
-// order into (panoramic index b_i, R_i) pairs, and fixes the retained-beam
-// count of Eq. 27: the three top-k means of a descending list satisfy
-// mean(k_low) >= mean(k_mid) >= mean(k_full) whenever k_low <= k_mid <= k_full
-// (a running mean of a descending list never grows), so their median is the
-// mean over the median of the three k values.
+// TAM scoring (Eq. 22-31), and the stand-alone launch of the scan
+// preparation (scan_prep.cuh) for batches that cast no rays.
 //
 // k_tam: one warp per (survivor, orientation m).  For each valid beam i the
 // endpoint cell is hypothesis + round-half-up(R_i * D_{(b_i + m) mod N_s} /
@@ -37,6 +28,7 @@
 #include <stdint.h>
 
 #include "relo_internal.h"
+#include "scan_prep.cuh"
 
 namespace relo {
 
@@ -121,95 +113,14 @@ __host__ __device__ constexpr int tam_offs_stride(int vpl) {
     return ((vpl + 3) & ~3) + ((((vpl + 3) & ~3) / 4) % 2 == 0 ? 4 : 0);
 }
 
-// exact float of an integer 0 <= v < 2^23 (the float 2^23 + v, less 2^23)
-__device__ __forceinline__ float int_float(uint32_t v) { return __uint_as_float(0x4b000000u | v) - 8388608.0f; }
-// the integer of an integral float 0 <= f < 2^23
-__device__ __forceinline__ uint32_t float_int(float f) { return __float_as_uint(f + 8388608.0f) & 0x7fffffu; }
-
-// CTA (request, 0) does the scan preparation above and resets the request's
-// selection buffers (argmax keys 0, shifts and local top-k -1, selection
-// state 0); all CTAs (request, y) share the fill of its TAM scores with NaN
-// (unscored), so a batch needs no separate memsets.
-__global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ reqs, BatchState *bs) {
-    __shared__ int warp_cnt[32];
-    __shared__ long long warp_sum[32];
-    __shared__ int s_base;
+// CTA (request, 0) does the scan preparation of scan_prep.cuh and all CTAs
+// (request, y) share the fill of its TAM scores with NaN; this launch serves
+// batches whose requests all read resident synthesized scans (otherwise the
+// ray-cast launch does the same work first).
+__global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ reqs) {
     const ReqDesc &d = reqs[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = d.n_beams;
-    // every CTA of the request (blockIdx.y) fills its share of the TAM scores
-    const int nT = d.K * d.n_orient;
-    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < nT; i += gridDim.y * blockDim.x)
-        d.T[i] = __int_as_float(0x7fffffff);
-    if (blockIdx.y != 0) return;
-    if (threadIdx.x == 0) s_base = 0;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        bs->ray_work = 0u;
-        bs->cast_work = 0u;
-        bs->dda_steps = 0ull;
-    }
-    for (int i = threadIdx.x; i < d.K; i += blockDim.x) {
-        d.best_key[i] = 0ull;
-        d.best_m[i] = -1;
-    }
-    for (int i = threadIdx.x; i < d.n_batches * d.L; i += blockDim.x) d.local[i] = -1;
-    if (threadIdx.x == 0) {
-        d.state->best = 0ull;
-        d.state->n_tam_evals = 0;
-        d.state->n_batches = 0;
-        d.state->done = 0;
-    }
-    long long my_sum = 0;
-    __syncthreads();
-    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
-        const int i = c0 + threadIdx.x;
-        int R = 0;
-        bool ok = false;
-        if (i < n) {
-            const float z = d.ranges[(size_t)i * d.skip];
-            ok = isfinite(z) && z > 0.0f && z < d.max_range;
-            if (ok) R = (int)__double2ll_rn(__ddiv_rn(__dmul_rn((double)z, 65536.0), d.resd));
-        }
-        my_sum += R;
-        const unsigned bal = __ballot_sync(kFull, ok);
-        if (lane == 0) warp_cnt[warp] = __popc(bal);
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < (int)(blockDim.x >> 5) ? warp_cnt[lane] : 0;
-            int incl = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            warp_cnt[lane] = incl - v;   // exclusive
-        }
-        __syncthreads();
-        if (ok) {
-            const int pos = s_base + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
-            d.vbR[pos] = make_int2(d.b[i], R);
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_base += warp_cnt[warp] + __popc(bal);
-        __syncthreads();
-    }
-    for (int o = 16; o > 0; o >>= 1) my_sum += __shfl_xor_sync(kFull, my_sum, o);
-    if (lane == 0) warp_sum[warp] = my_sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_sum[w];
-        const int N = s_base;
-        int km = (int)floor(__dmul_rn(d.a_mid, (double)N));
-        if (km < 1) km = 1;
-        int kl = (int)floor(__dmul_rn(d.a_low, (double)N));
-        if (kl < 1) kl = 1;
-        int lo = km < kl ? km : kl, hi = km < kl ? kl : km;
-        int k = N < lo ? lo : (N > hi ? hi : N);   // median of {N, km, kl}
-        d.scan->sum_real = tot;
-        d.scan->n_valid = N;
-        d.scan->k_ret = k;
-        d.scan->dda_steps = 0ull;
-    }
+    scan_prep_fill(d, blockIdx.y, gridDim.y);
+    if (blockIdx.y == 0) scan_prep_request(d);
 }
 
 // Work is split into tasks (request, block of kTamQ consecutive orientations,
@@ -464,8 +375,8 @@ int occupancy_for(int vpl, bool h2, size_t smem) {
 
 int tam_vpl_for(int max_beams) { return vpl_bucket(max_beams); }
 
-cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, BatchState *bs, cudaStream_t s) {
-    k_scan_prep<<<dim3(R, 8), 1024, 0, s>>>(reqs, bs);
+cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s) {
+    k_scan_prep<<<dim3(R, 8), 1024, 0, s>>>(reqs);
     return cudaGetLastError();
 }
 
