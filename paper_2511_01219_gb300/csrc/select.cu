@@ -4,10 +4,11 @@
 // all positions, the ordered set is cut into batches).  Keys are
 // numerator << 21 | index, so they are unique and ascending key order is
 // (SMAD, index) order.  One CTA histograms the 11 bits below the keys' highest
-// set bit, finds the digit holding the K-th smallest key, and sorts the keys
-// up to that digit with a bitonic network, keeping the first K; when too many
-// keys share that digit it falls back to an MSB-first radix select over 8-bit
-// digits.
+// set bit, finds the digit holding the K-th smallest key, and orders the keys
+// up to that digit (by rank counting when they are few: keys are unique),
+// keeping the first K;
+// when too many keys share that digit it falls back to an MSB-first radix
+// select over 8-bit digits.
 //
 // k_select_batch: after TAM has scored one batch, the per-hypothesis
 // orientation argmax of Eq. 22 (already reduced by TAM into one 64-bit key per
@@ -50,6 +51,29 @@ __device__ void bitonic_sort(unsigned long long *v, int n_pow2) {
     }
 }
 
+constexpr int kRankMax = 512;   // up to this many keys, rank counting (one barrier) beats the sorting network
+
+// The first K of n unique keys v[0 .. n) (v has room for the next power of two)
+// in ascending order into the survivor list: by rank counting (each key's
+// position is the number of smaller keys) for a few keys, else by sorting.
+__device__ void order_out(unsigned long long *v, int n, int K, int32_t *survivors) {
+    if (n <= kRankMax) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long me = v[i];
+            int rank = 0;
+            for (int k = 0; k < n; ++k) rank += v[k] < me ? 1 : 0;   // every thread reads the same v[k]
+            if (rank < K) survivors[rank] = (int32_t)(me & ((1ull << kHypBits) - 1));
+        }
+        return;
+    }
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = n + threadIdx.x; i < P; i += blockDim.x) v[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort(v, P);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) survivors[i] = (int32_t)(v[i] & ((1ull << kHypBits) - 1));
+}
+
 constexpr int kTopkBins = 2048;   // first pass: the 11 bits below the keys' highest set bit
 
 // one CTA per request
@@ -58,8 +82,6 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     const ReqDesc &d = reqs[blockIdx.x];
     const unsigned long long *keys_g = d.keys;
     const int n = d.n_hyp, K = d.K;
-    int Kp = 1;
-    while (Kp < K) Kp <<= 1;
     unsigned long long *sortbuf = sm;                                          // [2 * Kp_cap]
     unsigned int *hist = reinterpret_cast<unsigned int *>(sm + 2 * Kp_cap);    // [kTopkBins]
     unsigned long long *keys_s = sm + 2 * Kp_cap + kTopkBins / 2;              // [stage_cap]
@@ -135,13 +157,8 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
             base = __shfl_sync(0xffffffffu, base, 0);
             if (take) sortbuf[base + __popc(bal & ((1u << lane) - 1u))] = k;
         }
-        int P = 1;
-        while (P < n_sel) P <<= 1;
-        for (int i = n_sel + threadIdx.x; i < P; i += blockDim.x) sortbuf[i] = ~0ull;
         __syncthreads();
-        bitonic_sort(sortbuf, P);
-        for (int i = threadIdx.x; i < K; i += blockDim.x)
-            d.survivors[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
+        order_out(sortbuf, n_sel, K, d.survivors);
         return;
     }
 
@@ -195,11 +212,8 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
         base = __shfl_sync(0xffffffffu, base, 0);
         if (take) sortbuf[base + __popc(bal & ((1u << lane) - 1u))] = k;
     }
-    for (int i = K + threadIdx.x; i < Kp; i += blockDim.x) sortbuf[i] = ~0ull;
     __syncthreads();
-    bitonic_sort(sortbuf, Kp);
-    for (int i = threadIdx.x; i < K; i += blockDim.x)
-        d.survivors[i] = (int32_t)(sortbuf[i] & ((1ull << kHypBits) - 1));
+    order_out(sortbuf, K, K, d.survivors);
 }
 
 // The request's pose, score and counters into its relo_result (one thread).
@@ -248,9 +262,11 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
     __shared__ unsigned long long v[kMaxBatch];
     __shared__ int s_skip;
     const ReqDesc &d = reqs[blockIdx.x];
+    const int n_batches = d.n_batches;
+    const bool none_valid = d.scan->n_valid <= 0, early = d.early_stop;
     for (int batch_idx = batch_lo; batch_idx < batch_hi; ++batch_idx) {
     __syncthreads();   // the previous batch's ranks and state updates are done
-    if (threadIdx.x == 0) s_skip = batch_idx >= d.n_batches || d.state->done || d.scan->n_valid <= 0;
+    if (threadIdx.x == 0) s_skip = batch_idx >= n_batches || none_valid || (early && d.state->done);
     __syncthreads();
     if (!s_skip) {
         SelectState *st = d.state;
