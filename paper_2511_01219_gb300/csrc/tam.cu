@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 // table is reloaded only when a CTA moves to another request's task.
 constexpr int kTamQ = 4;
 
-// resident CTAs per SM the register budget is sized for
-__host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 40 ? 6 : 2) : (vpl <= 24 ? 3 : 2); }
+// resident CTAs per SM the register budget is sized for (measured per values-per-lane class)
+__host__ __device__ constexpr int tam_min_blocks(int vpl, bool h2) { return h2 ? (vpl <= 24 ? 6 : vpl <= 40 ? 5 : 4) : (vpl <= 24 ? 3 : 2); }
 
 template <int VPL, bool H2>
 __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam(const ReqDesc *__restrict__ reqs,
