@@ -30,6 +30,8 @@
 // (kScanStore) that later requests with the same map, hypotheses, N_s and
 // limit read without casting (kScanRead).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "relo_internal.h"
@@ -664,15 +666,25 @@ cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pa
                         cudaStream_t s) {
     if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
     const size_t wb = smad_warp_bytes(max_ns_pad);
-    int wpc = 8;   // warps per CTA, within 200 KiB of shared memory
-    while (wpc > 1 && (size_t)wpc * wb > (size_t)200 * 1024) --wpc;
-    const size_t smem = (size_t)wpc * wb;
-    cudaError_t e = cudaFuncSetAttribute(k_smad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // warps per CTA: the most resident warps per SM that shared memory allows
+    // (a long row's scratch fills an SM before its thread limit; smaller CTAs
+    // waste less of it), the larger CTA on ties
+    cudaError_t e = cudaFuncSetAttribute(k_smad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::min((size_t)8 * wb, (size_t)200 * 1024));
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smad, wpc * 32, smem);
-    if (e != cudaSuccess) return e;
+    int wpc = 0, occ = 0;
+    for (int w = 8; w >= 1; --w) {
+        if ((size_t)w * wb > (size_t)200 * 1024) continue;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_smad, w * 32, (size_t)w * wb);
+        if (e != cudaSuccess) return e;
+        if (o * w > occ * wpc) {
+            wpc = w;
+            occ = o;
+        }
+    }
     if (occ < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)wpc * wb;
     long long grid = (long long)n_sm * occ;
     const long long need = ((long long)total_hyp + wpc - 1) / wpc;
     if (grid > need) grid = need;
