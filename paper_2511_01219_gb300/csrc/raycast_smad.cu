@@ -2,7 +2,9 @@
 //
 // Two kernels per batch.  k_cast casts every ray of every hypothesis, 32
 // neighbouring directions per warp (lane = ray, so the lanes of a warp trace
-// rays of similar length), into a per-request table of Q16 ranges.  k_smad
+// rays of similar length), into a per-request table of Q16 ranges.  Work
+// items run over the hypotheses for one 32-direction chunk after another, so
+// the warps in flight share a few directions' tables (they stay in L1).  k_smad
 // then reads a hypothesis's row, forms chunk prefixes that
 // give the cyclic prefix sum S of Eq. 17 at any index, evaluates the window
 // sums of Eq. 18 for the orientations m of Eq. 15 with two lookups per FoV
@@ -337,10 +339,10 @@ __global__ void __launch_bounds__(kCastThreads, 6) k_cast(const ReqDesc *__restr
             else hi = mid - 1;
         }
         const ReqDesc &d = reqs[lo];
-        const int nch = d.ns_pad >> 5;
         const int local = g - s_base[lo];
-        const int h = local / nch;
-        const int j = ((local - h * nch) << 5) + lane;
+        const int jc = local / d.n_hyp;   // hypothesis-minor: concurrent warps share 32 directions' tables
+        const int h = local - jc * d.n_hyp;
+        const int j = (jc << 5) + lane;
         if (j < d.ns) {
             const int2 hc = d.hyps[h];
             const int2 dir = d.D[j];
