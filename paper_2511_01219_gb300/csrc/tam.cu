@@ -13,7 +13,8 @@
 // search ends on.  The counts run on fp16 patterns 0x6400 + b, two beams per
 // instruction, while C + 1 <= 6143.  A shared-memory table holds
 // l(b) and sqrt(C) - sqrt(b) for every b in [0, C]; with those and the exact
-// integer sum of b, one lane per orientation evaluates Eq. 27-31:
+// integer sum of b, the warp evaluates Eq. 27-30 and, after the block's
+// orientations, one lane per orientation takes the exponential and Eq. 31:
 //     wp = exp(Lbar),  d_max - dbar = res * sum(sqrt(C) - sqrt(b)) / N,
 //     s_d = min(d_max - dbar, d_max - d_min) / (d_max - d_min),
 //     var = res^2 * sum(b) / N - dbar^2,  c = exp(-var / 2),
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
             const int2 hc = d.hyps[d.survivors[s]];
             const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
             int hint = -1;   // the previous orientation's k-th smallest value
+            float e_arg = 0.0f, e_sd = 0.0f;   // lane qi: orientation qi's exponent and s_d
             for (int qi = 0; qi < nq; ++qi) {
                 const int *ol = offs + (qi * 32 + lane) * kS;   // this lane's offsets, slot s = beam 32 s + lane
                 int sumb = 0;
@@ -313,20 +315,27 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                     sl += __shfl_xor_sync(kFull, sl, o);
                 }
                 sumb = __reduce_add_sync(kFull, sumb);
-                if (lane == 0) {
-                    const int q = q0 + qi;
-                    // top-k sum of l: every b <= bk, less the cle - k ties at bk beyond the k-th
+                {
+                    // Eq. 27-30 from the warp totals every lane holds; the top-k sum of l is every
+                    // b <= bk less the cle - k ties at bk beyond the k-th; lane qi keeps the exponent
+                    // of exp(Lbar) * exp(-var / 2) and s_d
                     const float lbar = (sl - (float)(cle - k) * lut[bk].x) * s_ep[0];
                     const float dd = s_ep[1] * sgs;   // d_max - dbar
                     const float dbar = d_max - dd;
-                    const float sd = fminf(dd, s_ep[2]) * s_ep[3];
                     const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
-                    const float T = cbrtf(expf(lbar - 0.5f * var) * sd);
+                    if (lane == qi) {
+                        e_arg = lbar - 0.5f * var;
+                        e_sd = fminf(dd, s_ep[2]) * s_ep[3];
+                    }
+                }
+            }
+            if (lane < nq) {   // Eq. 31, one lane per orientation of the block
+                const int q = q0 + lane;
+                const float T = cbrtf(expf(e_arg) * e_sd);
                 d.T[(size_t)s * d.n_orient + q] = T;
                 const unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) |
                                                (unsigned long long)(0xffffffffu - (unsigned)q);
                 atomicMax(d.best_key + s, key);
-                }
             }
         }
     }
