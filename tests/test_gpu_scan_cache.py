@@ -8,7 +8,8 @@ ranges).  The path that casts is itself checked against the oracle in
 test_gpu_parity.py; here every comparison is against a context without the
 cache.  Also covered: invalidation when the map or the hypotheses change,
 LRU eviction under a small budget, two requests of one geometry in one batch,
-and the served form.
+a batch mixing a request that reads stored scans with one that casts, and the
+served form.
 """
 import numpy as np
 import pytest
@@ -180,6 +181,34 @@ def test_one_geometry_twice_in_one_batch(relo):
         assert [r.as_dict() for r in ctx.relocalize_batch(items)] == want
     assert ctx.scan_cache_stats() == {"tables": 1, "bytes": 4 * len(hyps) * 120 + 8 * len(hyps) * 40, "hits": 2,
                                       "misses": 2, "evictions": 0, "win_tables": 1, "win_hits": 2}
+    ctx.close()
+
+
+@pytest.mark.parametrize("reader_first", [True, False])
+def test_batch_mixing_stored_and_cast_scans(relo, reader_first):
+    """One batch in which one request reads its map's resident scans and the
+    other casts rays: the ray-cast launch prepares both requests' real scans
+    (Eq. 16, 26-27), the reader's included, whichever place it takes."""
+    g1, h1 = small_map(seed=8)
+    g2, h2 = small_map(seed=9, n=96, n_hyp=300)
+    z1, ang = scan_from(g1, h1, 3, 90, 120, 0.7, seed=5)
+    z2, _ = scan_from(g2, h2, 9, 90, 120, -1.1, seed=6)
+    prm = dict(n_orient=40, topk=16, batch=8, local_topk=4, early_stop=0, max_range=5.0)
+    want1 = fresh_result(relo, g1, 0.05, h1, z1, ang, 4.0, **prm)
+    want2 = fresh_result(relo, g2, 0.05, h2, z2, ang, 4.0, **prm)
+    ctx = relo.Relo(scan_cache_bytes=GIB, **prm)
+    m1 = ctx.load_map(g1, 0.05)
+    ctx.set_hypotheses(m1, workloads.cell_centres(h1, 0.05))
+    m2 = ctx.load_map(g2, 0.05)
+    ctx.set_hypotheses(m2, workloads.cell_centres(h2, 0.05))
+    assert ctx.relocalize(m1, z1, ang, 4.0).as_dict() == want1   # stores map 1's scans
+    items = [(m1, z1, ang, 4.0), (m2, z2, ang, 4.0)]
+    want = [want1, want2]
+    if not reader_first:
+        items, want = items[::-1], want[::-1]
+    assert [r.as_dict() for r in ctx.relocalize_batch(items)] == want
+    st = ctx.scan_cache_stats()
+    assert st["tables"] == 2 and st["misses"] == 2 and st["hits"] == 1
     ctx.close()
 
 
