@@ -15,6 +15,8 @@ Paper references (arXiv 2511.01219):
   * Eq. 13: panoramic synthesized scan              -> synth_scan()
   * Eq. 16-20: SMAD                                 -> smad()
   * Eq. 22-31: TAM and orientation selection        -> tam(), best_orientation()
+  * Eq. 21 (Remark 5): CAER in place of SMAD         -> caer()
+  * Eq. 32-34: wp_LF, wp_baseline, TAM_mean          -> tam(metric=3, 2, 1)
   * Sec. III intro, Remarks 2-3, Sec. IV-C params:
     SMAD ordering, batches, local top-k, tau        -> relocalize()
 
@@ -72,6 +74,7 @@ def _L():
             "oracle_cast_ray": (I64, [P, I, I, I, I, I64, I64, I64, P, P, P]),
             "oracle_synth_scan": (None, [P, I, I, I, I, I, P, I64, P, P, P]),
             "oracle_smad": (None, [P, I, I, P, I, I, P, I64, P, P, I, I64, I, I, P, P, I]),
+            "oracle_caer": (None, [P, I, I, P, I, I, P, I64, P, P, I, I, I, P, P, I]),
             "oracle_tam": (None, [P, P, I, I, P, P, I, I, P, P, P, P, I, P, P, P, I]),
             "oracle_max_threads": (I, []),
         }
@@ -120,6 +123,8 @@ class Params:
     local_topk: int = 20
     tau: float = 0.95
     n_skip_beam: int = 1
+    coarse: int = 0     # ranking metric: 0 SMAD (Eq. 16-20), 1 CAER (Eq. 21)
+    fine: int = 0       # scoring metric: 0 TAM (Eq. 31), 1 TAM_mean (Eq. 34), 2 wp_baseline (Eq. 33), 3 wp_LF (Eq. 32)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -240,6 +245,27 @@ def smad_metres(num, pl: dict) -> np.ndarray:
     return np.asarray(num, np.float64) / float(pl["len"].sum()) / 65536.0 * pl["res"]
 
 
+def caer(grid, hyps: np.ndarray, pl: dict, n_threads: int = 0):
+    """Eq. 21 for every hypothesis: (numerator int64, minimising m int32), the
+    numerator being the sum over the FoV beams of |R_i - synthesized range|
+    (Q16; invalid beams count 0), minimised over the orientations SMAD uses."""
+    g = np.ascontiguousarray(grid, dtype=np.int8)
+    H, W = g.shape
+    h = np.ascontiguousarray(hyps, dtype=np.int32)
+    n = len(h)
+    num = np.zeros(n, np.int64)
+    mm = np.zeros(n, np.int32)
+    R = np.ascontiguousarray(pl["R"], dtype=np.int64)
+    _L().oracle_caer(_p(g), W, H, _p(h), n, pl["ns"], _p(pl["D"]), pl["rmax_q16"], _p(pl["b"]), _p(R), pl["n"],
+                     pl["n_enum"], int(pl["panoramic"]), _p(num), _p(mm), n_threads or max_threads())
+    return num, mm
+
+
+def coarse(grid, hyps: np.ndarray, pl: dict, prm: "Params", n_threads: int = 0):
+    """The ranking metric prm.coarse selects: SMAD (0) or CAER (1)."""
+    return caer(grid, hyps, pl, n_threads) if prm.coarse == 1 else smad(grid, hyps, pl, n_threads)
+
+
 def rank(num: np.ndarray, k: int) -> np.ndarray:
     """SMAD ordering: hypotheses sorted by (numerator, index), first k kept."""
     order = sorted(range(len(num)), key=lambda i: (int(num[i]), i))
@@ -251,8 +277,10 @@ def rank(num: np.ndarray, k: int) -> np.ndarray:
 # ----------------------------------------------------------------------------------------------
 
 def tam(grid, pairs_xy: np.ndarray, pairs_m: np.ndarray, pl: dict, prm: Params, res: float,
-        d2tab: np.ndarray | None = None, n_threads: int = 0, components: bool = False):
-    """Eq. 23-31 for each (hypothesis cell, m) pair; float64 scores."""
+        d2tab: np.ndarray | None = None, n_threads: int = 0, components: bool = False, metric: int | None = None):
+    """Eq. 23-31 for each (hypothesis cell, m) pair; float64 scores.  metric
+    (default prm.fine): 0 TAM, 1 TAM_mean (Eq. 34), 2 wp_baseline (Eq. 33),
+    3 wp_LF (Eq. 32)."""
     if pl["n_valid"] == 0:
         raise PlanError(E_NO_VALID_BEAMS, "scan has no valid beam")
     g = np.ascontiguousarray(grid, dtype=np.int8)
@@ -262,8 +290,8 @@ def tam(grid, pairs_xy: np.ndarray, pairs_m: np.ndarray, pl: dict, prm: Params, 
     n = len(mm)
     out = np.zeros(n, np.float64)
     comp = np.zeros((n, 5), np.float64) if components else None
-    params = np.array([prm.z_hit, prm.sigma_hit, prm.z_rand, prm.eps, res, prm.d_max, pl["a_mid"], pl["a_low"]],
-                      np.float64)
+    params = np.array([prm.z_hit, prm.sigma_hit, prm.z_rand, prm.eps, res, prm.d_max, pl["a_mid"], pl["a_low"],
+                       float(prm.fine if metric is None else metric)], np.float64)
     d2c = None if d2tab is None else np.ascontiguousarray(d2tab, dtype=np.int64)
     d2p = None if d2c is None else _p(d2c)
     _L().oracle_tam(_p(g), d2p, W, H, _p(xy), _p(mm), n, pl["ns"], _p(pl["D"]), _p(pl["b"]), _p(pl["R"]),
@@ -297,9 +325,10 @@ def best_orientation(T_row) -> int:
 
 def relocalize(grid, res: float, hyps: np.ndarray, ranges, angles, max_range: float, prm: Params,
                d2tab: np.ndarray | None = None, n_threads: int = 0, early_stop: bool = True) -> dict:
-    """SMAD ranking, then batched TAM orientation selection with local top-k
-    and early termination (Sec. III intro; ICP is not part of this path, so
-    the re-evaluated score of a local top-k pose is its first TAM score).
+    """SMAD ranking (CAER with prm.coarse = 1), then batched TAM orientation
+    selection (the metric prm.fine picks) with local top-k and early
+    termination (Sec. III intro; ICP is not part of this path, so the
+    re-evaluated score of a local top-k pose is its first TAM score).
 
     With early_stop False every survivor is scored (the "TAM on the top K"
     form); otherwise batches stop after the first whose best score >= tau.
@@ -307,7 +336,7 @@ def relocalize(grid, res: float, hyps: np.ndarray, ranges, angles, max_range: fl
     pl = plan(ranges, angles, max_range, res, prm)
     if len(hyps) == 0:
         raise ValueError("no hypotheses")
-    num, m_smad = smad(grid, hyps, pl, n_threads)
+    num, m_smad = coarse(grid, hyps, pl, prm, n_threads)
     K = min(prm.topk, len(hyps))
     surv = rank(num, K)
     if d2tab is None and grid.size <= (1 << 21):

@@ -4,7 +4,10 @@
  * Plain, slow, FP64/int64 C that restates, step by step, what the paper's
  * scoring path computes: the EDT lookup table (Sec. III-A item 3), the
  * panoramic map-synthesized scan (Eq. 13), SMAD (Eq. 16-20), and TAM
- * (Eq. 23-31).  Only tests, the smoke check and the benchmark's CPU-baseline
+ * (Eq. 23-31); and the metrics the paper sets against them: CAER (Eq. 21,
+ * Remark 5) in place of SMAD, and the likelihood-field sum (Eq. 32), its
+ * normalised form (Eq. 33) and the arithmetic-mean fusion (Eq. 34) in place
+ * of TAM.  Only tests, the smoke check and the benchmark's CPU-baseline
  * leg may load this library; the GPU library never does.  It shares no code,
  * header or table with the GPU library.
  *
@@ -327,6 +330,43 @@ void oracle_smad(const int8_t *grid, int W, int H, const int32_t *hyp_xy, int n_
     }
 }
 
+/*
+ * CAER (Eq. 21) for every hypothesis: the numerator
+ *     sum_i |R_i - syn[(b_i + m) mod N_s]|
+ * over every beam i of the FoV intervals (the intervals are exactly the
+ * beams' panoramic indices b_i; an invalid beam carries the placeholder 0, as
+ * in SMAD), minimised over the same orientations as SMAD (Eq. 20: m = 0 only
+ * when lambda >= 0.9); the denominator sum_k |I_k| is shared by every
+ * hypothesis and orientation, so numerators compare CAER.  Ties keep the
+ * smaller m.  R holds the n beams' Q16 ranges (0 for invalid ones).
+ */
+void oracle_caer(const int8_t *grid, int W, int H, const int32_t *hyp_xy, int n_hyp, int ns,
+                 const int64_t *D, int64_t rmax_q16, const int32_t *b, const int64_t *R, int n, int n_enum,
+                 int panoramic, int64_t *num_out, int32_t *m_out, int n_threads) {
+    (void)n_threads;
+#ifdef _OPENMP
+    #pragma omp parallel for num_threads(n_threads > 0 ? n_threads : 1) schedule(dynamic, 4)
+#endif
+    for (int h = 0; h < n_hyp; ++h) {
+        int64_t *syn = (int64_t *)malloc(sizeof(int64_t) * ns);
+        oracle_synth_scan(grid, W, H, hyp_xy[2 * h], hyp_xy[2 * h + 1], ns, D, rmax_q16, syn, NULL, NULL);
+        int64_t best = -1;
+        int32_t best_m = 0;
+        int m_end = panoramic ? 1 : ns;
+        for (int m = 0; m < m_end; m += n_enum) {
+            int64_t e = 0;
+            for (int i = 0; i < n; ++i) {
+                int64_t d = R[i] - syn[(b[i] + m) % ns];
+                e += d < 0 ? -d : d;
+            }
+            if (best < 0 || e < best) { best = e; best_m = m; }
+        }
+        num_out[h] = best;
+        m_out[h] = best_m;
+        free(syn);
+    }
+}
+
 /* ================================================================================
  * TAM (Eq. 23-31) for a list of (hypothesis, m) pairs.
  * ============================================================================== */
@@ -335,6 +375,7 @@ typedef struct {
     double z_hit, sigma_hit, z_rand, eps;
     double res, d_max;
     double a_mid, a_low;       /* Eq. 25 retention ratios (already evaluated at lambda) */
+    int metric;                /* 0 TAM (Eq. 31), 1 TAM_mean (Eq. 34), 2 wp_baseline (Eq. 33), 3 wp_LF (Eq. 32) */
 } tam_params;
 
 static int cmp_desc(const void *a, const void *b) {
@@ -352,6 +393,10 @@ static int cmp_desc(const void *a, const void *b) {
  * means, (Eq. 28) exp of it, (Eq. 29) s_d with d_min = res / 2, (Eq. 30) c from
  * the population variance of the d_i, and (Eq. 31) the cube root of the
  * product.  comp[0..4] (optional) receives L_bar, wp, s_d, c, mean d.
+ * With p->metric the score is instead the arithmetic mean (wp + s_d + c) / 3
+ * of the same components (Eq. 34), the likelihood-field sum
+ * wp_LF = sum of l_i over all N beams (Eq. 32), or its normalised form
+ * (exp(wp_LF / N) s_d)^(1/2) (Eq. 33: no retention, no c).
  */
 static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, int hx, int hy, int m, int ns,
                       const int64_t *D, const int32_t *b, const int64_t *R, const uint8_t *valid, int n,
@@ -391,6 +436,8 @@ static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, in
         mean[t] = s / ks[t];
     }
     /* median of three */
+    double lf = 0.0;   /* Eq. 32: every beam, before any retention */
+    for (int i = 0; i < N; ++i) lf += ell[i];
     double a = mean[0], bb = mean[1], c3 = mean[2], med;
     if ((a <= bb && bb <= c3) || (c3 <= bb && bb <= a)) med = bb;
     else if ((bb <= a && a <= c3) || (c3 <= a && a <= bb)) med = a;
@@ -407,7 +454,13 @@ static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, in
     if (dt > p->d_max) dt = p->d_max;
     double sd = 1.0 - (dt - dmin) / (p->d_max - dmin);
     double c = exp(-0.5 * var);
-    double T = cbrt(wp * sd * c);
+    double T;
+    switch (p->metric) {
+    case 1: T = (wp + sd + c) / 3.0; break;          /* Eq. 34 */
+    case 2: T = sqrt(exp(lf / N) * sd); break;        /* Eq. 33 */
+    case 3: T = lf; break;                            /* Eq. 32 */
+    default: T = cbrt(wp * sd * c); break;            /* Eq. 31 */
+    }
     if (comp) { comp[0] = med; comp[1] = wp; comp[2] = sd; comp[3] = c; comp[4] = dmean; }
     return T;
 }
@@ -416,13 +469,15 @@ static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, in
  * TAM scores for n_pairs (hypothesis cell, m) pairs.  d2tab (row-major, from
  * oracle_edt_full) may be NULL, in which case distances come from
  * oracle_d2_capped.  params: z_hit, sigma_hit, z_rand, eps, res, d_max, a_mid,
- * a_low.  comp (optional) receives 5 components per pair.
+ * a_low, metric (0-3, see tam_one).  comp (optional) receives 5 components per
+ * pair.
  */
 void oracle_tam(const int8_t *grid, const int64_t *d2tab, int W, int H, const int32_t *pair_xy,
                 const int32_t *pair_m, int n_pairs, int ns, const int64_t *D, const int32_t *b,
                 const int64_t *R, const uint8_t *valid, int n, const double *params, double *T_out,
                 double *comp, int n_threads) {
-    tam_params p = {params[0], params[1], params[2], params[3], params[4], params[5], params[6], params[7]};
+    tam_params p = {params[0], params[1], params[2], params[3], params[4], params[5], params[6], params[7],
+                    (int)params[8]};
     (void)n_threads;
 #ifdef _OPENMP
     #pragma omp parallel for num_threads(n_threads > 0 ? n_threads : 1) schedule(dynamic, 8)

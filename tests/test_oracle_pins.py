@@ -401,6 +401,130 @@ def test_tam_median_is_kmid_mean_and_sd_can_vanish():
 
 
 # ------------------------------------------------------------------------------------------
+# Eq. 21 and Eq. 32-34: the metrics the paper sets against SMAD and TAM
+# ------------------------------------------------------------------------------------------
+
+def two_class_case():
+    """The scene of test_tam_two_distance_classes_closed_form: n1 beams end on
+    the solid half (d = 0), the others leave the map (d = d_max)."""
+    H, W = 120, 120
+    g = np.zeros((H, W), np.int8)
+    g[60:, :] = 100
+    ns, n = 200, 100
+    ang = workloads.beam_angles(n, ns)
+    prm = oracle.Params(n_orient=20)
+    pl0 = oracle.plan(np.ones(n, np.float32), ang, 1000.0, RES, prm)
+    z = np.empty(n, np.float32)
+    n1 = 0
+    for i in range(n):
+        j = pl0["b"][i] % ns
+        if pl0["D"][2 * j + 1] / 2 ** 30 > 0.3:
+            z[i] = 10 * RES
+            n1 += 1
+        else:
+            z[i] = 500 * RES
+    return g, prm, oracle.plan(z, ang, 1000.0, RES, prm), n1, n
+
+
+def test_fine_metrics_two_distance_classes_closed_form():
+    """wp_LF sums l over every beam, n1 l(0) + n2 l(d_max), with no retention
+    (Eq. 32); wp_baseline is (exp(wp_LF / N) s_d)^(1/2) (Eq. 33); TAM_mean is
+    the arithmetic mean of the retained exp(L_bar), s_d and c (Eq. 34)."""
+    g, prm, pl, n1, N = two_class_case()
+    n2 = N - n1
+    l0, l1 = ell(0.0, prm), ell(prm.d_max, prm)
+    lam = N / pl["ns"]
+    k_mid = max(1, math.floor((prm.a_mid_min + lam * (prm.a_mid_max - prm.a_mid_min)) * N))
+    wp = math.exp((min(k_mid, n1) * l0 + max(0, k_mid - n1) * l1) / k_mid)
+    p = n2 / N
+    sd = 1 - (max(p * prm.d_max, RES / 2) - RES / 2) / (prm.d_max - RES / 2)
+    c = math.exp(-p * (1 - p) * prm.d_max ** 2 / 2)
+    lf = n1 * l0 + n2 * l1
+    xy, m = np.array([[60, 59]]), np.array([0])
+    got = [oracle.tam(g, xy, m, pl, prm, RES, metric=k)[0] for k in range(4)]
+    assert math.isclose(got[0], (wp * sd * c) ** (1 / 3), rel_tol=1e-12)
+    assert math.isclose(got[1], (wp + sd + c) / 3, rel_tol=1e-12)
+    assert math.isclose(got[2], math.sqrt(math.exp(lf / N) * sd), rel_tol=1e-12)
+    assert math.isclose(got[3], lf, rel_tol=1e-12)
+    assert 0 < n1 < N and got[2] < got[0]   # the unretained off-map beams pull the baseline down
+
+
+def test_fine_metrics_all_endpoints_on_obstacles():
+    """d = 0 for every beam: l = log(z_hit + z_rand + eps) = log wp, s_d = c = 1."""
+    g = np.full((30, 30), 100, np.int8)
+    g[15, 15] = 0
+    prm = oracle.Params(n_orient=8)
+    ang = workloads.beam_angles(50, 64)
+    pl = oracle.plan(np.full(50, 4 * RES, np.float32), ang, 10.0, RES, prm)
+    wp = 1.0 + 1e-6
+    xy, m = np.array([[15, 15]] * 8), np.arange(8) * 8
+    for k, want in ((1, (wp + 2) / 3), (2, math.sqrt(wp)), (3, 50 * math.log(wp))):
+        assert np.allclose(oracle.tam(g, xy, m, pl, prm, RES, metric=k), want, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fine_metric_bounds(seed):
+    """Arithmetic mean >= geometric mean of (wp, s_d, c): TAM_mean >= TAM;
+    every l <= log(z_hit + z_rand + eps), so wp_LF <= N log(...) and
+    wp_baseline <= 1."""
+    g, hyps, ang, n_orient = room_case(seed)
+    prm = oracle.Params(n_orient=n_orient)
+    z = np.random.default_rng(seed).uniform(0.1, 3.0, len(ang)).astype(np.float32)
+    pl = oracle.plan(z, ang, 4.0, RES, prm)
+    xy = np.repeat(hyps[:8], 5, axis=0)
+    m = np.tile(np.arange(5) * 3 * pl["n_enum"], 8)
+    T, comp = oracle.tam(g, xy, m, pl, prm, RES, components=True, metric=0)
+    Tm = oracle.tam(g, xy, m, pl, prm, RES, metric=1)
+    Tb = oracle.tam(g, xy, m, pl, prm, RES, metric=2)
+    Tl = oracle.tam(g, xy, m, pl, prm, RES, metric=3)
+    assert np.all(Tm >= T * (1 - 1e-14)) and np.any(Tm > T * (1 + 1e-3))
+    assert np.all((Tb >= 0) & (Tb <= 1))
+    assert np.all(Tl <= pl["n_valid"] * math.log(prm.z_hit + prm.z_rand + prm.eps) + 1e-9)
+    assert np.allclose((Tm * 3 - comp[:, 2] - comp[:, 3]), comp[:, 1], rtol=1e-12)   # same components as TAM
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_caer_bounds_smad(seed):
+    """|sum (a - b)| <= sum |a - b| at every m, so the minimum CAER numerator
+    is at least the minimum SMAD numerator (Eq. 19 vs Eq. 21)."""
+    g, hyps, ang, n_orient = room_case(seed)
+    prm = oracle.Params(n_orient=n_orient)
+    z = np.random.default_rng(seed).uniform(0.1, 3.0, len(ang)).astype(np.float32)
+    z[::9] = 0.0
+    pl = oracle.plan(z, ang, 4.0, RES, prm)
+    cn, cm = oracle.caer(g, hyps, pl)
+    sn, sm = oracle.smad(g, hyps, pl)
+    assert np.all(cn >= sn) and np.any(cn > sn)
+    assert np.all(cm % pl["n_enum"] == 0)
+
+
+def test_caer_equals_smad_when_every_real_range_is_longer():
+    """Real ranges all longer than every synthesized range (a 40-cell room,
+    real beams at 3.9 m): every beam difference is positive, the triangle
+    inequality is an equality, and CAER and SMAD agree in value and m."""
+    g, hyps, ang, n_orient = room_case(2)
+    prm = oracle.Params(n_orient=n_orient)
+    pl = oracle.plan(np.full(len(ang), 3.9, np.float32), ang, 4.0, RES, prm)
+    cn, cm = oracle.caer(g, hyps, pl)
+    sn, sm = oracle.smad(g, hyps, pl)
+    assert np.array_equal(cn, sn) and np.array_equal(cm, sm)
+
+
+def test_caer_on_a_map_without_obstacles():
+    """No obstacle: every synthesized range is 0 (no hit), so the numerator is
+    the sum of the real Q16 ranges at every m and the first m is kept."""
+    g = np.zeros((50, 50), np.int8)
+    ang = workloads.beam_angles(90, 120)
+    z = np.random.default_rng(5).uniform(0.1, 2.0, 90).astype(np.float32)
+    z[::11] = np.inf
+    pl = oracle.plan(z, ang, 3.0, RES, oracle.Params(n_orient=40))
+    hyps = np.array([[5, 5], [25, 30], [49, 0]], np.int32)
+    cn, cm = oracle.caer(g, hyps, pl)
+    want = sum(int(np.rint(float(v) * 65536.0 / RES)) for v in z if np.isfinite(v) and 0 < v < 3.0)
+    assert cn.tolist() == [want] * 3 and cm.tolist() == [0] * 3
+
+
+# ------------------------------------------------------------------------------------------
 # invariants of the whole scoring path
 # ------------------------------------------------------------------------------------------
 
