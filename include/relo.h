@@ -73,14 +73,28 @@ typedef struct relo_params {
     int32_t ray_tables;                                /* 1 (default): trace rays tile by tile with per-direction
                                                           tables built once per (N_s, max_range); 0: step cell by
                                                           cell.  Same cells and ranges either way. */
+    int32_t coarse_metric;                             /* ranking metric: RELO_COARSE_SMAD (default, Eq. 16-20) or
+                                                          RELO_COARSE_CAER (Eq. 21, Remark 5: the beam-wise mean
+                                                          absolute range error over the same orientations) */
+    int32_t fine_metric;                               /* scoring metric: RELO_FINE_TAM (default, Eq. 31),
+                                                          RELO_FINE_TAM_MEAN (Eq. 34), RELO_FINE_BASELINE (Eq. 33)
+                                                          or RELO_FINE_LF (Eq. 32, a sum of log-likelihoods, so
+                                                          negative; tau compares against it as it is) */
 } relo_params;
+
+#define RELO_COARSE_SMAD 0
+#define RELO_COARSE_CAER 1
+#define RELO_FINE_TAM 0
+#define RELO_FINE_TAM_MEAN 1
+#define RELO_FINE_BASELINE 2
+#define RELO_FINE_LF 3
 
 /* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */
 typedef struct relo_result {
     double x, y, theta;     /* selected pose: cell centre (metres) and theta_m wrapped to [-pi, pi) */
-    double tam;             /* its TAM score, Eq. 31 */
-    double smad;            /* SMAD of its position, Eq. 20, metres */
-    int64_t smad_num;       /* SMAD numerator |sum R_real - W_m| in Q16 cell units */
+    double tam;             /* its score by the fine metric: TAM (Eq. 31) unless fine_metric says otherwise */
+    double smad;            /* the coarse metric of its position, metres: SMAD (Eq. 20) or CAER (Eq. 21) */
+    int64_t smad_num;       /* its numerator in Q16 cell units: |sum R_real - W_m|, or sum |R_i - R^_{i+m}| */
     int64_t n_smad_evals;   /* hypothesis x orientation SMAD evaluations performed */
     int64_t n_tam_evals;    /* hypothesis x orientation TAM evaluations performed */
     int32_t hyp;            /* index of the selected hypothesis in the context's set */

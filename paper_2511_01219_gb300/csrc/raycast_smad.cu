@@ -301,6 +301,45 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
+// CAER (Eq. 21) of hypothesis h, by one warp: its synthesized row in the
+// warp's shared memory, then for each orientation of the SMAD set the lanes
+// sum |R_i - row[(b_i + m) mod N_s]| over every beam (invalid beams carry R
+// = 0, as in SMAD) and the warp adds the lane sums; the minimum over m (ties
+// to the smaller m) is written like a SMAD numerator, so the ranking that
+// follows is unchanged.  O(beams) per orientation, where SMAD's window sums
+// are O(intervals): the cost Remark 5 describes.
+__device__ __forceinline__ void caer_hypothesis(const ReqDesc &d, int h, uint32_t *srow, int lane) {
+    const int ns = d.ns, n = d.n_beams;
+    const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
+    for (int j = lane; j < ns; j += 32) srow[j] = __ldg(row + j);
+    __syncwarp();
+    const int32_t *__restrict__ b = d.b;
+    const int32_t *__restrict__ Rq = d.Rall;
+    unsigned long long best = ~0ull;
+    for (int q = 0; q < d.n_m; ++q) {
+        const int m = q * d.n_enum;
+        unsigned long long e = 0;
+        for (int i = lane; i < n; i += 32) {
+            int j = __ldg(b + i) + m;
+            if (j >= ns) j -= ns;
+            const int diff = __ldg(Rq + i) - (int)srow[j];   // both in [0, 2^31)
+            e += (unsigned)(diff < 0 ? -diff : diff);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
+        const unsigned long long key = (e << 20) | (unsigned)q;
+        best = key < best ? key : best;
+    }
+    if (lane == 0) {
+        const unsigned long long num = best >> 20;
+        const int q = (int)(best & 0xfffffu);
+        d.keys[h] = (num << kHypBits) | (unsigned long long)h;
+        d.smad_num[h] = (long long)num;
+        d.smad_m[h] = q * d.n_enum;
+    }
+    __syncwarp();   // the row reads are done before the next hypothesis rewrites it
+}
+
 // shared memory of one SMAD warp: in-chunk prefixes [ns_pad + 32] and chunk prefixes [ns_pad / 32 + 1]
 __host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
     return (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7) + (size_t)(ns_pad / 32 + 1) * 8;
@@ -391,6 +430,10 @@ __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, 
         const ReqDesc &d = reqs[lo];
         const int h = g - s_base[lo];
         const int ns = d.ns, ns_pad = d.ns_pad, nch = ns_pad >> 5;
+        if (d.coarse == kCoarseCaer) {
+            caer_hypothesis(d, h, reinterpret_cast<uint32_t *>(mine), lane);
+            continue;
+        }
         uint32_t *inner = reinterpret_cast<uint32_t *>(mine);
         long long *chunkP = reinterpret_cast<long long *>(mine + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
         const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;

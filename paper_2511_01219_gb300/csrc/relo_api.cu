@@ -254,6 +254,10 @@ int ensure(relo_ctx *ctx, T **p, size_t *cap, size_t need, const char *what) {
     return rc;
 }
 
+static_assert(kCoarseCaer == RELO_COARSE_CAER && kFineTamMean == RELO_FINE_TAM_MEAN &&
+                  kFineBaseline == RELO_FINE_BASELINE && kFineLF == RELO_FINE_LF,
+              "metric codes");
+
 int check_params(relo_ctx *ctx, const relo_params &p) {
     if (!(p.z_hit > 0) || !(p.sigma_hit > 0) || !(p.z_rand >= 0) || !(p.eps > 0))
         return fail(ctx, RELO_E_INVALID_ARG, "Eq. 23 needs z_hit > 0, sigma_hit > 0, z_rand >= 0, eps > 0");
@@ -268,6 +272,10 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
     if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
     if (!(p.max_range > 0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
     if (p.scan_cache_bytes < 0) return fail(ctx, RELO_E_INVALID_ARG, "scan_cache_bytes must be >= 0");
+    if (p.coarse_metric < RELO_COARSE_SMAD || p.coarse_metric > RELO_COARSE_CAER)
+        return fail(ctx, RELO_E_INVALID_ARG, "coarse_metric must be RELO_COARSE_SMAD or RELO_COARSE_CAER");
+    if (p.fine_metric < RELO_FINE_TAM || p.fine_metric > RELO_FINE_LF)
+        return fail(ctx, RELO_E_INVALID_ARG, "fine_metric must be one of RELO_FINE_TAM .. RELO_FINE_LF");
     return RELO_OK;
 }
 
@@ -887,7 +895,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         }
     } wnew{ctx, {}, false};
     for (int r = 0; r < R; ++r) {
-        if (!tab[r]) continue;
+        if (!tab[r] || p.coarse_metric != RELO_COARSE_SMAD) continue;   // window sums serve SMAD only
         WinTable *w = find_win(tab[r], *pr[r].P);
         if (w && !wnew.has(w)) {
             wmode[r] = kWinRead;
@@ -909,7 +917,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         const Prepared &q = pr[r];
         const int n = q.P->n, nh = q.m->n_hyp, K = q.K;
         off[r] = total;
-        total += align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
+        total += align_up(sizeof(int2) * n) + align_up(4ull * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
                  align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
                  align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
         if (mode[r] == kScanCast) total += align_up(4ull * nh * q.P->ns);   // the request's synthesized ranges
@@ -983,6 +991,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             return x;
         };
         d.vbR = (int2 *)take(sizeof(int2) * P.n);
+        d.Rall = (int32_t *)take(4ull * P.n);
+        d.coarse = p.coarse_metric;
+        d.fine = p.fine_metric;
         d.scan = (ScanInfo *)take(sizeof(ScanInfo));
         d.keys = (unsigned long long *)take(8ull * m.n_hyp);
         d.smad_num = (long long *)take(8ull * m.n_hyp);
@@ -1391,6 +1402,8 @@ void relo_default_params(relo_params *p) {
     p->hbm_budget = 0;
     p->max_range = 30.0;
     p->ray_tables = 1;
+    p->coarse_metric = RELO_COARSE_SMAD;
+    p->fine_metric = RELO_FINE_TAM;
 }
 
 int relo_create(const relo_params *p, void *stream, relo_ctx **out) {

@@ -3,10 +3,30 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace relo {
 
 constexpr int kTile = 8;               // the occupancy bitmap is stored in 8x8-cell tiles
+// metric codes of relo_params::coarse_metric / fine_metric
+constexpr int kCoarseCaer = 1;
+constexpr int kFineTamMean = 1, kFineBaseline = 2, kFineLF = 3;
+
+// An unsigned code of a float that orders like the float (negative scores
+// too, as the log-likelihood sum of Eq. 32 is): sign bit set for >= 0 floats,
+// every bit flipped for negative ones.  0 lies below every finite score.
+__host__ __device__ inline unsigned int score_code(float f) {
+    unsigned int u;
+    memcpy(&u, &f, 4);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float score_of(unsigned int c) {
+    const unsigned int u = (c & 0x80000000u) ? (c & 0x7fffffffu) : ~c;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 constexpr int kMaxClamp = 8100;        // C = (d_max/res)^2 <= 90^2 so the TAM table fits shared memory
 constexpr int kMaxValidBeams = 2048;   // register-resident TAM selection holds <= 64 values per lane
 constexpr int kMaxNs = 8192;           // panoramic beam count
@@ -133,6 +153,7 @@ struct ReqDesc {
     // map tables
     const uint64_t *bits;
     const uint16_t *field;       // padded clamped field, pointer to cell (0, 0)
+    int coarse, fine;            // ranking and scoring metrics (RELO_COARSE_*, RELO_FINE_*)
     const float2 *lut;           // [C+2] (l(b), sqrt(C) - sqrt(b)); entry C+1 = (0, 0) marks "no beam"
     int W, H, TW, TH, C, Wp, P;
     float res, res2, d_max, d_min;
@@ -158,6 +179,7 @@ struct ReqDesc {
     long long n_smad_evals;
     // buffers
     int2 *vbR;                   // [n_beams]
+    int32_t *Rall;               // [n_beams] every beam's Q16 range in beam order, 0 for an invalid beam (CAER)
     ScanInfo *scan;
     unsigned long long *keys;    // [n_hyp]
     long long *smad_num;         // [n_hyp]

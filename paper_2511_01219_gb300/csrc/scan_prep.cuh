@@ -7,7 +7,7 @@
 // R_i = llrint(z_i * 65536 / res) for valid beams (finite, 0 < z < max_range;
 // invalid beams count 0, Eq. 16 and the placeholder rule after Eq. 20), sums
 // them, compacts the valid beams in order into (panoramic index b_i, R_i)
-// pairs, and fixes the retained-beam count of Eq. 27: the three top-k means of
+// pairs (and keeps every beam's R_i, 0 if invalid, for CAER), and fixes the retained-beam count of Eq. 27: the three top-k means of
 // a descending list satisfy mean(k_low) >= mean(k_mid) >= mean(k_full)
 // whenever k_low <= k_mid <= k_full (a running mean of a descending list never
 // grows), so their median is the mean over the median of the three k values.
@@ -60,6 +60,7 @@ static __device__ __noinline__ void scan_prep_request(const ReqDesc &d) {
             const float z = d.ranges[(size_t)i * d.skip];
             ok = isfinite(z) && z > 0.0f && z < d.max_range;
             if (ok) R = (int)__double2ll_rn(__ddiv_rn(__dmul_rn((double)z, 65536.0), d.resd));
+            d.Rall[i] = R;
         }
         my_sum += R;
         const unsigned bal = __ballot_sync(full, ok);

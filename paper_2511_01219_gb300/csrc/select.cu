@@ -239,7 +239,7 @@ __device__ void finalize_request(const ReqDesc &d) {
         r.status = RELO_OK;
         r.hyp = h;
         r.m = m;
-        r.tam = (double)__uint_as_float(tb);
+        r.tam = (double)score_of(tb);
         r.x = d.ox + ((double)c.x + 0.5) * d.resd;
         r.y = d.oy + ((double)c.y + 0.5) * d.resd;
         double th = (double)m * (2.0 * M_PI) / (double)d.ns;
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
                 if (cand > st->best) st->best = cand;
                 st->n_batches += 1;
                 st->n_tam_evals += (long long)nb * d.n_orient;
-                if (d.early_stop && (double)__uint_as_float(tb) >= d.tau) st->done = 1;
+                if (d.early_stop && (double)score_of(tb) >= d.tau) st->done = 1;
             }
         }
         for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;

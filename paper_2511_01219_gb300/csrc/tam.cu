@@ -21,8 +21,14 @@
 //     T = cbrt(wp * s_d * c).
 // Summing sqrt(C) - sqrt(b) (never negative) instead of sqrt(b) keeps s_d
 // accurate when dbar is close to d_max.  Each score is written out and folded
-// into a per-survivor 64-bit key (T bits, then smaller m) with atomicMax:
-// that is the orientation argmax of Eq. 22.
+// into a per-survivor 64-bit key (the score's order-preserving code, then
+// smaller m) with atomicMax: that is the orientation argmax of Eq. 22.
+//
+// The scoring metric can be switched to those the paper compares TAM with:
+// TAM_mean = (wp + s_d + c) / 3 (Eq. 34) from the same components, and the
+// likelihood-field sum wp_LF = sum of l over every valid beam (Eq. 32) or its
+// normalised form (exp(wp_LF / N) s_d)^(1/2) (Eq. 33), which keep every beam
+// (k = N: no retention and no search).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
     __shared__ int s_base[kMaxBatchRequests + 1];
     __shared__ int s_skip, s_lut_r;
     __shared__ float s_ep[5];   // per-task constants of the epilogue
+    __shared__ int s_fine;      // the task's scoring metric (read where needed, not held in a register)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
     if (threadIdx.x == 0) {
@@ -173,10 +180,12 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         const ReqDesc &d = reqs[r];
         const TamSeg sg = segs[r];
         const int N = d.scan->n_valid;
-        const int k = d.scan->k_ret;
+        // the likelihood-field metrics (Eq. 32-33) keep every beam: no retention, no k-th value to find
+        const int k = d.fine < kFineBaseline ? d.scan->k_ret : N;
         __syncthreads();   // the previous task's reads of offs / lut are done
         if (threadIdx.x == 0) {
             s_skip = d.state->done || N <= 0;
+            s_fine = d.fine;
             s_ep[0] = 1.0f / (float)k;                // 1 / k
             s_ep[1] = d.res / (float)N;               // res / N
             s_ep[2] = d.d_max - d.d_min;              // span of Eq. 29
@@ -272,7 +281,12 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                         const int gt = __reduce_add_sync(kFull, (int)(__half_as_ushort(__low2half(tot)) & 0x3ffu));
                         return 32 * VPL - gt;
                     };
-                    bk = kth_smallest(count_le, k, C, N, hint, cle);
+                    if (s_fine < kFineBaseline) {
+                        bk = kth_smallest(count_le, k, C, N, hint, cle);
+                    } else {
+                        bk = C;   // every valid beam
+                        cle = N;
+                    }
                     const uint32_t bkb = kHalfBias + (uint32_t)bk;
 #pragma unroll
                     for (int t = 0; t < VPL / 2; ++t) {
@@ -300,7 +314,12 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                         for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)x) ? 1 : 0;
                         return __reduce_add_sync(kFull, c);
                     };
-                    bk = kth_smallest(count_le, k, C, N, hint, cle);
+                    if (s_fine < kFineBaseline) {
+                        bk = kth_smallest(count_le, k, C, N, hint, cle);
+                    } else {
+                        bk = C;
+                        cle = N;
+                    }
 #pragma unroll
                     for (int t = 0; t < VPL; ++t) {
                         const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
@@ -317,23 +336,35 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                 sumb = __reduce_add_sync(kFull, sumb);
                 {
                     // Eq. 27-30 from the warp totals every lane holds; the top-k sum of l is every
-                    // b <= bk less the cle - k ties at bk beyond the k-th; lane qi keeps the exponent
-                    // of exp(Lbar) * exp(-var / 2) and s_d
-                    const float lbar = (sl - (float)(cle - k) * lut[bk].x) * s_ep[0];
+                    // b <= bk less the cle - k ties at bk beyond the k-th; lane qi keeps what its
+                    // orientation's score still needs: for TAM the exponent of exp(Lbar) exp(-var / 2)
+                    // and s_d
+                    const float topsum = sl - (float)(cle - k) * lut[bk].x;
+                    const float lbar = topsum * s_ep[0];
                     const float dd = s_ep[1] * sgs;   // d_max - dbar
                     const float dbar = d_max - dd;
                     const float var = fmaxf(s_ep[4] * (float)sumb - dbar * dbar, 0.0f);
+                    const float sd = fminf(dd, s_ep[2]) * s_ep[3];
+                    const int fine = s_fine;
+                    float a = lbar - 0.5f * var;
+                    if (fine == kFineTamMean) a = expf(lbar) + expf(-0.5f * var);   // wp + c (Eq. 34)
+                    else if (fine == kFineBaseline) a = lbar;                       // wp_LF / N (Eq. 33)
+                    else if (fine == kFineLF) a = topsum;                           // wp_LF (Eq. 32)
                     if (lane == qi) {
-                        e_arg = lbar - 0.5f * var;
-                        e_sd = fminf(dd, s_ep[2]) * s_ep[3];
+                        e_arg = a;
+                        e_sd = sd;
                     }
                 }
             }
-            if (lane < nq) {   // Eq. 31, one lane per orientation of the block
+            if (lane < nq) {   // the score of orientation q0 + lane
                 const int q = q0 + lane;
-                const float T = cbrtf(expf(e_arg) * e_sd);
+                const int fine = s_fine;
+                float T = cbrtf(expf(e_arg) * e_sd);                                   // TAM, Eq. 31
+                if (fine == kFineTamMean) T = (e_arg + e_sd) * (1.0f / 3.0f);         // Eq. 34
+                else if (fine == kFineBaseline) T = sqrtf(expf(e_arg) * e_sd);        // Eq. 33
+                else if (fine == kFineLF) T = e_arg;                                  // Eq. 32
                 d.T[(size_t)s * d.n_orient + q] = T;
-                const unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) |
+                const unsigned long long key = ((unsigned long long)score_code(T) << 32) |
                                                (unsigned long long)(0xffffffffu - (unsigned)q);
                 atomicMax(d.best_key + s, key);
             }

@@ -150,19 +150,19 @@ def test_synth_scans_bit_exact(relo, workload, cfg, n_check):
 # ------------------------------------------------------------------------------------------
 
 def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95, n_skip=1, sample_tam=None,
-              d_max=2.0):
+              d_max=2.0, coarse=0, fine=0):
     prm = oracle.Params(n_orient=wl.n_orient, topk=K, batch=batch, local_topk=local_topk, tau=tau,
-                        n_skip_beam=n_skip, d_max=d_max)
+                        n_skip_beam=n_skip, d_max=d_max, coarse=coarse, fine=fine)
     ctx, mid, got = run(relo, wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, n_orient=wl.n_orient,
                         topk=K, batch=batch, local_topk=local_topk, tau=tau, early_stop=int(early_stop),
-                        n_skip_beam=n_skip, d_max=d_max)
+                        n_skip_beam=n_skip, d_max=d_max, coarse_metric=coarse, fine_metric=fine)
     pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
     Kc = min(K, len(wl.hyps))
     B = min(batch, Kc)
     nb = -(-Kc // B)
     st = stages(relo, ctx, len(wl.hyps), Kc, pl["n_orient"], nb, local_topk)
-    # SMAD and ranking: bit-exact
-    num, mm = oracle.smad(wl.grid, wl.hyps, pl)
+    # SMAD (or CAER) and ranking: bit-exact
+    num, mm = oracle.coarse(wl.grid, wl.hyps, pl, prm)
     assert np.array_equal(st["num"], num)
     assert np.array_equal(st["m"], mm)
     surv = oracle.rank(num, Kc)
@@ -224,6 +224,45 @@ def test_selection_counts_either_side_of_fp16_range(relo, workload, d_max):
     def T_at(h, m):
         return float(oracle.tam(wl.grid, np.array([wl.hyps[h]]), np.array([m]), pl, prm, wl.res, d2)[0])
     check_pose(got, want["hyp"], want["m"], T_at)
+    ctx.close()
+
+
+@pytest.mark.parametrize("fine", [1, 2, 3])
+def test_fine_metrics_match_oracle(relo, workload, fine):
+    """TAM_mean (Eq. 34), wp_baseline (Eq. 33) and wp_LF (Eq. 32, negative
+    sums) scored in place of TAM: every score within 1e-5 of the oracle's
+    magnitude, the orientation argmax, and the selected pose."""
+    wl = workload(0)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, fine=fine)
+    want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
+                             early_stop=False)
+
+    def T_at(h, m):
+        return float(oracle.tam(wl.grid, np.array([wl.hyps[h]]), np.array([m]), pl, prm, wl.res, d2)[0])
+    check_pose(got, want["hyp"], want["m"], T_at)
+    if fine == 3:
+        assert got.tam < 0
+    ctx.close()
+
+
+def test_caer_ranking_matches_oracle(relo, workload):
+    """CAER (Eq. 21) in place of SMAD: numerators, minimising m and the
+    survivor list bit-exact; TAM on those survivors within tolerance."""
+    wl = workload(0)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, coarse=1)
+    assert not pl["panoramic"]
+    sn, _ = oracle.smad(wl.grid, wl.hyps, pl)
+    assert np.all(st["num"] >= sn)   # Eq. 21 bounds Eq. 19 at every m
+    ctx.close()
+
+
+def test_caer_panoramic_and_fine_metric_together(relo):
+    """A full-circle scan (Eq. 20: m = 0 only) ranked by CAER and scored by
+    wp_baseline, with early termination."""
+    wl = small_case(n_beams=120, ns=120)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, 12, batch=4, local_topk=2, coarse=1, fine=2,
+                                                             early_stop=True, tau=0.5)
+    assert pl["panoramic"] and (st["m"] == 0).all()
     ctx.close()
 
 

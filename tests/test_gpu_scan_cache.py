@@ -212,6 +212,24 @@ def test_batch_mixing_stored_and_cast_scans(relo, reader_first):
     ctx.close()
 
 
+def test_caer_reads_stored_scans_without_window_tables(relo):
+    """CAER needs the synthesized rows themselves: with resident scans it reads
+    the stored table and builds no window table (those serve SMAD only)."""
+    g, hyps = small_map(seed=10)
+    z, ang = scan_from(g, hyps, 12, 90, 120, 1.9, seed=7)
+    prm = dict(n_orient=40, topk=16, batch=8, local_topk=4, early_stop=0, max_range=5.0, coarse_metric=1)
+    want = fresh_result(relo, g, 0.05, hyps, z, ang, 4.0, **prm)
+    ctx = relo.Relo(scan_cache_bytes=GIB, **prm)
+    mid = ctx.load_map(g, 0.05)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, 0.05))
+    for _ in range(3):
+        assert ctx.relocalize(mid, z, ang, 4.0).as_dict() == want
+    st = ctx.scan_cache_stats()
+    assert st["tables"] == 1 and st["hits"] == 2 and st["misses"] == 1
+    assert st["win_tables"] == 0 and st["win_hits"] == 0
+    ctx.close()
+
+
 def test_served_stream_with_tables_equals_alone(relo):
     """Served form with resident scans: requests on several maps and sensors,
     in waves while others run, each give their alone (uncached) result."""
