@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (default: min(steps, 200))")
-    ap.add_argument("--workload", default="office", choices=["office", "batched", "served"],
+    ap.add_argument("--workload", default="office", choices=["office", "batched", "served", "sweep"],
                     help="office: one request (default); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
     ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,3000,4000,5000,6000,7000,8000,10000,12000",
@@ -433,6 +433,75 @@ def run_reference(args, world, rank):
     }
 
 
+def run_sweep(args, world, rank, local, dist):
+    """Translation-affinity sweep in the manner of Fig. 8, on the office map:
+    15 positions 0.1 m apart through the scan's true position (along the axis
+    whose cells are all free) x 36 orientations 10 degrees apart from the true
+    one = 540 poses, scored by each scoring metric (TAM, TAM_mean, wp_baseline,
+    wp_LF).  For every position it reports whether the true orientation still
+    scores best among the 36, and the time of one sweep."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    import workloads
+
+    torch.cuda.set_device(local)
+    wl = workloads.config(CONFIG_INDEX)
+    gx, gy, gth = wl.gt_pose
+    cx, cy = int(round(gx / wl.res - 0.5)), int(round(gy / wl.res - 0.5))
+    step = int(round(0.1 / wl.res))
+    offs = np.arange(-7, 8) * step
+    free = wl.grid < 65
+    axis = None
+    for ax, (dx, dy) in enumerate(((1, 0), (0, 1))):
+        cells = np.stack([cx + dx * offs, cy + dy * offs], 1)
+        inside = (cells[:, 0] >= 0) & (cells[:, 0] < wl.grid.shape[1]) & (cells[:, 1] >= 0) & (cells[:, 1] < wl.grid.shape[0])
+        if inside.all() and free[cells[:, 1], cells[:, 0]].all():
+            axis = "xy"[ax]
+            break
+    if axis is None:
+        raise RuntimeError("no axis through the true position with 15 free cells")
+    n_s = wl.n_s
+    m_true = int(round(gth / (2 * math.pi) * n_s)) % n_s
+    q_true = m_true // (n_s // 360)
+    sweep_q = [(q_true + 10 * j) % 360 for j in range(36)]   # 10-degree steps from the true orientation
+    metrics = ["tam", "tam_mean", "baseline", "lf"]
+    out = {}
+    for fine, name in enumerate(metrics):
+        ctx = relo.Relo(n_orient=360, topk=len(cells), batch=len(cells), local_topk=1, early_stop=0, fine_metric=fine)
+        mid = ctx.load_map(wl.grid, wl.res)
+        ctx.set_hypotheses(mid, workloads.cell_centres(cells.astype(np.int32), wl.res))
+        for _ in range(3):
+            ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 20
+        for _ in range(reps):
+            ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        surv = ctx.stage(relo.STAGE_SURVIVORS, torch.empty(len(cells), dtype=torch.int32, device="cuda")).cpu().numpy()
+        T = ctx.stage(relo.STAGE_TAM, torch.empty(len(cells) * 360, dtype=torch.float32, device="cuda"))
+        T = T.cpu().numpy().reshape(len(cells), 360)
+        rows = np.empty_like(T)
+        rows[surv] = T                     # back to position order
+        sw = rows[:, sweep_q]              # 15 positions x 36 orientations
+        wins = [bool(np.argmax(sw[i]) == 0) for i in range(len(cells))]
+        best = np.unravel_index(np.argmax(sw), sw.shape)
+        out[name] = {"true_orientation_best_at_offsets_m": [round(float(o) * wl.res, 2) for o, w in zip(offs, wins) if w],
+                     "fraction": round(sum(wins) / len(wins), 3),
+                     "global_best": {"offset_m": round(float(offs[best[0]]) * wl.res, 2), "orientation_deg": 10 * int(best[1])},
+                     "ms_per_sweep": round(ms, 3)}
+        ctx.close()
+    return {"metric": "translation affinity (true orientation best among 36 at each of 15 offsets)", "value": None,
+            "unit": None, "n_gpus": world, "data": "synthetic office map and noisy scan (config 1)",
+            "config": {"workload": f"sweep: 15 positions 0.1 m apart along {axis} x 36 orientations 10 deg apart = 540 poses",
+                       "true_pose": [round(float(gx), 3), round(float(gy), 3), round(float(gth), 4)]},
+            "metrics": out}
+
+
 def run_batched(args, world, rank, local, dist):
     """64 independent relocalizations per step (mixed map sizes, beam counts,
     FoVs and hypothesis counts), one launch per stage, all inputs resident."""
@@ -681,7 +750,7 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "ours" and args.workload != "office":
         dist = dist_init(world)
-        fn = run_batched if args.workload == "batched" else run_served
+        fn = {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.workload]
         line = fn(args, world, rank, local, dist)
         if rank == 0:
             print(json.dumps(line))
