@@ -17,6 +17,8 @@ Paper references (arXiv 2511.01219):
   * Eq. 22-31: TAM and orientation selection        -> tam(), best_orientation()
   * Eq. 21 (Remark 5): CAER in place of SMAD         -> caer()
   * Eq. 32-34: wp_LF, wp_baseline, TAM_mean          -> tam(metric=3, 2, 1)
+  * Sec. III overview, Remark 2: ICP refinement of
+    the local top-k and re-evaluation               -> icp(), tam_pose(), relocalize(icp_iters=)
   * Sec. III intro, Remarks 2-3, Sec. IV-C params:
     SMAD ordering, batches, local top-k, tau        -> relocalize()
 
@@ -75,6 +77,10 @@ def _L():
             "oracle_synth_scan": (None, [P, I, I, I, I, I, P, I64, P, P, P]),
             "oracle_smad": (None, [P, I, I, P, I, I, P, I64, P, P, I, I64, I, I, P, P, I]),
             "oracle_caer": (None, [P, I, I, P, I, I, P, I64, P, P, I, I, I, P, P, I]),
+            "oracle_nearest_occupied": (I, [P, P, I, I, I, I, I64, P, P]),
+            "oracle_rigid_fit": (I, [P, P, I, P, P, P]),
+            "oracle_icp": (I, [P, P, I, I, D, I64, P, P, I, I, P]),
+            "oracle_tam_pose": (None, [P, P, I, I, P, I, P, P, I, P, P, I]),
             "oracle_tam": (None, [P, P, I, I, P, P, I, I, P, P, P, P, I, P, P, P, I]),
             "oracle_max_threads": (I, []),
         }
@@ -310,6 +316,80 @@ def tam_grid(grid, hyps: np.ndarray, sel: np.ndarray, pl: dict, prm: Params, res
     return T.reshape(len(sel), len(m_list))
 
 
+# ----------------------------------------------------------------------------------------------
+# ICP refinement and re-evaluation at continuous poses
+# ----------------------------------------------------------------------------------------------
+
+def scan_points(pl: dict, res: float):
+    """The valid beams as sensor-frame ranges (metres) and angles: z_i =
+    R_i res / 65536 (the Q16 range) and a_i = 2 pi b_i / N_s (its panoramic
+    grid angle), so a continuous pose (cell centre, theta_m) reproduces the
+    endpoints of the integer rule up to rounding."""
+    v = pl["valid"].astype(bool)
+    z = np.ascontiguousarray(pl["R"][v].astype(np.float64) * res / 65536.0)
+    a = np.ascontiguousarray(pl["b"][v].astype(np.float64) * (2.0 * math.pi / pl["ns"]))
+    return z, a
+
+
+def _clamp(prm: Params, res: float) -> int:
+    return int(round(prm.d_max / res)) ** 2
+
+
+def nearest_occupied(grid, x: int, y: int, cap: int, d2tab=None):
+    """The nearest occupied cell to cell (x, y) within squared cell distance
+    cap (ties: smaller dy, then smaller dx), or None."""
+    g = np.ascontiguousarray(grid, dtype=np.int8)
+    H, W = g.shape
+    d2c = None if d2tab is None else np.ascontiguousarray(d2tab, dtype=np.int64)
+    ox, oy = ctypes.c_int(0), ctypes.c_int(0)
+    ok = _L().oracle_nearest_occupied(_p(g), None if d2c is None else _p(d2c), W, H, x, y, cap, ctypes.byref(ox),
+                                      ctypes.byref(oy))
+    return (int(ox.value), int(oy.value)) if ok else None
+
+
+def rigid_fit(w: np.ndarray, c: np.ndarray):
+    """(phi, tx, ty) minimising sum |R(phi) w_i + t - c_i|^2, or None for fewer than 2 pairs."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    phi, tx, ty = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    ok = _L().oracle_rigid_fit(_p(w), _p(c), len(w), ctypes.byref(phi), ctypes.byref(tx), ctypes.byref(ty))
+    return (phi.value, tx.value, ty.value) if ok else None
+
+
+def icp_points(grid, pose, z, a, res: float, C: int, iters: int, d2tab=None):
+    """ICP of the beams (z, a) from pose (x, y, theta): (refined pose, iterations)."""
+    g = np.ascontiguousarray(grid, dtype=np.int8)
+    H, W = g.shape
+    d2c = None if d2tab is None else np.ascontiguousarray(d2tab, dtype=np.int64)
+    ps = np.array(pose, np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    it = _L().oracle_icp(_p(g), None if d2c is None else _p(d2c), W, H, res, C, _p(z), _p(a), len(z), iters, _p(ps))
+    return ps, int(it)
+
+
+def icp(grid, pose, pl: dict, prm: Params, res: float, iters: int, d2tab=None):
+    """ICP of the scan's valid beams from pose, pairs kept within d_max."""
+    z, a = scan_points(pl, res)
+    return icp_points(grid, pose, z, a, res, _clamp(prm, res), iters, d2tab)
+
+
+def tam_pose(grid, poses, pl: dict, prm: Params, res: float, d2tab=None, metric: int | None = None,
+             n_threads: int = 0) -> np.ndarray:
+    """The score (prm.fine unless metric is given) at continuous poses [n, 3] for the scan's valid beams."""
+    g = np.ascontiguousarray(grid, dtype=np.int8)
+    H, W = g.shape
+    ps = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 3))
+    z, a = scan_points(pl, res)
+    params = np.array([prm.z_hit, prm.sigma_hit, prm.z_rand, prm.eps, res, prm.d_max, pl["a_mid"], pl["a_low"],
+                       float(prm.fine if metric is None else metric)], np.float64)
+    d2c = None if d2tab is None else np.ascontiguousarray(d2tab, dtype=np.int64)
+    out = np.zeros(len(ps), np.float64)
+    _L().oracle_tam_pose(_p(g), None if d2c is None else _p(d2c), W, H, _p(ps), len(ps), _p(z), _p(a), len(z),
+                         _p(params), _p(out), n_threads or max_threads())
+    return out
+
+
 def best_orientation(T_row) -> int:
     """Eq. 22: argmax over Theta, ties to the smaller m (returns the position in Theta)."""
     best = 0
@@ -324,11 +404,15 @@ def best_orientation(T_row) -> int:
 # ----------------------------------------------------------------------------------------------
 
 def relocalize(grid, res: float, hyps: np.ndarray, ranges, angles, max_range: float, prm: Params,
-               d2tab: np.ndarray | None = None, n_threads: int = 0, early_stop: bool = True) -> dict:
+               d2tab: np.ndarray | None = None, n_threads: int = 0, early_stop: bool = True,
+               icp_iters: int = 0) -> dict:
     """SMAD ranking (CAER with prm.coarse = 1), then batched TAM orientation
     selection (the metric prm.fine picks) with local top-k and early
-    termination (Sec. III intro; ICP is not part of this path, so the
-    re-evaluated score of a local top-k pose is its first TAM score).
+    termination (Sec. III intro).  With icp_iters > 0 each local top-k pose
+    is refined by icp_iters ICP iterations and scored again at its continuous
+    pose (tam_pose); a batch's best is then the best re-evaluated score, and
+    the result is that refined pose.  With icp_iters = 0 the re-evaluated
+    score of a local top-k pose is its first TAM score.
 
     With early_stop False every survivor is scored (the "TAM on the top K"
     form); otherwise batches stop after the first whose best score >= tau.
@@ -358,16 +442,23 @@ def relocalize(grid, res: float, hyps: np.ndarray, ranges, angles, max_range: fl
         scored.sort(key=lambda t: (-t[0], t[1]))
         local = scored[: prm.local_topk]
         batches.append(local)
-        if best is None or local[0][0] > best[0]:
-            best = local[0]
-        if early_stop and local[0][0] >= prm.tau:
+        reev = []
+        for (t0, pos, h, m) in local:   # re-evaluation of the local top-k, in local order
+            pose = ((hyps[h][0] + 0.5) * res, (hyps[h][1] + 0.5) * res, m * 2.0 * math.pi / pl["ns"])
+            if icp_iters > 0:
+                pose, _ = icp(grid, pose, pl, prm, res, icp_iters, d2tab)
+                t0 = float(tam_pose(grid, [pose], pl, prm, res, d2tab)[0])
+            reev.append((t0, pos, h, m, tuple(float(v) for v in pose)))
+        top = max(reev, key=lambda t: (t[0], -t[1]))
+        if best is None or top[0] > best[0]:
+            best = top
+        if early_stop and top[0] >= prm.tau:
             break
-    T_best, rank_pos, h, m = best
-    hx, hy = (int(v) for v in hyps[h])
-    theta = m * 2.0 * math.pi / pl["ns"]
+    T_best, rank_pos, h, m, pose = best
+    theta = math.remainder(pose[2], 2.0 * math.pi)
     if theta >= math.pi:
         theta -= 2.0 * math.pi
-    return dict(hyp=h, m=m, tam=T_best, x=(hx + 0.5) * res, y=(hy + 0.5) * res, theta=theta,
+    return dict(hyp=h, m=m, tam=T_best, x=pose[0], y=pose[1], theta=theta,
                 smad_num=int(num[h]), smad=float(smad_metres(num[h], pl)), survivors=surv, smad_nums=num,
                 smad_m=m_smad, per_hyp=per_hyp, batches=batches, n_batches=len(batches),
                 n_smad_evals=len(hyps) * (1 if pl["panoramic"] else pl["n_orient"]), n_tam_evals=n_tam,

@@ -4,10 +4,11 @@
  * Plain, slow, FP64/int64 C that restates, step by step, what the paper's
  * scoring path computes: the EDT lookup table (Sec. III-A item 3), the
  * panoramic map-synthesized scan (Eq. 13), SMAD (Eq. 16-20), and TAM
- * (Eq. 23-31); and the metrics the paper sets against them: CAER (Eq. 21,
+ * (Eq. 23-31); the metrics the paper sets against them: CAER (Eq. 21,
  * Remark 5) in place of SMAD, and the likelihood-field sum (Eq. 32), its
  * normalised form (Eq. 33) and the arithmetic-mean fusion (Eq. 34) in place
- * of TAM.  Only tests, the smoke check and the benchmark's CPU-baseline
+ * of TAM; and the ICP refinement of the local top-k poses with their
+ * re-evaluation at continuous poses (Sec. III overview, Remark 2).  Only tests, the smoke check and the benchmark's CPU-baseline
  * leg may load this library; the GPU library never does.  It shares no code,
  * header or table with the GPU library.
  *
@@ -384,41 +385,11 @@ static int cmp_desc(const void *a, const void *b) {
 }
 
 /*
- * One TAM score.  For each valid beam i at orientation m the endpoint cell is
- * the hypothesis cell plus round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46);
- * its obstacle distance is d_i = res * sqrt(min(d2, C)), C = (d_max/res)^2,
- * and an endpoint off the map takes d_max.  Then (Eq. 23) l_i, (Eq. 24) the
- * descending sort, (Eq. 26) k_full = N, k_mid = max(1, floor(a_mid N)),
- * k_low = max(1, floor(a_low N)), (Eq. 27) the median of the three top-k
- * means, (Eq. 28) exp of it, (Eq. 29) s_d with d_min = res / 2, (Eq. 30) c from
- * the population variance of the d_i, and (Eq. 31) the cube root of the
- * product.  comp[0..4] (optional) receives L_bar, wp, s_d, c, mean d.
- * With p->metric the score is instead the arithmetic mean (wp + s_d + c) / 3
- * of the same components (Eq. 34), the likelihood-field sum
- * wp_LF = sum of l_i over all N beams (Eq. 32), or its normalised form
- * (exp(wp_LF / N) s_d)^(1/2) (Eq. 33: no retention, no c).
+ * The score of Eq. 23-31 (or of the metric p->metric selects, see tam_one)
+ * from the N beam-endpoint obstacle distances dist[0 .. N) (metres); ell is
+ * scratch of N doubles.  NaN when N = 0.
  */
-static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, int hx, int hy, int m, int ns,
-                      const int64_t *D, const int32_t *b, const int64_t *R, const uint8_t *valid, int n,
-                      const tam_params *p, double *dist, double *ell, double *comp) {
-    int64_t C = llround(p->d_max / p->res);
-    C = C * C;
-    int N = 0;
-    for (int i = 0; i < n; ++i) {
-        if (!valid[i]) continue;
-        int j = (b[i] + m) % ns;
-        int64_t ox = floor_div_pow2(R[i] * D[2 * j] + ((int64_t)1 << 45), 46);
-        int64_t oy = floor_div_pow2(R[i] * D[2 * j + 1] + ((int64_t)1 << 45), 46);
-        int64_t ex = hx + ox, ey = hy + oy;
-        int64_t q;
-        if (ex < 0 || ey < 0 || ex >= W || ey >= H) q = C;
-        else if (d2tab) {
-            q = d2tab[(size_t)ey * W + ex];
-            if (q < 0 || q > C) q = C;
-        } else q = oracle_d2_capped(grid, W, H, (int)ex, (int)ey, C);
-        dist[N] = p->res * sqrt((double)q);
-        ++N;
-    }
+static double score_of_distances(const double *dist, double *ell, int N, const tam_params *p, double *comp) {
     if (N == 0) return NAN;
     for (int i = 0; i < N; ++i) {
         double d = dist[i];
@@ -466,6 +437,45 @@ static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, in
 }
 
 /*
+ * One TAM score.  For each valid beam i at orientation m the endpoint cell is
+ * the hypothesis cell plus round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46);
+ * its obstacle distance is d_i = res * sqrt(min(d2, C)), C = (d_max/res)^2,
+ * and an endpoint off the map takes d_max.  Then (Eq. 23) l_i, (Eq. 24) the
+ * descending sort, (Eq. 26) k_full = N, k_mid = max(1, floor(a_mid N)),
+ * k_low = max(1, floor(a_low N)), (Eq. 27) the median of the three top-k
+ * means, (Eq. 28) exp of it, (Eq. 29) s_d with d_min = res / 2, (Eq. 30) c from
+ * the population variance of the d_i, and (Eq. 31) the cube root of the
+ * product.  comp[0..4] (optional) receives L_bar, wp, s_d, c, mean d.
+ * With p->metric the score is instead the arithmetic mean (wp + s_d + c) / 3
+ * of the same components (Eq. 34), the likelihood-field sum
+ * wp_LF = sum of l_i over all N beams (Eq. 32), or its normalised form
+ * (exp(wp_LF / N) s_d)^(1/2) (Eq. 33: no retention, no c).
+ */
+static double tam_one(const int8_t *grid, const int64_t *d2tab, int W, int H, int hx, int hy, int m, int ns,
+                      const int64_t *D, const int32_t *b, const int64_t *R, const uint8_t *valid, int n,
+                      const tam_params *p, double *dist, double *ell, double *comp) {
+    int64_t C = llround(p->d_max / p->res);
+    C = C * C;
+    int N = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!valid[i]) continue;
+        int j = (b[i] + m) % ns;
+        int64_t ox = floor_div_pow2(R[i] * D[2 * j] + ((int64_t)1 << 45), 46);
+        int64_t oy = floor_div_pow2(R[i] * D[2 * j + 1] + ((int64_t)1 << 45), 46);
+        int64_t ex = hx + ox, ey = hy + oy;
+        int64_t q;
+        if (ex < 0 || ey < 0 || ex >= W || ey >= H) q = C;
+        else if (d2tab) {
+            q = d2tab[(size_t)ey * W + ex];
+            if (q < 0 || q > C) q = C;
+        } else q = oracle_d2_capped(grid, W, H, (int)ex, (int)ey, C);
+        dist[N] = p->res * sqrt((double)q);
+        ++N;
+    }
+    return score_of_distances(dist, ell, N, p, comp);
+}
+
+/*
  * TAM scores for n_pairs (hypothesis cell, m) pairs.  d2tab (row-major, from
  * oracle_edt_full) may be NULL, in which case distances come from
  * oracle_d2_capped.  params: z_hit, sigma_hit, z_rand, eps, res, d_max, a_mid,
@@ -487,6 +497,145 @@ void oracle_tam(const int8_t *grid, const int64_t *d2tab, int W, int H, const in
         double *ell = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
         T_out[q] = tam_one(grid, d2tab, W, H, pair_xy[2 * q], pair_xy[2 * q + 1], pair_m[q], ns, D, b, R,
                            valid, n, &p, dist, ell, comp ? &comp[5 * q] : NULL);
+        free(dist);
+        free(ell);
+    }
+}
+
+/* ================================================================================
+ * ICP refinement and re-evaluation at continuous poses: the framework's last
+ * step (Sec. III overview: the local top-k poses are aligned to the whole map
+ * by ICP, then scored again; Remark 2 names the operator).  The paper does not
+ * specify the ICP variant; this is point-to-point ICP against the centres of
+ * occupied cells, pairs found through the exact EDT and kept within d_max.
+ * ============================================================================== */
+
+/*
+ * The nearest occupied cell to cell (x, y) when its squared distance d2 (the
+ * exact EDT value there) is at most cap: the cells (x + dx, y + dy) with
+ * dx^2 + dy^2 = d2 are tried in order of increasing dy, then increasing dx,
+ * and the first occupied one on the map is returned (1, with *ox, *oy); 0 when
+ * (x, y) is off the map, no cell is occupied, or d2 > cap.
+ */
+int oracle_nearest_occupied(const int8_t *grid, const int64_t *d2tab, int W, int H, int x, int y, int64_t cap,
+                            int *ox, int *oy) {
+    if (x < 0 || y < 0 || x >= W || y >= H) return 0;
+    int64_t d2 = d2tab ? d2tab[(size_t)y * W + x] : oracle_d2_capped(grid, W, H, x, y, cap + 1);
+    if (d2 < 0 || d2 > cap) return 0;
+    int64_t r = isqrt64(d2);
+    for (int64_t dy = -r; dy <= r; ++dy) {
+        int64_t rest = d2 - dy * dy;
+        int64_t s = isqrt64(rest);
+        if (s * s != rest) continue;
+        for (int sign = -1; sign <= 1; sign += 2) {
+            int64_t dx = sign * s;
+            if (sign > 0 && s == 0) break;   /* dx = 0 was tried as -0 */
+            int64_t cx = x + dx, cy = y + dy;
+            if (cx < 0 || cy < 0 || cx >= W || cy >= H) continue;
+            if (is_occupied(grid[(size_t)cy * W + cx])) { *ox = (int)cx; *oy = (int)cy; return 1; }
+        }
+    }
+    return 0;
+}
+
+/*
+ * The rigid motion (rotation phi, translation t) that minimises
+ * sum_i |R(phi) w_i + t - c_i|^2 over n point pairs (w, c interleaved x, y):
+ * with the centroids mw, mc and the centred points w', c',
+ * phi = atan2(sum (w'_x c'_y - w'_y c'_x), sum (w'_x c'_x + w'_y c'_y)) and
+ * t = mc - R(phi) mw.  Returns 0 when n < 2.
+ */
+int oracle_rigid_fit(const double *w, const double *c, int n, double *phi, double *tx, double *ty) {
+    if (n < 2) return 0;
+    double mwx = 0, mwy = 0, mcx = 0, mcy = 0;
+    for (int i = 0; i < n; ++i) { mwx += w[2 * i]; mwy += w[2 * i + 1]; mcx += c[2 * i]; mcy += c[2 * i + 1]; }
+    mwx /= n; mwy /= n; mcx /= n; mcy /= n;
+    double sxy = 0, sdot = 0;
+    for (int i = 0; i < n; ++i) {
+        double ax = w[2 * i] - mwx, ay = w[2 * i + 1] - mwy, bx = c[2 * i] - mcx, by = c[2 * i + 1] - mcy;
+        sxy += ax * by - ay * bx;
+        sdot += ax * bx + ay * by;
+    }
+    double f = atan2(sxy, sdot);
+    *phi = f;
+    *tx = mcx - (cos(f) * mwx - sin(f) * mwy);
+    *ty = mcy - (sin(f) * mwx + cos(f) * mwy);
+    return 1;
+}
+
+/*
+ * ICP from pose = (x, y, theta) (metres, radians; refined in place) for n
+ * beams with sensor-frame ranges z (metres) and angles a.  Each iteration maps
+ * beam i to the world point (x + z_i cos(theta + a_i), y + z_i sin(theta +
+ * a_i)), pairs it with the centre of the nearest occupied cell to the cell it
+ * falls in (kept when that squared cell distance is at most C, i.e. within
+ * d_max), fits the rigid motion of the pairs and composes it with the pose.
+ * It stops after iters iterations, when fewer than 2 pairs remain, or when the
+ * motion is below 1e-9 rad and 1e-9 m.  Returns the iterations applied.
+ */
+int oracle_icp(const int8_t *grid, const int64_t *d2tab, int W, int H, double res, int64_t C, const double *z,
+               const double *a, int n, int iters, double *pose) {
+    double *w = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
+    double *c = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
+    int it = 0;
+    for (; it < iters; ++it) {
+        int k = 0;
+        for (int i = 0; i < n; ++i) {
+            double wx = pose[0] + z[i] * cos(pose[2] + a[i]);
+            double wy = pose[1] + z[i] * sin(pose[2] + a[i]);
+            int ox, oy;
+            if (!oracle_nearest_occupied(grid, d2tab, W, H, (int)floor(wx / res), (int)floor(wy / res), C, &ox, &oy))
+                continue;
+            w[2 * k] = wx; w[2 * k + 1] = wy;
+            c[2 * k] = (ox + 0.5) * res; c[2 * k + 1] = (oy + 0.5) * res;
+            ++k;
+        }
+        double f, tx, ty;
+        if (!oracle_rigid_fit(w, c, k, &f, &tx, &ty)) break;
+        double nx = cos(f) * pose[0] - sin(f) * pose[1] + tx;
+        double ny = sin(f) * pose[0] + cos(f) * pose[1] + ty;
+        double moved = fabs(nx - pose[0]) + fabs(ny - pose[1]);
+        pose[0] = nx; pose[1] = ny; pose[2] += f;
+        if (fabs(f) < 1e-9 && moved < 1e-9) { ++it; break; }
+    }
+    free(w);
+    free(c);
+    return it;
+}
+
+/*
+ * The score (TAM or the metric params[8] selects) at continuous poses
+ * (x, y, theta interleaved) for n beams with sensor-frame ranges z (metres)
+ * and angles a: beam i ends in the cell (floor(wx / res), floor(wy / res)) of
+ * its world point; its distance is res * sqrt(min(d2, C)), d_max off the map,
+ * as in tam_one.  params as oracle_tam.
+ */
+void oracle_tam_pose(const int8_t *grid, const int64_t *d2tab, int W, int H, const double *poses, int n_poses,
+                     const double *z, const double *a, int n, const double *params, double *T_out, int n_threads) {
+    tam_params p = {params[0], params[1], params[2], params[3], params[4], params[5], params[6], params[7],
+                    (int)params[8]};
+    int64_t C = llround(p.d_max / p.res);
+    C = C * C;
+    (void)n_threads;
+#ifdef _OPENMP
+    #pragma omp parallel for num_threads(n_threads > 0 ? n_threads : 1) schedule(dynamic, 8)
+#endif
+    for (int q = 0; q < n_poses; ++q) {
+        double *dist = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+        double *ell = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+        const double *ps = poses + 3 * q;
+        for (int i = 0; i < n; ++i) {
+            int64_t ex = (int64_t)floor((ps[0] + z[i] * cos(ps[2] + a[i])) / p.res);
+            int64_t ey = (int64_t)floor((ps[1] + z[i] * sin(ps[2] + a[i])) / p.res);
+            int64_t d2;
+            if (ex < 0 || ey < 0 || ex >= W || ey >= H) d2 = C;
+            else if (d2tab) {
+                d2 = d2tab[(size_t)ey * W + ex];
+                if (d2 < 0 || d2 > C) d2 = C;
+            } else d2 = oracle_d2_capped(grid, W, H, (int)ex, (int)ey, C);
+            dist[i] = p.res * sqrt((double)d2);
+        }
+        T_out[q] = score_of_distances(dist, ell, n, &p, NULL);
         free(dist);
         free(ell);
     }

@@ -525,6 +525,123 @@ def test_caer_on_a_map_without_obstacles():
 
 
 # ------------------------------------------------------------------------------------------
+# ICP refinement and re-evaluation at continuous poses (Sec. III overview, Remark 2)
+# ------------------------------------------------------------------------------------------
+
+def test_rigid_fit_recovers_a_rigid_motion():
+    """Pairs related exactly by a rotation and a translation give them back."""
+    rng = np.random.default_rng(0)
+    for phi, t in ((0.3, (1.5, -0.7)), (-2.9, (0.0, 4.0)), (1e-7, (1e-7, 0.0))):
+        w = rng.uniform(-5, 5, (12, 2))
+        R = np.array([[math.cos(phi), -math.sin(phi)], [math.sin(phi), math.cos(phi)]])
+        c = w @ R.T + np.array(t)
+        f, tx, ty = oracle.rigid_fit(w, c)
+        assert math.isclose(f, phi, abs_tol=1e-12) and np.allclose((tx, ty), t, atol=1e-12)
+    assert oracle.rigid_fit(np.zeros((1, 2)), np.zeros((1, 2))) is None
+
+
+def test_nearest_occupied_ties_and_range():
+    """Four occupied cells at squared distance 25 from (20, 20) ((+-3, +-4)
+    and (0, 5)): the first in (dy, dx) order is (17, 16); beyond cap: none."""
+    g = np.zeros((41, 41), np.int8)
+    for dx, dy in ((3, 4), (-3, 4), (0, 5), (3, -4)):
+        g[20 + dy, 20 + dx] = 100
+    d2 = oracle.edt(g)
+    assert d2[20, 20] == 25
+    assert oracle.nearest_occupied(g, 20, 20, 25, d2) == (23, 16)   # dy = -4 first, then dx = +3
+    assert oracle.nearest_occupied(g, 20, 20, 24, d2) is None
+    assert oracle.nearest_occupied(g, 20, 20, 25) == (23, 16)       # without the table: the capped search
+
+
+def pillar_scene():
+    """Occupied single cells far apart (>= 6 cells), and beams aimed exactly
+    at their centres from a true pose."""
+    g = np.zeros((120, 120), np.int8)
+    pillars = [(20, 30), (90, 25), (100, 80), (35, 95), (60, 60), (15, 70), (75, 105), (105, 45)]
+    for x, y in pillars:
+        g[y, x] = 100
+    true = (55.3 * RES, 48.7 * RES, 0.4)
+    z, a = [], []
+    for x, y in pillars:
+        cx, cy = (x + 0.5) * RES, (y + 0.5) * RES
+        z.append(math.hypot(cx - true[0], cy - true[1]))
+        a.append(math.atan2(cy - true[1], cx - true[0]) - true[2])
+    return g, true, np.array(z), np.array(a)
+
+
+def test_icp_one_step_on_exact_pairs():
+    """From a pose off by 0.6 cm, -0.7 cm and 0.1 degree every beam still falls
+    next to its own pillar, the pairs are exact, and one fit lands on the
+    true pose; the next iteration moves nothing."""
+    g, true, z, a = pillar_scene()
+    C = int(round(2.0 / RES)) ** 2
+    start = (true[0] + 0.006, true[1] - 0.007, true[2] + math.radians(0.1))
+    pose, it = oracle.icp_points(g, start, z, a, RES, C, 1)
+    assert it == 1 and np.allclose(pose, true, atol=1e-10)
+    pose2, it2 = oracle.icp_points(g, start, z, a, RES, C, 10)
+    assert it2 == 2 and np.allclose(pose2, true, atol=1e-10)
+
+
+def test_icp_drops_pairs_beyond_d_max():
+    """Beams that end in open space with no occupied cell within d_max (here 4
+    cells, C = 16) take no part: the result is the same with or without them."""
+    g, true, z, a = pillar_scene()
+    C = 16
+    start = (true[0] + 0.006, true[1] - 0.007, true[2] + math.radians(0.1))
+    za = np.concatenate([z, [0.3, 0.45]])               # endpoints 6 and 9 cells from the pose, far from every pillar
+    aa = np.concatenate([a, [2.0, -2.5]])
+    for i in (len(z), len(z) + 1):
+        wx = start[0] + za[i] * math.cos(start[2] + aa[i])
+        wy = start[1] + za[i] * math.sin(start[2] + aa[i])
+        assert oracle.nearest_occupied(g, int(wx // RES), int(wy // RES), C) is None
+        assert oracle.nearest_occupied(g, int(wx // RES), int(wy // RES), 40 ** 2) is not None
+    p1, _ = oracle.icp_points(g, start, z, a, RES, C, 5)
+    p2, _ = oracle.icp_points(g, start, za, aa, RES, C, 5)
+    assert np.array_equal(p1, p2)
+
+
+def test_tam_at_continuous_pose_equals_integer_rule_away_from_cell_edges():
+    """At a hypothesis cell centre and orientation theta_m the continuous
+    endpoint floor((x_c + z cos) / res) equals the integer rule cell +
+    round-half-up(R D / 2^46) unless the endpoint lies within 1e-6 cells of a
+    cell edge; wherever no beam does, the two scores are equal."""
+    g, hyps, ang, n_orient = room_case(1)
+    prm = oracle.Params(n_orient=n_orient)
+    z = np.random.default_rng(1).uniform(0.1, 1.5, len(ang)).astype(np.float32)
+    pl = oracle.plan(z, ang, 4.0, RES, prm)
+    zz, aa = oracle.scan_points(pl, RES)
+    d2 = oracle.edt(g)
+    checked = 0
+    for h in hyps[:10]:
+        for m in range(0, pl["ns"], 7 * pl["n_enum"]):
+            pose = ((h[0] + 0.5) * RES, (h[1] + 0.5) * RES, m * 2 * math.pi / pl["ns"])
+            ex = (pose[0] + zz * np.cos(pose[2] + aa)) / RES
+            ey = (pose[1] + zz * np.sin(pose[2] + aa)) / RES
+            margin = min(np.abs(ex - np.round(ex)).min(), np.abs(ey - np.round(ey)).min())
+            if margin < 1e-6:
+                continue
+            t_int = oracle.tam(g, np.array([h]), np.array([m]), pl, prm, RES, d2)[0]
+            t_pose = oracle.tam_pose(g, [pose], pl, prm, RES, d2)[0]
+            assert t_int == t_pose
+            checked += 1
+    assert checked >= 20
+
+
+def test_relocalize_with_icp_refines_a_noise_free_pose():
+    """A scan rendered from a pose between cells: with ICP the selected pose
+    moves towards the true one and scores at least as well as without."""
+    g, hyps, ang, n_orient = room_case(2)
+    prm = oracle.Params(n_orient=n_orient, topk=10, batch=10, local_topk=3)
+    true = ((hyps[5][0] + 0.8) * RES, (hyps[5][1] + 0.3) * RES, 0.5)
+    z = workloads.render_scan(g, RES, true, ang, 6.0)
+    plain = oracle.relocalize(g, RES, hyps, z, ang, 6.0, prm, early_stop=False)
+    refined = oracle.relocalize(g, RES, hyps, z, ang, 6.0, prm, early_stop=False, icp_iters=10)
+    err = lambda r: math.hypot(r["x"] - true[0], r["y"] - true[1])
+    assert err(refined) < err(plain)
+    assert refined["tam"] >= plain["tam"]
+
+
+# ------------------------------------------------------------------------------------------
 # invariants of the whole scoring path
 # ------------------------------------------------------------------------------------------
 
