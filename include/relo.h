@@ -80,6 +80,12 @@ typedef struct relo_params {
                                                           RELO_FINE_TAM_MEAN (Eq. 34), RELO_FINE_BASELINE (Eq. 33)
                                                           or RELO_FINE_LF (Eq. 32, a sum of log-likelihoods, so
                                                           negative; tau compares against it as it is) */
+    int32_t icp_iters;                                 /* > 0: each batch's local top-k poses are refined by up to
+                                                          this many point-to-point ICP iterations against the map's
+                                                          occupied cells and scored again at the refined continuous
+                                                          pose (Sec. III overview, Remark 2); the batch's best and the
+                                                          result are then the best re-evaluated pose.  0 (default):
+                                                          no refinement */
 } relo_params;
 
 #define RELO_COARSE_SMAD 0
@@ -91,7 +97,8 @@ typedef struct relo_params {
 
 /* Result of one relocalization (Eq. 9 restricted to the scored hypotheses). */
 typedef struct relo_result {
-    double x, y, theta;     /* selected pose: cell centre (metres) and theta_m wrapped to [-pi, pi) */
+    double x, y, theta;     /* selected pose: cell centre (metres) and theta_m wrapped to [-pi, pi); with
+                               icp_iters > 0 the refined continuous pose */
     double tam;             /* its score by the fine metric: TAM (Eq. 31) unless fine_metric says otherwise */
     double smad;            /* the coarse metric of its position, metres: SMAD (Eq. 20) or CAER (Eq. 21) */
     int64_t smad_num;       /* its numerator in Q16 cell units: |sum R_real - W_m|, or sum |R_i - R^_{i+m}| */

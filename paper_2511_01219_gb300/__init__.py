@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
         ("topk", ctypes.c_int32), ("batch", ctypes.c_int32), ("local_topk", ctypes.c_int32),
         ("n_skip_beam", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
         ("max_range", ctypes.c_double), ("scan_cache_bytes", ctypes.c_int64), ("ray_tables", ctypes.c_int32),
-        ("coarse_metric", ctypes.c_int32), ("fine_metric", ctypes.c_int32),
+        ("coarse_metric", ctypes.c_int32), ("fine_metric", ctypes.c_int32), ("icp_iters", ctypes.c_int32),
     ]
 
 COARSE_SMAD, COARSE_CAER = 0, 1

@@ -276,6 +276,7 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
         return fail(ctx, RELO_E_INVALID_ARG, "coarse_metric must be RELO_COARSE_SMAD or RELO_COARSE_CAER");
     if (p.fine_metric < RELO_FINE_TAM || p.fine_metric > RELO_FINE_LF)
         return fail(ctx, RELO_E_INVALID_ARG, "fine_metric must be one of RELO_FINE_TAM .. RELO_FINE_LF");
+    if (p.icp_iters < 0 || p.icp_iters > 1000) return fail(ctx, RELO_E_INVALID_ARG, "icp_iters must be in [0, 1000]");
     return RELO_OK;
 }
 
@@ -917,6 +918,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         const Prepared &q = pr[r];
         const int n = q.P->n, nh = q.m->n_hyp, K = q.K;
         off[r] = total;
+        total += align_up(24ull * K) + align_up(4ull * K);   // refined poses and re-evaluated scores
         total += align_up(sizeof(int2) * n) + align_up(4ull * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
                  align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
                  align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
@@ -994,6 +996,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.Rall = (int32_t *)take(4ull * P.n);
         d.coarse = p.coarse_metric;
         d.fine = p.fine_metric;
+        d.icp_iters = p.icp_iters;
+        d.d2map = m.dev.d2;
+        d.grid = m.dev.grid;
+        d.ref_pose = (double *)take(24ull * q.K);
+        d.reev = (float *)take(4ull * q.K);
         d.scan = (ScanInfo *)take(sizeof(ScanInfo));
         d.keys = (unsigned long long *)take(8ull * m.n_hyp);
         d.smad_num = (long long *)take(8ull * m.n_hyp);
@@ -1108,8 +1115,18 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             CK(timed_on(ctx, st, 4, 1, [&] { return launch_tam(rq, R, sg, tp, st); }), "TAM");
         }
         const int lo = any_early ? bi : 0, hi = any_early ? bi + 1 : max_batches;
-        CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, lo, hi, bi == tam_rounds - 1, st); }),
-           "batch selection");
+        const bool last = bi == tam_rounds - 1;
+        if (p.icp_iters > 0) {
+            // the local top-k, their ICP refinement and re-evaluation, then the batch's best
+            CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, lo, hi, false, true, st); }),
+               "batch selection");
+            CK(timed_on(ctx, st, 5, 1, [&] { return launch_icp(rq, R, lo, hi, p.local_topk, max_beams, st); }),
+               "ICP refinement");
+            CK(timed_on(ctx, st, 5, 1, [&] { return launch_icp_best(rq, R, lo, hi, last, st); }), "batch selection");
+        } else {
+            CK(timed_on(ctx, st, 5, 1, [&] { return launch_select_batch(rq, R, lo, hi, last, false, st); }),
+               "batch selection");
+        }
     }
     created.keep = true;
     wnew.keep = true;
@@ -1404,6 +1421,7 @@ void relo_default_params(relo_params *p) {
     p->ray_tables = 1;
     p->coarse_metric = RELO_COARSE_SMAD;
     p->fine_metric = RELO_FINE_TAM;
+    p->icp_iters = 0;
 }
 
 int relo_create(const relo_params *p, void *stream, relo_ctx **out) {

@@ -154,6 +154,11 @@ struct ReqDesc {
     const uint64_t *bits;
     const uint16_t *field;       // padded clamped field, pointer to cell (0, 0)
     int coarse, fine;            // ranking and scoring metrics (RELO_COARSE_*, RELO_FINE_*)
+    int icp_iters;               // ICP iterations per local top-k pose (0: no refinement)
+    const int32_t *d2map;        // [H*W] exact squared EDT, -1 = no obstacle (ICP pairs)
+    const int8_t *grid;          // [H*W] the occupancy grid (ICP pairs)
+    double *ref_pose;            // [K][3] refined pose (x, y, theta) of each refined survivor (map metres)
+    float *reev;                 // [K] its re-evaluated score
     const float2 *lut;           // [C+2] (l(b), sqrt(C) - sqrt(b)); entry C+1 = (0, 0) marks "no beam"
     int W, H, TW, TH, C, Wp, P;
     float res, res2, d_max, d_min;
@@ -270,7 +275,14 @@ int tam_vpl_for(int max_beams);
 TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
                  int max_beams, int max_C, int n_sm, TamSeg *segs);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
-// selection of batch indexes batch_lo .. batch_hi - 1 in order; with last, also every request's result
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s);
+// selection of batch indexes batch_lo .. batch_hi - 1 in order; with last, also every request's result.
+// With icp, only the local top-k (launch_icp and launch_icp_best take the rest).
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, bool icp,
+                                cudaStream_t s);
+// ICP refinement and re-evaluation of the local top-k of batches batch_lo .. batch_hi - 1, then their best,
+// early termination and (with last) the results
+cudaError_t launch_icp(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, int max_L, int max_beams,
+                       cudaStream_t s);
+cudaError_t launch_icp_best(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s);
 
 }  // namespace relo

@@ -240,9 +240,17 @@ __device__ void finalize_request(const ReqDesc &d) {
         r.hyp = h;
         r.m = m;
         r.tam = (double)score_of(tb);
-        r.x = d.ox + ((double)c.x + 0.5) * d.resd;
-        r.y = d.oy + ((double)c.y + 0.5) * d.resd;
-        double th = (double)m * (2.0 * M_PI) / (double)d.ns;
+        double th;
+        if (d.icp_iters > 0) {   // the refined continuous pose
+            const double *ps = d.ref_pose + 3 * (size_t)s;
+            r.x = d.ox + ps[0];
+            r.y = d.oy + ps[1];
+            th = remainder(ps[2], 2.0 * M_PI);
+        } else {
+            r.x = d.ox + ((double)c.x + 0.5) * d.resd;
+            r.y = d.oy + ((double)c.y + 0.5) * d.resd;
+            th = (double)m * (2.0 * M_PI) / (double)d.ns;
+        }
         if (th >= M_PI) th -= 2.0 * M_PI;
         r.theta = th;
         r.smad_num = d.smad_num[h];
@@ -256,9 +264,10 @@ __device__ void finalize_request(const ReqDesc &d) {
 // terminated early).  Keys (TAM descending, then survivor position) are
 // unique, so each survivor's rank is the number of smaller keys; ranks below
 // L fill the local top-k directly.  With last, the launch also writes every
-// request's result.
+// request's result.  With icp the launch stops at the local top-k and the
+// counters: k_icp refines and re-scores them, k_icp_best takes their best.
 __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict__ reqs, int batch_lo, int batch_hi,
-                                                       int last) {
+                                                       int last, int icp) {
     __shared__ unsigned long long v[kMaxBatch];
     __shared__ int s_skip;
     const ReqDesc &d = reqs[blockIdx.x];
@@ -292,10 +301,12 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
                 const unsigned tb = ~(unsigned)(me >> 32);
                 const unsigned s = (unsigned)(me & 0xffffffffu);
                 const unsigned long long cand = ((unsigned long long)tb << 32) | (0xffffffffu - s);
-                if (cand > st->best) st->best = cand;
                 st->n_batches += 1;
                 st->n_tam_evals += (long long)nb * d.n_orient;
-                if (d.early_stop && (double)score_of(tb) >= d.tau) st->done = 1;
+                if (!icp) {
+                    if (cand > st->best) st->best = cand;
+                    if (d.early_stop && (double)score_of(tb) >= d.tau) st->done = 1;
+                }
             }
         }
         for (int r = nb + threadIdx.x; r < L; r += blockDim.x) d.local[(size_t)batch_idx * L + r] = -1;
@@ -305,6 +316,36 @@ __global__ void __launch_bounds__(1024) k_select_batch(const ReqDesc *__restrict
         __syncthreads();   // the selection state of this launch is complete
         if (threadIdx.x == 0) finalize_request(d);
     }
+}
+
+// One thread per request, after k_icp: for batches batch_lo .. batch_hi - 1
+// in order (each skipped when the request has fewer or already terminated),
+// the best re-evaluated local top-k pose (ties to the earlier survivor) joins
+// the running best, and early termination follows its score (the overview of
+// Sec. III: the test is made on the re-evaluated score).  With last, the
+// result.
+__global__ void k_icp_best(const ReqDesc *__restrict__ reqs, int R, int batch_lo, int batch_hi, int last) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const ReqDesc &d = reqs[r];
+    SelectState *st = d.state;
+    if (d.scan->n_valid > 0) {
+        for (int b = batch_lo; b < batch_hi && b < d.n_batches; ++b) {
+            if (st->done) break;
+            unsigned long long top = 0ull;
+            for (int i = 0; i < d.L; ++i) {
+                const int s = d.local[(size_t)b * d.L + i];
+                if (s < 0) continue;
+                const unsigned long long key = ((unsigned long long)score_code(d.reev[s]) << 32) |
+                                               (0xffffffffu - (unsigned)s);
+                top = key > top ? key : top;
+            }
+            if (top == 0ull) continue;
+            if (top > st->best) st->best = top;
+            if (d.early_stop && (double)score_of((unsigned)(top >> 32)) >= d.tau) st->done = 1;
+        }
+    }
+    if (last) finalize_request(d);
 }
 
 }  // namespace
@@ -322,8 +363,14 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s) {
-    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_lo, batch_hi, last ? 1 : 0);
+cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, bool icp,
+                                cudaStream_t s) {
+    k_select_batch<<<R, 1024, 0, s>>>(reqs, batch_lo, batch_hi, last ? 1 : 0, icp ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_icp_best(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s) {
+    k_icp_best<<<(R + 63) / 64, 64, 0, s>>>(reqs, R, batch_lo, batch_hi, last ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-5
+RES = 0.05
 
 
 @pytest.fixture(scope="module")
@@ -264,6 +265,47 @@ def test_caer_panoramic_and_fine_metric_together(relo):
                                                              early_stop=True, tau=0.5)
     assert pl["panoramic"] and (st["m"] == 0).all()
     ctx.close()
+
+
+def icp_case(relo, g, hyps, z, ang, max_range, early, **kw):
+    prm = oracle.Params(n_orient=kw.get("n_orient", 40), topk=kw.get("topk", 12), batch=kw.get("batch", 6),
+                        local_topk=kw.get("local_topk", 3), tau=kw.get("tau", 0.95))
+    d2 = oracle.edt(g)
+    want = oracle.relocalize(g, RES, hyps, z, ang, max_range, prm, d2tab=d2, early_stop=early, icp_iters=10)
+    ctx, mid, got = run(relo, g, RES, hyps, z, ang, max_range, n_orient=prm.n_orient, topk=prm.topk, batch=prm.batch,
+                        local_topk=prm.local_topk, tau=prm.tau, early_stop=int(early), icp_iters=10)
+    ctx.close()
+    assert got.status == 0 and got.n_batches == want["n_batches"]
+    if (got.hyp, got.m) == (want["hyp"], want["m"]):
+        dth = math.remainder(got.theta - want["theta"], 2 * math.pi)
+        assert abs(got.x - want["x"]) <= 1e-6 and abs(got.y - want["y"]) <= 1e-6 and abs(dth) <= 1e-6
+    assert abs(got.tam - want["tam"]) <= RTOL * abs(want["tam"])
+    return got, want
+
+
+@pytest.mark.parametrize("early", [False, True])
+def test_icp_refinement_matches_oracle(relo, early):
+    """ICP of every local top-k pose (10 iterations) and its re-evaluation at
+    the refined continuous pose: the selected hypothesis, orientation and
+    refined pose equal the oracle's (1e-6 m and rad), the re-evaluated score
+    within 1e-5; a scan rendered between cells, with and without early
+    termination."""
+    g = workloads.make_room(2, n=40, n_boxes=4)
+    free = np.argwhere(g == 0)[:, ::-1]
+    hyps = free[np.random.default_rng(2).choice(len(free), 25, replace=False)].astype(np.int32)
+    ang = workloads.beam_angles(90, 120)
+    true = ((hyps[5][0] + 0.8) * RES, (hyps[5][1] + 0.3) * RES, 0.5)
+    z = workloads.render_scan(g, RES, true, ang, 6.0)
+    got, want = icp_case(relo, g, hyps, z, ang, 6.0, early, tau=0.5)
+    plain = oracle.relocalize(g, RES, hyps, z, ang, 6.0, oracle.Params(n_orient=40, topk=12, batch=6, local_topk=3,
+                                                                       tau=0.5), early_stop=early)
+    assert math.hypot(got.x - true[0], got.y - true[1]) < math.hypot(plain["x"] - true[0], plain["y"] - true[1])
+
+
+def test_icp_on_the_room_workload(relo, workload):
+    wl = workload(0)
+    icp_case(relo, wl.grid, wl.hyps, wl.ranges, wl.angles, wl.max_range, False, n_orient=wl.n_orient, topk=16,
+             batch=8, local_topk=4)
 
 
 def test_warehouse_full_size_sampled(relo, workload):
