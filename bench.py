@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--fine", default="tam", choices=["tam", "tam_mean", "baseline", "lf"],
                     help="office workload: scoring metric, TAM (Eq. 31), TAM_mean (Eq. 34), wp_baseline (Eq. 33) "
                          "or wp_LF (Eq. 32)")
+    ap.add_argument("--icp-iters", type=int, default=0,
+                    help="office workload: ICP iterations per local top-k pose before its re-evaluation (0: none)")
     ap.add_argument("--serve-configs", default="8x2,16x3,64x3",
                     help="served: max_batch x max_inflight settings to measure (the best is reported)")
     return ap.parse_args()
@@ -207,7 +209,7 @@ def run_ours(args, world, rank, local, dist):
     torch.cuda.set_stream(stream)
     ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0, stream=stream,
                     coarse_metric=["smad", "caer"].index(args.coarse),
-                    fine_metric=["tam", "tam_mean", "baseline", "lf"].index(args.fine))
+                    fine_metric=["tam", "tam_mean", "baseline", "lf"].index(args.fine), icp_iters=args.icp_iters)
     grid_d = torch.tensor(wl.grid, device="cuda")
     hyps_d = torch.tensor(wl.hyps, device="cuda")
     z_d = torch.tensor(wl.ranges, device="cuda")
@@ -307,7 +309,8 @@ def run_ours(args, world, rank, local, dist):
         "config": {"workload": WORKLOAD, "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
                    "n_orient": wl.n_orient, "n_beams": len(wl.ranges), "n_s": wl.n_s, "topk": wl.topk,
                    "evals_per_step": evals_per_step, "l2": "flushed before every timed step (256 MiB write)",
-                   "ranking": args.coarse, "scoring": args.fine, "parallelism": f"replicas x{world}"},
+                   "ranking": args.coarse, "scoring": args.fine, "icp_iters": args.icp_iters,
+                   "parallelism": f"replicas x{world}"},
         "relocalizations_per_s": world * args.steps / (t_max / 1e3),
         "latency_ms": {"p50": pct[len(pct) // 2], "p99": pct[min(len(pct) - 1, int(math.ceil(0.99 * len(pct))) - 1)]},
         "gpu_launches": int(launches),

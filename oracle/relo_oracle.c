@@ -564,28 +564,47 @@ int oracle_rigid_fit(const double *w, const double *c, int n, double *phi, doubl
 }
 
 /*
+ * A beam's world point and cell at pose (x, y) with ct = cos(theta), st =
+ * sin(theta): the sensor-frame point s = (z cos a, z sin a) rotated and moved,
+ * wx = x + (ct sx - st sy), wy = y + (st sx + ct sy), each product and sum
+ * rounded on its own; its cell is floor(w * (1 / res)).
+ */
+static void world_point(double x, double y, double ct, double st, double sx, double sy, double inv_res, double *wx,
+                        double *wy, int *cx, int *cy) {
+    double ax = ct * sx, bx = st * sy, ay = st * sx, by = ct * sy;
+    *wx = x + (ax - bx);
+    *wy = y + (ay + by);
+    *cx = (int)floor(*wx * inv_res);
+    *cy = (int)floor(*wy * inv_res);
+}
+
+/*
  * ICP from pose = (x, y, theta) (metres, radians; refined in place) for n
  * beams with sensor-frame ranges z (metres) and angles a.  Each iteration maps
- * beam i to the world point (x + z_i cos(theta + a_i), y + z_i sin(theta +
- * a_i)), pairs it with the centre of the nearest occupied cell to the cell it
- * falls in (kept when that squared cell distance is at most C, i.e. within
- * d_max), fits the rigid motion of the pairs and composes it with the pose.
- * It stops after iters iterations, when fewer than 2 pairs remain, or when the
- * motion is below 1e-9 rad and 1e-9 m.  Returns the iterations applied.
+ * beam i to its world point (world_point), pairs it with the centre of the
+ * nearest occupied cell to the cell it falls in (kept when that squared cell
+ * distance is at most C, i.e. within d_max), fits the rigid motion of the
+ * pairs and composes it with the pose.  It stops after iters iterations, when
+ * fewer than 2 pairs remain, or when the motion is below 1e-9 rad and 1e-9 m.
+ * Returns the iterations applied.
  */
 int oracle_icp(const int8_t *grid, const int64_t *d2tab, int W, int H, double res, int64_t C, const double *z,
                const double *a, int n, int iters, double *pose) {
     double *w = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
     double *c = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
+    double *sx = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *sy = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) { sx[i] = z[i] * cos(a[i]); sy[i] = z[i] * sin(a[i]); }
+    const double inv_res = 1.0 / res;
     int it = 0;
     for (; it < iters; ++it) {
         int k = 0;
+        const double ct = cos(pose[2]), st = sin(pose[2]);
         for (int i = 0; i < n; ++i) {
-            double wx = pose[0] + z[i] * cos(pose[2] + a[i]);
-            double wy = pose[1] + z[i] * sin(pose[2] + a[i]);
-            int ox, oy;
-            if (!oracle_nearest_occupied(grid, d2tab, W, H, (int)floor(wx / res), (int)floor(wy / res), C, &ox, &oy))
-                continue;
+            double wx, wy;
+            int cx, cy, ox, oy;
+            world_point(pose[0], pose[1], ct, st, sx[i], sy[i], inv_res, &wx, &wy, &cx, &cy);
+            if (!oracle_nearest_occupied(grid, d2tab, W, H, cx, cy, C, &ox, &oy)) continue;
             w[2 * k] = wx; w[2 * k + 1] = wy;
             c[2 * k] = (ox + 0.5) * res; c[2 * k + 1] = (oy + 0.5) * res;
             ++k;
@@ -600,15 +619,17 @@ int oracle_icp(const int8_t *grid, const int64_t *d2tab, int W, int H, double re
     }
     free(w);
     free(c);
+    free(sx);
+    free(sy);
     return it;
 }
 
 /*
  * The score (TAM or the metric params[8] selects) at continuous poses
  * (x, y, theta interleaved) for n beams with sensor-frame ranges z (metres)
- * and angles a: beam i ends in the cell (floor(wx / res), floor(wy / res)) of
- * its world point; its distance is res * sqrt(min(d2, C)), d_max off the map,
- * as in tam_one.  params as oracle_tam.
+ * and angles a: beam i ends in the cell of its world point (world_point); its
+ * distance is res * sqrt(min(d2, C)), d_max off the map, as in tam_one.
+ * params as oracle_tam.
  */
 void oracle_tam_pose(const int8_t *grid, const int64_t *d2tab, int W, int H, const double *poses, int n_poses,
                      const double *z, const double *a, int n, const double *params, double *T_out, int n_threads) {
@@ -624,9 +645,12 @@ void oracle_tam_pose(const int8_t *grid, const int64_t *d2tab, int W, int H, con
         double *dist = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
         double *ell = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
         const double *ps = poses + 3 * q;
+        const double ct = cos(ps[2]), st = sin(ps[2]), inv_res = 1.0 / p.res;
         for (int i = 0; i < n; ++i) {
-            int64_t ex = (int64_t)floor((ps[0] + z[i] * cos(ps[2] + a[i])) / p.res);
-            int64_t ey = (int64_t)floor((ps[1] + z[i] * sin(ps[2] + a[i])) / p.res);
+            double wx, wy;
+            int cx, cy;
+            world_point(ps[0], ps[1], ct, st, z[i] * cos(a[i]), z[i] * sin(a[i]), inv_res, &wx, &wy, &cx, &cy);
+            int64_t ex = cx, ey = cy;
             int64_t d2;
             if (ex < 0 || ey < 0 || ex >= W || ey >= H) d2 = C;
             else if (d2tab) {
