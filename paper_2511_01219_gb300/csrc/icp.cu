@@ -36,32 +36,22 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kIcpThreads = 256;
 constexpr int kIcpWarps = kIcpThreads / 32;
 
-__device__ __forceinline__ int isqrt_floor(int v) {   // v >= 0
-    int r = (int)sqrtf((float)v);
-    while (r * r > v) --r;
-    while ((r + 1) * (r + 1) <= v) ++r;
-    return r;
-}
-
 // The nearest occupied cell to cell (x, y) when its squared distance is at
-// most cap: the cells at exactly the EDT distance, by increasing dy, then dx.
+// most cap (<= C): the cells at exactly the EDT distance, by increasing dy,
+// then dx, from the map's table of the offsets at each squared distance.
 __device__ bool nearest_occupied(const ReqDesc &d, int x, int y, int cap, int &ox, int &oy) {
     if (x < 0 || y < 0 || x >= d.W || y >= d.H) return false;
     const int d2 = d.d2map[(size_t)y * d.W + x];
     if (d2 < 0 || d2 > cap) return false;
-    const int r = isqrt_floor(d2);
-    for (int dy = -r; dy <= r; ++dy) {
-        const int rest = d2 - dy * dy;
-        const int s = isqrt_floor(rest);
-        if (s * s != rest) continue;
-        for (int k = 0; k < (s == 0 ? 1 : 2); ++k) {
-            const int cx = x + (k == 0 ? -s : s), cy = y + dy;
-            if (cx < 0 || cy < 0 || cx >= d.W || cy >= d.H) continue;
-            if (d.grid[(size_t)cy * d.W + cx] >= 65) {
-                ox = cx;
-                oy = cy;
-                return true;
-            }
+    const int e1 = d.sq_off[d2 + 1];
+    for (int e = d.sq_off[d2]; e < e1; ++e) {
+        const short2 o = d.sq_rep[e];
+        const int cx = x + o.y, cy = y + o.x;
+        if (cx < 0 || cy < 0 || cx >= d.W || cy >= d.H) continue;
+        if (d.grid[(size_t)cy * d.W + cx] >= 65) {
+            ox = cx;
+            oy = cy;
+            return true;
         }
     }
     return false;

@@ -82,6 +82,8 @@ struct MapSlot {
     int2 *hyps = nullptr;
     int n_hyp = 0, hyp_cap = 0;
     float2 *lut = nullptr;
+    int32_t *sq_off = nullptr;   // [kMaxClamp + 2] and [kMaxLatticePoints]: the cells at each squared distance
+    short2 *sq_rep = nullptr;
     size_t bytes = 0;
     std::vector<ScanTable *> tables;
 };
@@ -314,6 +316,35 @@ int build_lut(relo_ctx *ctx, MapSlot &m) {
         m.bytes += sizeof(float2) * (kMaxClamp + 2);
     }
     CK(cudaMemcpyAsync(m.lut, h.data(), sizeof(float2) * (C + 2), cudaMemcpyHostToDevice, ctx->stream), "lut upload");
+    // every (dy, dx) with dy^2 + dx^2 = n <= C, grouped by n and ordered by dy, then dx: the candidates ICP
+    // tries, nearest first, when it pairs a beam with an occupied cell
+    std::vector<int32_t> off(C + 2, 0);
+    std::vector<short2> rep;
+    for (int n = 0; n <= C; ++n) {
+        off[n] = (int32_t)rep.size();
+        const int r = (int)sqrt((double)n) + 1;
+        for (int dy = -r; dy <= r; ++dy) {
+            const int rest = n - dy * dy;
+            if (rest < 0) continue;
+            int s = (int)sqrt((double)rest);
+            while (s * s > rest) --s;
+            while ((s + 1) * (s + 1) <= rest) ++s;
+            if (s * s != rest) continue;
+            rep.push_back(make_short2((short)dy, (short)-s));
+            if (s > 0) rep.push_back(make_short2((short)dy, (short)s));
+        }
+    }
+    off[C + 1] = (int32_t)rep.size();
+    if (!m.sq_off) {
+        int rc = dev_alloc(ctx, (void **)&m.sq_off, sizeof(int32_t) * (kMaxClamp + 2), "pairing table");
+        if (!rc) rc = dev_alloc(ctx, (void **)&m.sq_rep, sizeof(short2) * kMaxLatticePoints, "pairing table");
+        if (rc) return rc;
+        m.bytes += sizeof(int32_t) * (kMaxClamp + 2) + sizeof(short2) * kMaxLatticePoints;
+    }
+    CK(cudaMemcpyAsync(m.sq_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream),
+       "pairing table upload");
+    CK(cudaMemcpyAsync(m.sq_rep, rep.data(), sizeof(short2) * rep.size(), cudaMemcpyHostToDevice, ctx->stream),
+       "pairing table upload");
     return RELO_OK;
 }
 
@@ -655,6 +686,8 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.bits, sizeof(uint64_t) * occupancy_words(m.dev.TW, m.dev.TH));
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
     dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
+    dev_free(ctx, m.sq_off, sizeof(int32_t) * (kMaxClamp + 2));
+    dev_free(ctx, m.sq_rep, sizeof(short2) * kMaxLatticePoints);
     m = MapSlot();
 }
 
@@ -999,6 +1032,8 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.icp_iters = p.icp_iters;
         d.d2map = m.dev.d2;
         d.grid = m.dev.grid;
+        d.sq_off = m.sq_off;
+        d.sq_rep = m.sq_rep;
         d.ref_pose = (double *)take(24ull * q.K);
         d.reev = (float *)take(4ull * q.K);
         d.scan = (ScanInfo *)take(sizeof(ScanInfo));

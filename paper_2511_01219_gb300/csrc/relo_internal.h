@@ -28,6 +28,7 @@ __host__ __device__ inline float score_of(unsigned int c) {
 }
 
 constexpr int kMaxClamp = 8100;        // C = (d_max/res)^2 <= 90^2 so the TAM table fits shared memory
+constexpr int kMaxLatticePoints = 25445;   // integer (dy, dx) with dy^2 + dx^2 <= kMaxClamp
 constexpr int kMaxValidBeams = 2048;   // register-resident TAM selection holds <= 64 values per lane
 constexpr int kMaxNs = 8192;           // panoramic beam count
 constexpr int kMaxTopk = 4096;
@@ -157,6 +158,8 @@ struct ReqDesc {
     int icp_iters;               // ICP iterations per local top-k pose (0: no refinement)
     const int32_t *d2map;        // [H*W] exact squared EDT, -1 = no obstacle (ICP pairs)
     const int8_t *grid;          // [H*W] the occupancy grid (ICP pairs)
+    const int32_t *sq_off;       // [C+2] start of the offsets with dy^2 + dx^2 = n in sq_rep, for n in [0, C + 1]
+    const short2 *sq_rep;        // (dy, dx) offsets by n, each n's ordered by dy, then dx (the ICP pairing order)
     double *ref_pose;            // [K][3] refined pose (x, y, theta) of each refined survivor (map metres)
     float *reev;                 // [K] its re-evaluated score
     const float2 *lut;           // [C+2] (l(b), sqrt(C) - sqrt(b)); entry C+1 = (0, 0) marks "no beam"
