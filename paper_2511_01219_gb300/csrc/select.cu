@@ -1,9 +1,9 @@
 // Coarse ranking and batched selection.
 //
-// k_topk: the K hypotheses with the smallest SMAD (Sec. III intro: SMAD orders
-// all positions, the ordered set is cut into batches).  Keys are
-// numerator << 21 | index, so they are unique and ascending key order is
-// (SMAD, index) order.  One CTA histograms the 11 bits below the keys' highest
+// k_topk: the K hypotheses with the smallest SMAD (or CAER; Sec. III intro:
+// the coarse metric orders all positions, the ordered set is cut into
+// batches).  Keys are numerator << 21 | index, so they are unique and
+// ascending key order is (numerator, index) order.  One CTA histograms the 11 bits below the keys' highest
 // set bit, finds the digit holding the K-th smallest key, and orders the keys
 // up to that digit (by rank counting when they are few: keys are unique),
 // keeping the first K;
@@ -15,6 +15,11 @@
 // survivor), the batch's local top-k by TAM (ties to the earlier survivor) by
 // rank counting, the running best over batches, and the early-termination
 // flag once a batch's best reaches tau (Remark 2).
+//
+// With ICP refinement on, k_select_batch stops at the local top-k; k_icp
+// (icp.cu) refines and re-scores those poses, and k_icp_best takes the
+// running best and the early-termination test on the re-evaluated scores (the
+// overview of Sec. III).
 //
 // The last selection launch also writes the selected pose and counters into
 // each request's relo_result.
