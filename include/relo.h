@@ -280,6 +280,28 @@ int relo_set_profiling_mask(relo_ctx *ctx, uint32_t stage_mask);
 int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32_t n, int32_t reset,
                      int64_t *kernels_out);
 
+/* Positional hypotheses by the traversability-constrained RRT (Algorithm 1,
+ * Sec. III-A, Remark 4) on the GPU, in batched-expansion form: each round
+ * draws its ceil(W H res^2 / rho^2) random points at once and extends them
+ * against the tree as the round began (nearest node, adaptive step
+ * eta in [r_robot, eta_max] from the clearance there, segment checked every
+ * res / 2 for clearance >= r_robot, inside the map); the accepted points join
+ * in sample order; voxels of side rho keep their first node; rounds stop once
+ * one adds at most eps_gain voxels (or after max_rounds).  The result covers
+ * the reachable free space like the one-point-at-a-time tree, not with the
+ * same points.  clearance_dev: float32 [h][w] metres to the nearest occupied
+ * or unknown cell centre (device).  p0x, p0y: the start, metres from the map
+ * corner.  seed: the counter-based sampler's key.  node_cap bounds the tree.
+ * Writes up to cap representatives (x, y float32 metres, in order of first
+ * insertion) to xy_dev and their count, the rounds run and the tree size to
+ * n_out, rounds_out, nodes_out (host).  Blocking; allocates its scratch for
+ * the call and frees it.  RELO_E_INVALID_ARG for bad sizes, a start off the
+ * map or a rho that gives more than 2^26 points per round; RELO_E_CUDA. */
+int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w, int32_t h, double res, double p0x,
+                            double p0y, double rho, double eta_max, double r_robot, int32_t eps_gain, uint64_t seed,
+                            int32_t max_rounds, int32_t node_cap, float *xy_dev, int32_t cap, int32_t *n_out,
+                            int32_t *rounds_out, int32_t *nodes_out);
+
 /* Allocation-free EDT.  The paper has no counterpart to this entry point; it
  * serves callers that may not allocate device memory once running, such as a
  * robot's real-time localisation loop that allocates only at start-up, or a

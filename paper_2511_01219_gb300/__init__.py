@@ -40,7 +40,7 @@ EXPORTED = [
     "relo_set_hypotheses_cells_dev", "relo_relocalize", "relo_relocalize_dev", "relo_get_stage",
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
-    "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask",
+    "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask", "relo_rrt_hypotheses_dev",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
             "relo_poll": (ctypes.c_int, [P, I64, P, P]),
             "relo_serve_stop": (ctypes.c_int, [P]),
             "relo_scan_cache_stats": (ctypes.c_int, [P, P, I32]),
+            "relo_rrt_hypotheses_dev": (ctypes.c_int, [P, P, I32, I32, D, D, D, D, D, D, I32, ctypes.c_uint64, I32, I32,
+                                                       P, I32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -313,6 +315,20 @@ class Relo:
         v = (ctypes.c_int64 * 7)()
         self._check(self._L.relo_scan_cache_stats(self._h, v, 7), "scan_cache_stats")
         return dict(zip(["tables", "bytes", "hits", "misses", "evictions", "win_tables", "win_hits"], list(v)))
+
+    def rrt_hypotheses(self, clearance_t, res: float, p0, rho: float, eta_max: float = 0.6, r_robot: float = 0.21,
+                       eps_gain: int = 2, seed: int = 0, max_rounds: int = 500, node_cap: int = 4_000_000,
+                       cap: int = 1_000_000):
+        """Algorithm 1 on the GPU (batched expansion): (xy float32 [n, 2] metres on the device, rounds, nodes)."""
+        import torch
+        h, w = clearance_t.shape
+        xy = torch.empty((cap, 2), dtype=torch.float32, device=clearance_t.device)
+        n, r, nn = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._L.relo_rrt_hypotheses_dev(self._h, _t_ptr(clearance_t), w, h, res, float(p0[0]),
+                                                   float(p0[1]), rho, eta_max, r_robot, eps_gain, seed, max_rounds,
+                                                   node_cap, _t_ptr(xy), cap, ctypes.byref(n), ctypes.byref(r),
+                                                   ctypes.byref(nn)), "rrt_hypotheses")
+        return xy[: n.value], r.value, nn.value
 
     def kernels_launched(self) -> int:
         k = ctypes.c_int64(0)

@@ -1828,6 +1828,22 @@ int relo_serve_stop(relo_ctx *ctx) {
     return RELO_OK;
 }
 
+int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w, int32_t h, double res, double p0x,
+                            double p0y, double rho, double eta_max, double r_robot, int32_t eps_gain, uint64_t seed,
+                            int32_t max_rounds, int32_t node_cap, float *xy_dev, int32_t cap, int32_t *n_out,
+                            int32_t *rounds_out, int32_t *nodes_out) {
+    if (!ctx || !clearance_dev || !xy_dev || !n_out || !rounds_out || !nodes_out)
+        return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    if (w < 1 || h < 1 || w > 16384 || h > 16384 || !(res > 0) || !(rho > 0) || !(eta_max > 0) || !(r_robot > 0) ||
+        eps_gain < 0 || max_rounds < 1 || node_cap < 1 || cap < 0)
+        return fail(ctx, RELO_E_INVALID_ARG, "bad RRT arguments");
+    const char *err = "";
+    const int rc = rrt_sample_dev(clearance_dev, w, h, res, p0x, p0y, rho, eta_max, r_robot, eps_gain, seed,
+                                  max_rounds, node_cap, xy_dev, cap, n_out, rounds_out, nodes_out, ctx->stream, &err);
+    if (rc) return fail(ctx, rc, std::string("RRT: ") + err);
+    return RELO_OK;
+}
+
 int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {
     if (!ctx || (!out && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     long long tables = 0;

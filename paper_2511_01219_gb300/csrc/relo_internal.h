@@ -287,5 +287,9 @@ cudaError_t launch_select_batch(const ReqDesc *reqs, int R, int batch_lo, int ba
 cudaError_t launch_icp(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, int max_L, int max_beams,
                        cudaStream_t s);
 cudaError_t launch_icp_best(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s);
+// Algorithm 1 in batched-expansion form (rrt.cu); blocking on s; *err names a failure
+int rrt_sample_dev(const float *clr, int W, int H, double res, double p0x, double p0y, double rho, double eta_max,
+                   double r_robot, int eps_gain, uint64_t seed, int max_rounds, int node_cap, float *xy_out, int cap,
+                   int *n_out, int *rounds_out, int *nodes_out, cudaStream_t s, const char **err);
 
 }  // namespace relo

@@ -1,0 +1,85 @@
+"""Positional hypotheses by the traversability-constrained RRT (Algorithm 1)
+on the GPU, in batched-expansion form, against the serial generator.
+
+The batched form extends every point of a round against the tree as the
+round began, so its node set differs from the one-point-at-a-time tree; what
+must agree is what the hypotheses are for (Sec. III-A): the reachable free
+space is covered as well (every traversable cell reachable from the start
+lies within one voxel diagonal of a hypothesis as often), about as many
+hypotheses come out, each on a traversable cell, at most one per voxel of
+side rho, and a seed gives the same set every time.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+RES = 0.05
+R_ROBOT = 0.21
+
+
+@pytest.fixture(scope="module")
+def relo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    return relo
+
+
+def coverage(xy, clr, p0, radius):
+    """Fraction of the traversable cells reachable from p0 (4-connected) within radius of a hypothesis."""
+    from scipy.ndimage import label
+    from scipy.spatial import cKDTree
+    lab, _ = label(clr >= R_ROBOT)
+    reach = lab == lab[int(p0[1] / RES), int(p0[0] / RES)]
+    ys, xs = np.nonzero(reach)
+    d, _ = cKDTree(xy).query(np.stack([(xs + 0.5) * RES, (ys + 0.5) * RES], 1))
+    return float((d <= radius).mean())
+
+
+def scene(which):
+    g = workloads.make_room(1000) if which == "room" else workloads.make_office(1001)[:256, :256]
+    clr = workloads.clearance_table(g, RES)
+    p0 = workloads.free_start(g, RES, R_ROBOT, 7, clr)
+    n_target = 200 if which == "room" else 600
+    rho = math.sqrt(float((clr >= R_ROBOT).sum()) * RES * RES / (1.1 * n_target))
+    return g, clr, p0, rho
+
+
+@pytest.mark.parametrize("which", ["room", "office"])
+def test_gpu_rrt_covers_like_the_serial_sampler(relo, which):
+    import torch
+    g, clr, p0, rho = scene(which)
+    xs, _, _ = workloads.rrt(g, RES, p0, rho, 0.6, R_ROBOT, 2, 7, clr=clr)
+    ctx = relo.Relo()
+    clr_d = torch.tensor(clr, device="cuda")
+    xy_d, rounds, nodes = ctx.rrt_hypotheses(clr_d, RES, p0, rho, 0.6, R_ROBOT, 2, seed=7)
+    xy = xy_d.cpu().numpy()
+    again, _, _ = ctx.rrt_hypotheses(clr_d, RES, p0, rho, 0.6, R_ROBOT, 2, seed=7)
+    ctx.close()
+    assert np.array_equal(again.cpu().numpy(), xy)                     # deterministic for a seed
+    assert 0.8 * len(xs) <= len(xy) <= 1.25 * len(xs)
+    radius = rho * math.sqrt(2.0)
+    assert coverage(xy.astype(np.float64), clr, p0, radius) >= coverage(xs, clr, p0, radius) - 0.02
+    cells = np.floor(xy / np.float32(RES)).astype(np.int64)             # the kernel's float32 cell rule
+    c = clr[cells[:, 1], cells[:, 0]]
+    assert (c >= R_ROBOT - RES).all() and (c >= R_ROBOT).mean() >= 0.99
+    vox = np.floor(xy.astype(np.float64) / rho).astype(np.int64)
+    assert len(np.unique(vox, axis=0)) >= 0.99 * len(vox)               # one per voxel (float32 edges aside)
+    assert np.allclose(xy[0], p0, atol=1e-5) and rounds >= 2 and nodes >= len(xy)
+
+
+def test_gpu_rrt_rejects_a_start_off_the_map(relo):
+    import torch
+    g, clr, p0, rho = scene("room")
+    ctx = relo.Relo()
+    with pytest.raises(relo.ReloError):
+        ctx.rrt_hypotheses(torch.tensor(clr, device="cuda"), RES, (-1.0, 0.5), rho)
+    ctx.close()
