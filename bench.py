@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (default: min(steps, 200))")
-    ap.add_argument("--workload", default="office", choices=["office", "batched", "served", "sweep"],
+    ap.add_argument("--workload", default="office", choices=["office", "batched", "served", "sweep", "rrt"],
                     help="office: one request (default); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
     ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,3000,4000,5000,6000,7000,8000,10000,12000",
@@ -499,10 +499,63 @@ def run_sweep(args, world, rank, local, dist):
                      "ms_per_sweep": round(ms, 3)}
         ctx.close()
     return {"metric": "translation affinity (true orientation best among 36 at each of 15 offsets)", "value": None,
-            "unit": None, "n_gpus": world, "data": "synthetic office map and noisy scan (config 1)",
+            "unit": None, "n_gpus": world, "data": "synthetic office map (1024x1024 at 0.05 m) and noisy scan",
             "config": {"workload": f"sweep: 15 positions 0.1 m apart along {axis} x 36 orientations 10 deg apart = 540 poses",
                        "true_pose": [round(float(gx), 3), round(float(gy), 3), round(float(gth), 4)]},
             "metrics": out}
+
+
+def run_rrt(args, world, rank, local, dist):
+    """Hypothesis generation (Algorithm 1) on the office map (1024^2 at 0.05 m,
+    rho for about 5000 hypotheses): the GPU sampler (sub-batched nearest-node
+    search, in-order resolve: the serial tree for its random points) against
+    the serial generator on one host core, with counts, rounds, tree sizes and
+    the coverage of the reachable traversable cells."""
+    import numpy as np
+    import torch
+    from scipy.ndimage import label
+    from scipy.spatial import cKDTree
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    import workloads
+
+    torch.cuda.set_device(local)
+    wl = workloads.config(CONFIG_INDEX)
+    res, r_robot, seed = wl.res, 0.21, 7
+    clr = workloads.clearance_table(wl.grid, res)
+    p0 = workloads.free_start(wl.grid, res, r_robot, seed, clr)
+    rho = math.sqrt(float((clr >= r_robot).sum()) * res * res / (1.1 * 5000))
+    lab, _ = label(clr >= r_robot)
+    reach = lab == lab[int(p0[1] / res), int(p0[0] / res)]
+    ys, xs = np.nonzero(reach)
+    cells = np.stack([(xs + 0.5) * res, (ys + 0.5) * res], 1)
+
+    def cover(xy):
+        d, _ = cKDTree(np.asarray(xy, np.float64)).query(cells)
+        return round(float((d <= rho * math.sqrt(2.0)).mean()), 4)
+
+    t0 = time.perf_counter()
+    xs_, n_serial, r_serial = workloads.rrt(wl.grid, res, p0, rho, 0.6, r_robot, 2, seed, clr=clr)
+    t_serial = time.perf_counter() - t0
+    ctx = relo.Relo()
+    clr_d = torch.tensor(clr, device="cuda")
+    ctx.rrt_hypotheses(clr_d, res, p0, rho, 0.6, r_robot, 2, seed=seed)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xy, r_gpu, n_gpu = ctx.rrt_hypotheses(clr_d, res, p0, rho, 0.6, r_robot, 2, seed=seed)
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    ctx.close()
+    return {"metric": "hypothesis generation time (Algorithm 1)", "value": round(t_gpu * 1e3, 2), "unit": "ms",
+            "higher_is_better": False, "n_gpus": world, "data": "synthetic office map (1024x1024 at 0.05 m)",
+            "config": {"workload": f"rrt: office 1024x1024 @0.05 m, rho {rho:.3f} m, eta_max 0.6 m, r_robot 0.21 m, "
+                                   "eps_gain 2"},
+            "gpu": {"ms": round(t_gpu * 1e3, 2), "hypotheses": int(len(xy)), "rounds": r_gpu, "nodes": n_gpu,
+                    "coverage": cover(xy.cpu().numpy())},
+            "serial_cpu": {"ms": round(t_serial * 1e3, 2), "hypotheses": int(len(xs_)), "rounds": r_serial,
+                           "nodes": n_serial, "coverage": cover(xs_), "cores": 1}}
 
 
 def run_batched(args, world, rank, local, dist):
@@ -753,7 +806,7 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "ours" and args.workload != "office":
         dist = dist_init(world)
-        fn = {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.workload]
+        fn = {"batched": run_batched, "served": run_served, "sweep": run_sweep, "rrt": run_rrt}[args.workload]
         line = fn(args, world, rank, local, dist)
         if rank == 0:
             print(json.dumps(line))

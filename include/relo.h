@@ -281,17 +281,19 @@ int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32
                      int64_t *kernels_out);
 
 /* Positional hypotheses by the traversability-constrained RRT (Algorithm 1,
- * Sec. III-A, Remark 4) on the GPU, in batched-expansion form: each round
- * draws its ceil(W H res^2 / rho^2) random points at once and extends them
- * against the tree as the round began (nearest node, adaptive step
- * eta in [r_robot, eta_max] from the clearance there, segment checked every
- * res / 2 for clearance >= r_robot, inside the map); the accepted points join
- * in sample order; voxels of side rho keep their first node; rounds stop once
- * one adds at most eps_gain voxels (or after max_rounds).  The result covers
- * the reachable free space like the one-point-at-a-time tree, not with the
- * same points.  clearance_dev: float32 [h][w] metres to the nearest occupied
- * or unknown cell centre (device).  p0x, p0y: the start, metres from the map
- * corner.  seed: the counter-based sampler's key.  node_cap bounds the tree.
+ * Sec. III-A, Remark 4) on the GPU: each round draws ceil(W H res^2 / rho^2)
+ * random points from a counter-based generator keyed by (seed, round, index)
+ * and extends each from its nearest node (adaptive step eta in [r_robot,
+ * eta_max] from the clearance there, segment checked every res / 2 for
+ * clearance >= r_robot, inside the map); voxels of side rho keep their first
+ * node; rounds stop once one adds at most eps_gain voxels (or after
+ * max_rounds, or once the tree holds node_cap nodes).  The nearest-node
+ * searches of 256 points run at once and the points are then taken in sample
+ * order, so the tree is the one-point-at-a-time tree for those random points,
+ * in float32 arithmetic rounded at every step.  clearance_dev: float32
+ * [h][w] metres to the nearest occupied or unknown cell centre (device).
+ * p0x, p0y: the start, metres from the map corner.  seed: the counter-based
+ * sampler's key.  node_cap bounds the tree.
  * Writes up to cap representatives (x, y float32 metres, in order of first
  * insertion) to xy_dev and their count, the rounds run and the tree size to
  * n_out, rounds_out, nodes_out (host).  Blocking; allocates its scratch for

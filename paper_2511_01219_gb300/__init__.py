@@ -319,7 +319,8 @@ class Relo:
     def rrt_hypotheses(self, clearance_t, res: float, p0, rho: float, eta_max: float = 0.6, r_robot: float = 0.21,
                        eps_gain: int = 2, seed: int = 0, max_rounds: int = 500, node_cap: int = 4_000_000,
                        cap: int = 1_000_000):
-        """Algorithm 1 on the GPU (batched expansion): (xy float32 [n, 2] metres on the device, rounds, nodes)."""
+        """Algorithm 1 on the GPU (the serial tree for the sampler's random points): (xy float32 [n, 2] metres on
+        the device, in node order, rounds, nodes)."""
         import torch
         h, w = clearance_t.shape
         xy = torch.empty((cap, 2), dtype=torch.float32, device=clearance_t.device)

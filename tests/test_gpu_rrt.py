@@ -1,11 +1,15 @@
 """Positional hypotheses by the traversability-constrained RRT (Algorithm 1)
-on the GPU, in batched-expansion form, against the serial generator.
+on the GPU.
 
-The batched form extends every point of a round against the tree as the
-round began, so its node set differs from the one-point-at-a-time tree; what
-must agree is what the hypotheses are for (Sec. III-A): the reachable free
-space is covered as well (every traversable cell reachable from the start
-lies within one voxel diagonal of a hypothesis as often), about as many
+The GPU sampler searches the nearest nodes of a sub-batch of points at once
+and then resolves the sub-batch in sample order, so it must grow exactly the
+tree that Algorithm 1 grows one point at a time from the same random points
+in float32: the representatives, the rounds and the tree size are compared
+bit for bit with the serial float32 program (tests/rrt_f32.py).  Against the
+serial generator that builds the workloads' hypotheses (other random points),
+what must agree is what the hypotheses are for (Sec. III-A): the reachable
+free space is covered as well (every traversable cell reachable from the
+start lies within one voxel diagonal of a hypothesis as often), about as many
 hypotheses come out, each on a traversable cell, at most one per voxel of
 side rho, and a seed gives the same set every time.
 """
@@ -45,12 +49,41 @@ def coverage(xy, clr, p0, radius):
 
 
 def scene(which):
-    g = workloads.make_room(1000) if which == "room" else workloads.make_office(1001)[:256, :256]
+    g = {"room": lambda: workloads.make_room(1000),
+         "office": lambda: workloads.make_office(1001)[:256, :256],
+         "office512": lambda: workloads.make_office(1001)[:512, :512]}[which]()
     clr = workloads.clearance_table(g, RES)
     p0 = workloads.free_start(g, RES, R_ROBOT, 7, clr)
-    n_target = 200 if which == "room" else 600
+    n_target = {"room": 200, "office": 600, "office512": 2000}[which]
     rho = math.sqrt(float((clr >= R_ROBOT).sum()) * RES * RES / (1.1 * n_target))
     return g, clr, p0, rho
+
+
+@pytest.mark.parametrize("which,seed", [("room", 7), ("room", 123), ("office", 7), ("office512", 7)])
+def test_gpu_rrt_is_the_serial_tree(relo, which, seed):
+    import torch
+    from rrt_f32 import serial_rrt
+    g, clr, p0, rho = scene(which)
+    want, want_rounds, want_nodes = serial_rrt(clr, RES, p0, rho, 0.6, R_ROBOT, 2, seed)
+    ctx = relo.Relo()
+    xy_d, rounds, nodes = ctx.rrt_hypotheses(torch.tensor(clr, device="cuda"), RES, p0, rho, 0.6, R_ROBOT, 2,
+                                             seed=seed)
+    ctx.close()
+    assert (rounds, nodes) == (want_rounds, want_nodes)
+    assert np.array_equal(xy_d.cpu().numpy(), want)
+
+
+def test_gpu_rrt_node_cap_ends_the_tree_like_the_serial_program(relo):
+    import torch
+    from rrt_f32 import serial_rrt
+    g, clr, p0, rho = scene("room")
+    want, want_rounds, want_nodes = serial_rrt(clr, RES, p0, rho, 0.6, R_ROBOT, 2, 7, node_cap=300)
+    ctx = relo.Relo()
+    xy_d, rounds, nodes = ctx.rrt_hypotheses(torch.tensor(clr, device="cuda"), RES, p0, rho, 0.6, R_ROBOT, 2,
+                                             seed=7, node_cap=300)
+    ctx.close()
+    assert nodes == want_nodes == 300 and rounds == want_rounds
+    assert np.array_equal(xy_d.cpu().numpy(), want)
 
 
 @pytest.mark.parametrize("which", ["room", "office"])
