@@ -40,7 +40,7 @@ ROOFLINE_STAGES = ["raycast", "smad", "tam"]   # kernels timed inside the timed 
 CONFIG_INDEX = 1
 WORKLOAD = ("office 1024x1024 @0.05 m, 5000 RRT hypotheses x 360 orientations, 1081-beam 270-deg noisy scan "
             "(N_s 1440), TAM on SMAD top 256 (all batches scored)")
-OPS_PER_DDA_STEP = 13     # integer operations one ray-cast step needs (ray-cast roofline)
+OPS_PER_DDA_STEP = 13     # integer operations of one DDA cell step: the unit of the ray cast's ALU roofline
 L2_FLUSH_BYTES = 256 << 20
 
 

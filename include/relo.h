@@ -188,7 +188,7 @@ int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float 
 int relo_poll(relo_ctx *ctx, int64_t ticket, relo_result *out, double *latency_s);
 int relo_serve_stop(relo_ctx *ctx);
 
-/* A batch of independent relocalizations (configs with many requests, and
+/* A batch of independent relocalizations (workloads with many requests, and
  * the served form): each request names a loaded map (with its hypotheses), a
  * scan and its sensor geometry; maps, beam counts, hypothesis counts and FoVs
  * may all differ.  Every stage runs once for the whole batch: one launch per

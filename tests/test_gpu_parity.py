@@ -4,8 +4,10 @@ Bit-exact: EDT d2, clamped field and occupancy; synthesized ranges and hit
 cells; SMAD numerators and minimising shifts; the SMAD survivor list; the
 per-batch local top-k (up to TAM ties); counters.  Floating point: every TAM
 score within 1e-5 relative of the FP64 oracle (the float32 epilogue's error
-budget is about 1e-6, derived in the design doc's tolerance section); the selected
-pose identical unless the oracle scores the two candidates within 1e-5.
+budget is about 1.5e-6: float32 table entries, a per-lane then shuffle-tree
+top-k sum, and a cube root that divides the product's relative error by 3);
+the selected pose identical unless the oracle scores the two candidates
+within 1e-5.
 """
 import math
 
