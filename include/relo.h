@@ -73,9 +73,13 @@ typedef struct relo_params {
     int32_t ray_tables;                                /* 1 (default): trace rays tile by tile with per-direction
                                                           tables built once per (N_s, max_range); 0: step cell by
                                                           cell.  Same cells and ranges either way. */
-    int32_t coarse_metric;                             /* ranking metric: RELO_COARSE_SMAD (default, Eq. 16-20) or
+    int32_t coarse_metric;                             /* ranking metric: RELO_COARSE_SMAD (default, Eq. 16-20),
                                                           RELO_COARSE_CAER (Eq. 21, Remark 5: the beam-wise mean
-                                                          absolute range error over the same orientations) */
+                                                          absolute range error over the same orientations) or
+                                                          RELO_COARSE_SMAD_DIRECT (SMAD with every window sum of
+                                                          Eq. 18 added up position by position, without the prefix
+                                                          sums of Eq. 17: the Table II ablation; same results, more
+                                                          work; resident window tables are not used for it) */
     int32_t fine_metric;                               /* scoring metric: RELO_FINE_TAM (default, Eq. 31),
                                                           RELO_FINE_TAM_MEAN (Eq. 34), RELO_FINE_BASELINE (Eq. 33)
                                                           or RELO_FINE_LF (Eq. 32, a sum of log-likelihoods, so
@@ -90,6 +94,7 @@ typedef struct relo_params {
 
 #define RELO_COARSE_SMAD 0
 #define RELO_COARSE_CAER 1
+#define RELO_COARSE_SMAD_DIRECT 2
 #define RELO_FINE_TAM 0
 #define RELO_FINE_TAM_MEAN 1
 #define RELO_FINE_BASELINE 2

@@ -274,8 +274,9 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
     if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
     if (!(p.max_range > 0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
     if (p.scan_cache_bytes < 0) return fail(ctx, RELO_E_INVALID_ARG, "scan_cache_bytes must be >= 0");
-    if (p.coarse_metric < RELO_COARSE_SMAD || p.coarse_metric > RELO_COARSE_CAER)
-        return fail(ctx, RELO_E_INVALID_ARG, "coarse_metric must be RELO_COARSE_SMAD or RELO_COARSE_CAER");
+    if (p.coarse_metric < RELO_COARSE_SMAD || p.coarse_metric > RELO_COARSE_SMAD_DIRECT)
+        return fail(ctx, RELO_E_INVALID_ARG,
+                    "coarse_metric must be RELO_COARSE_SMAD, RELO_COARSE_CAER or RELO_COARSE_SMAD_DIRECT");
     if (p.fine_metric < RELO_FINE_TAM || p.fine_metric > RELO_FINE_LF)
         return fail(ctx, RELO_E_INVALID_ARG, "fine_metric must be one of RELO_FINE_TAM .. RELO_FINE_LF");
     if (p.icp_iters < 0 || p.icp_iters > 1000) return fail(ctx, RELO_E_INVALID_ARG, "icp_iters must be in [0, 1000]");
@@ -1131,7 +1132,12 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         CK(timed_on(ctx, st, 2, 1, [&] { return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st); }),
            "ray cast");
     if (total_smad > 0)
-        CK(timed_on(ctx, st, 6, 1, [&] { return launch_smad(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st); }),
+        CK(timed_on(ctx, st, 6, 1,
+                    [&] {
+                        return p.coarse_metric == RELO_COARSE_SMAD_DIRECT
+                                   ? launch_smad_direct(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st)
+                                   : launch_smad(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st);
+                    }),
            "SMAD");
     if (total_build > 0) {
         CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_build(rq, R, total_build, max_ns_pad, max_nm, st); }),

@@ -153,12 +153,16 @@ def test_synth_scans_bit_exact(relo, workload, cfg, n_check):
 # ------------------------------------------------------------------------------------------
 
 def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95, n_skip=1, sample_tam=None,
-              d_max=2.0, coarse=0, fine=0):
+              d_max=2.0, coarse=0, fine=0, gpu_coarse=None):
+    """The whole path against the oracle; gpu_coarse (default: coarse) is the
+    library's ranking-metric code where it differs from the oracle's (the
+    direct-window-sum SMAD is the oracle's SMAD, code 0)."""
     prm = oracle.Params(n_orient=wl.n_orient, topk=K, batch=batch, local_topk=local_topk, tau=tau,
                         n_skip_beam=n_skip, d_max=d_max, coarse=coarse, fine=fine)
     ctx, mid, got = run(relo, wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, n_orient=wl.n_orient,
                         topk=K, batch=batch, local_topk=local_topk, tau=tau, early_stop=int(early_stop),
-                        n_skip_beam=n_skip, d_max=d_max, coarse_metric=coarse, fine_metric=fine)
+                        n_skip_beam=n_skip, d_max=d_max, coarse_metric=coarse if gpu_coarse is None else gpu_coarse,
+                        fine_metric=fine)
     pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
     Kc = min(K, len(wl.hyps))
     B = min(batch, Kc)
@@ -267,6 +271,33 @@ def test_caer_panoramic_and_fine_metric_together(relo):
                                                              early_stop=True, tau=0.5)
     assert pl["panoramic"] and (st["m"] == 0).all()
     ctx.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_smad_by_direct_window_sums_matches_oracle(relo, workload, cfg):
+    """SMAD with every Eq. 18 window sum added up position by position (no
+    Eq. 17 prefix sums, the Table II ablation): numerators, minimising m and
+    the survivor list bit-exact against the oracle, whose SMAD is that form;
+    the selected pose as with the prefix sums."""
+    wl = workload(cfg)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, coarse=0, gpu_coarse=2,
+                                                             sample_tam=None if cfg == 0 else 6)
+    ctx.close()
+    ctx2, _, ref = run(relo, wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, n_orient=wl.n_orient,
+                       topk=wl.topk, early_stop=0)
+    assert (got.hyp, got.m, got.smad_num) == (ref.hyp, ref.m, ref.smad_num) and got.tam == ref.tam
+    ctx2.close()
+
+
+def test_smad_by_direct_window_sums_panoramic_and_ragged(relo):
+    """The direct form on a full-circle scan (Eq. 20: m = 0 only) and on a
+    partial scan whose FoV wraps past beam 0, with early termination."""
+    for n_beams, ns in ((120, 120), (90, 120)):
+        wl = small_case(n_beams=n_beams, ns=ns)
+        ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, 12, batch=4, local_topk=2, coarse=0,
+                                                                 gpu_coarse=2, early_stop=True, tau=0.5)
+        assert pl["panoramic"] == (n_beams == ns)
+        ctx.close()
 
 
 def icp_case(relo, g, hyps, z, ang, max_range, early, **kw):
