@@ -79,7 +79,11 @@ typedef struct relo_params {
                                                           RELO_COARSE_SMAD_DIRECT (SMAD with every window sum of
                                                           Eq. 18 added up position by position, without the prefix
                                                           sums of Eq. 17: the Table II ablation; same results, more
-                                                          work; resident window tables are not used for it) */
+                                                          work; resident window tables are not used for it) or
+                                                          RELO_COARSE_NONE (no coarse ranking, Table II's arm
+                                                          without SMAD ordering: no rays are cast, every numerator
+                                                          is 0 at m = 0, so the survivors are the first topk
+                                                          hypotheses in the order they were set) */
     int32_t fine_metric;                               /* scoring metric: RELO_FINE_TAM (default, Eq. 31),
                                                           RELO_FINE_TAM_MEAN (Eq. 34), RELO_FINE_BASELINE (Eq. 33)
                                                           or RELO_FINE_LF (Eq. 32, a sum of log-likelihoods, so
@@ -95,6 +99,7 @@ typedef struct relo_params {
 #define RELO_COARSE_SMAD 0
 #define RELO_COARSE_CAER 1
 #define RELO_COARSE_SMAD_DIRECT 2
+#define RELO_COARSE_NONE 3
 #define RELO_FINE_TAM 0
 #define RELO_FINE_TAM_MEAN 1
 #define RELO_FINE_BASELINE 2

@@ -129,7 +129,7 @@ class Params:
     local_topk: int = 20
     tau: float = 0.95
     n_skip_beam: int = 1
-    coarse: int = 0     # ranking metric: 0 SMAD (Eq. 16-20), 1 CAER (Eq. 21)
+    coarse: int = 0     # ranking metric: 0 SMAD (Eq. 16-20), 1 CAER (Eq. 21), 3 none (Table II, no ordering)
     fine: int = 0       # scoring metric: 0 TAM (Eq. 31), 1 TAM_mean (Eq. 34), 2 wp_baseline (Eq. 33), 3 wp_LF (Eq. 32)
 
 
@@ -268,7 +268,12 @@ def caer(grid, hyps: np.ndarray, pl: dict, n_threads: int = 0):
 
 
 def coarse(grid, hyps: np.ndarray, pl: dict, prm: "Params", n_threads: int = 0):
-    """The ranking metric prm.coarse selects: SMAD (0) or CAER (1)."""
+    """The ranking metric prm.coarse selects: SMAD (0), CAER (1), or none (3:
+    the Table II arm without SMAD ordering, where TAM takes the hypotheses in
+    their own order: every numerator 0 at m = 0, so rank() keeps the index
+    order)."""
+    if prm.coarse == 3:
+        return np.zeros(len(hyps), np.int64), np.zeros(len(hyps), np.int32)
     return caer(grid, hyps, pl, n_threads) if prm.coarse == 1 else smad(grid, hyps, pl, n_threads)
 
 
@@ -461,5 +466,6 @@ def relocalize(grid, res: float, hyps: np.ndarray, ranges, angles, max_range: fl
     return dict(hyp=h, m=m, tam=T_best, x=pose[0], y=pose[1], theta=theta,
                 smad_num=int(num[h]), smad=float(smad_metres(num[h], pl)), survivors=surv, smad_nums=num,
                 smad_m=m_smad, per_hyp=per_hyp, batches=batches, n_batches=len(batches),
-                n_smad_evals=len(hyps) * (1 if pl["panoramic"] else pl["n_orient"]), n_tam_evals=n_tam,
+                n_smad_evals=0 if prm.coarse == 3 else len(hyps) * (1 if pl["panoramic"] else pl["n_orient"]),
+                n_tam_evals=n_tam,
                 plan=pl)

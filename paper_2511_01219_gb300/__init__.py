@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
         ("coarse_metric", ctypes.c_int32), ("fine_metric", ctypes.c_int32), ("icp_iters", ctypes.c_int32),
     ]
 
-COARSE_SMAD, COARSE_CAER, COARSE_SMAD_DIRECT = 0, 1, 2
+COARSE_SMAD, COARSE_CAER, COARSE_SMAD_DIRECT, COARSE_NONE = 0, 1, 2, 3
 FINE_TAM, FINE_TAM_MEAN, FINE_BASELINE, FINE_LF = 0, 1, 2, 3
 
 

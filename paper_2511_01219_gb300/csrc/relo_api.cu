@@ -274,9 +274,8 @@ int check_params(relo_ctx *ctx, const relo_params &p) {
     if (p.n_orient < 0) return fail(ctx, RELO_E_INVALID_ARG, "n_orient must be >= 0");
     if (!(p.max_range > 0)) return fail(ctx, RELO_E_INVALID_ARG, "max_range must be positive");
     if (p.scan_cache_bytes < 0) return fail(ctx, RELO_E_INVALID_ARG, "scan_cache_bytes must be >= 0");
-    if (p.coarse_metric < RELO_COARSE_SMAD || p.coarse_metric > RELO_COARSE_SMAD_DIRECT)
-        return fail(ctx, RELO_E_INVALID_ARG,
-                    "coarse_metric must be RELO_COARSE_SMAD, RELO_COARSE_CAER or RELO_COARSE_SMAD_DIRECT");
+    if (p.coarse_metric < RELO_COARSE_SMAD || p.coarse_metric > RELO_COARSE_NONE)
+        return fail(ctx, RELO_E_INVALID_ARG, "coarse_metric must be one of RELO_COARSE_SMAD .. RELO_COARSE_NONE");
     if (p.fine_metric < RELO_FINE_TAM || p.fine_metric > RELO_FINE_LF)
         return fail(ctx, RELO_E_INVALID_ARG, "fine_metric must be one of RELO_FINE_TAM .. RELO_FINE_LF");
     if (p.icp_iters < 0 || p.icp_iters > 1000) return fail(ctx, RELO_E_INVALID_ARG, "icp_iters must be in [0, 1000]");
@@ -859,8 +858,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     const relo_params &p = ctx->p;
     ++ctx->batch_seq;
     cudaStream_t st = sl.stream;
+    const bool cast = p.coarse_metric != RELO_COARSE_NONE;   // without a coarse ranking no rays are cast
     std::vector<RayTab *> rtab((size_t)R, nullptr);
-    for (int r = 0; r < R; ++r) rtab[r] = ray_tables_for(ctx, *pr[r].P, pr[r].lim, st);
+    for (int r = 0; r < R && cast; ++r) rtab[r] = ray_tables_for(ctx, *pr[r].P, pr[r].lim, st);
     // Resident synthesized scans: read a table stored by an earlier launch, or
     // store a new one (one writer per table; other requests of this batch
     // with the same geometry cast into their scratch).  Tables this batch
@@ -881,7 +881,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             }
         }
     } created{ctx, {}, false};
-    if (p.scan_cache_bytes > 0) {
+    if (p.scan_cache_bytes > 0 && cast) {
         for (int r = 0; r < R; ++r) {
             MapSlot &m = *pr[r].m;
             ScanTable *t = find_table(m, pr[r].P->ns, pr[r].lim);
@@ -957,7 +957,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
                  align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
                  align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
         if (mode[r] == kScanCast) total += align_up(4ull * nh * q.P->ns);   // the request's synthesized ranges
-        if (mode[r] != kScanRead) total_chunks += (long long)nh * (((q.P->ns + 31) & ~31) >> 5);
+        if (mode[r] != kScanRead && cast) total_chunks += (long long)nh * (((q.P->ns + 31) & ~31) >> 5);
         if ((long long)total_hyp + nh > (1ll << 30) || total_chunks > (1ll << 31) - 1)
             return fail(ctx, RELO_E_INVALID_ARG, "batch too large");
         total_hyp += nh;
@@ -1019,7 +1019,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.L = p.local_topk;
         d.early_stop = p.early_stop;
         d.tau = p.tau;
-        d.n_smad_evals = (long long)m.n_hyp * P.n_m;
+        d.n_smad_evals = cast ? (long long)m.n_hyp * P.n_m : 0;
         unsigned char *a = sl.arena + off[r];
         auto take = [&a](size_t bytes) {
             unsigned char *x = a;
@@ -1134,6 +1134,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     if (total_smad > 0)
         CK(timed_on(ctx, st, 6, 1,
                     [&] {
+                        if (!cast) return launch_rank_by_index(rq, R, total_smad, ctx->n_sm, st);
                         return p.coarse_metric == RELO_COARSE_SMAD_DIRECT
                                    ? launch_smad_direct(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st)
                                    : launch_smad(rq, R, total_smad, max_ns_pad, sl.bs, ctx->n_sm, st);

@@ -265,6 +265,8 @@ cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pa
 // the same SMAD by direct window sums, without the prefix sums of Eq. 17 (the Table II ablation)
 cudaError_t launch_smad_direct(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
                                cudaStream_t s);
+// no coarse ranking: numerator 0 and m = 0 for every hypothesis of the batch (Table II's arm without SMAD ordering)
+cudaError_t launch_rank_by_index(const ReqDesc *reqs, int R, int total_hyp, int n_sm, cudaStream_t s);
 // SMAD of the window-build requests' hypotheses, storing their sorted window keys
 cudaError_t launch_win_build(const ReqDesc *reqs, int R, int total, int max_ns_pad, int max_nm, cudaStream_t s);
 // SMAD of the window-read requests' hypotheses by search in their window keys

@@ -1,5 +1,7 @@
-// SMAD by direct window sums: the "without prefix sums" arm of Table II.
+// The ablation arms of Table II: SMAD by direct window sums (without prefix
+// sums), and no coarse ranking at all (without SMAD ordering).
 //
+// SMAD by direct window sums.
 // The numerator |sum_real - W_m| and its minimum over Theta (Eq. 18-20) are
 // the prefix-sum form's, with W_m summed position by position over the FoV
 // intervals for every m instead of read from the cyclic prefix sums of Eq.
@@ -81,7 +83,39 @@ __global__ void __launch_bounds__(kDirectWarps * 32) k_smad_direct(const ReqDesc
     }
 }
 
+// No coarse ranking: numerator 0 and m = 0 for every hypothesis, so the
+// top-K (ordered by numerator, then index) keeps the hypotheses in the order
+// they were set.  One thread per hypothesis slot of the batch.
+__global__ void __launch_bounds__(256) k_rank_by_index(const ReqDesc *__restrict__ reqs, int R, int total_hyp) {
+    __shared__ int s_base[kMaxBatchRequests + 1];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = reqs[r].hyp_base;
+    if (threadIdx.x == 0) s_base[R] = total_hyp;
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_hyp; g += gridDim.x * blockDim.x) {
+        int lo = 0, hi = R - 1;   // last request whose base <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_base[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDesc &d = reqs[lo];
+        const int h = g - s_base[lo];
+        d.keys[h] = (unsigned long long)h;   // numerator 0 << kHypBits | h
+        d.smad_num[h] = 0;
+        d.smad_m[h] = 0;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_rank_by_index(const ReqDesc *reqs, int R, int total_hyp, int n_sm, cudaStream_t s) {
+    if (R < 1 || R > kMaxBatchRequests || n_sm < 1) return cudaErrorInvalidValue;
+    long long grid = ((long long)total_hyp + 255) / 256;
+    if (grid > 4ll * n_sm) grid = 4ll * n_sm;
+    if (grid < 1) grid = 1;
+    k_rank_by_index<<<(int)grid, 256, 0, s>>>(reqs, R, total_hyp);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_smad_direct(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
                                cudaStream_t s) {

@@ -196,7 +196,7 @@ def full_case(relo, wl, K, early_stop=False, batch=200, local_topk=20, tau=0.95,
             assert abs(T_or[r_i, q_gpu] - T_or[r_i, q_or]) <= RTOL * T_or[r_i, q_or]
     assert got.status == 0 and got.n_batches == info[7]
     assert got.n_tam_evals == n_scored * pl["n_orient"]
-    assert got.n_smad_evals == len(wl.hyps) * (1 if pl["panoramic"] else pl["n_orient"])
+    assert got.n_smad_evals == (0 if coarse == 3 else len(wl.hyps) * (1 if pl["panoramic"] else pl["n_orient"]))
     return ctx, got, st, pl, prm, d2, surv, rows, T_or
 
 
@@ -298,6 +298,27 @@ def test_smad_by_direct_window_sums_panoramic_and_ragged(relo):
                                                                  gpu_coarse=2, early_stop=True, tau=0.5)
         assert pl["panoramic"] == (n_beams == ns)
         ctx.close()
+
+
+@pytest.mark.parametrize("early,tau", [(False, 0.95), (True, 0.5)])
+def test_no_ordering_arm_matches_oracle(relo, workload, early, tau):
+    """Table II's arm without SMAD ordering: zero numerators at m = 0, every
+    hypothesis a survivor in its own order, then TAM batch by batch with the
+    local top-k and early termination as the oracle takes them."""
+    wl = workload(0)
+    n = len(wl.hyps)
+    ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, n, batch=50, local_topk=5, coarse=3,
+                                                             early_stop=early, tau=tau)
+    assert (st["num"] == 0).all() and (st["m"] == 0).all()
+    assert np.array_equal(st["surv"], np.arange(n))
+    want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
+                             early_stop=early)
+    assert got.n_batches == want["n_batches"] and (early or got.n_batches == -(-n // 50))
+
+    def T_at(h, m):
+        return float(oracle.tam(wl.grid, np.array([wl.hyps[h]]), np.array([m]), pl, prm, wl.res, d2)[0])
+    check_pose(got, want["hyp"], want["m"], T_at)
+    ctx.close()
 
 
 def icp_case(relo, g, hyps, z, ang, max_range, early, **kw):

@@ -710,3 +710,27 @@ def test_relocalize_early_termination_and_batches():
     assert r2["n_batches"] == 4 and r2["n_tam_evals"] == 20 * n_orient
     best = max((v[1], -k) for k, v in r2["per_hyp"].items())
     assert math.isclose(r2["tam"], best[0])
+
+
+def test_no_ordering_arm_scores_the_hypotheses_in_their_own_order():
+    """Table II's arm without SMAD ordering: zero numerators at m = 0, so the
+    survivors are the hypotheses in index order.  Scored in full (K = N_h),
+    it selects the same best TAM score as the SMAD-ordered run over every
+    hypothesis (the set is the same, only the batch order differs); with
+    early termination its first batch is the first `batch` hypotheses."""
+    g, hyps, ang, n_orient = room_case(20)
+    n = len(hyps)
+    z = np.random.default_rng(2).uniform(0.2, 1.5, len(ang)).astype(np.float32)
+    none = oracle.Params(n_orient=n_orient, topk=n, batch=6, local_topk=3, tau=-1.0, coarse=3)
+    pl = oracle.plan(z, ang, 5.0, RES, none)
+    num, mm = oracle.coarse(g, hyps, pl, none)
+    assert (num == 0).all() and (mm == 0).all()
+    r = oracle.relocalize(g, RES, hyps, z, ang, 5.0, none, early_stop=False)
+    assert np.array_equal(r["survivors"], np.arange(n)) and r["n_smad_evals"] == 0
+    ordered = oracle.relocalize(g, RES, hyps, z, ang, 5.0,
+                                oracle.Params(n_orient=n_orient, topk=n, batch=6, local_topk=3, tau=-1.0),
+                                early_stop=False)
+    assert not np.array_equal(ordered["survivors"], r["survivors"])   # SMAD does reorder this case
+    assert r["tam"] == ordered["tam"] and r["n_tam_evals"] == ordered["n_tam_evals"] == n * n_orient
+    first = oracle.relocalize(g, RES, hyps, z, ang, 5.0, none)      # tau = -1: stop after the first batch
+    assert first["n_batches"] == 1 and sorted(first["per_hyp"]) == list(range(6))
