@@ -71,3 +71,24 @@ def test_missing_library_fails_loudly(monkeypatch, relo):
     monkeypatch.setattr(relo, "_lib", None)
     with pytest.raises(ImportError):
         relo.lib()
+
+
+def test_python_constants_match_the_header_defines(relo):
+    """Every RELO_* integer define has the same value in the binding (status
+    codes, ranking and scoring metric codes, stage ids)."""
+    text = open(HEADER).read()
+    defines = {m.group(1): int(m.group(2)) for m in
+               re.finditer(r"#define RELO_([A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)}
+    assert len(defines) >= 25
+    checked = 0
+    for name, value in defines.items():
+        if name == "N_STAGES":
+            assert len(relo.STAGES) == value
+        elif hasattr(relo, name):
+            assert getattr(relo, name) == value, name
+        else:
+            continue
+        checked += 1
+    skipped = sorted(n for n in defines if n != "N_STAGES" and not hasattr(relo, n))
+    assert skipped == [], skipped
+    assert checked == len(defines)
