@@ -734,3 +734,19 @@ def test_no_ordering_arm_scores_the_hypotheses_in_their_own_order():
     assert r["tam"] == ordered["tam"] and r["n_tam_evals"] == ordered["n_tam_evals"] == n * n_orient
     first = oracle.relocalize(g, RES, hyps, z, ang, 5.0, none)      # tau = -1: stop after the first batch
     assert first["n_batches"] == 1 and sorted(first["per_hyp"]) == list(range(6))
+
+
+def test_panoramic_grid_size_follows_eq14_reading():
+    """N_s = N_orient q with q the rounded N 360 / (FoV N_orient) clamped so
+    that N <= N_s <= 2N (Eq. 14 needs an integer N_s): 504 for 360 beams over
+    270 deg at 72 orientations, 1440 for 1081 beams over 270 deg at 360 and
+    for 1440 beams over 360 deg at 720."""
+    assert workloads.choose_ns(360, 270.0, 72) == 504
+    assert workloads.choose_ns(1081, 270.0, 360) == 1440
+    assert workloads.choose_ns(1440, 360.0, 720) == 1440
+    for n in (90, 360, 541, 720, 1081, 1440):
+        for fov in (180.0, 225.0, 270.0, 300.0, 360.0):
+            for n_orient in (36, 72, 360):
+                ns = workloads.choose_ns(n, fov, n_orient)
+                assert ns % n_orient == 0
+                assert n <= ns <= 2 * n or (ns == n_orient * -(-n // n_orient) and ns > 2 * n)
