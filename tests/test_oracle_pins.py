@@ -750,3 +750,22 @@ def test_panoramic_grid_size_follows_eq14_reading():
                 ns = workloads.choose_ns(n, fov, n_orient)
                 assert ns % n_orient == 0
                 assert n <= ns <= 2 * n or (ns == n_orient * -(-n // n_orient) and ns > 2 * n)
+
+
+def test_quantised_endpoints_move_room_scores_less_than_1e4(workload):
+    """The continuous mode as a diagnostic: TAM with the integer endpoint
+    rule (Q16 ranges, Q30 directions, round half up) against TAM with FP64
+    endpoints and floor, at 40 seeded (hypothesis, orientation) poses of the
+    room workload: within 1e-4 relative."""
+    wl = workload(0)
+    prm = oracle.Params(n_orient=wl.n_orient, topk=wl.topk)
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    d2 = oracle.edt(wl.grid)
+    rng = np.random.default_rng(5)
+    sel = rng.choice(len(wl.hyps), 40, replace=False)
+    ms = rng.integers(0, pl["n_orient"], 40) * pl["n_enum"]
+    tq = oracle.tam(wl.grid, wl.hyps[sel], ms, pl, prm, wl.res, d2)
+    poses = [((wl.hyps[h][0] + 0.5) * wl.res, (wl.hyps[h][1] + 0.5) * wl.res, m * 2 * math.pi / pl["ns"])
+             for h, m in zip(sel, ms)]
+    tc = oracle.tam_pose(wl.grid, poses, pl, prm, wl.res, d2)
+    assert np.allclose(tq, tc, rtol=1e-4, atol=0)
