@@ -564,18 +564,16 @@ int oracle_rigid_fit(const double *w, const double *c, int n, double *phi, doubl
 }
 
 /*
- * A beam's world point and cell at pose (x, y) with ct = cos(theta), st =
- * sin(theta): the sensor-frame point s = (z cos a, z sin a) rotated and moved,
- * wx = x + (ct sx - st sy), wy = y + (st sx + ct sy), each product and sum
- * rounded on its own; its cell is floor(w * (1 / res)).
+ * A beam's world point at pose (x, y, theta): the point at range z along the
+ * world direction theta + a, w = (x + z cos(theta + a), y + z sin(theta + a)),
+ * and the cell that contains it, (floor(w_x / res), floor(w_y / res)).
  */
-static void world_point(double x, double y, double ct, double st, double sx, double sy, double inv_res, double *wx,
-                        double *wy, int *cx, int *cy) {
-    double ax = ct * sx, bx = st * sy, ay = st * sx, by = ct * sy;
-    *wx = x + (ax - bx);
-    *wy = y + (ay + by);
-    *cx = (int)floor(*wx * inv_res);
-    *cy = (int)floor(*wy * inv_res);
+static void world_point(double x, double y, double theta, double z, double a, double res, double *wx, double *wy,
+                        int *cx, int *cy) {
+    *wx = x + z * cos(theta + a);
+    *wy = y + z * sin(theta + a);
+    *cx = (int)floor(*wx / res);
+    *cy = (int)floor(*wy / res);
 }
 
 /*
@@ -592,18 +590,13 @@ int oracle_icp(const int8_t *grid, const int64_t *d2tab, int W, int H, double re
                const double *a, int n, int iters, double *pose) {
     double *w = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
     double *c = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
-    double *sx = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
-    double *sy = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
-    for (int i = 0; i < n; ++i) { sx[i] = z[i] * cos(a[i]); sy[i] = z[i] * sin(a[i]); }
-    const double inv_res = 1.0 / res;
     int it = 0;
     for (; it < iters; ++it) {
         int k = 0;
-        const double ct = cos(pose[2]), st = sin(pose[2]);
         for (int i = 0; i < n; ++i) {
             double wx, wy;
             int cx, cy, ox, oy;
-            world_point(pose[0], pose[1], ct, st, sx[i], sy[i], inv_res, &wx, &wy, &cx, &cy);
+            world_point(pose[0], pose[1], pose[2], z[i], a[i], res, &wx, &wy, &cx, &cy);
             if (!oracle_nearest_occupied(grid, d2tab, W, H, cx, cy, C, &ox, &oy)) continue;
             w[2 * k] = wx; w[2 * k + 1] = wy;
             c[2 * k] = (ox + 0.5) * res; c[2 * k + 1] = (oy + 0.5) * res;
@@ -619,8 +612,6 @@ int oracle_icp(const int8_t *grid, const int64_t *d2tab, int W, int H, double re
     }
     free(w);
     free(c);
-    free(sx);
-    free(sy);
     return it;
 }
 
@@ -645,11 +636,10 @@ void oracle_tam_pose(const int8_t *grid, const int64_t *d2tab, int W, int H, con
         double *dist = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
         double *ell = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
         const double *ps = poses + 3 * q;
-        const double ct = cos(ps[2]), st = sin(ps[2]), inv_res = 1.0 / p.res;
         for (int i = 0; i < n; ++i) {
             double wx, wy;
             int cx, cy;
-            world_point(ps[0], ps[1], ct, st, z[i] * cos(a[i]), z[i] * sin(a[i]), inv_res, &wx, &wy, &cx, &cy);
+            world_point(ps[0], ps[1], ps[2], z[i], a[i], p.res, &wx, &wy, &cx, &cy);
             int64_t ex = cx, ey = cy;
             int64_t d2;
             if (ex < 0 || ey < 0 || ex >= W || ey >= H) d2 = C;

@@ -321,7 +321,23 @@ def test_no_ordering_arm_matches_oracle(relo, workload, early, tau):
     ctx.close()
 
 
+def edge_margin(pl, pose, res=RES):
+    """Smallest distance, in cells, from a valid beam's world point at a
+    continuous pose (x + z cos(theta + a), y + z sin(theta + a)) to a cell
+    edge.  Where it is tiny the containing cell depends on rounding, and two
+    correct programs may put the point in either neighbour."""
+    z, a = oracle.scan_points(pl, res)
+    w = np.concatenate([(pose[0] + z * np.cos(pose[2] + a)) / res, (pose[1] + z * np.sin(pose[2] + a)) / res])
+    f = w - np.floor(w)
+    return float(np.minimum(f, 1.0 - f).min())
+
+
 def icp_case(relo, g, hyps, z, ang, max_range, early, **kw):
+    """ICP (10 iterations) of every local top-k pose through the library
+    against the oracle's plain arithmetic.  The scans are noisy, so no beam
+    ends on a cell edge at either refined pose; the test checks that margin,
+    without which the two cell assignments (and with them the pairs and the
+    scores) could legitimately differ."""
     prm = oracle.Params(n_orient=kw.get("n_orient", 40), topk=kw.get("topk", 12), batch=kw.get("batch", 6),
                         local_topk=kw.get("local_topk", 3), tau=kw.get("tau", 0.95))
     d2 = oracle.edt(g)
@@ -330,6 +346,9 @@ def icp_case(relo, g, hyps, z, ang, max_range, early, **kw):
                         local_topk=prm.local_topk, tau=prm.tau, early_stop=int(early), icp_iters=10)
     ctx.close()
     assert got.status == 0 and got.n_batches == want["n_batches"]
+    pl = want["plan"]
+    assert edge_margin(pl, (want["x"], want["y"], want["theta"])) > 1e-6
+    assert edge_margin(pl, (got.x, got.y, got.theta)) > 1e-6
     if (got.hyp, got.m) == (want["hyp"], want["m"]):
         dth = math.remainder(got.theta - want["theta"], 2 * math.pi)
         assert abs(got.x - want["x"]) <= 1e-6 and abs(got.y - want["y"]) <= 1e-6 and abs(dth) <= 1e-6
@@ -342,14 +361,15 @@ def test_icp_refinement_matches_oracle(relo, early):
     """ICP of every local top-k pose (10 iterations) and its re-evaluation at
     the refined continuous pose: the selected hypothesis, orientation and
     refined pose equal the oracle's (1e-6 m and rad), the re-evaluated score
-    within 1e-5; a scan rendered between cells, with and without early
-    termination."""
+    within 1e-5; a scan rendered between cells with 5 mm range noise, with and
+    without early termination."""
     g = workloads.make_room(2, n=40, n_boxes=4)
     free = np.argwhere(g == 0)[:, ::-1]
     hyps = free[np.random.default_rng(2).choice(len(free), 25, replace=False)].astype(np.int32)
     ang = workloads.beam_angles(90, 120)
     true = ((hyps[5][0] + 0.8) * RES, (hyps[5][1] + 0.3) * RES, 0.5)
-    z = workloads.render_scan(g, RES, true, ang, 6.0)
+    z = workloads.add_noise(workloads.render_scan(g, RES, true, ang, 6.0), 6.0, 5, sigma=0.005, drop_frac=0.0,
+                            short_frac=0.0)
     got, want = icp_case(relo, g, hyps, z, ang, 6.0, early, tau=0.5)
     plain = oracle.relocalize(g, RES, hyps, z, ang, 6.0, oracle.Params(n_orient=40, topk=12, batch=6, local_topk=3,
                                                                        tau=0.5), early_stop=early)
@@ -357,8 +377,11 @@ def test_icp_refinement_matches_oracle(relo, early):
 
 
 def test_icp_on_the_room_workload(relo, workload):
+    """The room workload's scan (noise-free by definition) with 5 mm range
+    noise added, so that no endpoint sits on a cell edge."""
     wl = workload(0)
-    icp_case(relo, wl.grid, wl.hyps, wl.ranges, wl.angles, wl.max_range, False, n_orient=wl.n_orient, topk=16,
+    z = workloads.add_noise(wl.ranges, wl.max_range, 6, sigma=0.005, drop_frac=0.0, short_frac=0.0)
+    icp_case(relo, wl.grid, wl.hyps, z, wl.angles, wl.max_range, False, n_orient=wl.n_orient, topk=16,
              batch=8, local_topk=4)
 
 
