@@ -325,9 +325,14 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
  * input and the output, and the scratch is a file-scope device array of
  * fixed size (4.5 MiB per device, held until the process exits).
  * Returns RELO_E_INVALID_ARG for null pointers or w, h outside [1, 1024],
- * RELO_E_CUDA if a CUDA call fails.  The first call on a device looks up the
- * scratch address with that device current: make it before any stream
- * capture.  Calls share the scratch, so calls that overlap on the GPU race. */
+ * RELO_E_CUDA if a CUDA call or a launch fails, or if a CUDA error from
+ * earlier work is already pending in the calling thread (nothing is then
+ * launched and that error is left pending).  The first call on a device looks
+ * up the scratch address with that device current: make it before any stream
+ * capture.  That address is kept until the process exits, so after
+ * cudaDeviceReset, or any other reset of the device's primary context, do not
+ * call this entry point on that device again in the same process.  Calls
+ * share the scratch, so calls that overlap on the GPU race. */
 int relo_edt_noalloc(const int8_t *grid_dev, int32_t w, int32_t h, int32_t *d2_dev, void *stream);
 
 #ifdef __cplusplus

@@ -18,6 +18,14 @@
 //     process exits.
 //   - The first call on a device looks up the scratch's device address with
 //     that device current; make that first call before any stream capture.
+//     The address is kept for the life of the process: after cudaDeviceReset
+//     (or any reset of the device's primary context) the module, and with it
+//     the scratch, is gone, so do not call this entry point on that device
+//     again in the same process.
+//   - A CUDA error already pending in the calling thread (left by earlier
+//     work) is reported as RELO_E_CUDA before anything is launched, and is
+//     left in place for its owner; each of the three launches is checked on
+//     its own, and a failed launch stops the call.
 //   - All calls on one device share the scratch: calls whose work overlaps on
 //     the GPU (for example on two streams at once) race and give wrong
 //     results.  Each call overwrites every scratch element it reads, so
@@ -137,11 +145,16 @@ extern "C" int relo_edt_noalloc(const int8_t *grid_dev, int32_t w, int32_t h, in
     int32_t *colsq = nullptr;
     int2 *summ = nullptr;
     if (scratch_for_current_device(&colsq, &summ) != cudaSuccess) return RELO_E_CUDA;
+    // an error left by the caller's own earlier work: report it, launch nothing, leave it pending
+    if (cudaPeekAtLastError() != cudaSuccess) return RELO_E_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int S = (h + kNoAllocSegRows - 1) / kNoAllocSegRows;
     const dim3 grid((w + 127) / 128, S);
     k_na_summary<<<grid, 128, 0, s>>>(grid_dev, w, h, summ);
+    if (cudaGetLastError() != cudaSuccess) return RELO_E_CUDA;
     k_na_columns<<<grid, 128, 0, s>>>(grid_dev, w, h, S, summ, colsq);
+    if (cudaGetLastError() != cudaSuccess) return RELO_E_CUDA;
     k_na_rows<<<h, 256, (size_t)w * sizeof(int32_t), s>>>(colsq, w, d2_dev);
-    return cudaGetLastError() == cudaSuccess ? RELO_OK : RELO_E_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return RELO_E_CUDA;
+    return RELO_OK;
 }
