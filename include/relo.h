@@ -335,6 +335,24 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
  * share the scratch, so calls that overlap on the GPU race. */
 int relo_edt_noalloc(const int8_t *grid_dev, int32_t w, int32_t h, int32_t *d2_dev, void *stream);
 
+/* L2 bandwidth probes: the denominators of the scoring kernels' L2 roofline
+ * (the TAM field and the synthesized ranges are L2-resident, so HBM copy
+ * bandwidth does not bound those kernels).  The paper has no counterpart.
+ * relo_probe_l2_stream reads the device buffer buf_dev (bytes: a multiple of
+ * 16; 16-byte aligned; small enough to stay in L2) once untimed to bring it
+ * into L2, then `passes` times with 16-byte loads from every SM, and writes the
+ * device time of those passes (ms) to *ms: bytes * passes / time is the
+ * streaming L2 read rate.  relo_probe_l2_gather first reads the uint16 array
+ * buf_dev of 2^log2_elems elements (log2_elems in [10, 31]) once, then makes
+ * at least `gathers` 2-byte loads at uniformly random positions (eight in
+ * flight per thread), writing the time to *ms and the loads made to
+ * *gathers_done.  Both run on stream (NULL = default), block until done, write
+ * no device memory and allocate none.  RELO_E_INVALID_ARG for null pointers
+ * and bad sizes, RELO_E_CUDA if a CUDA call fails. */
+int relo_probe_l2_stream(const void *buf_dev, int64_t bytes, int32_t passes, void *stream, float *ms);
+int relo_probe_l2_gather(const uint16_t *buf_dev, int32_t log2_elems, int64_t gathers, void *stream, float *ms,
+                         int64_t *gathers_done);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,7 @@ EXPORTED = [
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
     "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask", "relo_rrt_hypotheses_dev",
+    "relo_probe_l2_stream", "relo_probe_l2_gather",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
@@ -120,6 +121,8 @@ def lib() -> ctypes.CDLL:
             "relo_set_profiling_mask": (ctypes.c_int, [P, ctypes.c_uint32]),
             "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
             "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
+            "relo_probe_l2_stream": (ctypes.c_int, [P, I64, I32, P, P]),
+            "relo_probe_l2_gather": (ctypes.c_int, [P, I32, I64, P, P, P]),
             "relo_relocalize_batch": (ctypes.c_int, [P, P, I32, P]),
             "relo_relocalize_batch_dev": (ctypes.c_int, [P, P, I32, P]),
             "relo_serve_start": (ctypes.c_int, [P, I32, I32, I64]),
@@ -412,3 +415,28 @@ class Relo:
 
 def result_from_bytes(b: bytes) -> Result:
     return Result.from_buffer_copy(b)
+
+
+def probe_l2(stream_bytes: int = 32 << 20, passes: int = 50, gather_log2: int = 24, gathers: int = 1 << 30) -> dict:
+    """L2 read rates of this GPU (relo_probe_l2_stream / relo_probe_l2_gather):
+    streaming 16-byte loads over an L2-resident buffer, and uniformly random
+    2-byte loads from an L2-resident uint16 array.  Returns GB/s and gathers/s."""
+    import torch
+    L = lib()
+    buf = torch.zeros(stream_bytes, dtype=torch.uint8, device="cuda")
+    ms = ctypes.c_float(0)
+    s = torch.cuda.current_stream().cuda_stream
+    rc = L.relo_probe_l2_stream(ctypes.c_void_p(buf.data_ptr()), stream_bytes, passes, ctypes.c_void_p(s),
+                                ctypes.byref(ms))
+    if rc != OK:
+        raise ReloError(rc, "relo_probe_l2_stream")
+    stream_gbs = stream_bytes * passes / (ms.value / 1e3) / 1e9
+    arr = torch.randint(0, 1 << 15, (1 << gather_log2,), dtype=torch.int16, device="cuda")
+    done = ctypes.c_int64(0)
+    rc = L.relo_probe_l2_gather(ctypes.c_void_p(arr.data_ptr()), gather_log2, gathers, ctypes.c_void_p(s),
+                                ctypes.byref(ms), ctypes.byref(done))
+    if rc != OK:
+        raise ReloError(rc, "relo_probe_l2_gather")
+    gps = done.value / (ms.value / 1e3)
+    return {"stream_gbs": stream_gbs, "stream_bytes": stream_bytes,
+            "gather_per_s": gps, "gather_2b_gbs": 2.0 * gps / 1e9, "gather_array_bytes": 2 << gather_log2}
