@@ -1,11 +1,12 @@
 #!/usr/bin/env python3
 """Benchmark of the relocalization scoring path on GB300.
 
-One step = one pass of the whole path over the office workload (1024x1024
-grid at 0.05 m, 5000 RRT hypotheses, 1081-beam 270-degree noisy scan, 360
-orientations, TAM on the SMAD top 256): EDT map precompute, scan
-preparation, ray cast + SMAD for every hypothesis, SMAD top-K, batched TAM
-over every orientation of every survivor, orientation argmax, local top-k.
+One step = one pass of the whole path over the warehouse workload (4096x4096
+grid at 0.05 m, 20000 RRT hypotheses, 1440-beam 360-degree noisy scan, 720
+orientations, TAM on the SMAD top 1024; --config 1 takes the office
+workload instead): EDT map precompute, scan preparation, ray cast + SMAD for
+every hypothesis, SMAD top-K, batched TAM over every orientation of every
+survivor, orientation argmax, local top-k.
 
 value: hypothesis x orientation evaluations (SMAD + TAM) per second with all
 inputs resident in HBM; each step is timed with CUDA events on the library's
@@ -13,9 +14,15 @@ stream and L2 is flushed (256 MiB write) before every timed step.
 e2e: the same metric through the host entry points (relo_update_map,
 relo_set_hypotheses, relo_relocalize) from pinned host buffers, host<->device
 copies included, wall-clock per step.
+batched / served: the same line also carries the batched form (64 mixed
+requests per step in one launch per stage) and the served form (Poisson
+arrivals against 8 resident maps: best relocalizations/s at p99 <= 50 ms,
+continuous batching against the one-request-at-a-time pipeline, with and
+without resident tables).
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload, scaled to the same metric.
+--impl reference times the FP64 CPU oracle on the host cores, each step a
+bounded sample of the same workload (its value is the sample's evaluations
+over the sample's measured time, nothing extrapolated).
 """
 from __future__ import annotations
 
@@ -37,10 +44,20 @@ sys.path.insert(0, ROOT)
 METRIC = "hypothesis×orientation evals/s (SMAD+TAM); relocalizations/s at p99 latency"
 UNIT = "evals/s"
 ROOFLINE_STAGES = ["raycast", "smad", "tam"]   # kernels timed inside the timed region for their roofline
-CONFIG_INDEX = 1
-WORKLOAD = ("office 1024x1024 @0.05 m, 5000 RRT hypotheses x 360 orientations, 1081-beam 270-deg noisy scan "
-            "(N_s 1440), TAM on SMAD top 256 (all batches scored)")
-OPS_PER_DDA_STEP = 13     # integer operations of one DDA cell step: the unit of the ray cast's ALU roofline
+OFFICE = 1      # the office workload (sweep, table2, rrt)
+DATA = {1: "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
+        2: "synthetic (seeded warehouse map, RRT hypotheses, noisy LiDAR scan)"}
+WORKLOADS = {
+    1: ("office 1024x1024 @0.05 m, 5000 RRT hypotheses x 360 orientations, 1081-beam 270-deg noisy scan "
+        "(N_s 1440), TAM on SMAD top 256 (all batches scored)"),
+    2: ("warehouse 4096x4096 @0.05 m, 20000 RRT hypotheses x 720 orientations, 1440-beam 360-deg noisy scan "
+        "(N_s 1440), TAM on SMAD top 1024 (all batches scored)"),
+}
+# Integer operations of one DDA cell step, the unit of the ray cast's ALU
+# roofline: the survey's estimate is 8-10, and ncu on the office cast counts
+# 154.28 M warp instructions x 27.02 active lanes / 413.26 M cell steps = 10.1
+# thread instructions per step.
+OPS_PER_DDA_STEP = 10
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -50,24 +67,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS),
+                    help="single-request workload: 2 = warehouse 4096^2 (default), 1 = office 1024^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (default: min(steps, 200))")
-    ap.add_argument("--workload", default="office", choices=["office", "batched", "served", "sweep", "rrt", "table2"],
-                    help="office: one request (default); batched: 64 mixed requests per step; "
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep", "rrt", "table2"],
+                    help="single: one request per step on --config's workload (default; the line also carries the "
+                         "batched and served forms unless --no-extras); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
-    ap.add_argument("--rates", default="200,400,600,800,1000,1500,2000,3000,4000,5000,6000,7000,8000,10000,12000",
-                    help="served: arrival rates per second")
+    ap.add_argument("--no-extras", action="store_true", help="single: leave out the batched and served forms")
+    ap.add_argument("--extra-steps", type=int, default=10, help="single: timed steps of the batched form")
+    ap.add_argument("--rates", default="",
+                    help="served: arrival rates per second (default: a ladder that grows by 1.5x from 250/s until "
+                         "p99 passes 50 ms, then bisects the last step twice)")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals per rate")
     ap.add_argument("--coarse", default="smad", choices=["smad", "caer", "smad_direct"],
-                    help="office workload: ranking metric, SMAD (Eq. 19-20), CAER (Eq. 21) or SMAD by direct "
+                    help="single workload: ranking metric, SMAD (Eq. 19-20), CAER (Eq. 21) or SMAD by direct "
                          "window sums (the Table II ablation without prefix sums); the rooflines assume SMAD")
     ap.add_argument("--fine", default="tam", choices=["tam", "tam_mean", "baseline", "lf"],
-                    help="office workload: scoring metric, TAM (Eq. 31), TAM_mean (Eq. 34), wp_baseline (Eq. 33) "
+                    help="single workload: scoring metric, TAM (Eq. 31), TAM_mean (Eq. 34), wp_baseline (Eq. 33) "
                          "or wp_LF (Eq. 32)")
     ap.add_argument("--icp-iters", type=int, default=0,
-                    help="office workload: ICP iterations per local top-k pose before its re-evaluation (0: none)")
-    ap.add_argument("--serve-configs", default="8x2,16x3,64x3",
+                    help="single workload: ICP iterations per local top-k pose before its re-evaluation (0: none)")
+    ap.add_argument("--serve-configs", default="16x3",
                     help="served: max_batch x max_inflight settings to measure (the best is reported)")
     return ap.parse_args()
 
@@ -177,13 +200,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def committed_traffic(stage: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source
-    is unchanged since the capture (else None)."""
+def committed_traffic(stage: str, config: int, key: str = "dram_bytes_per_launch"):
+    """DRAM (or, with key, L2) bytes per launch from the committed ncu summary
+    of this workload, if the kernel source is unchanged since the capture
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(stage)
-    except (OSError, ValueError):
+        rec = json.load(open(path)).get(f"config{config}", {}).get(stage)
+    except (OSError, ValueError, AttributeError):
         return None
     if not rec:
         return None
@@ -192,7 +216,7 @@ def committed_traffic(stage: str):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return rec["dram_bytes_per_launch"] if h == rec["source_sha"] else None
+    return rec.get(key) if h == rec["source_sha"] else None
 
 
 def run_ours(args, world, rank, local, dist):
@@ -205,7 +229,7 @@ def run_ours(args, world, rank, local, dist):
     import workloads
 
     torch.cuda.set_device(local)
-    wl = workloads.config(CONFIG_INDEX)
+    wl = workloads.config(args.config)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0, stream=stream,
@@ -271,19 +295,33 @@ def run_ours(args, world, rank, local, dist):
     info = ctx.scan_info()
     n_valid, n_orient, K = info[3], info[1], info[6]
     peaks, peak_kind = measured_peaks()
+    l2 = relo.probe_l2()
     bd_total = sum(bd_ms.values())
     shares = {k: v / bd_total for k, v in bd_ms.items()}
     dominant = max(bd_ms, key=bd_ms.get)
     tam_bytes = 2.0 * n_valid * K * n_orient * args.steps          # 2 B field read per valid beam per (h, m)
+    hbm = peaks["hbm_gbs"]
     roof = {}
     if stage_ms["tam"] > 0:
         gbs = tam_bytes / (stage_ms["tam"] / 1e3) / 1e9
-        roof["tam"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                       "frac": round(gbs / peaks["hbm_gbs"], 4),
+        roof["tam"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(gbs / hbm, 4),
                        # the counters were taken with TAM scoring; the other metrics run another epilogue
-                       "traffic": committed_traffic("tam") if args.fine == "tam" else None,
+                       "traffic": committed_traffic("tam", args.config) if args.fine == "tam" else None,
                        "peak_source": f"{peak_kind} hbm_gbs",
+                       "frac_hbm": round(gbs / hbm, 4),
+                       "gathers_per_s": round(gbs * 1e9 / 2.0),
+                       # the gathers against the rate of 2-byte gathers with no locality at all
+                       "frac_random_gather": round(gbs / l2["gather_2b_gbs"], 4),
+                       "random_gather_peak_per_s": round(l2["gather_per_s"]),
                        "avg_launch_ms": round(stage_ms["tam"] / max(stage_n["tam"], 1), 4)}
+        # the L2 -> SM bytes the kernel really moves (ncu, per launch) against the streaming L2 rate
+        l2b = committed_traffic("tam", args.config, key="l2_bytes_per_launch") if args.fine == "tam" else None
+        roof["tam"]["l2_traffic"] = l2b
+        roof["tam"]["frac_l2"] = (round(l2b / (roof["tam"]["avg_launch_ms"] / 1e3) / 1e9 / l2["stream_gbs"], 4)
+                                  if l2b else None)
+        roof["tam"]["l2_peak"] = round(l2["stream_gbs"], 1)
+        roof["tam"]["l2_peak_source"] = "streaming 16-byte reads of an L2-resident buffer (relo_probe_l2_stream)"
     dda = info[8]
     if stage_ms["raycast"] > 0 and dda:
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -292,26 +330,32 @@ def run_ours(args, world, rank, local, dist):
         tops = ops / (stage_ms["raycast"] / 1e3) / 1e12
         roof["raycast"] = {"bound": "alu", "achieved": round(tops, 3), "peak": round(peak_tops, 2),
                            "unit": "Tops/s", "frac": round(tops / peak_tops, 4),
-                           "traffic": committed_traffic("raycast"),
+                           "traffic": committed_traffic("raycast", args.config),
                            "peak_source": f"128 int32 lanes x {sm_count} SMs x {peaks.get('sm_max_mhz')} MHz",
+                           "ops_per_dda_step": OPS_PER_DDA_STEP,
+                           "ops_source": "ncu: 10.1 thread instructions per DDA cell step on the office cast",
                            "dda_steps_per_step": dda,
                            "avg_launch_ms": round(stage_ms["raycast"] / max(stage_n["raycast"], 1), 4)}
     if stage_ms["smad"] > 0:
         smad_bytes = 4.0 * info[0] * info[9] * args.steps          # one Q16 range per (hypothesis, direction)
         gbs = smad_bytes / (stage_ms["smad"] / 1e3) / 1e9
-        roof["smad"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": round(gbs / peaks["hbm_gbs"], 4),
+        roof["smad"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(gbs / hbm, 4),
                         # the counters are the prefix-sum SMAD kernel's; other rankings run other code
-                        "traffic": committed_traffic("smad") if args.coarse == "smad" else None,
+                        "traffic": committed_traffic("smad", args.config) if args.coarse == "smad" else None,
                         "peak_source": f"{peak_kind} hbm_gbs",
+                        "frac_hbm": round(gbs / hbm, 4),
+                        "frac_l2": round(gbs / l2["stream_gbs"], 4),
+                        "l2_peak": round(l2["stream_gbs"], 1),
+                        "l2_peak_source": "streaming 16-byte reads of an L2-resident buffer (relo_probe_l2_stream)",
                         "avg_launch_ms": round(stage_ms["smad"] / max(stage_n["smad"], 1), 4)}
     main_roof = roof.get(dominant) or roof.get("tam")
     pct = sorted(per_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "i32/i64+f32", "data": "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
-        "config": {"workload": WORKLOAD, "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
+        "dtype": "i32/i64+f32", "data": DATA[args.config],
+        "config": {"workload": WORKLOADS[args.config], "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
                    "n_orient": wl.n_orient, "n_beams": len(wl.ranges), "n_s": wl.n_s, "topk": wl.topk,
                    "evals_per_step": evals_per_step, "l2": "flushed before every timed step (256 MiB write)",
                    "ranking": args.coarse, "scoring": args.fine, "icp_iters": args.icp_iters,
@@ -332,7 +376,21 @@ def run_ours(args, world, rank, local, dist):
         line["e2e"] = run_e2e(args, ctx, mid, wl, relo, torch, flush, dist, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+    line["l2_probe"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in l2.items()}
     ctx.close()
+    del flush
+    if not args.no_extras:
+        b = run_batched(args, world, rank, local, dist, steps=args.extra_steps)
+        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "relocalizations_per_s", "latency_ms",
+                                             "gpu_launches", "stage_ms_per_step", "clocks")}
+        line["batched"]["workload"] = b["config"]["workload"]
+        line["batched"]["steps"] = b["steps"]
+        line["batched"]["evals_per_step"] = b["config"]["evals_per_step"]
+        sv = run_served(args, world, rank, local, dist)
+        line["served"] = {k: sv[k] for k in ("value", "unit", "best_rate_p99_le_50ms", "seconds_per_rate",
+                                             "pose_agreement", "pool")}
+        line["served"]["workload"] = sv["config"]["workload"]
+        line["served"]["ladders"] = {m: sv[m] for m in sv["modes"]}
     return line
 
 
@@ -375,46 +433,44 @@ def run_e2e(args, ctx, mid, wl, relo, torch, flush, dist, world):
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------------------------
 
-def oracle_sample(wl, n_smad: int, n_tam_hyp: int, threads: int):
-    """Times the oracle on a bounded sample and scales to the full workload.
-
-    Phases: EDT of the whole map; SMAD of n_smad hypotheses; TAM of the
-    first n_tam_hyp hypotheses (standing in for as many survivors: the cost
-    does not depend on which) x all orientations.  Returns (evals/s of the
-    full workload, estimated seconds per full step, description)."""
+def oracle_step(wl, n_smad: int, n_tam_hyp: int, threads: int):
+    """One pass of the oracle over a sample of the workload: the EDT of the
+    whole map, SMAD of n_smad hypotheses spread over the set, and TAM of
+    n_tam_hyp hypotheses (standing in for as many survivors: the cost does not
+    depend on which) x every orientation.  Returns (evaluations made, seconds,
+    description); nothing is scaled."""
     import numpy as np
 
     import oracle
     prm = oracle.Params(n_orient=wl.n_orient, topk=wl.topk)
     t0 = time.perf_counter()
     d2 = oracle.edt(wl.grid, threads)
-    t_edt = time.perf_counter() - t0
     pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
     sel = np.arange(0, len(wl.hyps), max(1, len(wl.hyps) // n_smad))[:n_smad]
-    t0 = time.perf_counter()
     oracle.smad(wl.grid, wl.hyps[sel], pl, threads)
-    t_smad = time.perf_counter() - t0
-    t0 = time.perf_counter()
     oracle.tam_grid(wl.grid, wl.hyps, np.arange(n_tam_hyp), pl, prm, wl.res, d2, threads)
-    t_tam = time.perf_counter() - t0
+    dt = time.perf_counter() - t0
     n_m = 1 if pl["panoramic"] else pl["n_orient"]
-    K = min(wl.topk, len(wl.hyps))
-    est = t_edt + t_smad * len(wl.hyps) / len(sel) + t_tam * K / n_tam_hyp
-    evals = len(wl.hyps) * n_m + K * pl["n_orient"]
-    desc = (f"EDT of the full map + SMAD of {len(sel)}/{len(wl.hyps)} hypotheses + TAM of {n_tam_hyp} hypotheses "
-            f"(for {K} survivors) x {pl['n_orient']} orientations, scaled to the full step")
-    return evals / est, est, desc
+    evals = len(sel) * n_m + n_tam_hyp * pl["n_orient"]
+    full = len(sel) == len(wl.hyps) and n_tam_hyp == min(wl.topk, len(wl.hyps))
+    desc = (f"{'the full step' if full else 'a sample of the step'}: EDT of the whole map + SMAD of "
+            f"{len(sel)}/{len(wl.hyps)} hypotheses + TAM of {n_tam_hyp} hypotheses x {pl['n_orient']} orientations "
+            f"({'as many as the survivors' if full else 'the step scores ' + str(min(wl.topk, len(wl.hyps)))}); "
+            "value = evaluations made / measured time, no scaling")
+    return evals, dt, desc
 
 
 def cpu_baseline(wl):
-    """The oracle on all host cores, and on one core (a smaller sample)."""
+    """The oracle on all host cores over the whole step (every hypothesis's
+    SMAD, TAM of as many hypotheses as the step has survivors)."""
     import oracle
     threads = oracle.max_threads()
-    v, est, desc = oracle_sample(wl, n_smad=len(wl.hyps), n_tam_hyp=min(wl.topk, len(wl.hyps)), threads=threads)
-    v1, est1, desc1 = oracle_sample(wl, n_smad=100, n_tam_hyp=4, threads=1)
-    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
-            "est_s_per_step": est,
-            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1, "est_s_per_step": est1}}
+    evals, dt, desc = oracle_step(wl, n_smad=len(wl.hyps), n_tam_hyp=min(wl.topk, len(wl.hyps)), threads=threads)
+    return {"value": evals / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "s_per_step": dt}
+
+
+# the reference arm's step: a bounded sample of the workload (about 1-3 s on 16 host cores)
+REF_SAMPLE = {1: (1000, 32), 2: (4000, 96)}
 
 
 def run_reference(args, world, rank):
@@ -423,23 +479,24 @@ def run_reference(args, world, rank):
     import oracle
     import workloads
     oracle.build()
-    wl = workloads.config(CONFIG_INDEX)
+    wl = workloads.config(args.config)
     threads = oracle.max_threads()
+    n_smad, n_tam = REF_SAMPLE[args.config]
     for _ in range(max(args.warmup, 0)):
-        oracle_sample(wl, 100, 2, threads)
-    vals, ests = [], []
-    desc = ""
+        oracle_step(wl, n_smad, n_tam, threads)
+    total_evals, total_s, desc = 0, 0.0, ""
     for _ in range(args.steps):
-        v, est, desc = oracle_sample(wl, 100, 2, threads)
-        vals.append(v)
-        ests.append(est)
-    total = sum(ests)
-    value = len(ests) / total * (vals[0] * ests[0])    # evals per step / mean seconds per step
+        e, dt, desc = oracle_step(wl, n_smad, n_tam, threads)
+        total_evals += e
+        total_s += dt
+    value = total_evals / total_s
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ests), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
-        "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": DATA[args.config],
+        "config": {"workload": WORKLOADS[args.config], "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
+                   "n_orient": wl.n_orient, "n_beams": len(wl.ranges), "n_s": wl.n_s, "topk": wl.topk,
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -461,7 +518,7 @@ def run_sweep(args, world, rank, local, dist):
     import workloads
 
     torch.cuda.set_device(local)
-    wl = workloads.config(CONFIG_INDEX)
+    wl = workloads.config(OFFICE)
     gx, gy, gth = wl.gt_pose
     cx, cy = int(round(gx / wl.res - 0.5)), int(round(gy / wl.res - 0.5))
     step = int(round(0.1 / wl.res))
@@ -535,7 +592,7 @@ def run_table2(args, world, rank, local, dist):
     import workloads
 
     torch.cuda.set_device(local)
-    wl = workloads.config(CONFIG_INDEX)
+    wl = workloads.config(OFFICE)
     rng = np.random.default_rng(2511)
     n_enum = wl.n_s // wl.n_orient
     K = min(len(wl.hyps), 4096)
@@ -601,7 +658,7 @@ def run_rrt(args, world, rank, local, dist):
     import workloads
 
     torch.cuda.set_device(local)
-    wl = workloads.config(CONFIG_INDEX)
+    wl = workloads.config(OFFICE)
     res, r_robot, seed = wl.res, 0.21, 7
     clr = workloads.clearance_table(wl.grid, res)
     p0 = workloads.free_start(wl.grid, res, r_robot, seed, clr)
@@ -637,9 +694,10 @@ def run_rrt(args, world, rank, local, dist):
                            "nodes": n_serial, "coverage": cover(xs_), "cores": 1}}
 
 
-def run_batched(args, world, rank, local, dist):
+def run_batched(args, world, rank, local, dist, steps=None):
     """64 independent relocalizations per step (mixed map sizes, beam counts,
     FoVs and hypothesis counts), one launch per stage, all inputs resident."""
+    n_steps = steps or args.steps
     import numpy as np
     import torch
 
@@ -675,13 +733,13 @@ def run_batched(args, world, rank, local, dist):
     ctx.set_profiling(True)
     ctx.stage_times(reset=True)
     k0 = ctx.kernels_launched()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
     barrier(dist)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    for i in range(args.steps):
+    for i in range(n_steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
         ctx.relocalize_batch_dev(items, res_t)
@@ -693,12 +751,12 @@ def run_batched(args, world, rank, local, dist):
     total = sum(per)
     stage_ms, stage_n, k1 = ctx.stage_times(reset=True)
     t_max = max_over_ranks(dist, total)
-    value = sum_over_ranks(dist, float(evals * args.steps)) / (t_max / 1e3)
+    value = sum_over_ranks(dist, float(evals * n_steps)) / (t_max / 1e3)
     pct = sorted(per)
     ctx.close()
     return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_steps, "warmup": args.warmup,
+        "ms_per_step": t_max / n_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32/i64+f32", "data": "synthetic (seeded office/warehouse maps, free-space hypotheses, noisy scans)",
         "config": {"workload": "batched: 64 independent relocalizations per step (map sides 512-2048, beams "
                                "541/720/1081/1440, FoV 180-360 deg, 1k-20k hypotheses, 360 orientations, TAM on the "
@@ -706,10 +764,10 @@ def run_batched(args, world, rank, local, dist):
                    "requests": len(items), "evals_per_step": evals,
                    "hypotheses": int(sum(len(i.hyps) for i in ins)),
                    "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "relocalizations_per_s": world * len(items) * args.steps / (t_max / 1e3),
+        "relocalizations_per_s": world * len(items) * n_steps / (t_max / 1e3),
         "latency_ms": {"p50": pct[len(pct) // 2], "p99": pct[min(len(pct) - 1, int(math.ceil(0.99 * len(pct))) - 1)]},
         "gpu_launches": int(k1 - k0),
-        "stage_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
+        "stage_ms_per_step": {k: round(v / n_steps, 5) for k, v in stage_ms.items()},
         "clocks": clk,
     }
 
@@ -719,14 +777,17 @@ def run_served(args, world, rank, local, dist):
     rate, for four ways of serving the same requests:
 
     plain           one request at a time (relo_relocalize), rays cast per request
-    plain_tables    one request at a time, synthesized scans read from the
-                    resident per-map tables (scan_cache_bytes)
+    plain_tables    one request at a time, synthesized scans and window sums read
+                    from the resident per-map tables (scan_cache_bytes)
     served_cast     continuous batching (relo_serve_start / submit / poll), rays cast
     served          continuous batching with the resident tables
 
     Every mode first runs each pooled request once (sensor plans, kernels and,
-    with tables, the tables themselves are then resident: steady state).  A
-    mode's rate ladder stops once its p99 passes 1 s (it is saturated)."""
+    with tables, the tables themselves are then resident: steady state).  The
+    rate ladder (unless --rates is given) starts at 250/s and grows by 1.5x
+    until p99 passes 50 ms, then bisects the last step twice; the best rate of
+    a mode is the highest throughput measured with p99 <= 50 ms.  Each served
+    result is compared with the same request run alone (pose agreement)."""
     import numpy as np
     import torch
 
@@ -738,8 +799,8 @@ def run_served(args, world, rank, local, dist):
     torch.cuda.set_device(local)
     maps = workloads.served_maps()
     pool = workloads.served_scans(maps)
-    rates = [float(x) for x in args.rates.split(",")]
     table_bytes = 16 << 30
+    P99 = 50.0
 
     def make_ctx(tables):
         ctx = relo.Relo(n_orient=360, topk=256, batch=200, local_topk=20, early_stop=1, tau=0.95, stream="private",
@@ -758,10 +819,13 @@ def run_served(args, world, rank, local, dist):
         n = max(1, int(rate * args.duration))
         return np.cumsum(rng.exponential(1.0 / rate, size=n)), rng.integers(len(pool), size=n)
 
-    def stats(lat, span):
+    def stats(lat, span, agree=None):
         lat = np.sort(np.asarray(lat))
-        return {"throughput": len(lat) / span, "p50_ms": float(1e3 * lat[len(lat) // 2]),
-                "p99_ms": float(1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]), "n": int(len(lat))}
+        out = {"throughput": len(lat) / span, "p50_ms": float(1e3 * lat[len(lat) // 2]),
+               "p99_ms": float(1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]), "n": int(len(lat))}
+        if agree is not None:
+            out["pose_agreement"] = float(np.mean(agree)) if agree else None
+        return out
 
     def run_plain(ctx, reqs, rate, seed):
         t_arr, which = arrivals(rate, seed)
@@ -775,9 +839,9 @@ def run_served(args, world, rank, local, dist):
             lat.append(time.perf_counter() - t0 - ta)
         return stats(lat, time.perf_counter() - t0)
 
-    def run_srv(ctx, reqs, rate, seed, agree):
+    def run_srv(ctx, reqs, rate, seed):
         t_arr, which = arrivals(rate, seed)
-        lat, pending = [], []
+        lat, pending, agree = [], [], []
         t0 = time.perf_counter()
         i = 0
         while i < len(t_arr) or pending:
@@ -797,44 +861,54 @@ def run_served(args, world, rank, local, dist):
             pending = still
             if i < len(t_arr) and not pending:
                 time.sleep(max(0.0, min(t_arr[i] - (time.perf_counter() - t0), 0.0005)))
-        return stats(lat, time.perf_counter() - t0)
+        return stats(lat, time.perf_counter() - t0, agree)
+
+    def ladder(run):
+        tab = {}
+        if args.rates:
+            for k, rate in enumerate(float(x) for x in args.rates.split(",")):
+                tab[rate] = run(rate, 4242 + k)
+                if tab[rate]["p99_ms"] > 1000.0:
+                    break
+            return dict(sorted(tab.items()))
+        rate, k = 250.0, 0
+        while True:
+            tab[rate] = run(rate, 4242 + k)
+            k += 1
+            if tab[rate]["p99_ms"] > P99 or rate > 60000:
+                break
+            rate = round(rate * 1.5, 1)
+        ok = [r for r in tab if tab[r]["p99_ms"] <= P99]
+        lo, hi = (max(ok) if ok else 0.0), rate
+        for _ in range(2):
+            mid = round(0.5 * (lo + hi), 1)
+            if mid <= 0:
+                break
+            tab[mid] = run(mid, 5242 + k)
+            k += 1
+            if tab[mid]["p99_ms"] <= P99:
+                lo = mid
+            else:
+                hi = mid
+        return dict(sorted(tab.items()))
 
     out = {}
     alone = None
     tables_info = None
     serve_cfgs = [tuple(int(v) for v in c.split("x")) for c in args.serve_configs.split(",")]
-    modes = [("plain", False, None), ("plain_tables", True, None), ("served_cast", False, max(serve_cfgs))]
-    modes += [(f"served_{b}x{f}", True, (b, f)) for (b, f) in serve_cfgs]
+    modes = [("plain", False, None), ("plain_tables", True, None), ("served_cast", False, serve_cfgs[0])]
+    modes += [("served" if j == 0 else f"served_{b}x{f}", True, (b, f)) for j, (b, f) in enumerate(serve_cfgs)]
     for mode, tables, cfg in modes:
         ctx, reqs, results = make_ctx(tables)
         if alone is None:
             alone = results
         assert results == alone, "resident tables changed a result"
-        agree = []
-        tab = {}
         if cfg is not None:
             ctx.serve_start(max_batch=cfg[0], max_inflight=cfg[1], hbm_budget=8 << 30)
-        run = (lambda rate, seed: run_srv(ctx, reqs, rate, seed, agree)) if cfg is not None else \
-            (lambda rate, seed: run_plain(ctx, reqs, rate, seed))
-        for k, rate in enumerate(rates):
-            tab[rate] = run(rate, 4242 + k)
-            if tab[rate]["p99_ms"] > 1000.0:
-                break
-        # refine between the fastest rate that kept p99 <= 50 ms and the next one tried
-        ok = [r for r in tab if tab[r]["p99_ms"] <= 50.0]
-        above = [r for r in tab if ok and r > max(ok)]
-        if ok and above:
-            lo, hi = max(ok), min(above)
-            for k, f in enumerate((0.25, 0.5, 0.75)):
-                rate = round(lo + f * (hi - lo), 1)
-                tab[rate] = run(rate, 5242 + k)
-        tab = dict(sorted(tab.items()))
-        if cfg is not None:
+            tab = ladder(lambda rate, seed: run_srv(ctx, reqs, rate, seed))
             ctx.serve_stop()
-            out[mode + "_pose_agreement"] = float(np.mean(agree)) if agree else None
-        if tables:
-            tables_info = ctx.scan_cache_stats()
-        if cfg is None:
+        else:
+            tab = ladder(lambda rate, seed: run_plain(ctx, reqs, rate, seed))
             # device time per stage for one pass over the pool, one request at a time
             ctx.stage_times(reset=True)
             ctx.set_profiling(True)
@@ -843,39 +917,48 @@ def run_served(args, world, rank, local, dist):
             ms, _, _ = ctx.stage_times(reset=True)
             ctx.set_profiling(False)
             out[mode + "_stage_ms_per_request"] = {k: round(v / len(reqs), 5) for k, v in ms.items()}
+        if tables:
+            tables_info = ctx.scan_cache_stats()
         out[mode] = {str(k): v for k, v in tab.items()}
         ctx.close()
         torch.cuda.synchronize()
 
-    def best(tab, cap=None):
-        ok = [v["throughput"] for k, v in tab.items() if v["p99_ms"] <= 50.0 and (cap is None or float(k) <= cap)]
+    def best(tab):
+        ok = [v["throughput"] for v in tab.values() if v["p99_ms"] <= P99]
         return max(ok) if ok else 0.0
-    bests = {m: best(out[m]) for m, _, _ in modes}
-    bests_cfg = {m: best(out[m], 2000.0) for m in bests}
-    served_modes = [m for m, t, c in modes if t and c is not None]
-    best_served = max(served_modes, key=lambda m: bests[m])
-    bests["served"] = bests[best_served]
-    b_srv, b_pln = bests["served"], bests["plain"]
+
+    names = [m for m, _, _ in modes]
+    bests = {m: best(out[m]) for m in names}
+    agreement = {}
+    for m, _, cfg in modes:
+        if cfg is not None:
+            vals = [(v["pose_agreement"], v["n"]) for v in out[m].values() if v.get("pose_agreement") is not None]
+            agreement[m] = sum(a * n for a, n in vals) / max(sum(n for _, n in vals), 1) if vals else None
+
+    def ratio(a, b):
+        return round(bests[a] / bests[b], 3) if bests[b] > 0 else None
     return {
-        "metric": METRIC, "value": b_srv, "unit": "relocalizations/s", "n_gpus": world, "steps": len(rates),
-        "warmup": len(pool), "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": bests["served"], "unit": "relocalizations/s", "n_gpus": world,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32/i64+f32", "data": "synthetic (8 resident maps 512^2..4096^2, pooled noisy scans, Poisson arrivals)",
         "config": {"workload": "served: 8 resident maps (two each of 512^2, 1024^2, 2048^2, 4096^2; 1250/5000/10000/"
                                "20000 hypotheses), Poisson arrivals, beams 541/720/1081/1440, 360 orientations, TAM "
                                "in batches of 200 of the top 256 with tau 0.95; continuous batching (max batch x "
-                               "batches in flight as listed, 8 GiB admission budget, 16 GiB of resident synthesized "
-                               "scans and window tables) vs one request at a time",
-                   "rates_per_s": rates, "seconds_per_rate": args.duration, "parallelism": "1 GPU"},
+                               f"batches in flight {args.serve_configs}, 8 GiB admission budget, 16 GiB of resident "
+                               "synthesized scans and window tables) vs one request at a time",
+                   "parallelism": "1 GPU"},
+        "seconds_per_rate": args.duration,
+        "modes": names,
         **out,
         "scan_tables": tables_info,
         "pool": {"requests": len(pool),
                  "tam_batches_mean": float(np.mean([r["n_batches"] for r in alone])),
                  "early_stopped_fraction": float(np.mean([r["n_batches"] < -(-256 // 200) for r in alone]))},
-        "best_served_config": best_served,
-        "best_rate_p99_le_50ms": {**bests, "ratio_served_vs_plain": (b_srv / b_pln) if b_pln > 0 else None,
-                                  "ratio_served_vs_plain_tables": (b_srv / bests["plain_tables"])
-                                  if bests["plain_tables"] > 0 else None},
-        "best_rate_p99_le_50ms_rates_le_2000": bests_cfg,
+        "pose_agreement": agreement,
+        "best_rate_p99_le_50ms": {**{m: round(v, 1) for m, v in bests.items()},
+                                  "ratio_served_vs_plain": ratio("served", "plain"),
+                                  "ratio_served_vs_plain_tables": ratio("served", "plain_tables"),
+                                  "ratio_served_cast_vs_plain": ratio("served_cast", "plain")},
     }
 
 
@@ -883,7 +966,7 @@ def main():
     faulthandler.enable()
     args = parse()
     world, rank, local = dist_env()
-    if args.impl == "ours" and args.workload != "office":
+    if args.impl == "ours" and args.workload != "single":
         dist = dist_init(world)
         fn = {"batched": run_batched, "served": run_served, "sweep": run_sweep, "rrt": run_rrt,
               "table2": run_table2}[args.workload]

@@ -480,8 +480,32 @@ def config(i: int, seed: int | None = None) -> Workload:
        5000 hypotheses, top 256, noise model of add_noise().
     2: 4096x4096 warehouse, 1440 beams over 360 deg, 720 orientations, 20000
        hypotheses, top 1024, same noise model.
+
+    With the environment variable RELO_WORKLOAD_CACHE naming a directory, a
+    generated workload is saved there and read back by later calls (input
+    generation only; the arrays are the same).
     """
     seed = 1000 + i if seed is None else seed
+    cache = os.environ.get("RELO_WORKLOAD_CACHE")
+    path = os.path.join(cache, f"config{i}_{seed}.npz") if cache else None
+    if path and os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return Workload(name=f"config{i}", grid=z["grid"], res=float(z["res"]), hyps=z["hyps"], ranges=z["ranges"],
+                        angles=z["angles"], max_range=float(z["max_range"]), n_orient=int(z["n_orient"]),
+                        topk=int(z["topk"]), n_s=int(z["n_s"]), gt_pose=tuple(float(v) for v in z["gt"]),
+                        extra={"rho": float(z["rho"]), "seed": seed})
+    wl = _config(i, seed)
+    if path:
+        os.makedirs(cache, exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}.npz"
+        np.savez(tmp, grid=wl.grid, res=wl.res, hyps=wl.hyps, ranges=wl.ranges, angles=wl.angles,
+                 max_range=wl.max_range, n_orient=wl.n_orient, topk=wl.topk, n_s=wl.n_s, gt=np.array(wl.gt_pose),
+                 rho=wl.extra["rho"])
+        os.replace(tmp, path)
+    return wl
+
+
+def _config(i: int, seed: int) -> Workload:
     res = 0.05
     if i == 0:
         grid = make_room(seed)
