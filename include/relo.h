@@ -43,7 +43,7 @@ extern "C" {
 #define RELO_E_NO_HYPOTHESES (-3)
 #define RELO_E_OVER_BUDGET (-4)     /* the request or map does not fit the context's HBM budget */
 #define RELO_E_CUDA (-5)            /* a CUDA call failed; the context should be destroyed */
-#define RELO_E_TIMEOUT (-6)
+#define RELO_E_TIMEOUT (-6)         /* a served request's deadline passed before it was admitted */
 #define RELO_E_NO_VALID_BEAMS (-7)  /* no beam with 0 < z < max_range */
 #define RELO_E_NOT_FOUND (-8)       /* unknown map id or ticket */
 
@@ -195,6 +195,14 @@ int relo_relocalize_dev(relo_ctx *ctx, int32_t map_id, const float *ranges_dev, 
 int relo_serve_start(relo_ctx *ctx, int32_t max_batch, int32_t max_inflight, int64_t hbm_budget);
 int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
                 float max_range, int64_t *ticket);
+/* relo_submit with a deadline: a request still waiting for admission
+ * timeout_s seconds after this call (HBM budget or busy slots) is never
+ * launched and completes with RELO_E_TIMEOUT; once admitted it runs to the
+ * end.  timeout_s = 0: no deadline (relo_submit); negative or NaN:
+ * RELO_E_INVALID_ARG.  The deadline is kept by the serving thread on the
+ * host; nothing waits on the device. */
+int relo_submit_until(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                      float max_range, double timeout_s, int64_t *ticket);
 int relo_poll(relo_ctx *ctx, int64_t ticket, relo_result *out, double *latency_s);
 int relo_serve_stop(relo_ctx *ctx);
 
@@ -313,6 +321,31 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
                             double p0y, double rho, double eta_max, double r_robot, int32_t eps_gain, uint64_t seed,
                             int32_t max_rounds, int32_t node_cap, float *xy_dev, int32_t cap, int32_t *n_out,
                             int32_t *rounds_out, int32_t *nodes_out);
+
+/* Hypotheses by Algorithm 1 (the traversability-constrained RRT of Sec.
+ * III-A with NearestNode, AdaptiveExpandDist, ExtendPoint,
+ * TraversabilityCheck and VoxelDownsample, and the gain stop of Remark 4)
+ * from the occupancy grid itself.  grid: host int8 [h][w], row-major, the
+ * cell values of relo_load_map; the RRT stands only on traversable cells
+ * (0 <= v < 65: unknown v < 0 and occupied v >= 65 are blocked, as is the
+ * outside of the map).  MinDistToObstacle (Sec. III-A item 3) is a per-cell
+ * clearance table built on the device by the library's exact EDT: res times
+ * the distance from the cell centre to the nearest blocked cell centre, the
+ * cells just outside the map counting as blocked (FP64 square root and
+ * product, rounded once to float32).  The tree then grows as in
+ * relo_rrt_hypotheses_dev with that table (same arguments).  Writes up to cap
+ * representatives (x, y metres from the map corner, in order of first
+ * insertion; float32 values widened) to the host array xy_out [cap][2], their
+ * count, the rounds run and the tree size to n_out, rounds_out, nodes_out,
+ * and, if clearance_out is not NULL, the clearance table (host float [h][w],
+ * metres).  Blocking; allocates its device scratch for the call and frees it.
+ * RELO_E_INVALID_ARG for bad sizes (w, h in [1, 16382]), a start off the map
+ * or a rho that gives more than 2^26 points per round; RELO_E_OVER_BUDGET if
+ * the scratch exceeds the context's HBM budget; RELO_E_CUDA. */
+int relo_rrt_sample(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, double res, double p0x, double p0y,
+                    double rho, double eta_max, double r_robot, int32_t eps_gain, uint64_t seed, int32_t max_rounds,
+                    int32_t node_cap, double *xy_out, int32_t cap, int32_t *n_out, int32_t *rounds_out,
+                    int32_t *nodes_out, float *clearance_out);
 
 /* Allocation-free EDT.  The paper has no counterpart to this entry point; it
  * serves callers that may not allocate device memory once running, such as a

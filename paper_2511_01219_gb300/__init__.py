@@ -41,7 +41,8 @@ EXPORTED = [
     "relo_synth_scans_dev", "relo_set_profiling", "relo_stage_times", "relo_edt_noalloc",
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
     "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask", "relo_rrt_hypotheses_dev",
-    "relo_probe_l2_stream", "relo_probe_l2_gather",
+    "relo_probe_l2_stream", "relo_probe_l2_gather", "relo_rrt_sample",
+    "relo_submit_until",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
@@ -122,11 +123,14 @@ def lib() -> ctypes.CDLL:
             "relo_stage_times": (ctypes.c_int, [P, P, P, I32, I32, P]),
             "relo_edt_noalloc": (ctypes.c_int, [P, I32, I32, P, P]),
             "relo_probe_l2_stream": (ctypes.c_int, [P, I64, I32, P, P]),
+            "relo_rrt_sample": (ctypes.c_int, [P, P, I32, I32, D, D, D, D, D, D, I32, ctypes.c_uint64, I32, I32, P,
+                                               I32, P, P, P, P]),
             "relo_probe_l2_gather": (ctypes.c_int, [P, I32, I64, P, P, P]),
             "relo_relocalize_batch": (ctypes.c_int, [P, P, I32, P]),
             "relo_relocalize_batch_dev": (ctypes.c_int, [P, P, I32, P]),
             "relo_serve_start": (ctypes.c_int, [P, I32, I32, I64]),
             "relo_submit": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
+            "relo_submit_until": (ctypes.c_int, [P, I32, P, P, I32, F, D, P]),
             "relo_poll": (ctypes.c_int, [P, I64, P, P]),
             "relo_serve_stop": (ctypes.c_int, [P]),
             "relo_scan_cache_stats": (ctypes.c_int, [P, P, I32]),
@@ -334,6 +338,23 @@ class Relo:
                                                    ctypes.byref(nn)), "rrt_hypotheses")
         return xy[: n.value], r.value, nn.value
 
+    def rrt_sample(self, grid: np.ndarray, res: float, p0, rho: float, eta_max: float = 0.6, r_robot: float = 0.21,
+                   eps_gain: int = 2, seed: int = 0, max_rounds: int = 500, node_cap: int = 4_000_000,
+                   cap: int = 1_000_000, with_clearance: bool = False):
+        """Algorithm 1 from the occupancy grid (host arrays): (xy float64 [n, 2] metres, rounds, nodes[,
+        clearance float32 [h, w] metres])."""
+        g = np.ascontiguousarray(grid, dtype=np.int8)
+        h, w = g.shape
+        xy = np.zeros((cap, 2), np.float64)
+        clr = np.zeros((h, w), np.float32) if with_clearance else None
+        n, r, nn = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._L.relo_rrt_sample(self._h, g.ctypes.data, w, h, res, float(p0[0]), float(p0[1]), rho,
+                                            eta_max, r_robot, eps_gain, seed, max_rounds, node_cap, xy.ctypes.data,
+                                            cap, ctypes.byref(n), ctypes.byref(r), ctypes.byref(nn),
+                                            None if clr is None else clr.ctypes.data), "rrt_sample")
+        out = (xy[: n.value].copy(), r.value, nn.value)
+        return out + (clr,) if with_clearance else out
+
     def kernels_launched(self) -> int:
         k = ctypes.c_int64(0)
         self._check(self._L.relo_stage_times(self._h, None, None, 0, 0, ctypes.byref(k)), "stage_times")
@@ -370,12 +391,18 @@ class Relo:
     def serve_start(self, max_batch: int = 64, max_inflight: int = 2, hbm_budget: int = 0):
         self._check(self._L.relo_serve_start(self._h, max_batch, max_inflight, hbm_budget), "serve_start")
 
-    def submit(self, map_id: int, ranges: np.ndarray, angles: np.ndarray, max_range: float) -> int:
+    def submit(self, map_id: int, ranges: np.ndarray, angles: np.ndarray, max_range: float,
+               timeout_s: float = 0.0) -> int:
+        """Queues a request (relo_submit; relo_submit_until with a deadline of timeout_s seconds)."""
         z = np.ascontiguousarray(ranges, dtype=np.float32)
         a = np.ascontiguousarray(angles, dtype=np.float32)
         t = ctypes.c_int64(0)
-        self._check(self._L.relo_submit(self._h, map_id, _np_ptr(z), _np_ptr(a), len(z), max_range, ctypes.byref(t)),
-                    "submit")
+        if timeout_s:
+            rc = self._L.relo_submit_until(self._h, map_id, _np_ptr(z), _np_ptr(a), len(z), max_range, timeout_s,
+                                           ctypes.byref(t))
+        else:
+            rc = self._L.relo_submit(self._h, map_id, _np_ptr(z), _np_ptr(a), len(z), max_range, ctypes.byref(t))
+        self._check(rc, "submit")
         return t.value
 
     def poll(self, ticket: int):

@@ -1224,6 +1224,8 @@ struct Ticket {
     relo_result result{};
     int status = RELO_PENDING;
     Clock::time_point t_submit, t_done;
+    bool has_deadline = false;
+    Clock::time_point deadline;   // a request still queued at this time completes with RELO_E_TIMEOUT
     size_t bytes = 0;
 };
 
@@ -1247,6 +1249,7 @@ struct Server {
     int max_batch = 64, max_inflight = 2;
     long long budget = 0;
     size_t inflight_bytes = 0;
+    int n_deadlines = 0;   // queued tickets with a deadline
     std::vector<InFlight> slots;
 };
 
@@ -1358,10 +1361,29 @@ void serve_loop(relo_ctx *ctx) {
         std::vector<Ticket *> cand;
         {
             std::unique_lock<std::mutex> lk(S->mu);
+            // queued requests whose deadline has passed are never admitted
+            if (S->n_deadlines > 0) {
+                const Clock::time_point now = Clock::now();
+                for (auto it = S->queue.begin(); it != S->queue.end();) {
+                    Ticket *t = *it;
+                    if (t->has_deadline && now >= t->deadline) {
+                        t->result.status = RELO_E_TIMEOUT;
+                        t->status = RELO_E_TIMEOUT;
+                        t->t_done = now;
+                        --S->n_deadlines;
+                        it = S->queue.erase(it);
+                        progressed = true;
+                    } else {
+                        ++it;
+                    }
+                }
+            }
             if (!S->running && S->queue.empty() && !any_busy) break;
             if (free_slot && !S->queue.empty()) {
                 while (!S->queue.empty() && (int)cand.size() < S->max_batch) {
-                    cand.push_back(S->queue.front());
+                    Ticket *t = S->queue.front();
+                    if (t->has_deadline) --S->n_deadlines;
+                    cand.push_back(t);
                     S->queue.pop_front();
                 }
             } else if (!progressed) {
@@ -1413,7 +1435,10 @@ void serve_loop(relo_ctx *ctx) {
         }
         if (!back.empty()) {
             std::lock_guard<std::mutex> lk(S->mu);
-            for (auto it = back.rbegin(); it != back.rend(); ++it) S->queue.push_front(*it);
+            for (auto it = back.rbegin(); it != back.rend(); ++it) {
+                if ((*it)->has_deadline) ++S->n_deadlines;
+                S->queue.push_front(*it);
+            }
         }
         if (!batch.empty()) launch_batch(ctx, *free_slot, batch, pr);
     }
@@ -1787,7 +1812,13 @@ int relo_serve_start(relo_ctx *ctx, int32_t max_batch, int32_t max_inflight, int
 
 int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
                 float max_range, int64_t *ticket) {
-    if (!ctx || !ranges || !angles || !ticket || n_beams < 2) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    return relo_submit_until(ctx, map_id, ranges, angles, n_beams, max_range, 0.0, ticket);
+}
+
+int relo_submit_until(relo_ctx *ctx, int32_t map_id, const float *ranges, const float *angles, int32_t n_beams,
+                      float max_range, double timeout_s, int64_t *ticket) {
+    if (!ctx || !ranges || !angles || !ticket || n_beams < 2 || !(timeout_s >= 0.0))
+        return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     Server *S = ctx->server;
     if (!S) return fail(ctx, RELO_E_INVALID_ARG, "not serving: call relo_serve_start first");
     Ticket *t = new (std::nothrow) Ticket();
@@ -1797,6 +1828,11 @@ int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float 
     t->angles.assign(angles, angles + n_beams);
     t->max_range = max_range;
     t->t_submit = Clock::now();
+    if (timeout_s > 0.0) {
+        t->has_deadline = true;
+        t->deadline = t->t_submit + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(
+                                        std::min(timeout_s, 1e9)));
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (!S->running) {
@@ -1806,6 +1842,7 @@ int relo_submit(relo_ctx *ctx, int32_t map_id, const float *ranges, const float 
         t->id = S->next_id++;
         S->tickets[t->id] = t;
         S->queue.push_back(t);
+        if (t->has_deadline) ++S->n_deadlines;
         *ticket = t->id;
     }
     S->cv.notify_one();
@@ -1849,6 +1886,74 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
                                   max_rounds, node_cap, xy_dev, cap, n_out, rounds_out, nodes_out, ctx->stream, &err);
     if (rc) return fail(ctx, rc, std::string("RRT: ") + err);
     return RELO_OK;
+}
+
+int relo_rrt_sample(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, double res, double p0x, double p0y,
+                    double rho, double eta_max, double r_robot, int32_t eps_gain, uint64_t seed, int32_t max_rounds,
+                    int32_t node_cap, double *xy_out, int32_t cap, int32_t *n_out, int32_t *rounds_out,
+                    int32_t *nodes_out, float *clearance_out) {
+    if (!ctx || !grid || (!xy_out && cap > 0) || !n_out || !rounds_out || !nodes_out)
+        return fail(ctx, RELO_E_INVALID_ARG, "null argument");
+    if (w < 1 || h < 1 || w > 16382 || h > 16382 || !(res > 0) || !(rho > 0) || !(eta_max > 0) || !(r_robot > 0) ||
+        eps_gain < 0 || max_rounds < 1 || node_cap < 1 || cap < 0)
+        return fail(ctx, RELO_E_INVALID_ARG, "bad RRT arguments");
+    cudaStream_t st = ctx->stream;
+    const size_t cells = (size_t)w * h;
+    // the ringed grid's EDT: a temporary map of (w + 2) x (h + 2) cells, no field border
+    MapDev t;
+    t.W = w + 2;
+    t.H = h + 2;
+    t.TW = (t.W + 7) / 8;
+    t.TH = (t.H + 7) / 8;
+    t.C = 65535;
+    t.P = 0;
+    t.Wp = t.W;
+    const size_t pc = (size_t)t.W * t.H;
+    int8_t *raw = nullptr;
+    float *clr = nullptr;
+    float2 *xy = nullptr;
+    struct { void **p; size_t bytes; } allocs[] = {
+        {(void **)&raw, cells}, {(void **)&t.grid, pc}, {(void **)&t.d2, pc * 4}, {(void **)&t.colsq, pc * 4},
+        {(void **)&t.summ, sizeof(int2) * (size_t)t.W * edt_segments(t.H)}, {(void **)&t.field, pc * 2},
+        {(void **)&t.bits, occupancy_words(t.TW, t.TH) * 8}, {(void **)&clr, cells * 4},
+        {(void **)&xy, sizeof(float2) * (size_t)(cap > 0 ? cap : 1)}};
+    int rc = RELO_OK;
+    for (auto &a : allocs)
+        if (rc == RELO_OK) rc = dev_alloc(ctx, a.p, a.bytes, "RRT clearance table");
+    cudaError_t e = cudaSuccess;
+    if (rc == RELO_OK) {
+        e = cudaMemcpyAsync(raw, grid, cells, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_rrt_blocked(raw, w, h, t.grid, st);
+        if (e == cudaSuccess) e = launch_edt(t, st);
+        if (e == cudaSuccess) e = launch_rrt_clearance(t.d2, w, h, res, clr, st);
+        if (e == cudaSuccess) ctx->kernels += 5;
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "RRT clearance table");
+    }
+    if (rc == RELO_OK) {
+        const char *err = "";
+        rc = rrt_sample_dev(clr, w, h, res, p0x, p0y, rho, eta_max, r_robot, eps_gain, seed, max_rounds, node_cap,
+                            reinterpret_cast<float *>(xy), cap, n_out, rounds_out, nodes_out, st, &err);
+        if (rc) rc = fail(ctx, rc, std::string("RRT: ") + err);
+    }
+    if (rc == RELO_OK) {
+        const int n = std::min(*n_out, cap);
+        std::vector<float2> host((size_t)(n > 0 ? n : 1));
+        if (n > 0) e = cudaMemcpyAsync(host.data(), xy, sizeof(float2) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && clearance_out)
+            e = cudaMemcpyAsync(clearance_out, clr, cells * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "RRT results");
+        } else {
+            for (int i = 0; i < n; ++i) {
+                xy_out[2 * i] = host[i].x;
+                xy_out[2 * i + 1] = host[i].y;
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    for (auto &a : allocs) dev_free(ctx, *a.p, a.bytes);
+    return rc;
 }
 
 int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {

@@ -293,6 +293,10 @@ cudaError_t launch_icp(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, i
                        cudaStream_t s);
 cudaError_t launch_icp_best(const ReqDesc *reqs, int R, int batch_lo, int batch_hi, bool last, cudaStream_t s);
 // Algorithm 1 in batched-expansion form (rrt.cu); blocking on s; *err names a failure
+// the RRT's blocked grid with a ring of blocked cells ((W + 2) x (H + 2), occupied = 100) and, from the squared
+// EDT of that grid, the clearance table res * sqrt(d2) (metres, W x H)
+cudaError_t launch_rrt_blocked(const int8_t *grid, int W, int H, int8_t *out, cudaStream_t s);
+cudaError_t launch_rrt_clearance(const int32_t *d2p, int W, int H, double res, float *clr, cudaStream_t s);
 int rrt_sample_dev(const float *clr, int W, int H, double res, double p0x, double p0y, double rho, double eta_max,
                    double r_robot, int eps_gain, uint64_t seed, int max_rounds, int node_cap, float *xy_out, int cap,
                    int *n_out, int *rounds_out, int *nodes_out, cudaStream_t s, const char **err);

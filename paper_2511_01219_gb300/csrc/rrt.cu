@@ -409,4 +409,49 @@ int rrt_sample_dev(const float *clr, int W, int H, double res, double p0x, doubl
     return rc;
 }
 
+namespace {
+
+// The grid the clearance EDT runs on: the map with a ring of one cell around
+// it, every cell occupied (100) that the RRT may not stand on (occupied,
+// v >= 65, or unknown, v < 0) and every ring cell occupied (the outside of
+// the map is blocked); traversable cells 0.
+__global__ void k_rrt_blocked(const int8_t *__restrict__ grid, int W, int H, int8_t *__restrict__ out) {
+    const int pw = W + 2, ph = H + 2;
+    const long long n = (long long)pw * ph;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / pw) - 1, x = (int)(i % pw) - 1;
+        bool blocked = true;
+        if (x >= 0 && y >= 0 && x < W && y < H) {
+            const int v = grid[(size_t)y * W + x];
+            blocked = v < 0 || v >= 65;
+        }
+        out[i] = blocked ? (int8_t)100 : (int8_t)0;
+    }
+}
+
+// MinDistToObstacle as a per-cell table (Sec. III-A item 3): res times the
+// distance from the cell centre to the nearest blocked cell centre, from the
+// exact squared EDT of the ringed grid (never -1: the ring is blocked); the
+// square root and the product in FP64, rounded once to float32.
+__global__ void k_rrt_clearance(const int32_t *__restrict__ d2p, int W, int H, double res, float *__restrict__ clr) {
+    const long long n = (long long)W * H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / W), x = (int)(i % W);
+        const int32_t v = d2p[(size_t)(y + 1) * (W + 2) + (x + 1)];
+        clr[i] = (float)(res * sqrt((double)v));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rrt_blocked(const int8_t *grid, int W, int H, int8_t *out, cudaStream_t s) {
+    k_rrt_blocked<<<1024, 256, 0, s>>>(grid, W, H, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rrt_clearance(const int32_t *d2p, int W, int H, double res, float *clr, cudaStream_t s) {
+    k_rrt_clearance<<<1024, 256, 0, s>>>(d2p, W, H, res, clr);
+    return cudaGetLastError();
+}
+
 }  // namespace relo

@@ -696,6 +696,32 @@ def test_served_admission_by_budget(relo, workload):
     ctx.close()
 
 
+def test_served_request_deadlines(relo, workload):
+    """A served request whose deadline passes while it waits for admission
+    completes with RELO_E_TIMEOUT and is never launched; the others run as
+    alone.  One slot and one request per batch: the second request can only be
+    admitted once the first has left the GPU, long after its 1-microsecond
+    deadline; the third has a deadline it can meet."""
+    ctx, reqs = served_setup(relo, workload)
+    alone = [ctx.relocalize(*r).as_dict() for r in reqs]
+    ctx.serve_start(max_batch=1, max_inflight=1)
+    t_first = ctx.submit(*reqs[0])
+    t_late = ctx.submit(*reqs[1], timeout_s=1e-6)
+    t_ok = ctx.submit(*reqs[2], timeout_s=60.0)
+    first, late, ok = poll_all(ctx, [t_first, t_late, t_ok])
+    ctx.serve_stop()
+    assert first[0] == relo.OK and first[1].as_dict() == alone[0]
+    assert late[0] == relo.E_TIMEOUT
+    assert ok[0] == relo.OK and ok[1].as_dict() == alone[2]
+    with pytest.raises(relo.ReloError):
+        ctx.serve_start(max_batch=1, max_inflight=1)
+        try:
+            ctx.submit(*reqs[0], timeout_s=-1.0)
+        finally:
+            ctx.serve_stop()
+    ctx.close()
+
+
 def test_survivors_when_every_smad_ties(relo):
     """A map without obstacles: every synthesized scan is empty, every SMAD
     numerator is the same, and the survivor keys differ only in the hypothesis

@@ -116,3 +116,43 @@ def test_gpu_rrt_rejects_a_start_off_the_map(relo):
     with pytest.raises(relo.ReloError):
         ctx.rrt_hypotheses(torch.tensor(clr, device="cuda"), RES, (-1.0, 0.5), rho)
     ctx.close()
+
+
+def blocked_clearance(g):
+    """MinDistToObstacle by definition, from the oracle's exact EDT: the grid
+    with a ring of blocked cells around it, every cell blocked that is
+    occupied (>= 65) or unknown (< 0); clearance = res * sqrt(d2) in FP64,
+    rounded once to float32."""
+    import oracle
+    ring = np.full((g.shape[0] + 2, g.shape[1] + 2), 100, np.int8)
+    ring[1:-1, 1:-1] = np.where((g < 0) | (g >= 65), 100, 0)
+    d2 = oracle.edt(ring)[1:-1, 1:-1]
+    return (RES * np.sqrt(d2.astype(np.float64))).astype(np.float32)
+
+
+@pytest.mark.parametrize("which", ["room", "office512"])
+def test_rrt_from_the_grid(relo, which):
+    """relo_rrt_sample builds the clearance table from the grid with the
+    library's EDT (bit for bit the definition over the oracle's EDT, and the
+    table the workloads computed with SciPy), then grows the same tree as the
+    clearance-taking sampler."""
+    import torch
+    g, clr, p0, rho = scene(which)
+    ctx = relo.Relo()
+    xy, rounds, nodes, got_clr = ctx.rrt_sample(g, RES, p0, rho, 0.6, R_ROBOT, 2, seed=11, with_clearance=True)
+    assert np.array_equal(got_clr, blocked_clearance(g))
+    assert np.array_equal(got_clr, clr)
+    ref, r_ref, n_ref = ctx.rrt_hypotheses(torch.tensor(clr, device="cuda"), RES, p0, rho, 0.6, R_ROBOT, 2, seed=11)
+    ctx.close()
+    assert (rounds, nodes) == (r_ref, n_ref)
+    assert np.array_equal(xy, ref.cpu().numpy().astype(np.float64))
+    assert len(xy) > 0
+
+
+def test_rrt_from_the_grid_rejects_a_start_off_the_map(relo):
+    g = workloads.make_room(1000)
+    ctx = relo.Relo()
+    with pytest.raises(relo.ReloError) as e:
+        ctx.rrt_sample(g, RES, (-1.0, 0.5), 0.3)
+    assert e.value.code == relo.E_INVALID_ARG
+    ctx.close()
