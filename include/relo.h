@@ -322,6 +322,32 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
                             int32_t max_rounds, int32_t node_cap, float *xy_dev, int32_t cap, int32_t *n_out,
                             int32_t *rounds_out, int32_t *nodes_out);
 
+/* Launch shapes of the batched stages: the knobs the project's autotuner
+ * (paper_2511_01219_gb300/autotune.py) sets from measurements.  The paper has
+ * no counterpart.  An entry overrides the built-in choice for the launches it
+ * matches; key values of 0 match anything; the first matching entry applies.
+ *   RELO_TUNE_TAM   key = {values-per-lane class of the request's TAM kernel
+ *                   (relo_tam_class), n_orient, K}; val = {survivors per TAM
+ *                   task (a multiple of 8 in [8, 128]; 0 keeps the built-in
+ *                   choice), resident CTAs per SM of the TAM launch (0: all
+ *                   that fit; a launch takes the smallest of its requests')}.
+ *   RELO_TUNE_CAST  key = {N_s of the batch's first ray-casting request, 0,
+ *                   0}; val = {CTAs per SM of the ray-cast launch (0: all that
+ *                   fit), 0}.
+ * relo_set_tuning copies the n entries (n = 0 clears the table).  Results do
+ * not depend on the shapes, only the time.  RELO_E_INVALID_ARG for a bad kind
+ * or value.  relo_tam_class returns the class for a scan of n_beams beams
+ * (after the n_skip_beam stride), or -1 if no TAM kernel holds it. */
+#define RELO_TUNE_TAM 1
+#define RELO_TUNE_CAST 2
+typedef struct relo_tune_entry {
+    int32_t kind;
+    int32_t key[3];
+    int32_t val[2];
+} relo_tune_entry;
+int relo_set_tuning(relo_ctx *ctx, const relo_tune_entry *entries, int32_t n);
+int relo_tam_class(int32_t n_beams);
+
 /* Hypotheses by Algorithm 1 (the traversability-constrained RRT of Sec.
  * III-A with NearestNode, AdaptiveExpandDist, ExtendPoint,
  * TraversabilityCheck and VoxelDownsample, and the gain stop of Remark 4)

@@ -42,7 +42,7 @@ EXPORTED = [
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
     "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask", "relo_rrt_hypotheses_dev",
     "relo_probe_l2_stream", "relo_probe_l2_gather", "relo_rrt_sample",
-    "relo_submit_until",
+    "relo_submit_until", "relo_set_tuning", "relo_tam_class",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
 
@@ -61,6 +61,11 @@ class Params(ctypes.Structure):
 
 COARSE_SMAD, COARSE_CAER, COARSE_SMAD_DIRECT, COARSE_NONE = 0, 1, 2, 3
 FINE_TAM, FINE_TAM_MEAN, FINE_BASELINE, FINE_LF = 0, 1, 2, 3
+TUNE_TAM, TUNE_CAST = 1, 2
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("key", ctypes.c_int32 * 3), ("val", ctypes.c_int32 * 2)]
 
 
 class Result(ctypes.Structure):
@@ -131,6 +136,8 @@ def lib() -> ctypes.CDLL:
             "relo_serve_start": (ctypes.c_int, [P, I32, I32, I64]),
             "relo_submit": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
             "relo_submit_until": (ctypes.c_int, [P, I32, P, P, I32, F, D, P]),
+            "relo_set_tuning": (ctypes.c_int, [P, P, I32]),
+            "relo_tam_class": (ctypes.c_int, [I32]),
             "relo_poll": (ctypes.c_int, [P, I64, P, P]),
             "relo_serve_stop": (ctypes.c_int, [P]),
             "relo_scan_cache_stats": (ctypes.c_int, [P, P, I32]),
@@ -355,6 +362,17 @@ class Relo:
         out = (xy[: n.value].copy(), r.value, nn.value)
         return out + (clr,) if with_clearance else out
 
+    def set_tuning(self, entries):
+        """Launch shapes (relo_set_tuning): entries [(kind, (k0, k1, k2), (v0, v1))]; [] clears."""
+        arr = (TuneEntry * max(len(entries), 1))()
+        for i, (kind, key, val) in enumerate(entries):
+            arr[i].kind = kind
+            for j in range(3):
+                arr[i].key[j] = int(key[j])
+            for j in range(2):
+                arr[i].val[j] = int(val[j])
+        self._check(self._L.relo_set_tuning(self._h, arr, len(entries)), "set_tuning")
+
     def kernels_launched(self) -> int:
         k = ctypes.c_int64(0)
         self._check(self._L.relo_stage_times(self._h, None, None, 0, 0, ctypes.byref(k)), "stage_times")
@@ -442,6 +460,11 @@ class Relo:
 
 def result_from_bytes(b: bytes) -> Result:
     return Result.from_buffer_copy(b)
+
+
+def tam_class(n_beams: int) -> int:
+    """The values-per-lane class of a scan's TAM kernel (relo_tam_class), the key of a TAM tuning entry."""
+    return int(lib().relo_tam_class(int(n_beams)))
 
 
 def probe_l2(stream_bytes: int = 32 << 20, passes: int = 50, gather_log2: int = 24, gathers: int = 1 << 30) -> dict:

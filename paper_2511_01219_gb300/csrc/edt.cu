@@ -120,7 +120,7 @@ __global__ void k_edt_col_final(const int8_t *__restrict__ grid, int W, int H, i
 // sentinel tests: a sentinel never improves the minimum.
 constexpr int kRowSentinel = 0x3fffffff;
 
-__global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int Wp, int32_t *__restrict__ d2,
+__global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int P, int Wp, int32_t *__restrict__ d2,
                            uint16_t *__restrict__ field) {
     extern __shared__ int32_t rowbuf[];   // [3W]: sentinels, the row, sentinels
     int32_t *row = rowbuf + W;
@@ -141,15 +141,16 @@ __global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int 
             best = v < best ? v : best;
         }
         d2[(size_t)y * W + x] = best >= kRowSentinel ? kD2None : best;
-        field[(size_t)y * Wp + x] = (uint16_t)(best > C ? C : best);
+        field[field_index(x + P, y + P, Wp)] = (uint16_t)(best > C ? C : best);
     }
 }
 
 // the border of the padded field: every cell outside the map reads C (d = d_max)
-__global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int P, int Wp, int C) {
-    const size_t n = (size_t)(H + 2 * P) * Wp;
+__global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int P, int Wp, int Hp, int C) {
+    const size_t n = (size_t)Hp * Wp;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / Wp) - P, x = (int)(i % Wp) - P;
+        const size_t c = i >> 3;   // column of a band, then the row inside the band (field_index)
+        const int y = (int)(c / Wp) * 8 + (int)(i & 7) - P, x = (int)(c % Wp) - P;
         if (x < 0 || y < 0 || x >= W || y >= H) fieldp[i] = (uint16_t)C;
     }
 }
@@ -163,13 +164,14 @@ __global__ void k_walk_border(uint64_t *__restrict__ wf, int TW, int TH) {
 }
 
 __global__ void k_map_tables(const int32_t *__restrict__ d2s, const uint16_t *__restrict__ fs,
-                             const uint64_t *__restrict__ bs, int W, int H, int TW, int Wp, int32_t *d2, uint16_t *field,
+                             const uint64_t *__restrict__ bs, int W, int H, int TW, int P, int Wp, int32_t *d2,
+                             uint16_t *field,
                              uint8_t *occ) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)W * H) return;
     int x = (int)(i % W), y = (int)(i / W);
     if (d2) d2[i] = d2s[i];
-    if (field) field[i] = fs[(size_t)y * Wp + x];
+    if (field) field[i] = fs[field_index(x + P, y + P, Wp)];
     if (occ) occ[i] = (uint8_t)((bs[(size_t)(y >> 3) * TW + (x >> 3)] >> (((y & 7) << 3) | (x & 7))) & 1ull);
 }
 
@@ -190,26 +192,24 @@ cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
     const dim3 cgrid((m.W + 127) / 128, S);
     k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.TW, m.TH, m.summ, m.bits);
     k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
-    uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
     size_t smem = (size_t)3 * m.W * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.Wp, m.d2, field00);
+    k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.P, m.Wp, m.d2, m.field);
     return cudaGetLastError();
 }
 
 cudaError_t launch_field_border(const MapDev &m, cudaStream_t s) {
-    k_field_border<<<1024, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.C);
+    k_field_border<<<1024, 256, 0, s>>>(m.field, m.W, m.H, m.P, m.Wp, m.Hp, m.C);
     k_walk_border<<<4, 256, 0, s>>>(m.bits + (size_t)m.TW * m.TH, m.TW, m.TH);
     return cudaGetLastError();
 }
 
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s) {
     size_t n = (size_t)m.W * m.H;
-    const uint16_t *field00 = m.field + (size_t)m.P * m.Wp + m.P;
-    k_map_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.d2, field00, m.bits, m.W, m.H, m.TW, m.Wp, d2, field,
+    k_map_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.d2, m.field, m.bits, m.W, m.H, m.TW, m.P, m.Wp, d2, field,
                                                              occ);
     return cudaGetLastError();
 }

@@ -692,13 +692,15 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
 
 }  // namespace
 
-cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s) {
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, int ctas_per_sm,
+                        cudaStream_t s) {
     if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
     if (total_chunks <= 0) return cudaSuccess;
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cast, kCastThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;   // a tuned launch shape
     const long long warps = (long long)total_chunks;
     long long grid = (long long)n_sm * occ;
     if (grid * (kCastThreads / 32) > warps) grid = (warps + kCastThreads / 32 - 1) / (kCastThreads / 32);

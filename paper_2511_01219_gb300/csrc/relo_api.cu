@@ -171,6 +171,8 @@ struct relo_ctx {
     // resident synthesized scans
     long long table_bytes = 0, cache_hits = 0, cache_misses = 0, cache_evictions = 0, win_hits = 0;
     unsigned long long table_clock = 0, batch_seq = 0;
+    // launch shapes chosen by the autotuner (relo_set_tuning)
+    std::vector<relo_tune_entry> tuning;
 };
 
 namespace {
@@ -254,6 +256,15 @@ int ensure(relo_ctx *ctx, T **p, size_t *cap, size_t need, const char *what) {
     int rc = dev_alloc(ctx, (void **)p, n * sizeof(T), what);
     if (rc == RELO_OK) *cap = n;
     return rc;
+}
+
+// the first tuning entry of this kind whose nonzero keys equal k0, k1, k2 (nullptr: none)
+const relo_tune_entry *tuned(const relo_ctx *ctx, int kind, int k0, int k1, int k2) {
+    for (const relo_tune_entry &e : ctx->tuning)
+        if (e.kind == kind && (!e.key[0] || e.key[0] == k0) && (!e.key[1] || e.key[1] == k1) &&
+            (!e.key[2] || e.key[2] == k2))
+            return &e;
+    return nullptr;
 }
 
 static_assert(kCoarseCaer == RELO_COARSE_CAER && kFineTamMean == RELO_FINE_TAM_MEAN &&
@@ -682,7 +693,7 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.summ, sizeof(int2) * (size_t)m.dev.W * edt_segments(m.dev.H));
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
-    dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * (m.dev.H + 2 * m.dev.P));
+    dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * m.dev.Hp);
     dev_free(ctx, m.dev.bits, sizeof(uint64_t) * occupancy_words(m.dev.TW, m.dev.TH));
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
     dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
@@ -708,9 +719,12 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     if (rc) return rc;
     m.dev.P = pad_for(ctx->p.max_range, res);
     if (m.dev.P < 1) return fail(ctx, RELO_E_INVALID_ARG, "max_range / res must be below 32768 cells");
-    m.dev.Wp = w + 2 * m.dev.P;
+    m.dev.Wp = (w + 2 * m.dev.P + 7) & ~7;
+    m.dev.Hp = (h + 2 * m.dev.P + 7) & ~7;
+    if (m.dev.Wp > 65535 || m.dev.Hp > 65535)
+        return fail(ctx, RELO_E_INVALID_ARG, "the map with its field border must stay below 65536 cells per side");
     const size_t cells = (size_t)w * h;
-    const size_t fcells = (size_t)m.dev.Wp * (h + 2 * m.dev.P);
+    const size_t fcells = (size_t)m.dev.Wp * m.dev.Hp;
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
         {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, occupancy_words(m.dev.TW, m.dev.TH) * 8},
@@ -943,6 +957,30 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         }
         win[r] = w;
     }
+    // TAM work of every batch index, one launch per class of requests with the
+    // same register-resident values per lane (a 541-beam request does not run
+    // at the width of a 1440-beam one); one class if the segment table would
+    // not fit the slot
+    std::vector<int> vcls((size_t)R);
+    for (int r = 0; r < R; ++r) {
+        vcls[r] = tam_vpl_for(pr[r].P->n);
+        if (vcls[r] < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
+    }
+    std::vector<int> classes(vcls);
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    int pre_max_batches = 0;
+    for (int r = 0; r < R; ++r) pre_max_batches = std::max(pre_max_batches, pr[r].n_batches);
+    if ((size_t)pre_max_batches * classes.size() * R > (size_t)kMaxBatches * kMaxBatchRequests) {
+        std::fill(vcls.begin(), vcls.end(), classes.back());
+        classes.assign(1, classes.back());
+    }
+    const int NC = (int)classes.size();
+    // survivors per TAM task: the autotuner's choice for the request's shape, else the built-in one
+    auto chunk_of = [&](int r) {
+        const relo_tune_entry *e = tuned(ctx, RELO_TUNE_TAM, vcls[r], pr[r].P->n_orient, pr[r].K);
+        return e && e->val[0] > 0 ? e->val[0] : tam_chunk_for(pr[r].K, pr[r].P->n_orient, ctx->n_sm);
+    };
     std::vector<ReqDesc> desc((size_t)R);
     std::vector<size_t> off((size_t)R);
     size_t total = 0;
@@ -954,7 +992,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         off[r] = total;
         total += align_up(24ull * K) + align_up(4ull * K);   // refined poses and re-evaluated scores
         total += align_up(sizeof(int2) * n) + align_up(4ull * n) + align_up(sizeof(ScanInfo)) + align_up(8ull * nh) * 2 +
-                 align_up(4ull * nh) + align_up(4ull * K) * 2 + align_up(4ull * K * q.P->n_orient) +
+                 align_up(4ull * nh) + align_up(4ull * K) * 3 + align_up(4ull * K * q.P->n_orient) +
+                 align_up(16ull * tam_chunk_cap(K, q.B, q.n_batches, chunk_of(r))) + align_up(4ull * (q.n_batches + 1)) +
+                 align_up(4ull * 8 * 32 * q.P->n_orient * tam_offs_stride_for(vcls[r])) +
                  align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
         if (mode[r] == kScanCast) total += align_up(4ull * nh * q.P->ns);   // the request's synthesized ranges
         if (mode[r] != kScanRead && cast) total_chunks += (long long)nh * (((q.P->ns + 31) & ~31) >> 5);
@@ -977,7 +1017,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         ReqDesc &d = desc[r];
         memset(&d, 0, sizeof d);
         d.bits = m.dev.bits;
-        d.field = m.dev.field + (size_t)m.dev.P * m.dev.Wp + m.dev.P;
+        d.field = m.dev.field;
         d.Wp = m.dev.Wp;
         d.P = m.dev.P;
         d.lut = m.lut;
@@ -1042,6 +1082,12 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         d.smad_num = (long long *)take(8ull * m.n_hyp);
         d.smad_m = (int32_t *)take(4ull * m.n_hyp);
         d.survivors = (int32_t *)take(4ull * q.K);
+        d.tam_chunk = chunk_of(r);
+        d.tam_stride = tam_offs_stride_for(vcls[r]);
+        d.tam_offs = (int32_t *)take(4ull * 8 * 32 * P.n_orient * d.tam_stride);
+        d.surv_perm = (int32_t *)take(4ull * q.K);
+        d.tam_chunks = (int4 *)take(16ull * tam_chunk_cap(q.K, q.B, q.n_batches, d.tam_chunk));
+        d.chunk_cnt = (int32_t *)take(4ull * (q.n_batches + 1));
         d.best_m = (int32_t *)take(4ull * q.K);
         d.T = (float *)take(4ull * q.K * P.n_orient);
         d.best_key = (unsigned long long *)take(8ull * q.K);
@@ -1068,23 +1114,6 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (d.win_mode == kWinBuild) max_nm = std::max(max_nm, d.n_m);
     }
     const int total_smad = base, total_build = bbase, total_read = rbase;
-    // TAM work of every batch index, one launch per class of requests with the
-    // same register-resident values per lane (a 541-beam request does not run
-    // at the width of a 1440-beam one); one class if the segment table would
-    // not fit the slot
-    std::vector<int> vcls((size_t)R);
-    for (int r = 0; r < R; ++r) {
-        vcls[r] = tam_vpl_for(pr[r].P->n);
-        if (vcls[r] < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
-    }
-    std::vector<int> classes(vcls);
-    std::sort(classes.begin(), classes.end());
-    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
-    if ((size_t)max_batches * classes.size() * R > (size_t)kMaxBatches * kMaxBatchRequests) {
-        std::fill(vcls.begin(), vcls.end(), classes.back());
-        classes.assign(1, classes.back());
-    }
-    const int NC = (int)classes.size();
     // Without early termination no batch waits on another's outcome: one TAM
     // round scores every batch's survivors and one selection launch takes the
     // batches in order (Remark 2's termination test is then never made).
@@ -1093,23 +1122,28 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     const int tam_rounds = any_early ? max_batches : std::min(max_batches, 1);
     std::vector<TamSeg> segs((size_t)max_batches * NC * R);
     std::vector<TamPlan> plans((size_t)max_batches * NC);
-    std::vector<int> nb((size_t)R), no((size_t)R), sb((size_t)R);
+    std::vector<int> blo((size_t)R), bhi((size_t)R);
     for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {
             int beams_c = 1, C_c = 0;
             for (int r = 0; r < R; ++r) {
-                const int s0 = any_early ? bi * desc[r].B : 0;
                 const bool in = vcls[r] == classes[c] && bi < desc[r].n_batches;
-                nb[r] = in ? (any_early ? std::min(desc[r].K, s0 + desc[r].B) - s0 : desc[r].K) : 0;
-                no[r] = desc[r].n_orient;
-                sb[r] = s0;
+                blo[r] = any_early ? bi : 0;
+                bhi[r] = in ? (any_early ? bi + 1 : desc[r].n_batches) : blo[r];
                 if (vcls[r] == classes[c]) {
                     beams_c = std::max(beams_c, pr[r].P->n);
                     C_c = std::max(C_c, pr[r].m->dev.C);
                 }
             }
+            int cps = 0;   // resident CTAs per SM: the smallest the class's requests are tuned to
+            for (int r = 0; r < R; ++r) {
+                if (vcls[r] != classes[c]) continue;
+                const relo_tune_entry *e = tuned(ctx, RELO_TUNE_TAM, vcls[r], desc[r].n_orient, desc[r].K);
+                if (e && e->val[1] > 0) cps = cps > 0 ? std::min(cps, e->val[1]) : e->val[1];
+            }
             TamPlan &tp = plans[(size_t)bi * NC + c];
-            tp = plan_tam(nb.data(), no.data(), sb.data(), R, beams_c, C_c, ctx->n_sm, &segs[((size_t)bi * NC + c) * R]);
+            tp = plan_tam(blo.data(), bhi.data(), R, beams_c, C_c, ctx->n_sm, cps,
+                          &segs[((size_t)bi * NC + c) * R]);
             if (tp.vpl < 0) return fail(ctx, RELO_E_INVALID_ARG, "no TAM kernel fits this beam count");
         }
     }
@@ -1129,7 +1163,14 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
     }
     if (total_chunks > 0)
-        CK(timed_on(ctx, st, 2, 1, [&] { return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, st); }),
+        CK(timed_on(ctx, st, 2, 1,
+                    [&] {
+                        int ns0 = 0;
+                        for (int r = 0; r < R && !ns0; ++r)
+                            if (mode[r] != kScanRead) ns0 = desc[r].ns;
+                        const relo_tune_entry *e = tuned(ctx, RELO_TUNE_CAST, ns0, 0, 0);
+                        return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, e ? e->val[0] : 0, st);
+                    }),
            "ray cast");
     if (total_smad > 0)
         CK(timed_on(ctx, st, 6, 1,
@@ -1149,6 +1190,13 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_read(rq, R, total_read, st); }), "SMAD by window tables");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
+    CK(timed_on(ctx, st, 3, 1, [&] { return launch_tam_chunks(rq, R, st); }), "TAM work order");
+    {
+        int max_no = 1;
+        for (int r = 0; r < R; ++r) max_no = std::max(max_no, desc[r].n_orient);
+        // the endpoint offset table O[m][i] of the request plan, per band phase (timed with the scan preparation)
+        CK(timed_on(ctx, st, 1, 1, [&] { return launch_tam_offsets(rq, R, max_no, st); }), "TAM offsets");
+    }
     for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {
             const TamPlan &tp = plans[(size_t)bi * NC + c];
@@ -1260,7 +1308,10 @@ size_t request_bytes(const relo_ctx *ctx, const Prepared &q) {
     const size_t n = (size_t)q.P->n, nh = (size_t)q.m->n_hyp, K = (size_t)q.K;
     const bool resident = ctx->p.scan_cache_bytes > 0 && find_table(*q.m, q.P->ns, q.lim) != nullptr;
     return align_up(sizeof(int2) * n) + align_up(sizeof(ScanInfo)) + align_up(8 * nh) * 2 + align_up(4 * nh) +
-           align_up(4 * K) * 2 + align_up(4 * K * q.P->n_orient) + align_up(8 * K) +
+           align_up(4 * K) * 3 + align_up(4 * K * q.P->n_orient) + align_up(8 * K) +
+           align_up(16ull * tam_chunk_cap(q.K, q.B, q.n_batches, tam_chunk_for(q.K, q.P->n_orient, ctx->n_sm))) +
+           align_up(4ull * (q.n_batches + 1)) +
+           align_up(4ull * 8 * 32 * q.P->n_orient * tam_offs_stride_for(tam_vpl_for(q.P->n))) +
            align_up(4ull * q.n_batches * ctx->p.local_topk) + align_up(sizeof(SelectState)) +
            align_up(sizeof(float) * q.P->n * ctx->p.n_skip_beam) + (resident ? 0 : align_up(4 * nh * q.P->ns));
 }
@@ -1907,14 +1958,15 @@ int relo_rrt_sample(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, dou
     t.TH = (t.H + 7) / 8;
     t.C = 65535;
     t.P = 0;
-    t.Wp = t.W;
-    const size_t pc = (size_t)t.W * t.H;
+    t.Wp = (t.W + 7) & ~7;
+    t.Hp = (t.H + 7) & ~7;
+    const size_t pc = (size_t)t.W * t.H, fc = (size_t)t.Wp * t.Hp;
     int8_t *raw = nullptr;
     float *clr = nullptr;
     float2 *xy = nullptr;
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&raw, cells}, {(void **)&t.grid, pc}, {(void **)&t.d2, pc * 4}, {(void **)&t.colsq, pc * 4},
-        {(void **)&t.summ, sizeof(int2) * (size_t)t.W * edt_segments(t.H)}, {(void **)&t.field, pc * 2},
+        {(void **)&t.summ, sizeof(int2) * (size_t)t.W * edt_segments(t.H)}, {(void **)&t.field, fc * 2},
         {(void **)&t.bits, occupancy_words(t.TW, t.TH) * 8}, {(void **)&clr, cells * 4},
         {(void **)&xy, sizeof(float2) * (size_t)(cap > 0 ? cap : 1)}};
     int rc = RELO_OK;
@@ -1955,6 +2007,21 @@ int relo_rrt_sample(relo_ctx *ctx, const int8_t *grid, int32_t w, int32_t h, dou
     for (auto &a : allocs) dev_free(ctx, *a.p, a.bytes);
     return rc;
 }
+
+int relo_set_tuning(relo_ctx *ctx, const relo_tune_entry *entries, int32_t n) {
+    if (!ctx || n < 0 || (n > 0 && !entries)) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < n; ++i) {
+        const relo_tune_entry &e = entries[i];
+        const bool ok = (e.kind == RELO_TUNE_TAM && e.val[0] >= 0 && e.val[0] <= 128 && e.val[0] % 8 == 0 &&
+                         e.val[1] >= 0 && e.val[1] <= 32) ||
+                        (e.kind == RELO_TUNE_CAST && e.val[0] >= 0 && e.val[0] <= 32);
+        if (!ok) return fail(ctx, RELO_E_INVALID_ARG, "bad tuning entry");
+    }
+    ctx->tuning.assign(entries, entries + n);
+    return RELO_OK;
+}
+
+int relo_tam_class(int32_t n_beams) { return n_beams < 1 ? -1 : tam_vpl_for(n_beams); }
 
 int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n) {
     if (!ctx || (!out && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");

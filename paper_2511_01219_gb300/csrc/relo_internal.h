@@ -41,14 +41,25 @@ struct MapDev {
     int W = 0, H = 0, TW = 0, TH = 0;
     int C = 0;                  // clamp (d_max / res)^2 used by the TAM field
     int32_t *d2 = nullptr;      // [H*W] exact squared EDT, -1 = no obstacle
-    uint16_t *field = nullptr;  // [(H+2P) * (W+2P)] min(d2, C), row-major with a border of P cells holding C
-    int P = 0, Wp = 0;          // border width and padded row length
+    uint16_t *field = nullptr;  // [Hp * Wp] min(d2, C) with a border of P cells holding C, in 8-row bands
+    int P = 0, Wp = 0, Hp = 0;  // border width; padded width and height (W + 2P, H + 2P rounded up to 8)
     uint64_t *bits = nullptr;   // occupancy, bit (y&7)*8 + (x&7): [TH*TW] the map (cells outside free), then the
                                 // four walk frames (walk_frame_words each: native, mirrored in x, y and both)
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
     int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
 };
+
+// The clamped field is stored in bands of 8 rows, each band column by
+// column: cell (x, y) of the padded grid (the map cell (x - P, y - P)) sits at
+// element 8 ((y / 8) Wp + x) + y % 8.  A 128-byte cache line then holds an
+// 8 x 8 block of cells (x a multiple of 8), so the endpoints of neighbouring
+// beams, which lie close together in x and in y, share lines; and the index
+// stays linear in x, so an endpoint offset (dx, dy) from a cell depends on the
+// cell only through y % 8 (its band phase).
+__host__ __device__ inline size_t field_index(int x, int y, int Wp) {
+    return (((size_t)(y >> 3) * (unsigned)Wp + (unsigned)x) << 3) + (unsigned)(y & 7);
+}
 
 // rows per column segment of the EDT column pass: at least 16, at most 64
 // segments, a multiple of 8 (the segment pass also builds the 8x8 tiles)
@@ -153,7 +164,7 @@ struct RayArgs {
 struct ReqDesc {
     // map tables
     const uint64_t *bits;
-    const uint16_t *field;       // padded clamped field, pointer to cell (0, 0)
+    const uint16_t *field;       // padded clamped field (8-row bands, field_index), pointer to padded cell (0, 0)
     int coarse, fine;            // ranking and scoring metrics (RELO_COARSE_*, RELO_FINE_*)
     int icp_iters;               // ICP iterations per local top-k pose (0: no refinement)
     const int32_t *d2map;        // [H*W] exact squared EDT, -1 = no obstacle (ICP pairs)
@@ -193,6 +204,15 @@ struct ReqDesc {
     long long *smad_num;         // [n_hyp]
     int32_t *smad_m;             // [n_hyp]
     int32_t *survivors;          // [K]
+    // TAM's work order: within each batch the survivor positions grouped by the band phase (y + P) % 8 of
+    // their cell, cut into chunks of at most tam_chunk of one phase: (phase, first, end) into surv_perm;
+    // the chunks of batches < b are tam_chunks[0, chunk_cnt[b])
+    int32_t *surv_perm;          // [K]
+    int32_t *tam_offs;           // [8][n_orient][32][tam_stride] TAM endpoint offsets by band phase (k_tam_offsets)
+    int tam_stride;              // slots per lane in tam_offs
+    int4 *tam_chunks;            // [sum over batches of ceil(n_b / tam_chunk) + 8]
+    int32_t *chunk_cnt;          // [n_batches + 1]
+    int tam_chunk;
     float *T;                    // [K * n_orient]
     unsigned long long *best_key;   // [K]
     int32_t *best_m;             // [K]
@@ -235,14 +255,34 @@ struct BatchState {
     unsigned long long dda_steps;   // cells entered by all rays of the batch
 };
 
-// TAM work of one request in one batch launch: survivors [s_begin, s_end),
-// split into n_chunks chunks of `chunk`, for each of its orientations; the
-// request's tasks are [task_base, task_base + n_orient * n_chunks).
+// TAM work of one request in one launch: the survivors of its batches
+// [batch_lo, batch_hi) (none when equal), for each of its orientations.  The
+// launch's tasks are (chunk of same-phase survivors, block of orientations);
+// the chunks are built on the device (launch_tam_chunks).
 struct TamSeg {
-    int task_base, s_begin, s_end, chunk, n_chunks;
+    int batch_lo, batch_hi;
 };
 
 constexpr int kMaxBatchRequests = 256;
+// survivors of one band phase per TAM task: the most (up to 64, a multiple of
+// 8) that still leave about three tasks (blocks of 4 orientations) per
+// resident CTA of five per SM, so the launch is not one ragged wave
+inline int tam_chunk_for(int K, int n_orient, int n_sm) {
+    const long long tasks_per_survivor = (n_orient + 3) / 4;
+    long long c = (long long)K * tasks_per_survivor / (3ll * 5 * n_sm);
+    c = c / 8 * 8;
+    return (int)(c < 8 ? 8 : c > 64 ? 64 : c);
+}
+// chunks of the TAM work order: per group of survivors (each batch, or all K as one group), its survivors in
+// chunks of one phase (at most one part chunk per phase); the per-batch count bounds both
+inline int tam_chunk_cap(int K, int B, int n_batches, int chunk) {
+    int cap = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        const int n = (K - b * B < B ? K - b * B : B);
+        cap += (n + chunk - 1) / chunk + 8;
+    }
+    return cap;
+}
 constexpr int kMaxBatches = 64;      // ceil(K / batch) limit, bounds the TamSeg table
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s);          // interior of the field, d2, bitmap
@@ -258,7 +298,8 @@ cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, ui
 // scan preparation alone, for a batch that casts no rays (launch_cast does it otherwise)
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s);
 // casts the total_chunks 32-ray chunks of the batch into the requests' scan tables
-cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, cudaStream_t s);
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, int ctas_per_sm,
+                        cudaStream_t s);
 // SMAD of every hypothesis of the batch from the requests' scan tables
 cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,
                         cudaStream_t s);
@@ -280,8 +321,15 @@ struct TamPlan {
 };
 // values per lane the TAM kernel holds for max_beams valid beams (-1 if too many)
 int tam_vpl_for(int max_beams);
-TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R,
-                 int max_beams, int max_C, int n_sm, TamSeg *segs);
+// the planned launch for the batches [batch_lo[r], batch_hi[r]) of each request r: segs[R], grid and kernel class
+TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams, int max_C, int n_sm,
+                 int ctas_per_sm, TamSeg *segs);
+// TAM's work order (surv_perm, tam_chunks, chunk_cnt) of every request, after the top-K
+cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s);
+// per-lane stride of the TAM endpoint offsets of a values-per-lane class
+int tam_offs_stride_for(int vpl);
+// every request's TAM endpoint offsets for all band phases and orientations (after the scan preparation)
+cudaError_t launch_tam_offsets(const ReqDesc *reqs, int R, int max_n_orient, cudaStream_t s);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
 // selection of batch indexes batch_lo .. batch_hi - 1 in order; with last, also every request's result.
 // With icp, only the local top-k (launch_icp and launch_icp_best take the rest).

@@ -5,7 +5,11 @@
 // endpoint cell is hypothesis + round-half-up(R_i * D_{(b_i + m) mod N_s} /
 // 2^46); its clamped squared distance b = min(d2, C) is read from the padded
 // field, whose border holds C (off-map endpoints take d = d_max), so the read
-// needs no bounds test.  The likelihood l
+// needs no bounds test.  The field is stored in bands of 8 rows (field_index):
+// a cache line holds an 8 x 8 block of cells, so the endpoints of
+// neighbouring beams share lines whichever way the contour runs, and an
+// endpoint's offset from its hypothesis depends on the hypothesis only
+// through its band phase (y + P) % 8.  The likelihood l
 // (Eq. 23) falls strictly as b grows, so the descending sort of Eq. 24 is the
 // ascending order of b: the warp finds the k-th smallest b by bisection over
 // [0, C] with register-resident values, and the top-k sum of l is
@@ -130,14 +134,53 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
     if (blockIdx.y == 0) scan_prep_request(d);
 }
 
-// Work is split into tasks (request, block of kTamQ consecutive orientations,
-// chunk of survivors).  A CTA first computes the endpoint offsets of its
-// block's orientations for every valid beam of the request,
-// round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis, as one linear
-// offset into the padded field, in shared memory; each warp then scores one
-// survivor at a time over the block's orientations, so the 64-bit offset
-// arithmetic is paid once per (orientation, beam) instead of once per
-// (survivor, orientation, beam).
+// Every request's endpoint offsets, once per batch: for band phase ph,
+// orientation q (m = q n_enum) and valid beam i, the field_index offset of the
+// endpoint cell round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis from
+// a cell of band phase ph (linear in the x offset, and in the y offset through
+// the bands crossed), laid out [ph][q][lane][slot] with the TAM kernel's
+// per-lane stride, so one block's offsets for one phase are one contiguous
+// span.  CTA (q, request) writes all eight phases of orientation q.
+__device__ void tam_offsets_one(const ReqDesc &d, int q) {
+    const int N = d.scan->n_valid;
+    const int m = q * d.n_enum;
+    const long long Wp8 = 8ll * d.Wp;
+    const int kS = d.tam_stride;
+    const size_t phase_step = (size_t)d.n_orient * 32 * kS;
+    int32_t *oq = d.tam_offs + (size_t)q * 32 * kS;
+    // k walks the orientation's table in memory order (lane-major), so every store is coalesced
+    for (int k = threadIdx.x; k < 32 * kS; k += blockDim.x) {
+        const int i = (k % kS) * 32 + k / kS;   // the beam in slot k % kS of lane k / kS
+        if (i >= N) continue;
+        const int2 bR = d.vbR[i];
+        int j = bR.x + m;
+        if (j >= d.ns) j -= d.ns;
+        const int2 dir = d.D[j];
+        const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
+        const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
+        // |ox|, |oy| < P keeps every endpoint inside the field's border
+#pragma unroll
+        for (int ph = 0; ph < 8; ++ph) {
+            const int v = ph + oy;
+            oq[ph * phase_step + k] = (int)(8ll * ox + Wp8 * (v >> 3)) + (v & 7);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_tam_offsets(const ReqDesc *__restrict__ reqs) {
+    const ReqDesc &d = reqs[blockIdx.y];
+    const int q = blockIdx.x;
+    if (q >= d.n_orient || d.state->done || !d.tam_offs) return;
+    tam_offsets_one(d, q);
+}
+
+// Work is split into tasks (request, chunk of survivors of one band phase,
+// block of kTamQ consecutive orientations); k_tam_chunks builds the chunks on
+// the device after the top-K.  A CTA copies the block's endpoint offsets for
+// its chunk's phase from the request's table (k_tam_offsets: one linear
+// offset per phase, orientation and valid beam, computed once per request)
+// into shared memory; each warp then scores its survivors of the chunk over
+// the block's orientations, every gather one add to the survivor's base.
 //
 // Selection.  The k-th smallest clamped d2 of a survivor rarely changes from
 // one orientation to the next (neighbouring orientations see nearly the same
@@ -162,15 +205,25 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
     __shared__ float s_ep[5];   // per-task constants of the epilogue
     __shared__ int s_fine;      // the task's scoring metric (read where needed, not held in a register)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) s_base[r] = segs[r].task_base;
+    // each request's tasks: its chunks in the launch's batches x its orientation blocks (counted on the device)
     if (threadIdx.x == 0) {
-        s_base[R] = total_tasks;
+        int base = 0;
+        for (int r = 0; r < R; ++r) {
+            s_base[r] = base;
+            const TamSeg sg = segs[r];
+            if (sg.batch_hi > sg.batch_lo) {
+                const ReqDesc &d = reqs[r];
+                base += (d.chunk_cnt[sg.batch_hi] - d.chunk_cnt[sg.batch_lo]) * ((d.n_orient + kTamQ - 1) / kTamQ);
+            }
+        }
+        s_base[R] = base;
         s_lut_r = -1;
     }
     __syncthreads();
+    total_tasks = s_base[R];
     float2 *lut = reinterpret_cast<float2 *>(smem);
     for (int task = blockIdx.x; task < total_tasks; task += gridDim.x) {
-        int lo = 0, hi = R - 1;   // last request whose task_base <= task
+        int lo = 0, hi = R - 1;   // the request whose tasks hold this one: last r with s_base[r] <= task
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_base[mid] <= task) lo = mid;
@@ -200,34 +253,29 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
         if (s_skip) continue;
         constexpr int kS = tam_offs_stride(VPL);
         int *offs = reinterpret_cast<int *>(smem + (((size_t)(d.C + 2) * sizeof(float2) + 15) & ~(size_t)15));
-        const int local = task - sg.task_base;
+        const int local = task - s_base[r];
         const int nblk = (d.n_orient + kTamQ - 1) / kTamQ;
         const int qb = local % nblk;
-        const int chunk = local / nblk;
+        const int4 ck = d.tam_chunks[d.chunk_cnt[sg.batch_lo] + local / nblk];   // (phase, first, end)
+        const int ph = ck.x;
         const int q0 = qb * kTamQ;
         const int nq = min(kTamQ, d.n_orient - q0);
-        for (int qi = 0; qi < nq; ++qi) {
-            const int m = (q0 + qi) * d.n_enum;
-            int *oq = offs + qi * 32 * kS;
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                const int2 bR = d.vbR[i];
-                int j = bR.x + m;
-                if (j >= d.ns) j -= d.ns;
-                const int2 dir = d.D[j];
-                const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
-                const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
-                oq[(i & 31) * kS + (i >> 5)] = oy * d.Wp + ox;   // |ox|, |oy| < P: inside the field's border
-            }
-        }
-        __syncthreads();
-        const int s_lo = sg.s_begin + chunk * sg.chunk;
-        const int s_hi = min(sg.s_end, s_lo + sg.chunk);
         const int C = d.C;
         const uint32_t none = (uint32_t)C + 1u;   // table entry with zero weight
         const float d_max = d.d_max;
-        for (int s = s_lo + warp; s < s_hi; s += kTamWarps) {
+        {
+            // the block's offsets for phase ph: nq x 32 x kS contiguous ints of the request's table
+            const int4 *src = reinterpret_cast<const int4 *>(d.tam_offs + ((size_t)ph * d.n_orient + q0) * 32 * kS);
+            int4 *dst = reinterpret_cast<int4 *>(offs);
+            const int n4 = nq * 32 * kS / 4;
+            for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+        }
+        __syncthreads();
+        for (int js = ck.y + warp; js < ck.z; js += kTamWarps) {
+            const int s = d.surv_perm[js];   // survivor position: its scores go to row s
             const int2 hc = d.hyps[d.survivors[s]];
-            const uint16_t *fh = d.field + (ptrdiff_t)hc.y * d.Wp + hc.x;
+            // the cell's column at the top of its band; the offsets of its phase lead to each endpoint
+            const uint16_t *fh = d.field + 8 * ((size_t)((hc.y + d.P) >> 3) * d.Wp + (hc.x + d.P));
             int hint = -1;   // the previous orientation's k-th smallest value
             float e_arg = 0.0f, e_sd = 0.0f;   // lane qi: orientation qi's exponent and s_d
             for (int qi = 0; qi < nq; ++qi) {
@@ -420,11 +468,56 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Chooses, per request, the number of survivor chunks per orientation so that
-// the whole launch's tasks fill whole waves of resident CTAs and whole rounds
-// of a CTA's warps, and lays the requests' tasks out one after another.
-TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *s_begin_per_req, int R, int max_beams,
-                 int max_C, int n_sm, TamSeg *segs) {
+// TAM's work order, one CTA per request: within each batch (with early
+// termination; without it TAM scores every batch in one launch, so all K
+// positions form one group), the survivor positions grouped by the band phase
+// (y + P) % 8 of their cell (the order inside a group is immaterial: every
+// position's scores are its own), then cut into chunks of at most tam_chunk
+// positions of one phase, so a CTA task computes one phase's endpoint offsets
+// for all its survivors.
+__global__ void __launch_bounds__(1024) k_tam_chunks(const ReqDesc *__restrict__ reqs) {
+    const ReqDesc &d = reqs[blockIdx.x];
+    __shared__ int s_cnt[8], s_next[8];
+    __shared__ int s_chunks;
+    if (threadIdx.x == 0) {
+        s_chunks = 0;
+        d.chunk_cnt[0] = 0;
+    }
+    const int groups = d.early_stop ? d.n_batches : 1;
+    for (int b = 0; b < groups; ++b) {
+        const int lo = b * d.B, hi = d.early_stop ? min(d.K, lo + d.B) : d.K;
+        if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_cnt[(d.hyps[d.survivors[i]].y + d.P) & 7], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = lo, nc = s_chunks;
+            for (int p = 0; p < 8; ++p) {
+                s_next[p] = run;
+                for (int f = run; f < run + s_cnt[p]; f += d.tam_chunk)
+                    d.tam_chunks[nc++] = make_int4(p, f, min(run + s_cnt[p], f + d.tam_chunk), 0);
+                run += s_cnt[p];
+            }
+            s_chunks = nc;
+            if (d.early_stop) d.chunk_cnt[b + 1] = nc;
+            else
+                for (int j = 1; j <= d.n_batches; ++j) d.chunk_cnt[j] = nc;
+        }
+        __syncthreads();
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            d.surv_perm[atomicAdd(&s_next[(d.hyps[d.survivors[i]].y + d.P) & 7], 1)] = i;
+        __syncthreads();
+    }
+}
+
+// The launch for the batches [batch_lo[r], batch_hi[r]) of every request:
+// its kernel class (values per lane and selection precision for the longest
+// scan and the largest clamp), the shared memory (table and one block's
+// endpoint offsets) and a grid of every resident CTA (or ctas_per_sm per SM
+// when that is fewer); the tasks are counted by the kernel from the
+// device-built chunk tables.
+TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams, int max_C, int n_sm,
+                 int ctas_per_sm, TamSeg *segs) {
     TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfMaxB};
     if (tp.vpl < 0) return tp;
     tp.smem = (((size_t)(max_C + 2) * sizeof(float2) + 15) & ~(size_t)15) +
@@ -434,46 +527,27 @@ TamPlan plan_tam(const int *nb_per_req, const int *n_orient_per_req, const int *
         tp.vpl = -1;
         return tp;
     }
-    const int slots = n_sm * occ;
-    long long orient_total = 0;
-    for (int r = 0; r < R; ++r)
-        if (nb_per_req[r] > 0) orient_total += n_orient_per_req[r];
-    int task = 0;
+    bool any = false;
     for (int r = 0; r < R; ++r) {
-        const int nb = nb_per_req[r];
-        TamSeg &g = segs[r];
-        g.task_base = task;
-        g.s_begin = s_begin_per_req[r];
-        g.s_end = g.s_begin + (nb > 0 ? nb : 0);
-        if (nb <= 0) {
-            g.chunk = 1;
-            g.n_chunks = 0;
-            continue;
-        }
-        // this request's share of the slots, in proportion to its orientations
-        const double share = (double)slots * n_orient_per_req[r] / (double)(orient_total > 0 ? orient_total : 1);
-        const int max_chunks = (nb + kTamWarps - 1) / kTamWarps;
-        int best_nc = 1;
-        double best_eff = -1.0;
-        for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
-            const int chunk = (nb + nc - 1) / nc;
-            const double tasks = (double)((n_orient_per_req[r] + kTamQ - 1) / kTamQ) * ((nb + chunk - 1) / chunk);
-            const double waves = ceil(tasks / (share > 1.0 ? share : 1.0));
-            const double eff = tasks / (waves * (share > 1.0 ? share : 1.0)) * (double)chunk /
-                               (double)(((chunk + kTamWarps - 1) / kTamWarps) * kTamWarps);
-            if (eff > best_eff + 1e-9) {
-                best_eff = eff;
-                best_nc = nc;
-            }
-        }
-        g.chunk = (nb + best_nc - 1) / best_nc;
-        g.n_chunks = (nb + g.chunk - 1) / g.chunk;
-        task += (n_orient_per_req[r] + kTamQ - 1) / kTamQ * g.n_chunks;
+        segs[r] = TamSeg{batch_lo[r], batch_hi[r]};
+        any = any || batch_hi[r] > batch_lo[r];
     }
-    tp.total_tasks = task;
-    tp.grid = task < slots ? task : slots;
-    if (tp.grid < 1) tp.grid = 1;
+    tp.total_tasks = any ? 1 : 0;
+    tp.grid = n_sm * (ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ);
     return tp;
+}
+
+int tam_offs_stride_for(int vpl) { return tam_offs_stride(vpl); }
+
+cudaError_t launch_tam_offsets(const ReqDesc *reqs, int R, int max_n_orient, cudaStream_t s) {
+    if (R <= 0 || max_n_orient <= 0) return cudaSuccess;
+    k_tam_offsets<<<dim3(max_n_orient, R), 256, 0, s>>>(reqs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s) {
+    k_tam_chunks<<<R, 1024, 0, s>>>(reqs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {

@@ -385,6 +385,35 @@ def test_icp_on_the_room_workload(relo, workload):
              batch=8, local_topk=4)
 
 
+@pytest.mark.parametrize("fine", [0, 1, 2, 3])
+def test_translation_sweep_matches_oracle(relo, workload, fine):
+    """The Fig. 8 sweep in kind (office workload): 15 cells 0.1 m apart through
+    the scan's true position x 36 orientations 10 degrees apart, scored by
+    each scoring metric (TAM, TAM_mean, wp_baseline, wp_LF) through the library
+    as bench.py's sweep runs it; every one of the 540 scores equals the
+    oracle's at the same pose within 1e-5 (of its magnitude)."""
+    torch = torch_()
+    wl = workload(1)
+    cells, offs, axis, qs = workloads.sweep_poses(wl)
+    ctx = relo.Relo(n_orient=360, topk=len(cells), batch=len(cells), local_topk=1, early_stop=0, fine_metric=fine)
+    mid = ctx.load_map(wl.grid, wl.res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(cells, wl.res))
+    got = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert got.status == relo.OK
+    surv = ctx.stage(relo.STAGE_SURVIVORS, torch.empty(len(cells), dtype=torch.int32, device="cuda")).cpu().numpy()
+    T = ctx.stage(relo.STAGE_TAM, torch.empty(len(cells) * 360, dtype=torch.float32, device="cuda"))
+    ctx.close()
+    rows = np.empty((len(cells), 360), np.float32)
+    rows[surv] = T.cpu().numpy().reshape(len(cells), 360)
+    prm = oracle.Params(n_orient=360, topk=len(cells))
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    d2 = oracle.edt(wl.grid)
+    pairs = np.repeat(cells, len(qs), axis=0)
+    ms = np.tile(np.array(qs, np.int32) * pl["n_enum"], len(cells))
+    want = oracle.tam(wl.grid, pairs, ms, pl, prm, wl.res, d2, metric=fine).reshape(len(cells), len(qs))
+    assert_tam_close(rows[:, qs], want)
+
+
 def test_warehouse_full_size_sampled(relo, workload):
     """4096^2 map, 20000 hypotheses, 720 orientations, K = 1024: SMAD and the
     survivor list bit-exact everywhere; TAM on 48 sampled survivors x 720."""
@@ -687,7 +716,7 @@ def test_served_admission_by_budget(relo, workload):
     (status, res, lat), = poll_all(ctx, [t])
     assert status == relo.E_OVER_BUDGET
     ctx.serve_stop()
-    ctx.serve_start(max_batch=8, max_inflight=2, hbm_budget=3 << 20)   # room for about one request at a time
+    ctx.serve_start(max_batch=8, max_inflight=2, hbm_budget=8 << 20)   # room for a request or two at a time
     tickets = [ctx.submit(*r) for r in reqs]
     done = poll_all(ctx, tickets)
     ctx.serve_stop()
@@ -719,6 +748,38 @@ def test_served_request_deadlines(relo, workload):
             ctx.submit(*reqs[0], timeout_s=-1.0)
         finally:
             ctx.serve_stop()
+    ctx.close()
+
+
+def test_launch_shapes_do_not_change_results(relo, workload):
+    """The autotuner's knobs (survivors per TAM task, resident CTAs per SM of
+    TAM and of the ray cast) change only the time: every TAM score and the
+    result are bitwise those of the built-in shapes; malformed entries are
+    rejected."""
+    torch = torch_()
+    wl = workload(1)
+    K = wl.topk
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=K, early_stop=0)
+    mid = ctx.load_map(wl.grid, wl.res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(wl.hyps, wl.res))
+
+    def scores():
+        r = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range).as_dict()
+        T = ctx.stage(relo.STAGE_TAM, torch.empty(K * wl.n_orient, dtype=torch.float32, device="cuda"))
+        return r, T.cpu().numpy()
+    base, T0 = scores()
+    cls = relo.tam_class(len(wl.ranges))
+    for entries in ([(relo.TUNE_TAM, (cls, wl.n_orient, K), (8, 1))],
+                    [(relo.TUNE_TAM, (0, 0, 0), (64, 2)), (relo.TUNE_CAST, (0, 0, 0), (2, 0))],
+                    [(relo.TUNE_TAM, (cls, 0, 0), (128, 0)), (relo.TUNE_CAST, (wl.n_s, 0, 0), (1, 0))]):
+        ctx.set_tuning(entries)
+        got, T = scores()
+        assert got == base
+        assert np.array_equal(T.view(np.uint32), T0.view(np.uint32))
+    for bad in ([(relo.TUNE_TAM, (0, 0, 0), (12, 0))], [(9, (0, 0, 0), (8, 0))], [(relo.TUNE_CAST, (0, 0, 0), (-1, 0))]):
+        with pytest.raises(relo.ReloError):
+            ctx.set_tuning(bad)
+    ctx.set_tuning([])
     ctx.close()
 
 

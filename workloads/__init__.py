@@ -425,6 +425,30 @@ def served_scans(maps, per_map: int = 6, seed: int = 1004, n_orient: int = 360):
     return pool
 
 
+def sweep_poses(wl, n_pos: int = 15, step_m: float = 0.1, n_orient_sweep: int = 36, orient_step_deg: int = 10):
+    """The poses of a translation-affinity sweep in the manner of Fig. 8: n_pos
+    cells step_m apart through the scan's true position along the first axis
+    (x, then y) whose cells are all free, and n_orient_sweep orientations
+    orient_step_deg apart starting at the true one (on a grid of 360
+    orientations).  Returns (cells int32 [n_pos, 2], offsets in cells, axis
+    name, orientation indices q of the 360-grid)."""
+    gx, gy, gth = wl.gt_pose
+    cx, cy = int(round(gx / wl.res - 0.5)), int(round(gy / wl.res - 0.5))
+    step = int(round(step_m / wl.res))
+    offs = (np.arange(n_pos) - n_pos // 2) * step
+    free = wl.grid < 65
+    for ax, (dx, dy) in enumerate(((1, 0), (0, 1))):
+        cells = np.stack([cx + dx * offs, cy + dy * offs], 1)
+        inside = ((cells[:, 0] >= 0) & (cells[:, 0] < wl.grid.shape[1]) & (cells[:, 1] >= 0) &
+                  (cells[:, 1] < wl.grid.shape[0]))
+        if inside.all() and free[cells[:, 1], cells[:, 0]].all():
+            m_true = int(round(gth / (2 * math.pi) * wl.n_s)) % wl.n_s
+            q_true = m_true // (wl.n_s // 360)
+            qs = [(q_true + orient_step_deg * j) % 360 for j in range(n_orient_sweep)]
+            return cells.astype(np.int32), offs, "xy"[ax], qs
+    raise RuntimeError("no axis through the true position with all sweep cells free")
+
+
 def cell_centres(cells: np.ndarray, res: float) -> np.ndarray:
     return (cells.astype(np.float64) + 0.5) * res
 
