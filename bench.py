@@ -72,11 +72,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (default: min(steps, 200))")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep", "rrt", "table2"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "served", "sweep", "rrt", "table2", "table3"],
                     help="single: one request per step on --config's workload (default; the line also carries the "
                          "batched and served forms unless --no-extras); batched: 64 mixed requests per step; "
                          "served: Poisson arrivals against 8 resident maps")
     ap.add_argument("--no-extras", action="store_true", help="single: leave out the batched and served forms")
+    ap.add_argument("--tune", action="store_true",
+                    help="batched / single: run the launch-shape autotuner first and update its cache for this GPU")
     ap.add_argument("--extra-steps", type=int, default=10, help="single: timed steps of the batched form")
     ap.add_argument("--rates", default="",
                     help="served: arrival rates per second (default: a ladder that grows by 1.5x from 250/s until "
@@ -219,6 +222,17 @@ def committed_traffic(stage: str, config: int, key: str = "dram_bytes_per_launch
     return rec.get(key) if h == rec["source_sha"] else None
 
 
+def apply_tuning(ctx, torch, local) -> dict:
+    """Loads the autotuner's cached launch shapes for this GPU into ctx, if a
+    cache exists (paper_2511_01219_gb300/tuning/<device>.json)."""
+    from paper_2511_01219_gb300 import autotune
+    path = autotune.cache_path(torch.cuda.get_device_name(local))
+    entries = autotune.load(path)
+    if entries:
+        ctx.set_tuning(entries)
+    return {"source": os.path.relpath(path, ROOT) if entries else None, "entries": len(entries)}
+
+
 def run_ours(args, world, rank, local, dist):
     import numpy as np
     import torch
@@ -242,6 +256,7 @@ def run_ours(args, world, rank, local, dist):
     mid = ctx.load_map_dev(grid_d, wl.res)
     ctx.set_hypotheses_cells_dev(mid, hyps_d)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    tuning = apply_tuning(ctx, torch, local)
 
     def step():
         ctx.update_map_dev(mid, grid_d)
@@ -250,6 +265,21 @@ def run_ours(args, world, rank, local, dist):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    if args.tune:
+        from paper_2511_01219_gb300 import autotune
+        cache = autotune.cache_path(torch.cuda.get_device_name(local))
+        res_tune = autotune.tune(ctx, step, [(len(wl.ranges), wl.n_orient, min(wl.topk, len(wl.hyps)))],
+                                 log=lambda s: print(s, file=sys.stderr))
+        merged = {(k, tuple(key)): val for k, key, val in autotune.load(cache)}
+        merged.update({(k, tuple(key)): val for k, key, val in res_tune["entries"]})
+        autotune.save(cache, [(k, key, val) for (k, key), val in merged.items()],
+                      {"device": torch.cuda.get_device_name(local), "workloads": "batched + single"})
+        tuning = apply_tuning(ctx, torch, local)
+        tuning["tuning_run"] = {"tam_ms": res_tune["tam_ms"], "cast_ms": res_tune["cast_ms"],
+                                "seconds": res_tune["seconds"], "trials": len(res_tune["trials"])}
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
     r = relo.result_from_bytes(bytes(res_d.cpu().numpy()))
     if r.status != relo.OK:
         raise RuntimeError(f"relocalization failed with status {r.status}")
@@ -371,6 +401,7 @@ def run_ours(args, world, rank, local, dist):
         "roofline": main_roof,
         "roofline_all": roof,
         "clocks": clk,
+        "tuning": tuning,
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, ctx, mid, wl, relo, torch, flush, dist, world)
@@ -382,7 +413,7 @@ def run_ours(args, world, rank, local, dist):
     if not args.no_extras:
         b = run_batched(args, world, rank, local, dist, steps=args.extra_steps)
         line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "relocalizations_per_s", "latency_ms",
-                                             "gpu_launches", "stage_ms_per_step", "clocks")}
+                                             "gpu_launches", "stage_ms_per_step", "clocks", "launch_shapes")}
         line["batched"]["workload"] = b["config"]["workload"]
         line["batched"]["steps"] = b["steps"]
         line["batched"]["evals_per_step"] = b["config"]["evals_per_step"]
@@ -520,23 +551,7 @@ def run_sweep(args, world, rank, local, dist):
     torch.cuda.set_device(local)
     wl = workloads.config(OFFICE)
     gx, gy, gth = wl.gt_pose
-    cx, cy = int(round(gx / wl.res - 0.5)), int(round(gy / wl.res - 0.5))
-    step = int(round(0.1 / wl.res))
-    offs = np.arange(-7, 8) * step
-    free = wl.grid < 65
-    axis = None
-    for ax, (dx, dy) in enumerate(((1, 0), (0, 1))):
-        cells = np.stack([cx + dx * offs, cy + dy * offs], 1)
-        inside = (cells[:, 0] >= 0) & (cells[:, 0] < wl.grid.shape[1]) & (cells[:, 1] >= 0) & (cells[:, 1] < wl.grid.shape[0])
-        if inside.all() and free[cells[:, 1], cells[:, 0]].all():
-            axis = "xy"[ax]
-            break
-    if axis is None:
-        raise RuntimeError("no axis through the true position with 15 free cells")
-    n_s = wl.n_s
-    m_true = int(round(gth / (2 * math.pi) * n_s)) % n_s
-    q_true = m_true // (n_s // 360)
-    sweep_q = [(q_true + 10 * j) % 360 for j in range(36)]   # 10-degree steps from the true orientation
+    cells, offs, axis, sweep_q = workloads.sweep_poses(wl)
     metrics = ["tam", "tam_mean", "baseline", "lf"]
     out = {}
     for fine, name in enumerate(metrics):
@@ -641,6 +656,88 @@ def run_table2(args, world, rank, local, dist):
             "arms": arms}
 
 
+def run_table3(args, world, rank, local, dist):
+    """Table III in kind on the office map: the batched loop of Sec. III
+    (batches of 200 survivors of the SMAD top-K, local top-20 refined by ICP
+    and scored again, early termination at tau = 0.95) with three scoring
+    metrics (wp_baseline of
+    Eq. 33, TAM_mean of Eq. 34, TAM of Eq. 31) over hypotheses from Algorithm 1
+    at rho = 1.0 m and 0.5 m (relo_rrt_sample, from the grid).  Eight seeded
+    trial poses on traversable cells with random headings, each with a noisy
+    1081-beam 270-degree scan (the office noise model).  Success as in Sec.
+    IV-C: position error < 0.5 m and heading error < 30 degrees.  Per arm:
+    success rate, mean / std of the time per relocalization (10 repeats per
+    trial), batches run."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_01219_gb300 as relo
+    import workloads
+
+    torch.cuda.set_device(local)
+    wl = workloads.config(OFFICE)
+    res, r_robot = wl.res, 0.21
+    rng = np.random.default_rng(2513)
+    trials = []
+    hyp_sets = {}
+    clr = workloads.clearance_table(wl.grid, res)
+    ok = np.argwhere(clr >= 2 * r_robot)
+    p0 = workloads.free_start(wl.grid, res, r_robot, 31, clr)
+    ctx0 = relo.Relo()
+    for rho in (1.0, 0.5):
+        xy, rounds, nodes = ctx0.rrt_sample(wl.grid, res, p0, rho, 0.6, r_robot, 2, seed=31)
+        cells = np.unique(np.floor(xy / res).astype(np.int32), axis=0)
+        hyp_sets[rho] = cells
+    ctx0.close()
+    angles = wl.angles
+    for t in range(8):
+        cy, cx = ok[int(rng.integers(len(ok)))]
+        x, y = (cx + rng.uniform(0.1, 0.9)) * res, (cy + rng.uniform(0.1, 0.9)) * res
+        th = float(rng.uniform(-math.pi, math.pi))
+        z = workloads.add_noise(workloads.render_scan(wl.grid, res, (x, y, th), angles, wl.max_range), wl.max_range,
+                                4000 + t)
+        trials.append(((x, y, th), z))
+    arms = {}
+    icp = args.icp_iters if args.icp_iters > 0 else 10   # the local top-k refined as in Sec. III
+    for rho, cells in hyp_sets.items():
+        K = min(len(cells), 4096)
+        for name, code in (("wp_baseline", relo.FINE_BASELINE), ("tam_mean", relo.FINE_TAM_MEAN), ("tam", relo.FINE_TAM)):
+            ctx = relo.Relo(n_orient=wl.n_orient, topk=K, batch=200, local_topk=20, tau=0.95, early_stop=1,
+                            fine_metric=code, icp_iters=icp)
+            mid = ctx.load_map(wl.grid, res)
+            ctx.set_hypotheses(mid, workloads.cell_centres(cells, res))
+            ms, batches, succ = [], [], 0
+            for (x, y, th), z in trials:
+                for _ in range(2):
+                    got = ctx.relocalize(mid, z, angles, wl.max_range)
+                torch.cuda.synchronize()
+                reps = 10
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    got = ctx.relocalize(mid, z, angles, wl.max_range)
+                ms.append((time.perf_counter() - t0) * 1e3 / reps)
+                batches.append(got.n_batches)
+                d_err = math.hypot(got.x - x, got.y - y)
+                a_err = abs(math.degrees(math.remainder(got.theta - th, 2 * math.pi)))
+                succ += int(d_err < 0.5 and a_err < 30.0)
+            arms[f"rho{rho}_{name}"] = {"hypotheses": int(len(cells)), "K": K,
+                                        "success_rate": round(succ / len(trials), 3),
+                                        "ms_per_relocalization_mean": round(float(np.mean(ms)), 3),
+                                        "ms_per_relocalization_std": round(float(np.std(ms)), 3),
+                                        "batches": batches}
+            ctx.close()
+    return {"metric": "Table III in kind: success and time per relocalization by scoring metric and rho",
+            "value": None, "unit": None, "n_gpus": world,
+            "data": "synthetic office map (1024x1024 at 0.05 m), 8 seeded trial poses with noisy scans",
+            "config": {"workload": "table3: RRT hypotheses (relo_rrt_sample) at rho 1.0 and 0.5 m, 360 orientations, "
+                                   "batches of 200 of the top K = min(N_h, 4096), local top-20 refined by "
+                                   f"{icp} ICP iterations, tau 0.95, early termination; success = position error "
+                                   "< 0.5 m and heading error < 30 deg"},
+            "arms": arms}
+
+
 def run_rrt(args, world, rank, local, dist):
     """Hypothesis generation (Algorithm 1) on the office map (1024^2 at 0.05 m,
     rho for about 5000 hypotheses): the GPU sampler (sub-batched nearest-node
@@ -723,8 +820,39 @@ def run_batched(args, world, rank, local, dist, steps=None):
         items.append((mid, z, it.angles, it.max_range, it.topk))
     res_t = torch.empty(len(items) * relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    for _ in range(max(args.warmup, 3)):
+    from paper_2511_01219_gb300 import autotune
+    cache = autotune.cache_path(torch.cuda.get_device_name(local))
+
+    def one():
         ctx.relocalize_batch_dev(items, res_t)
+    for _ in range(max(args.warmup, 3)):
+        one()
+    torch.cuda.synchronize()
+    # the same step with the library's built-in launch shapes, timed alone, before the tuned ones
+    builtin_ms = []
+    ctx.set_tuning([])
+    for i in range(n_steps):
+        flush.fill_(i & 0xFF)
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one()
+        b_.record(stream)
+        b_.synchronize()
+        builtin_ms.append(a.elapsed_time(b_))
+    shapes = [(len(it.ranges), 360, min(it.topk, len(it.hyps))) for it in ins]
+    tuned_info = None
+    if getattr(args, "tune", False):
+        res_tune = autotune.tune(ctx, one, shapes, log=lambda s: print(s, file=sys.stderr))
+        merged = {(k, tuple(key)): val for k, key, val in autotune.load(cache)}
+        merged.update({(k, tuple(key)): val for k, key, val in res_tune["entries"]})
+        autotune.save(cache, [(k, key, val) for (k, key), val in merged.items()],
+                      {"device": torch.cuda.get_device_name(local), "workloads": "batched + single"})
+        tuned_info = {"tam_ms": res_tune["tam_ms"], "cast_ms": res_tune["cast_ms"], "seconds": res_tune["seconds"],
+                      "trials": len(res_tune["trials"])}
+    entries = autotune.load(cache)
+    ctx.set_tuning(entries)
+    for _ in range(2):
+        one()
     torch.cuda.synchronize()
     raw = bytes(res_t.cpu().numpy())
     results = [relo.result_from_bytes(raw[i * relo.RESULT_BYTES:(i + 1) * relo.RESULT_BYTES]) for i in range(len(items))]
@@ -769,6 +897,11 @@ def run_batched(args, world, rank, local, dist, steps=None):
         "gpu_launches": int(k1 - k0),
         "stage_ms_per_step": {k: round(v / n_steps, 5) for k, v in stage_ms.items()},
         "clocks": clk,
+        "launch_shapes": {"tuned_entries": len(entries),
+                          "source": os.path.relpath(cache, ROOT) if entries else None,
+                          "ms_per_step_builtin": statistics.median(builtin_ms),
+                          "ms_per_step_tuned": statistics.median(per),
+                          "tuning_run": tuned_info},
     }
 
 
@@ -969,7 +1102,7 @@ def main():
     if args.impl == "ours" and args.workload != "single":
         dist = dist_init(world)
         fn = {"batched": run_batched, "served": run_served, "sweep": run_sweep, "rrt": run_rrt,
-              "table2": run_table2}[args.workload]
+              "table2": run_table2, "table3": run_table3}[args.workload]
         line = fn(args, world, rank, local, dist)
         if rank == 0:
             print(json.dumps(line))
