@@ -44,6 +44,7 @@ sys.path.insert(0, ROOT)
 METRIC = "hypothesis×orientation evals/s (SMAD+TAM); relocalizations/s at p99 latency"
 UNIT = "evals/s"
 ROOFLINE_STAGES = ["raycast", "smad", "tam"]   # kernels timed inside the timed region for their roofline
+SIDE_STAGES = ("edt_field",)   # stages the library runs on its side stream
 OFFICE = 1      # the office workload (sweep, table2, rrt)
 DATA = {1: "synthetic (seeded office map, RRT hypotheses, noisy LiDAR scan)",
         2: "synthetic (seeded warehouse map, RRT hypotheses, noisy LiDAR scan)"}
@@ -244,7 +245,9 @@ def run_ours(args, world, rank, local, dist):
 
     torch.cuda.set_device(local)
     wl = workloads.config(args.config)
-    stream = torch.cuda.Stream()
+    # a high-priority stream for the request path, so the map update's field pass (on the library's low-priority
+    # side stream) yields to the ray cast and SMAD
+    stream = torch.cuda.Stream(priority=-1)
     torch.cuda.set_stream(stream)
     ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0, stream=stream,
                     coarse_metric=["smad", "caer", "smad_direct"].index(args.coarse),
@@ -326,9 +329,12 @@ def run_ours(args, world, rank, local, dist):
     n_valid, n_orient, K = info[3], info[1], info[6]
     peaks, peak_kind = measured_peaks()
     l2 = relo.probe_l2()
-    bd_total = sum(bd_ms.values())
-    shares = {k: v / bd_total for k, v in bd_ms.items()}
-    dominant = max(bd_ms, key=bd_ms.get)
+    # the EDT's field pass runs on the library's side stream beside the ray cast: its event time is
+    # wall time on shared SMs, so the shares and the dominant kernel are over the main stream's stages
+    main_ms = {k: v for k, v in bd_ms.items() if k not in SIDE_STAGES}
+    bd_total = sum(main_ms.values())
+    shares = {k: v / bd_total for k, v in main_ms.items()}
+    dominant = max(main_ms, key=main_ms.get)
     tam_bytes = 2.0 * n_valid * K * n_orient * args.steps          # 2 B field read per valid beam per (h, m)
     hbm = peaks["hbm_gbs"]
     roof = {}
@@ -388,6 +394,10 @@ def run_ours(args, world, rank, local, dist):
         "config": {"workload": WORKLOADS[args.config], "map": list(wl.grid.shape), "n_hyp": len(wl.hyps),
                    "n_orient": wl.n_orient, "n_beams": len(wl.ranges), "n_s": wl.n_s, "topk": wl.topk,
                    "evals_per_step": evals_per_step, "l2": "flushed before every timed step (256 MiB write)",
+                   "timed_step": "map update from a device grid and its EDT, scan preparation, ray cast, SMAD, "
+                                 "top-K, TAM, selection (hypotheses stay resident; e2e uploads map, hypotheses and "
+                                 "scan from host buffers every step); the ray direction tables (k_ray_tables, once "
+                                 "per sensor geometry) are built before the timed region",
                    "ranking": args.coarse, "scoring": args.fine, "icp_iters": args.icp_iters,
                    "parallelism": f"replicas x{world}"},
         "relocalizations_per_s": world * args.steps / (t_max / 1e3),
@@ -396,7 +406,9 @@ def run_ours(args, world, rank, local, dist):
         "stage_ms_per_step": {k: round(v / n_bd, 5) for k, v in bd_ms.items()},
         "stage_share": {k: round(v, 4) for k, v in shares.items()},
         "stage_times": f"stage_ms_per_step and stage_share from {n_bd} further steps with every kernel bracketed by "
-                       f"events; the timed steps bracket only {', '.join(ROOFLINE_STAGES)} (the roofline kernels)",
+                       f"events; the timed steps bracket only {', '.join(ROOFLINE_STAGES)} (the roofline kernels); "
+                       f"{', '.join(SIDE_STAGES)} runs on the side stream beside the ray cast and is left out of the "
+                       f"shares",
         "dominant_kernel": dominant,
         "roofline": main_roof,
         "roofline_all": roof,
@@ -413,7 +425,8 @@ def run_ours(args, world, rank, local, dist):
     if not args.no_extras:
         b = run_batched(args, world, rank, local, dist, steps=args.extra_steps)
         line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "relocalizations_per_s", "latency_ms",
-                                             "gpu_launches", "stage_ms_per_step", "clocks", "launch_shapes")}
+                                             "gpu_launches", "stage_ms_per_step", "clocks", "launch_shapes",
+                                             "resident_tables")}
         line["batched"]["workload"] = b["config"]["workload"]
         line["batched"]["steps"] = b["steps"]
         line["batched"]["evals_per_step"] = b["config"]["evals_per_step"]
@@ -882,6 +895,36 @@ def run_batched(args, world, rank, local, dist, steps=None):
     value = sum_over_ranks(dist, float(evals * n_steps)) / (t_max / 1e3)
     pct = sorted(per)
     ctx.close()
+    # The same requests against resident synthesized scans and window sums: they depend only on (map, hypotheses,
+    # sensor), which a deployment keeps while the real scans change, so after the first step no ray is cast.
+    # Reported beside the step above, not in place of it.
+    ctx = relo.Relo(n_orient=360, topk=1024, batch=1024, local_topk=20, early_stop=0, stream=stream,
+                    scan_cache_bytes=32 << 30)
+    ctx.set_tuning(entries)
+    items2 = []
+    for it, (g, h, z) in zip(ins, zip(keep[0::3], keep[1::3], keep[2::3])):
+        mid = ctx.load_map_dev(g, it.res)
+        ctx.set_hypotheses_cells_dev(mid, h)
+        items2.append((mid, z, it.angles, it.max_range, it.topk))
+
+    def two():
+        ctx.relocalize_batch_dev(items2, res_t)
+    for _ in range(3):
+        two()
+    torch.cuda.synchronize()
+    raw2 = bytes(res_t.cpu().numpy())
+    same = raw2 == raw
+    tab_ms = []
+    for i in range(n_steps):
+        flush.fill_(i & 0xFF)
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        two()
+        b_.record(stream)
+        b_.synchronize()
+        tab_ms.append(a.elapsed_time(b_))
+    tables = ctx.scan_cache_stats()
+    ctx.close()
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_steps, "warmup": args.warmup,
         "ms_per_step": t_max / n_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -902,6 +945,9 @@ def run_batched(args, world, rank, local, dist, steps=None):
                           "ms_per_step_builtin": statistics.median(builtin_ms),
                           "ms_per_step_tuned": statistics.median(per),
                           "tuning_run": tuned_info},
+        "resident_tables": {"ms_per_step": statistics.median(tab_ms),
+                            "relocalizations_per_s": len(items) / (statistics.median(tab_ms) / 1e3),
+                            "results_equal": same, "tables": tables},
     }
 
 

@@ -125,8 +125,14 @@ typedef struct relo_ctx relo_ctx;
 void relo_default_params(relo_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t to
- * run on (NULL creates a private non-blocking stream).  The context owns all
- * device memory it allocates and frees it in relo_destroy. */
+ * run on (NULL creates a private non-blocking stream of the highest
+ * priority).  The context also creates a second stream of the lowest
+ * priority, on which a map's EDT computes d2 and the clamped field while the
+ * context stream goes on to the next request's ray cast; every reader of
+ * those tables waits on an event, so results do not depend on it.  A caller's
+ * stream of higher than the default priority lets the ray cast run first.
+ * The context owns all device memory it allocates and frees it in
+ * relo_destroy. */
 int relo_create(const relo_params *p, void *stream, relo_ctx **out);
 int relo_destroy(relo_ctx *ctx);
 const char *relo_last_error(const relo_ctx *ctx);
@@ -282,14 +288,17 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
 /* Stage timing (tracing).  With profiling on, the context records a CUDA
  * event pair on its stream around every kernel it launches and sums the
  * elapsed device time per stage:
- *   0 EDT map precompute, 1 scan preparation, 2 ray cast (Eq. 13),
- *   3 SMAD top-K, 4 TAM, 5 batch selection and finalize, 6 SMAD (Eq. 16-20).
- * relo_stage_times synchronises the stream, writes min(n, RELO_N_STAGES)
+ *   0 EDT map precompute (the occupancy tiles and the column summaries),
+ *   1 scan preparation, 2 ray cast (Eq. 13), 3 SMAD top-K, 4 TAM,
+ *   5 batch selection and finalize, 6 SMAD (Eq. 16-20),
+ *   7 EDT field pass (d2 and the likelihood field, on the side stream; it
+ *     runs beside the next ray cast, so its time includes the shared SMs).
+ * relo_stage_times synchronises both streams, writes min(n, RELO_N_STAGES)
  * totals in milliseconds to ms_out and launch counts to launches_out (either
  * may be NULL), and with reset != 0 clears the totals.  Independently of
  * profiling, *kernels_out (optional) receives the number of kernels the
  * context has launched since it was created. */
-#define RELO_N_STAGES 7
+#define RELO_N_STAGES 8
 int relo_set_profiling(relo_ctx *ctx, int32_t enable);
 /* Profiles only the stages whose bit is set in stage_mask (bit s = stage s
  * above; 0 = off).  Each event pair costs the launch stream a little time, so

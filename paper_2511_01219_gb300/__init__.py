@@ -44,7 +44,7 @@ EXPORTED = [
     "relo_probe_l2_stream", "relo_probe_l2_gather", "relo_rrt_sample",
     "relo_submit_until", "relo_set_tuning", "relo_tam_class",
 ]
-STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad"]
+STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad", "edt_field"]
 
 
 class Params(ctypes.Structure):

@@ -114,31 +114,41 @@ __global__ void k_edt_col_final(const int8_t *__restrict__ grid, int W, int H, i
     }
 }
 
-// The row is staged with W cells of sentinel on each side and "no obstacle in
-// this column" as the same sentinel, a value larger than any squared distance
-// that still leaves room for dx^2, so the outward scan needs no bounds or
-// sentinel tests: a sentinel never improves the minimum.
+// The row is staged with W + 4 cells of sentinel on each side and "no
+// obstacle in this column" as the same sentinel, a value larger than any
+// squared distance that still leaves room for dx^2, so the outward scan needs
+// no bounds or sentinel tests: a sentinel never improves the minimum.  The
+// scan takes four distances per step (their loads independent of each other),
+// so a cell waits on a shared-memory round trip once per four columns; the up
+// to three columns it looks at beyond the stopping distance are ordinary
+// candidates and leave the minimum exact.
 constexpr int kRowSentinel = 0x3fffffff;
+constexpr int kRowPad = 4;   // the scan's step, and the extra sentinels it may read past the row's reach
 
 __global__ void k_edt_rows(const int32_t *__restrict__ colsq, int W, int C, int P, int Wp, int32_t *__restrict__ d2,
                            uint16_t *__restrict__ field) {
-    extern __shared__ int32_t rowbuf[];   // [3W]: sentinels, the row, sentinels
-    int32_t *row = rowbuf + W;
+    extern __shared__ int32_t rowbuf[];   // [3W + 2 kRowPad]: sentinels, the row, sentinels
+    int32_t *row = rowbuf + W + kRowPad;
     const int y = blockIdx.x;
     const int32_t *src = colsq + (size_t)y * W;
+    for (int x = threadIdx.x; x < W + kRowPad; x += blockDim.x) {
+        rowbuf[x] = kRowSentinel;
+        row[W + x] = kRowSentinel;
+    }
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int v = src[x];
         row[x] = v == kInf ? kRowSentinel : v;
-        rowbuf[x] = kRowSentinel;
-        row[W + x] = kRowSentinel;
     }
     __syncthreads();
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         int best = row[x];
         const int reach = x > W - 1 - x ? x : W - 1 - x;   // past this both sides are sentinels
-        for (int dx = 1; dx <= reach && dx * dx < best; ++dx) {
-            const int v = min(row[x - dx], row[x + dx]) + dx * dx;
-            best = v < best ? v : best;
+        for (int dx = 1; dx <= reach && dx * dx < best; dx += kRowPad) {
+            const int a = min(row[x - dx], row[x + dx]) + dx * dx;
+            const int b = min(row[x - dx - 1], row[x + dx + 1]) + (dx + 1) * (dx + 1);
+            const int c = min(row[x - dx - 2], row[x + dx + 2]) + (dx + 2) * (dx + 2);
+            const int e4 = min(row[x - dx - 3], row[x + dx + 3]) + (dx + 3) * (dx + 3);
+            best = min(best, min(min(a, b), min(c, e4)));
         }
         d2[(size_t)y * W + x] = best >= kRowSentinel ? kD2None : best;
         field[field_index(x + P, y + P, Wp)] = (uint16_t)(best > C ? C : best);
@@ -187,18 +197,29 @@ __global__ void k_check_cells(const int2 *__restrict__ cells, int n, const uint6
 
 }  // namespace
 
-cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
+cudaError_t launch_edt_tiles(const MapDev &m, cudaStream_t s) {
     const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;
     const dim3 cgrid((m.W + 127) / 128, S);
     k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.TW, m.TH, m.summ, m.bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edt_field(const MapDev &m, cudaStream_t s) {
+    const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;
+    const dim3 cgrid((m.W + 127) / 128, S);
     k_edt_col_final<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, S, m.summ, m.colsq);
-    size_t smem = (size_t)3 * m.W * sizeof(int32_t);
+    size_t smem = ((size_t)3 * m.W + 2 * kRowPad) * sizeof(int32_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k_edt_rows<<<m.H, 256, smem, s>>>(m.colsq, m.W, m.C, m.P, m.Wp, m.d2, m.field);
     return cudaGetLastError();
+}
+
+cudaError_t launch_edt(const MapDev &m, cudaStream_t s) {
+    cudaError_t e = launch_edt_tiles(m, s);
+    return e == cudaSuccess ? launch_edt_field(m, s) : e;
 }
 
 cudaError_t launch_field_border(const MapDev &m, cudaStream_t s) {

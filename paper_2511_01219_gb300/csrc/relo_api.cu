@@ -86,6 +86,9 @@ struct MapSlot {
     short2 *sq_rep = nullptr;
     size_t bytes = 0;
     std::vector<ScanTable *> tables;
+    // the map's EDT runs in two parts: the occupancy tiles on the context stream (tiles_ready), then the field and
+    // d2 on the context's side stream (field_ready), overlapping the next request's ray cast
+    cudaEvent_t tiles_ready = nullptr, field_ready = nullptr;
 };
 
 // One request prepared for a batch.
@@ -173,6 +176,8 @@ struct relo_ctx {
     unsigned long long table_clock = 0, batch_seq = 0;
     // launch shapes chosen by the autotuner (relo_set_tuning)
     std::vector<relo_tune_entry> tuning;
+    // the second stream the EDT's field pass runs on
+    cudaStream_t side = nullptr;
 };
 
 namespace {
@@ -486,6 +491,18 @@ int edt_segments(int H) {
     return (H + L - 1) / L;
 }
 
+// The EDT of a map whose grid the context stream is about to hold: the occupancy tiles on the context stream, then
+// the field and d2 on the side stream (after the tiles, whose summaries they read).  Every later reader of the field
+// or d2 waits on field_ready; the next EDT of the map waits on it before its grid is overwritten.
+cudaError_t map_edt(relo_ctx *ctx, MapSlot &m) {
+    cudaError_t e = timed(ctx, 0, 1, [&] { return launch_edt_tiles(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = cudaEventRecord(m.tiles_ready, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, m.tiles_ready, 0);
+    if (e == cudaSuccess) e = timed_on(ctx, ctx->side, 7, 2, [&] { return launch_edt_field(m.dev, ctx->side); });
+    if (e == cudaSuccess) e = cudaEventRecord(m.field_ready, ctx->side);
+    return e;
+}
+
 MapSlot *get_map(relo_ctx *ctx, int id) {
     if (id < 0 || id >= (int)ctx->maps.size() || !ctx->maps[id].live) return nullptr;
     return &ctx->maps[id];
@@ -688,6 +705,9 @@ WinTable *new_win(relo_ctx *ctx, ScanTable *t, const SensorPlan &P, int n_hyp) {
 }
 
 void free_map(relo_ctx *ctx, MapSlot &m) {
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (m.tiles_ready) cudaEventDestroy(m.tiles_ready);
+    if (m.field_ready) cudaEventDestroy(m.field_ready);
     drop_tables(ctx, m);
     dev_free(ctx, m.dev.d2, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.colsq, sizeof(int32_t) * (size_t)m.dev.W * m.dev.H);
@@ -737,11 +757,15 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
         }
         m.bytes += a.bytes;
     }
-    cudaError_t e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    ctx->stream);
+    cudaError_t e = cudaEventCreateWithFlags(&m.tiles_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m.field_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m.dev.grid, grid, cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            ctx->stream);
     if (e == cudaSuccess) e = launch_field_border(m.dev, ctx->stream);
     if (e == cudaSuccess) ctx->kernels += 2;
-    if (e == cudaSuccess) e = timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); });
+    if (e == cudaSuccess) e = map_edt(ctx, m);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, m.field_ready, 0);
     if (e != cudaSuccess) {
         free_map(ctx, m);
         return cuda_fail(ctx, e, "map precompute");
@@ -1158,6 +1182,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     // the ray-cast launch prepares the scans first; a batch without rays to cast prepares them alone
     if (total_chunks <= 0) CK(timed_on(ctx, st, 1, 1, [&] { return launch_scan_prep(rq, R, st); }), "scan preparation");
     for (int r = 0; r < R; ++r) {
+        // the occupancy tiles (the cast) and, before TAM and ICP below, the field and d2 of a map whose EDT may
+        // still run on the side stream
+        if (st != ctx->stream) CK(cudaStreamWaitEvent(st, pr[r].m->tiles_ready, 0), "map tiles");
         if (mode[r] == kScanRead) CK(cudaStreamWaitEvent(st, tab[r]->written, 0), "scan table");
         if (wmode[r] == kWinRead) CK(cudaStreamWaitEvent(st, win[r]->built, 0), "window table");
         if (rtab[r]) CK(cudaStreamWaitEvent(st, rtab[r]->built, 0), "ray tables");
@@ -1191,6 +1218,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
     CK(timed_on(ctx, st, 3, 1, [&] { return launch_tam_chunks(rq, R, st); }), "TAM work order");
+    for (int r = 0; r < R; ++r) CK(cudaStreamWaitEvent(st, pr[r].m->field_ready, 0), "map field");
     {
         int max_no = 1;
         for (int r = 0; r < R; ++r) max_no = std::max(max_no, desc[r].n_orient);
@@ -1557,15 +1585,22 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
     ctx->blob = new (std::nothrow) Blob;
     cudaError_t e = ctx->blob ? cudaGetDevice(&ctx->device) : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    // The side stream (the EDT's field pass) gets the lowest priority, so the ray cast and SMAD of the context
+    // stream go first and the field pass fills what they leave; a stream the context creates itself gets the
+    // highest (a caller's stream keeps its own priority).
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) {
         if (stream) {
             ctx->stream = (cudaStream_t)stream;
         } else {
-            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            e = cudaStreamCreateWithPriority(&ctx->stream, cudaStreamNonBlocking, greatest);
             ctx->own_stream = e == cudaSuccess;
         }
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least);
     if (e != cudaSuccess) {
+        if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx->blob;
         delete ctx;
@@ -1597,6 +1632,10 @@ int relo_destroy(relo_ctx *ctx) {
         cudaEventDestroy(pe.b);
     }
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx->blob;
     delete ctx;
@@ -1622,8 +1661,10 @@ int relo_set_params(relo_ctx *ctx, const relo_params *p) {
             int C;
             if ((rc = clamp_for(ctx, p->d_max, m.res, &C))) return rc;
             m.dev.C = C;
+            CK(cudaStreamWaitEvent(ctx->stream, m.field_ready, 0), "map rebuild");
             CK(launch_field_border(m.dev, ctx->stream), "map rebuild");
-            CK(timed(ctx, 0, 3, [&] { return launch_edt(m.dev, ctx->stream); }), "map rebuild");
+            CK(map_edt(ctx, m), "map rebuild");
+            CK(cudaStreamWaitEvent(ctx->stream, m.field_ready, 0), "map rebuild");
             if ((rc = build_lut(ctx, m))) return rc;
         }
         CK(cudaStreamSynchronize(ctx->stream), "map rebuild");
@@ -1646,9 +1687,10 @@ int relo_update_map_dev(relo_ctx *ctx, int32_t map_id, const int8_t *grid_dev) {
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     drop_tables(ctx, *m);
+    CK(cudaStreamWaitEvent(ctx->stream, m->field_ready, 0), "map update");   // the last EDT still reads the grid
     CK(cudaMemcpyAsync(m->dev.grid, grid_dev, (size_t)m->dev.W * m->dev.H, cudaMemcpyDeviceToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(map_edt(ctx, *m), "map update");
     return RELO_OK;
 }
 
@@ -1657,9 +1699,10 @@ int relo_update_map(relo_ctx *ctx, int32_t map_id, const int8_t *grid) {
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
     drop_tables(ctx, *m);
+    CK(cudaStreamWaitEvent(ctx->stream, m->field_ready, 0), "map update");   // the last EDT still reads the grid
     CK(cudaMemcpyAsync(m->dev.grid, grid, (size_t)m->dev.W * m->dev.H, cudaMemcpyHostToDevice, ctx->stream),
        "map update");
-    CK(timed(ctx, 0, 3, [&] { return launch_edt(m->dev, ctx->stream); }), "map update");
+    CK(map_edt(ctx, *m), "map update");
     return RELO_OK;
 }
 
@@ -1676,6 +1719,7 @@ int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t
     if (!ctx) return RELO_E_INVALID_ARG;
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    CK(cudaStreamWaitEvent(ctx->stream, m->field_ready, 0), "map tables");
     CK(launch_map_tables(m->dev, d2_dev, field_dev, occ_dev, ctx->stream), "map tables");
     CK(cudaStreamSynchronize(ctx->stream), "map tables");
     return RELO_OK;
@@ -2054,6 +2098,7 @@ int relo_stage_times(relo_ctx *ctx, double *ms_out, int64_t *launches_out, int32
                      int64_t *kernels_out) {
     if (!ctx || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     CK(cudaStreamSynchronize(ctx->stream), "stage times");
+    if (ctx->side) CK(cudaStreamSynchronize(ctx->side), "stage times");
     for (auto &pe : ctx->pending) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, pe.a, pe.b), "stage times");

@@ -286,6 +286,10 @@ inline int tam_chunk_cap(int K, int B, int n_batches, int chunk) {
 constexpr int kMaxBatches = 64;      // ceil(K / batch) limit, bounds the TamSeg table
 
 cudaError_t launch_edt(const MapDev &m, cudaStream_t s);          // interior of the field, d2, bitmap
+// the same in two parts: the occupancy tiles and column summaries (all the ray cast needs), then, reading the
+// summaries and the grid, the column terms, d2 and the interior of the field (TAM and ICP)
+cudaError_t launch_edt_tiles(const MapDev &m, cudaStream_t s);
+cudaError_t launch_edt_field(const MapDev &m, cudaStream_t s);
 cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the constant borders of the field and walk frames (once per map)
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);

@@ -581,7 +581,9 @@ def test_profiling_then_blocking_call_then_close(relo, workload):
         ctx.relocalize_dev(mid, z, wl.angles, wl.max_range, res)
     ms, n, k = ctx.stage_times(reset=True)
     ctx.set_profiling(False)
-    assert n["raycast"] == 3 and n["smad"] == 3 and n["edt"] == 3 and all(v >= 0 for v in ms.values()) and k > 0
+    # an EDT is timed in two parts: the occupancy tiles, then the field pass on the side stream
+    assert n["raycast"] == 3 and n["smad"] == 3 and n["edt"] == 3 and n["edt_field"] == 3
+    assert all(v >= 0 for v in ms.values()) and k > 0
     out = ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
     assert out.status == 0
     ctx.close()
@@ -748,6 +750,40 @@ def test_served_request_deadlines(relo, workload):
             ctx.submit(*reqs[0], timeout_s=-1.0)
         finally:
             ctx.serve_stop()
+    ctx.close()
+
+
+def test_map_update_then_relocalize_without_waiting(relo, workload):
+    """relo_update_map_dev runs the field part of the EDT on a second stream,
+    overlapping the next request's ray cast; TAM and the table export wait for
+    it.  Back-to-back updates between two maps, each followed at once by a
+    relocalization and by the exported d2, give what a fresh context with
+    that map gives, and d2 equals the oracle's EDT."""
+    torch = torch_()
+    wl = workload(1)
+    other = workloads.make_office(77)
+    hyps = wl.hyps[other[wl.hyps[:, 1], wl.hyps[:, 0]] < 65]   # free on both maps
+    ref = {}
+    for name, g in (("a", wl.grid), ("b", other)):
+        c = relo.Relo(n_orient=wl.n_orient, topk=64, early_stop=0)
+        m = c.load_map(g, wl.res)
+        c.set_hypotheses(m, workloads.cell_centres(hyps, wl.res))
+        ref[name] = c.relocalize(m, wl.ranges, wl.angles, wl.max_range).as_dict()
+        c.close()
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=64, early_stop=0)
+    mid = ctx.load_map(wl.grid, wl.res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(hyps, wl.res))
+    grids = {"a": torch.tensor(wl.grid, device="cuda"), "b": torch.tensor(other, device="cuda")}
+    z = torch.tensor(wl.ranges, device="cuda")
+    out = torch.empty(relo.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for name in ("b", "a", "b", "b", "a"):
+        ctx.update_map_dev(mid, grids[name])
+        ctx.relocalize_dev(mid, z, wl.angles, wl.max_range, out)
+        got = relo.result_from_bytes(bytes(out.cpu().numpy())).as_dict()
+        assert got == ref[name], name
+    ctx.update_map_dev(mid, grids["b"])
+    d2, _, _ = ctx.map_tables(mid, other.shape)
+    assert np.array_equal(d2.cpu().numpy().astype(np.int64), oracle.edt(other))
     ctx.close()
 
 
