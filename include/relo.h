@@ -162,6 +162,21 @@ int relo_unload_map(relo_ctx *ctx, int32_t map_id);
  * d2_dev (int32, -1 = no obstacle), field_dev (uint16, clamped), occ_dev
  * (uint8, 1 = occupied).  Any pointer may be NULL. */
 int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t *field_dev, uint8_t *occ_dev);
+/* Copies a map's empty boxes of tiles, the table the ray cast of Eq. 13
+ * uses to cross empty space, into a caller device buffer of capacity uint16
+ * entries.  The map is cut into 8x8-cell tiles, TW = ceil(W / 8) by TH =
+ * ceil(H / 8); it is seen in four frames (f = 0 as is, 1 mirrored in x, 2
+ * mirrored in y, 3 in both: frame tile (tx, ty) is map tile (TW - 1 - tx)
+ * when mirrored in x, (TH - 1 - ty) in y), each with a last column and row
+ * of tiles that count as occupied; a tile is empty when none of its cells is
+ * occupied (>= 65) or outside the map.  Entry [f][ty][tx], row-major with
+ * TW + 1 entries per row and TH + 1 rows per frame, packs three sides, each
+ * at most 16 and 0 when the tile is not empty: bits 0-4 the largest s with
+ * the tiles [tx, tx + s) x [ty, ty + s) all empty, bits 5-9 the empty run
+ * [tx, tx + r) along the row, bits 10-14 the empty run [ty, ty + r) along the
+ * column.  *n_out (optional) receives 4 (TW + 1)(TH + 1); RELO_E_INVALID_ARG
+ * when capacity is smaller.  Blocking. */
+int relo_map_walk_boxes_dev(relo_ctx *ctx, int32_t map_id, uint16_t *boxes_dev, int64_t capacity, int64_t *n_out);
 
 /* Positional hypotheses of Eq. 6 (for example from the RRT of Algorithm 1).
  * xy: n (x, y) pairs in metres, snapped to the containing cell; every one

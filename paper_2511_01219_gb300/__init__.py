@@ -42,7 +42,7 @@ EXPORTED = [
     "relo_relocalize_batch", "relo_relocalize_batch_dev", "relo_serve_start", "relo_submit", "relo_poll",
     "relo_serve_stop", "relo_scan_cache_stats", "relo_set_profiling_mask", "relo_rrt_hypotheses_dev",
     "relo_probe_l2_stream", "relo_probe_l2_gather", "relo_rrt_sample",
-    "relo_submit_until", "relo_set_tuning", "relo_tam_class",
+    "relo_submit_until", "relo_set_tuning", "relo_tam_class", "relo_map_walk_boxes_dev",
 ]
 STAGES = ["edt", "scan_prep", "raycast", "topk", "tam", "select", "smad", "edt_field"]
 
@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "relo_update_map": (ctypes.c_int, [P, I32, P]),
             "relo_unload_map": (ctypes.c_int, [P, I32]),
             "relo_map_tables_dev": (ctypes.c_int, [P, I32, P, P, P]),
+            "relo_map_walk_boxes_dev": (ctypes.c_int, [P, I32, P, I64, P]),
             "relo_set_hypotheses": (ctypes.c_int, [P, I32, P, I32]),
             "relo_set_hypotheses_cells_dev": (ctypes.c_int, [P, I32, P, I32]),
             "relo_relocalize": (ctypes.c_int, [P, I32, P, P, I32, F, P]),
@@ -270,6 +271,18 @@ class Relo:
         self._check(self._L.relo_map_tables_dev(self._h, map_id, _t_ptr(d2), _t_ptr(fld), _t_ptr(occ)),
                     "map_tables")
         return d2, fld.to(torch.int32) & 0xFFFF, occ
+
+    def walk_boxes(self, map_id: int, shape):
+        """The ray walk's empty boxes of tiles (relo_map_walk_boxes_dev) as an int32 numpy array
+        [4, ceil(H/8) + 1, ceil(W/8) + 1] of the packed uint16 entries."""
+        import torch
+        H, W = shape
+        TW, TH = (W + 7) // 8, (H + 7) // 8
+        n = 4 * (TW + 1) * (TH + 1)
+        buf = torch.empty(n, dtype=torch.int16, device="cuda")
+        got = ctypes.c_int64(0)
+        self._check(self._L.relo_map_walk_boxes_dev(self._h, map_id, _t_ptr(buf), n, ctypes.byref(got)), "walk_boxes")
+        return (buf.cpu().numpy().view("uint16").astype("int32")).reshape(4, TH + 1, TW + 1)
 
     # ---- hypotheses ----------------------------------------------------------------------
     def set_hypotheses(self, map_id: int, xy: np.ndarray):

@@ -1,11 +1,12 @@
 // Map precompute: exact squared Euclidean distance transform (the EDT lookup
 // table of Sec. III-A item 3, used by the likelihood field of Eq. 23 and the
 // distance statistics of Eq. 29-30), its clamped padded copy for TAM, and the
-// tiled occupancy bitmap for ray casting (Eq. 13).
+// tiled occupancy bitmap for ray casting (Eq. 13) with, per walk frame, the
+// empty squares of tiles ahead of every tile.
 //
-// The clamped field is stored row-major with a border of P cells holding C on
-// every side, P at least the longest beam in cells, so every beam endpoint of
-// TAM falls inside the array and needs no bounds test.
+// The clamped field is stored in bands of 8 rows (field_index) with a border
+// of P cells holding C on every side, P at least the longest beam in cells, so
+// every beam endpoint of TAM falls inside the array and needs no bounds test.
 //
 // d2(x, y) = min over occupied (x', y') of (x - x')^2 + (y - y')^2 separates
 // into a column term g2(x', y) = min over occupied y' in column x' of
@@ -165,6 +166,59 @@ __global__ void k_field_border(uint16_t *__restrict__ fieldp, int W, int H, int 
     }
 }
 
+// Which walk-frame tiles are empty, one bit per tile: word [row][k] of a
+// frame row holds tiles 32 k .. 32 k + 31 (tiles past the row count as not
+// empty, and one more word of zeros ends every row).
+__global__ void k_walk_empty(const uint64_t *__restrict__ wf, int TW, uint32_t *__restrict__ emp) {
+    const unsigned WB = (unsigned)TW + 1u, SW = walk_empty_row_words(TW);
+    const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t row = blockIdx.y;   // frame * (TH + 1) + ty
+    const unsigned bal = __ballot_sync(0xffffffffu, x < WB && wf[row * WB + x] == 0ull);
+    if ((threadIdx.x & 31) == 0 && (x >> 5) < SW) emp[row * SW + (x >> 5)] = bal;
+}
+
+// The empty boxes ahead of every walk-frame tile (MapDev::reach).  A warp
+// takes 32 tiles of a row: lanes k < kReachMax load the emptiness words of
+// row ty + k covering its tiles and lanes kReachMax + k the next word, which
+// gives for each of the kReachMax rows from theirs which of the 64 tiles from
+// its first are empty.  A lane's row run is the block of set bits from its
+// own bit in the first mask, its column run the rows whose masks keep its
+// bit, and its square the largest s whose s rows' AND keeps s bits from its
+// own (a lane's bit plus kReachMax <= 31 + 16 stays inside the 64 bits, so
+// the masks reach far enough).
+__global__ void k_walk_reach(const uint32_t *__restrict__ emp, int TW, int TH, uint16_t *__restrict__ reach) {
+    static_assert(2 * kReachMax <= 32, "one emptiness word per lane");
+    const int lane = threadIdx.x & 31;
+    const unsigned WB = (unsigned)TW + 1u, HB = (unsigned)TH + 1u, SW = walk_empty_row_words(TW);
+    const unsigned strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (strip * 32u >= WB) return;   // the whole warp lies past the row
+    const unsigned fy = blockIdx.y, ty = fy % HB;   // frame * HB + ty
+    const unsigned k = (unsigned)lane % kReachMax, y = ty + k;
+    const uint32_t wv = y < HB && lane < 2 * kReachMax ? emp[(size_t)(fy + k) * SW + strip + lane / kReachMax] : 0u;
+    uint64_t E[kReachMax];
+#pragma unroll
+    for (int r = 0; r < kReachMax; ++r)
+        E[r] = (uint64_t)__shfl_sync(0xffffffffu, wv, r) | ((uint64_t)__shfl_sync(0xffffffffu, wv, r + kReachMax) << 32);
+    const unsigned xa = strip * 32u + lane;
+    if (xa >= WB) return;
+    // the run of set bits from bit lane of m, at most kReachMax: the sentinel bit keeps the
+    // argument of ffs nonzero when all 64 tiles from the warp's first are empty
+    auto run = [&](uint64_t m) { return __ffsll((long long)(~(m >> lane) | (1ull << kReachMax))) - 1; };
+    const int xr = run(E[0]);
+    int s = 0, yr = 0;
+    bool sq = true, col = true;
+    uint64_t A = ~0ull;
+#pragma unroll
+    for (int r = 0; r < kReachMax; ++r) {
+        col = col && ((E[r] >> lane) & 1ull);
+        if (col) yr = r + 1;
+        A &= E[r];
+        sq = sq && run(A) >= r + 1;
+        if (sq) s = r + 1;
+    }
+    reach[(size_t)fy * WB + xa] = (uint16_t)(s | (xr << 5) | (yr << 10));
+}
+
 // the last column and row of tiles of each walk frame: every bit set
 __global__ void k_walk_border(uint64_t *__restrict__ wf, int TW, int TH) {
     uint64_t *f = wf + (size_t)blockIdx.x * walk_frame_words(TW, TH);
@@ -201,6 +255,13 @@ cudaError_t launch_edt_tiles(const MapDev &m, cudaStream_t s) {
     const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;
     const dim3 cgrid((m.W + 127) / 128, S);
     k_edt_col_summary<<<cgrid, 128, 0, s>>>(m.grid, m.W, m.H, L, m.TW, m.TH, m.summ, m.bits);
+    if (m.reach) {
+        // the walk frames' empty boxes (their border tiles, full, were written when the map was loaded)
+        const unsigned WB = (unsigned)m.TW + 1u, SW = walk_empty_row_words(m.TW), rows = 4u * ((unsigned)m.TH + 1u);
+        uint32_t *emp = walk_empty_bits(m.reach, m.TW, m.TH);
+        k_walk_empty<<<dim3((32u * SW + 255u) / 256u, rows), 256, 0, s>>>(m.bits + (size_t)m.TW * m.TH, m.TW, emp);
+        k_walk_reach<<<dim3((WB + 255u) / 256u, rows), 256, 0, s>>>(emp, m.TW, m.TH, m.reach);
+    }
     return cudaGetLastError();
 }
 

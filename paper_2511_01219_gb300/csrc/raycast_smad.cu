@@ -188,15 +188,27 @@ __device__ __forceinline__ uint32_t cast_ray(const uint64_t *__restrict__ bits, 
 // staircase that only moves +x and +y the cell order along the ray is the
 // row-major bit order, so the lowest common bit is the hit.  Otherwise the
 // ray leaves the tile at the cell of step min(selx[|dx| + nx], sely[|dy| +
-// ny]), nx and ny being the x- and y-steps to the tile's far edges.  Same
-// cells, same hit, same range as cast_ray.
-__device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, int W, int H, int TW, int TH,
-                                             const RayTables &t, int ns, int j, int hx, int hy, int2 d, int *hit,
-                                             int *steps) {
+// ny]), nx and ny being the x- and y-steps to the tile's far edges.  An empty
+// tile is left as a whole box of empty tiles ahead (MapDev::reach) when that
+// box is larger: the run along the tile's row for a ray within about 14
+// degrees of the x axis, the run along its column within 14 degrees of the y
+// axis, the empty square otherwise; the same lookups then take the box's far
+// edges, since no cell inside it can stop the ray.  Same cells, same hit, same
+// range as cast_ray.
+__device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, const uint16_t *__restrict__ reach,
+                                             int W, int H, int TW, int TH, const RayTables &t, int ns, int j, int hx,
+                                             int hy, int2 d, int *hit, int *steps) {
     const bool xneg = d.x <= 0, yneg = d.y <= 0;
     const unsigned WB = (unsigned)TW + 1u;   // walk frame row, with the border column
-    const uint64_t *__restrict__ bq =
-        bits + (size_t)TW * TH + (size_t)((xneg ? 1 : 0) + (yneg ? 2 : 0)) * walk_frame_words(TW, TH);
+    const size_t frame = (size_t)((xneg ? 1 : 0) + (yneg ? 2 : 0)) * walk_frame_words(TW, TH);
+    const uint64_t *__restrict__ bq = bits + (size_t)TW * TH + frame;
+    const uint16_t *__restrict__ rq = reach + frame;
+    // which box of the packed reach the ray leaves: width (reach >> wsh) & 31, height (reach >> hsh) & 31, each
+    // at least 1 (bit 15 and up are 0, so a shift of 15 reads a side of 1 tile)
+    const long long adir = d.x < 0 ? -(long long)d.x : d.x, bdir = d.y < 0 ? -(long long)d.y : d.y;
+    const bool shallow = 4 * bdir <= adir, steep = 4 * adir <= bdir;
+    const unsigned wsh = shallow ? 5u : steep ? 15u : 0u;
+    const unsigned hsh = steep ? 10u : shallow ? 15u : 0u;
     const int xlo = xneg ? 8 * TW - W : 0, ylo = yneg ? 8 * TH - H : 0;   // the map in the ray's frame
     const int fx = xneg ? 8 * TW - 1 - hx : hx, fy = yneg ? 8 * TH - 1 - hy : hy;
     const uint16_t *__restrict__ selx = t.selx + j;
@@ -212,10 +224,19 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     int stop;   // 1 hit (or left the map), 2 range limit
     for (;;) {
         const int lx = cx & 7, ly = cy & 7;
-        // the tile's word and the exit steps are loaded together: one memory round trip per tile
-        const uint64_t word = __ldg(bq + ((unsigned)(cy >> 3) * WB + (unsigned)(cx >> 3)));
-        const uint32_t kx = __ldg(selx + (unsigned)(adx + 8 - lx) * uns);
-        const uint32_t ky = __ldg(sely + (unsigned)(ady + 8 - ly) * uns);
+        // the tile's word, its square and the tile's exit steps are loaded together: one memory round trip
+        // per tile (a second one when the ray leaves a larger square)
+        const unsigned ti = (unsigned)(cy >> 3) * WB + (unsigned)(cx >> 3);
+        const uint64_t word = __ldg(bq + ti);
+        const unsigned rv = __ldg(rq + ti);
+        uint32_t kx = __ldg(selx + (unsigned)(adx + 8 - lx) * uns);
+        uint32_t ky = __ldg(sely + (unsigned)(ady + 8 - ly) * uns);
+        const unsigned bw = max(1u, (rv >> wsh) & 31u), bh = max(1u, (rv >> hsh) & 31u);   // the box, in tiles
+        const int ex = 8 * (int)bw - lx, ey = 8 * (int)bh - ly;   // x- and y-steps to its far edges
+        if ((bw | bh) > 1u) {
+            kx = __ldg(selx + (unsigned)(adx + ex) * uns);
+            ky = __ldg(sely + (unsigned)(ady + ey) * uns);
+        }
         if (word) {
             // move the current cell to bit 0; bits that wrap into the row below
             // sit in columns the board's column mask removes
@@ -236,10 +257,10 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
             break;
         }
         if (kx < ky) {
-            adx += 8 - lx;
+            adx += ex;
             ady = (int)kx - adx;
         } else {
-            ady += 8 - ly;
+            ady += ey;
             adx = (int)ky - ady;
         }
         cx = fx + adx;
@@ -354,7 +375,7 @@ __host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
 // mix freely across the GPU.
 constexpr int kCastThreads = 256;
 
-__global__ void __launch_bounds__(kCastThreads, 6) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
+__global__ void __launch_bounds__(kCastThreads, 5) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
                                                        BatchState *bs) {
     __shared__ int s_base[kMaxBatchRequests + 1];
     const int lane = threadIdx.x & 31;
@@ -386,7 +407,8 @@ __global__ void __launch_bounds__(kCastThreads, 6) k_cast(const ReqDesc *__restr
             const int2 hc = d.hyps[h];
             const int2 dir = d.D[j];
             int hit, steps = 0;
-            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.W, d.H, d.TW, d.TH, d.rt, d.ns, j, hc.x, hc.y, dir, &hit, &steps)
+            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.reach, d.W, d.H, d.TW, d.TH, d.rt, d.ns, j, hc.x, hc.y, dir,
+                                                    &hit, &steps)
                                          : cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, dir, &hit, &steps);
             d.scan_table[(size_t)h * d.ns + j] = r;
             my_steps += (unsigned)steps;
@@ -683,7 +705,8 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
     const int2 hc = a.hyps[warp];
     for (int j = lane; j < a.ns; j += 32) {
         int hit, steps;
-        uint32_t r = a.tab.mask ? walk_ray(a.bits, a.W, a.H, a.TW, a.TH, a.tab, a.ns, j, hc.x, hc.y, a.D[j], &hit, &steps)
+        uint32_t r = a.tab.mask ? walk_ray(a.bits, a.reach, a.W, a.H, a.TW, a.TH, a.tab, a.ns, j, hc.x, hc.y, a.D[j],
+                                           &hit, &steps)
                                 : cast_ray(a.bits, a.W, a.H, a.TW, a.lim, hc.x, hc.y, a.D[j], &hit, &steps);
         ranges[(size_t)warp * a.ns + j] = r;
         if (hits) hits[(size_t)warp * a.ns + j] = hit;

@@ -495,7 +495,7 @@ int edt_segments(int H) {
 // the field and d2 on the side stream (after the tiles, whose summaries they read).  Every later reader of the field
 // or d2 waits on field_ready; the next EDT of the map waits on it before its grid is overwritten.
 cudaError_t map_edt(relo_ctx *ctx, MapSlot &m) {
-    cudaError_t e = timed(ctx, 0, 1, [&] { return launch_edt_tiles(m.dev, ctx->stream); });
+    cudaError_t e = timed(ctx, 0, m.dev.reach ? 3 : 1, [&] { return launch_edt_tiles(m.dev, ctx->stream); });
     if (e == cudaSuccess) e = cudaEventRecord(m.tiles_ready, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, m.tiles_ready, 0);
     if (e == cudaSuccess) e = timed_on(ctx, ctx->side, 7, 2, [&] { return launch_edt_field(m.dev, ctx->side); });
@@ -715,6 +715,7 @@ void free_map(relo_ctx *ctx, MapSlot &m) {
     dev_free(ctx, m.dev.grid, (size_t)m.dev.W * m.dev.H);
     dev_free(ctx, m.dev.field, sizeof(uint16_t) * (size_t)m.dev.Wp * m.dev.Hp);
     dev_free(ctx, m.dev.bits, sizeof(uint64_t) * occupancy_words(m.dev.TW, m.dev.TH));
+    dev_free(ctx, m.dev.reach, walk_reach_bytes(m.dev.TW, m.dev.TH));
     dev_free(ctx, m.hyps, sizeof(int2) * (size_t)m.hyp_cap);
     dev_free(ctx, m.lut, sizeof(float2) * (kMaxClamp + 2));
     dev_free(ctx, m.sq_off, sizeof(int32_t) * (kMaxClamp + 2));
@@ -748,6 +749,7 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     struct { void **p; size_t bytes; } allocs[] = {
         {(void **)&m.dev.d2, cells * 4}, {(void **)&m.dev.colsq, cells * 4}, {(void **)&m.dev.grid, cells},
         {(void **)&m.dev.field, fcells * 2}, {(void **)&m.dev.bits, occupancy_words(m.dev.TW, m.dev.TH) * 8},
+        {(void **)&m.dev.reach, walk_reach_bytes(m.dev.TW, m.dev.TH)},
         {(void **)&m.dev.summ, sizeof(int2) * (size_t)w * edt_segments(h)}};
     for (auto &a : allocs) {
         rc = dev_alloc(ctx, a.p, a.bytes, "map tables");
@@ -1041,6 +1043,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         ReqDesc &d = desc[r];
         memset(&d, 0, sizeof d);
         d.bits = m.dev.bits;
+        d.reach = m.dev.reach;
         d.field = m.dev.field;
         d.Wp = m.dev.Wp;
         d.P = m.dev.P;
@@ -1725,6 +1728,20 @@ int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t
     return RELO_OK;
 }
 
+int relo_map_walk_boxes_dev(relo_ctx *ctx, int32_t map_id, uint16_t *boxes_dev, int64_t capacity, int64_t *n_out) {
+    if (!ctx) return RELO_E_INVALID_ARG;
+    MapSlot *m = get_map(ctx, map_id);
+    if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
+    const int64_t n = (int64_t)(4 * walk_frame_words(m->dev.TW, m->dev.TH));
+    if (n_out) *n_out = n;
+    if (!boxes_dev || capacity < n) return fail(ctx, RELO_E_INVALID_ARG, "the buffer holds fewer than 4 (TW+1)(TH+1)");
+    // the boxes are written on the context stream with the occupancy tiles
+    CK(cudaMemcpyAsync(boxes_dev, m->dev.reach, sizeof(uint16_t) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream),
+       "walk boxes");
+    CK(cudaStreamSynchronize(ctx->stream), "walk boxes");
+    return RELO_OK;
+}
+
 int relo_set_hypotheses(relo_ctx *ctx, int32_t map_id, const double *xy, int32_t n) {
     if (!ctx || (!xy && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad hypothesis arguments");
     MapSlot *m = get_map(ctx, map_id);
@@ -1862,6 +1879,7 @@ int relo_synth_scans_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev
     RayArgs ra;
     memset(&ra, 0, sizeof ra);
     ra.bits = m->dev.bits;
+    ra.reach = m->dev.reach;
     ra.W = m->dev.W;
     ra.H = m->dev.H;
     ra.TW = m->dev.TW;

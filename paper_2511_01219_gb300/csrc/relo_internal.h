@@ -45,6 +45,8 @@ struct MapDev {
     int P = 0, Wp = 0, Hp = 0;  // border width; padded width and height (W + 2P, H + 2P rounded up to 8)
     uint64_t *bits = nullptr;   // occupancy, bit (y&7)*8 + (x&7): [TH*TW] the map (cells outside free), then the
                                 // four walk frames (walk_frame_words each: native, mirrored in x, y and both)
+    uint16_t *reach = nullptr;  // per walk-frame tile, the empty boxes of tiles ahead, then scratch (walk_reach_bytes);
+                                // nullptr: no ray is cast on this map
     int32_t *colsq = nullptr;   // [H*W] EDT column-pass scratch
     int2 *summ = nullptr;       // [S*W] EDT column-segment summaries (scratch)
     int8_t *grid = nullptr;     // [H*W] device copy of the grid
@@ -76,6 +78,29 @@ __host__ __device__ inline int edt_segment_rows(int H) {
 __host__ __device__ inline size_t walk_frame_words(int TW, int TH) { return (size_t)(TW + 1) * (TH + 1); }
 __host__ __device__ inline size_t occupancy_words(int TW, int TH) {
     return (size_t)TW * TH + 4 * walk_frame_words(TW, TH);
+}
+
+// Empty boxes ahead.  For every tile (tx, ty) of a walk frame, reach packs
+// three boxes of empty tiles that start at it, each side at most kReachMax
+// (all 0 when the tile itself is not empty): bits 0-4 the side s of the
+// largest square [tx, tx + s) x [ty, ty + s), bits 5-9 the run [tx, tx + r) x
+// {ty} along the tile's row, bits 10-14 the run {tx} x [ty, ty + r) along its
+// column.  A ray in that tile moves towards +x and +y, so every cell it enters
+// before it leaves a box lies inside it: the walk may leave the whole box in
+// one move.  The walk frames' last column and row are full, so a box never
+// leaves the map.
+constexpr int kReachMax = 16;
+// words per frame row of the tiles' emptiness bits (one more than the row needs: the 64-tile window of a row's last
+// 32 tiles reads it)
+__host__ __device__ inline unsigned walk_empty_row_words(int TW) { return ((unsigned)TW + 1u + 31u) / 32u + 1u; }
+// MapDev::reach: the packed boxes [4][TH + 1][TW + 1], then the emptiness bits [4 (TH + 1)][walk_empty_row_words]
+__host__ __device__ inline size_t walk_reach_bytes(int TW, int TH) {
+    const size_t boxes = (4 * walk_frame_words(TW, TH) * sizeof(uint16_t) + 15) & ~(size_t)15;
+    return boxes + (size_t)4 * ((size_t)TH + 1) * walk_empty_row_words(TW) * sizeof(uint32_t);
+}
+__host__ __device__ inline uint32_t *walk_empty_bits(uint16_t *reach, int TW, int TH) {
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(reach) +
+                                        ((4 * walk_frame_words(TW, TH) * sizeof(uint16_t) + 15) & ~(size_t)15));
 }
 
 __host__ __device__ inline size_t tile_index(int x, int y, int TW) {
@@ -133,12 +158,13 @@ __host__ __device__ inline int ray_sel_rows(int lim) {
     int r = (int)sqrt((double)lim);
     while ((long long)(r + 1) * (r + 1) <= (long long)lim) ++r;
     while ((long long)r * r > (long long)lim) --r;
-    return r + 9;   // a cell in range has |dx| <= sqrt(lim); a tile exit adds at most 8
+    return r + 8 * kReachMax + 1;   // a cell in range has |dx| <= sqrt(lim); leaving a square adds at most 8 kReachMax
 }
 
 // single-request arguments of the synthesized-scan export (relo_synth_scans_dev)
 struct RayArgs {
     const uint64_t *bits;   // the map's four occupancy frames (MapDev::bits)
+    const uint16_t *reach;  // their empty boxes ahead (MapDev::reach)
     int W, H, TW, TH;
     const int2 *D;          // [ns] Q30 directions
     int ns, ns_pad;         // ns_pad = ns rounded up to 32
@@ -164,6 +190,7 @@ struct RayArgs {
 struct ReqDesc {
     // map tables
     const uint64_t *bits;
+    const uint16_t *reach;       // empty boxes ahead in the walk frames (MapDev::reach)
     const uint16_t *field;       // padded clamped field (8-row bands, field_index), pointer to padded cell (0, 0)
     int coarse, fine;            // ranking and scoring metrics (RELO_COARSE_*, RELO_FINE_*)
     int icp_iters;               // ICP iterations per local top-k pose (0: no refinement)
