@@ -178,14 +178,14 @@ __global__ void k_walk_empty(const uint64_t *__restrict__ wf, int TW, uint32_t *
 }
 
 // The empty boxes ahead of every walk-frame tile (MapDev::reach).  A warp
-// takes 32 tiles of a row: lanes k < kReachMax load the emptiness words of
-// row ty + k covering its tiles and lanes kReachMax + k the next word, which
-// gives for each of the kReachMax rows from theirs which of the 64 tiles from
-// its first are empty.  A lane's row run is the block of set bits from its
-// own bit in the first mask, its column run the rows whose masks keep its
-// bit, and its square the largest s whose s rows' AND keeps s bits from its
-// own (a lane's bit plus kReachMax <= 31 + 16 stays inside the 64 bits, so
-// the masks reach far enough).
+// takes 32 tiles of a row: lanes k < kReachMax load the emptiness word of row
+// ty + k covering its tiles and lanes kReachMax + k the next word.  For each
+// of the kReachMax rows from theirs, a lane shifts the 64 bits of that pair
+// down by its own position, so bit i says whether the tile i to its right is
+// empty (i + 31 < 64: a window of kReachMax + 1 bits always fits).  Its row
+// run is the block of set bits from bit 0 of the first row, its column run
+// the rows that keep bit 0, and its square the largest s whose s rows' AND
+// keeps bits 0 .. s - 1.
 __global__ void k_walk_reach(const uint32_t *__restrict__ emp, int TW, int TH, uint16_t *__restrict__ reach) {
     static_assert(2 * kReachMax <= 32, "one emptiness word per lane");
     const int lane = threadIdx.x & 31;
@@ -194,29 +194,27 @@ __global__ void k_walk_reach(const uint32_t *__restrict__ emp, int TW, int TH, u
     if (strip * 32u >= WB) return;   // the whole warp lies past the row
     const unsigned fy = blockIdx.y, ty = fy % HB;   // frame * HB + ty
     const unsigned k = (unsigned)lane % kReachMax, y = ty + k;
-    const uint32_t wv = y < HB && lane < 2 * kReachMax ? emp[(size_t)(fy + k) * SW + strip + lane / kReachMax] : 0u;
-    uint64_t E[kReachMax];
-#pragma unroll
-    for (int r = 0; r < kReachMax; ++r)
-        E[r] = (uint64_t)__shfl_sync(0xffffffffu, wv, r) | ((uint64_t)__shfl_sync(0xffffffffu, wv, r + kReachMax) << 32);
-    const unsigned xa = strip * 32u + lane;
-    if (xa >= WB) return;
-    // the run of set bits from bit lane of m, at most kReachMax: the sentinel bit keeps the
-    // argument of ffs nonzero when all 64 tiles from the warp's first are empty
-    auto run = [&](uint64_t m) { return __ffsll((long long)(~(m >> lane) | (1ull << kReachMax))) - 1; };
-    const int xr = run(E[0]);
+    const uint32_t wv = y < HB ? emp[(size_t)(fy + k) * SW + strip + lane / kReachMax] : 0u;
+    uint32_t e0 = 0u, a = ~0u;
     int s = 0, yr = 0;
     bool sq = true, col = true;
-    uint64_t A = ~0ull;
 #pragma unroll
     for (int r = 0; r < kReachMax; ++r) {
-        col = col && ((E[r] >> lane) & 1ull);
+        const uint32_t e = __funnelshift_r(__shfl_sync(0xffffffffu, wv, r),
+                                           __shfl_sync(0xffffffffu, wv, r + kReachMax), (unsigned)lane);
+        if (r == 0) e0 = e;
+        col = col && (e & 1u);
         if (col) yr = r + 1;
-        A &= E[r];
-        sq = sq && run(A) >= r + 1;
+        a &= e;
+        const uint32_t mr = (2u << r) - 1u;   // bits 0 .. r
+        sq = sq && (a & mr) == mr;
         if (sq) s = r + 1;
+        if (!__any_sync(0xffffffffu, sq || col)) break;   // no lane's boxes grow further
     }
-    reach[(size_t)fy * WB + xa] = (uint16_t)(s | (xr << 5) | (yr << 10));
+    // the sentinel bit caps the row run at kReachMax
+    const int xr = __ffs((int)(~e0 | (1u << kReachMax))) - 1;
+    const unsigned xa = strip * 32u + lane;
+    if (xa < WB) reach[(size_t)fy * WB + xa] = (uint16_t)(s | (xr << 5) | (yr << 10));
 }
 
 // the last column and row of tiles of each walk frame: every bit set
