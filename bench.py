@@ -274,7 +274,7 @@ def run_ours(args, world, rank, local, dist):
         from paper_2511_01219_gb300 import autotune
         cache = autotune.cache_path(torch.cuda.get_device_name(local))
         res_tune = autotune.tune(ctx, step, [(len(wl.ranges), wl.n_orient, min(wl.topk, len(wl.hyps)))],
-                                 log=lambda s: print(s, file=sys.stderr))
+                                 log=lambda s: print(s, file=sys.stderr), single=True)
         merged = {(k, tuple(key)): val for k, key, val in autotune.load(cache)}
         merged.update({(k, tuple(key)): val for k, key, val in res_tune["entries"]})
         autotune.save(cache, [(k, key, val) for (k, key), val in merged.items()],

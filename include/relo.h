@@ -355,6 +355,10 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
  *                   task (a multiple of 8 in [8, 128]; 0 keeps the built-in
  *                   choice), resident CTAs per SM of the TAM launch (0: all
  *                   that fit; a launch takes the smallest of its requests')}.
+ *   RELO_TUNE_TAM_ONE  as RELO_TUNE_TAM, for a launch that serves a single
+ *                   request (its TAM tasks alone fill the GPU, so the best
+ *                   shape differs from a mixed batch's); such a launch falls
+ *                   back to RELO_TUNE_TAM entries when none matches.
  *   RELO_TUNE_CAST  key = {N_s of the batch's first ray-casting request, 0,
  *                   0}; val = {CTAs per SM of the ray-cast launch (0: all that
  *                   fit), 0}.
@@ -364,6 +368,7 @@ int relo_rrt_hypotheses_dev(relo_ctx *ctx, const float *clearance_dev, int32_t w
  * (after the n_skip_beam stride), or -1 if no TAM kernel holds it. */
 #define RELO_TUNE_TAM 1
 #define RELO_TUNE_CAST 2
+#define RELO_TUNE_TAM_ONE 3
 typedef struct relo_tune_entry {
     int32_t kind;
     int32_t key[3];

@@ -61,7 +61,7 @@ class Params(ctypes.Structure):
 
 COARSE_SMAD, COARSE_CAER, COARSE_SMAD_DIRECT, COARSE_NONE = 0, 1, 2, 3
 FINE_TAM, FINE_TAM_MEAN, FINE_BASELINE, FINE_LF = 0, 1, 2, 3
-TUNE_TAM, TUNE_CAST = 1, 2
+TUNE_TAM, TUNE_CAST, TUNE_TAM_ONE = 1, 2, 3
 
 
 class TuneEntry(ctypes.Structure):

@@ -10,6 +10,9 @@ chunk sizes and CTAs per SM, one bucket at a time (the others at their best
 so far), timing the stage with the library's own CUDA events over a few
 repetitions of the workload.  Shapes never change results, only time.
 
+A workload of single requests is tuned apart (``single``): one request's TAM
+tasks alone fill the GPU, so its best shape differs from a mixed batch's.
+
 The result is a list of tuning entries, cached in a JSON file per device
 (``tuning/<device>.json`` next to this module) and loaded into a context with
 ``Relo.set_tuning(load(path))``.
@@ -21,7 +24,7 @@ import os
 import statistics
 import time
 
-from . import TUNE_CAST, TUNE_TAM, tam_class
+from . import TUNE_CAST, TUNE_TAM, TUNE_TAM_ONE, tam_class
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CHUNKS = (8, 16, 24, 32, 48, 64)
@@ -72,20 +75,24 @@ def stage_ms(ctx, run, stage: str, reps: int) -> float:
     return statistics.median(vals)
 
 
-def tune(ctx, run, shapes, reps: int = 3, log=None) -> dict:
+def tune(ctx, run, shapes, reps: int = 3, log=None, single: bool = False) -> dict:
     """Measured search.  run(): one pass of the workload on ctx; shapes: its
-    requests' (n_beams after the beam stride, n_orient, K).  Returns
-    {"entries": [...], "cast_ms": (built-in, tuned), "tam_ms": (built-in, tuned),
-    "trials": [...]}; ctx is left with the tuned entries set."""
+    requests' (n_beams after the beam stride, n_orient, K).  With single, run()
+    issues one request per launch: the TAM entries are then RELO_TUNE_TAM_ONE
+    (launches of a single request look them up first) and the ray cast is left
+    to the batched tuning.  Returns {"entries": [...], "cast_ms": (built-in,
+    tuned), "tam_ms": (built-in, tuned), "trials": [...]}; ctx is left with the
+    tuned entries set."""
     t0 = time.time()
     trials = []
+    tam_kind = TUNE_TAM_ONE if single else TUNE_TAM
     ctx.set_tuning([])
     run()
     base_tam = stage_ms(ctx, run, "tam", reps)
     base_cast = stage_ms(ctx, run, "raycast", reps)
     trials.append({"entries": [], "tam_ms": base_tam, "raycast_ms": base_cast})
     best_cast, best_cast_ms = None, base_cast
-    for c in CAST_CTAS[1:]:
+    for c in (() if single else CAST_CTAS[1:]):
         e = [(TUNE_CAST, (0, 0, 0), (c, 0))]
         ctx.set_tuning(e)
         ms = stage_ms(ctx, run, "raycast", reps)
@@ -99,7 +106,7 @@ def tune(ctx, run, shapes, reps: int = 3, log=None) -> dict:
             for cps in TAM_CTAS:
                 cand = dict(chosen)
                 cand[b] = (chunk, cps)
-                e = [(TUNE_TAM, k, v) for k, v in cand.items()]
+                e = [(tam_kind, k, v) for k, v in cand.items()]
                 ctx.set_tuning(e)
                 ms = stage_ms(ctx, run, "tam", reps)
                 trials.append({"entries": e, "tam_ms": ms})
@@ -108,7 +115,7 @@ def tune(ctx, run, shapes, reps: int = 3, log=None) -> dict:
                     chosen = cand
         if log:
             log(f"bucket {b}: {chosen.get(b)} tam {best_tam_ms:.4f} ms ({time.time() - t0:.0f} s)")
-    entries = [(TUNE_TAM, k, v) for k, v in chosen.items()] + ([best_cast] if best_cast else [])
+    entries = [(tam_kind, k, v) for k, v in chosen.items()] + ([best_cast] if best_cast else [])
     ctx.set_tuning(entries)
     return {"entries": entries, "tam_ms": (base_tam, best_tam_ms), "cast_ms": (base_cast, best_cast_ms),
             "trials": trials, "seconds": time.time() - t0}

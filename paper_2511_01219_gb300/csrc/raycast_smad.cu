@@ -366,15 +366,19 @@ __host__ __device__ __forceinline__ size_t smad_warp_bytes(int ns_pad) {
     return (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7) + (size_t)(ns_pad / 32 + 1) * 8;
 }
 
-// Casting.  The batch's rays form one list of 32-ray chunks (request r owns
-// chunks [chunk_base_r, chunk_base_r + n_hyp_r * N_s_pad / 32), hypothesis
-// by hypothesis); every warp takes chunks from a device counter until none is
-// left, casts its 32 neighbouring directions (lane = ray) and writes their
-// ranges into the request's scan table, 128 contiguous bytes per chunk.  No
+// Casting.  The batch's rays form one list of work items (request r owns
+// items [chunk_base_r, chunk_base_r + ceil(n_hyp_r / G) * N_s_pad / 32), G =
+// cast_hyps hypotheses for one chunk of 32 directions each, hypothesis group
+// by hypothesis group); every warp takes items from a device counter until
+// none is left, casts its 32 neighbouring directions (lane = ray) from each
+// of the item's hypotheses in turn (the directions' setup is shared) and
+// writes their ranges into the request's scan table, 128 contiguous bytes per
+// hypothesis.  No
 // warp waits for another, so long and short rays, hypotheses and requests
 // mix freely across the GPU.
 constexpr int kCastThreads = 256;
 
+template <int G>
 __global__ void __launch_bounds__(kCastThreads, 5) k_cast(const ReqDesc *__restrict__ reqs, int R, int total_chunks,
                                                        BatchState *bs) {
     __shared__ int s_base[kMaxBatchRequests + 1];
@@ -400,18 +404,21 @@ __global__ void __launch_bounds__(kCastThreads, 5) k_cast(const ReqDesc *__restr
         }
         const ReqDesc &d = reqs[lo];
         const int local = g - s_base[lo];
-        const int jc = local / d.n_hyp;   // hypothesis-minor: concurrent warps share 32 directions' tables
-        const int h = local - jc * d.n_hyp;
+        const int nhc = (d.n_hyp + G - 1) / G;   // items per direction chunk (G = d.cast_hyps)
+        const int jc = local / nhc;   // hypothesis-minor: concurrent warps share 32 directions' tables
+        const int h0 = (local - jc * nhc) * G, h1 = min(h0 + G, d.n_hyp);
         const int j = (jc << 5) + lane;
         if (j < d.ns) {
-            const int2 hc = d.hyps[h];
             const int2 dir = d.D[j];
-            int hit, steps = 0;
-            const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.reach, d.W, d.H, d.TW, d.TH, d.rt, d.ns, j, hc.x, hc.y, dir,
-                                                    &hit, &steps)
-                                         : cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, dir, &hit, &steps);
-            d.scan_table[(size_t)h * d.ns + j] = r;
-            my_steps += (unsigned)steps;
+            for (int h = h0; h < h1; ++h) {
+                const int2 hc = d.hyps[h];
+                int hit, steps = 0;
+                const uint32_t r = d.rt.mask ? walk_ray(d.bits, d.reach, d.W, d.H, d.TW, d.TH, d.rt, d.ns, j, hc.x, hc.y,
+                                                        dir, &hit, &steps)
+                                             : cast_ray(d.bits, d.W, d.H, d.TW, d.lim, hc.x, hc.y, dir, &hit, &steps);
+                d.scan_table[(size_t)h * d.ns + j] = r;
+                my_steps += (unsigned)steps;
+            }
         }
     }
 #pragma unroll
@@ -715,12 +722,16 @@ __global__ void __launch_bounds__(256) k_synth(RayArgs a, uint32_t *__restrict__
 
 }  // namespace
 
-cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, int ctas_per_sm,
-                        cudaStream_t s) {
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, int cast_hyps, BatchState *bs, int n_sm,
+                        int ctas_per_sm, cudaStream_t s) {
     if (R < 1 || R > kMaxBatchRequests) return cudaErrorInvalidValue;
     if (total_chunks <= 0) return cudaSuccess;
+    // one instance per group size: a single hypothesis keeps the loop-free body
+    void (*kern)(const ReqDesc *, int, int, BatchState *) =
+        cast_hyps == 4 ? k_cast<4> : cast_hyps == 2 ? k_cast<2> : cast_hyps == 1 ? k_cast<1> : nullptr;
+    if (!kern) return cudaErrorInvalidValue;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cast, kCastThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCastThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;   // a tuned launch shape
@@ -728,7 +739,7 @@ cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState
     long long grid = (long long)n_sm * occ;
     if (grid * (kCastThreads / 32) > warps) grid = (warps + kCastThreads / 32 - 1) / (kCastThreads / 32);
     if (grid < R) grid = R;   // one CTA per request for the scan preparation
-    k_cast<<<(int)grid, kCastThreads, 0, s>>>(reqs, R, total_chunks, bs);
+    kern<<<(int)grid, kCastThreads, 0, s>>>(reqs, R, total_chunks, bs);
     return cudaGetLastError();
 }
 

@@ -272,6 +272,12 @@ const relo_tune_entry *tuned(const relo_ctx *ctx, int kind, int k0, int k1, int 
     return nullptr;
 }
 
+// TAM launch shape of a request: a launch of one request looks for its own entries first
+const relo_tune_entry *tuned_tam(const relo_ctx *ctx, int R, int cls, int n_orient, int K) {
+    const relo_tune_entry *e = R == 1 ? tuned(ctx, RELO_TUNE_TAM_ONE, cls, n_orient, K) : nullptr;
+    return e ? e : tuned(ctx, RELO_TUNE_TAM, cls, n_orient, K);
+}
+
 static_assert(kCoarseCaer == RELO_COARSE_CAER && kFineTamMean == RELO_FINE_TAM_MEAN &&
                   kFineBaseline == RELO_FINE_BASELINE && kFineLF == RELO_FINE_LF,
               "metric codes");
@@ -1004,7 +1010,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     const int NC = (int)classes.size();
     // survivors per TAM task: the autotuner's choice for the request's shape, else the built-in one
     auto chunk_of = [&](int r) {
-        const relo_tune_entry *e = tuned(ctx, RELO_TUNE_TAM, vcls[r], pr[r].P->n_orient, pr[r].K);
+        const relo_tune_entry *e = tuned_tam(ctx, R, vcls[r], pr[r].P->n_orient, pr[r].K);
         return e && e->val[0] > 0 ? e->val[0] : tam_chunk_for(pr[r].K, pr[r].P->n_orient, ctx->n_sm);
     };
     std::vector<ReqDesc> desc((size_t)R);
@@ -1023,7 +1029,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
                  align_up(4ull * 8 * 32 * q.P->n_orient * tam_offs_stride_for(vcls[r])) +
                  align_up(8ull * K) + align_up(4ull * q.n_batches * p.local_topk) + align_up(sizeof(SelectState));
         if (mode[r] == kScanCast) total += align_up(4ull * nh * q.P->ns);   // the request's synthesized ranges
-        if (mode[r] != kScanRead && cast) total_chunks += (long long)nh * (((q.P->ns + 31) & ~31) >> 5);
+        if (mode[r] != kScanRead && cast) total_chunks += cast_chunks(nh, q.P->ns, 1);
         if ((long long)total_hyp + nh > (1ll << 30) || total_chunks > (1ll << 31) - 1)
             return fail(ctx, RELO_E_INVALID_ARG, "batch too large");
         total_hyp += nh;
@@ -1034,6 +1040,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         max_C = std::max(max_C, q.m->dev.C);
         max_batches = std::max(max_batches, q.n_batches);
     }
+    // hypotheses per cast work item: group while every resident warp (5 CTAs of 8 warps per SM) keeps 32 or more
+    int cast_hyps = 1;
+    while (cast_hyps < kCastHypsMax && total_chunks >= 32ll * 2 * cast_hyps * 40 * ctx->n_sm) cast_hyps *= 2;
     int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
     if (rc) return rc;
     for (int r = 0; r < R; ++r) {
@@ -1137,10 +1146,12 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         if (d.win_mode == kWinNone) base += d.n_hyp;
         if (d.win_mode == kWinBuild) bbase += d.n_hyp;
         if (d.win_mode == kWinRead) rbase += d.n_hyp;
-        if (d.scan_mode != kScanRead) cbase += d.n_hyp * (d.ns_pad >> 5);
+        d.cast_hyps = cast_hyps;
+        if (d.scan_mode != kScanRead) cbase += (int)cast_chunks(d.n_hyp, d.ns, cast_hyps);
         if (d.win_mode == kWinBuild) max_nm = std::max(max_nm, d.n_m);
     }
     const int total_smad = base, total_build = bbase, total_read = rbase;
+    total_chunks = cast ? cbase : 0;   // the cast's work items after grouping hypotheses
     // Without early termination no batch waits on another's outcome: one TAM
     // round scores every batch's survivors and one selection launch takes the
     // batches in order (Remark 2's termination test is then never made).
@@ -1165,7 +1176,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
             int cps = 0;   // resident CTAs per SM: the smallest the class's requests are tuned to
             for (int r = 0; r < R; ++r) {
                 if (vcls[r] != classes[c]) continue;
-                const relo_tune_entry *e = tuned(ctx, RELO_TUNE_TAM, vcls[r], desc[r].n_orient, desc[r].K);
+                const relo_tune_entry *e = tuned_tam(ctx, R, vcls[r], desc[r].n_orient, desc[r].K);
                 if (e && e->val[1] > 0) cps = cps > 0 ? std::min(cps, e->val[1]) : e->val[1];
             }
             TamPlan &tp = plans[(size_t)bi * NC + c];
@@ -1199,7 +1210,7 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
                         for (int r = 0; r < R && !ns0; ++r)
                             if (mode[r] != kScanRead) ns0 = desc[r].ns;
                         const relo_tune_entry *e = tuned(ctx, RELO_TUNE_CAST, ns0, 0, 0);
-                        return launch_cast(rq, R, (int)total_chunks, sl.bs, ctx->n_sm, e ? e->val[0] : 0, st);
+                        return launch_cast(rq, R, (int)total_chunks, cast_hyps, sl.bs, ctx->n_sm, e ? e->val[0] : 0, st);
                     }),
            "ray cast");
     if (total_smad > 0)
@@ -2074,7 +2085,7 @@ int relo_set_tuning(relo_ctx *ctx, const relo_tune_entry *entries, int32_t n) {
     if (!ctx || n < 0 || (n > 0 && !entries)) return fail(ctx, RELO_E_INVALID_ARG, "bad arguments");
     for (int i = 0; i < n; ++i) {
         const relo_tune_entry &e = entries[i];
-        const bool ok = (e.kind == RELO_TUNE_TAM && e.val[0] >= 0 && e.val[0] <= 128 && e.val[0] % 8 == 0 &&
+        const bool ok = ((e.kind == RELO_TUNE_TAM || e.kind == RELO_TUNE_TAM_ONE) && e.val[0] >= 0 && e.val[0] <= 128 && e.val[0] % 8 == 0 &&
                          e.val[1] >= 0 && e.val[1] <= 32) ||
                         (e.kind == RELO_TUNE_CAST && e.val[0] >= 0 && e.val[0] <= 32);
         if (!ok) return fail(ctx, RELO_E_INVALID_ARG, "bad tuning entry");

@@ -90,6 +90,14 @@ __host__ __device__ inline size_t occupancy_words(int TW, int TH) {
 // one move.  The walk frames' last column and row are full, so a box never
 // leaves the map.
 constexpr int kReachMax = 16;
+// Hypotheses one ray-cast work item takes, for one chunk of 32 directions
+// (the directions' setup is then done once for all of them): at most
+// kCastHypsMax, fewer when the batch has too few rays to give every resident
+// warp some 32 items after grouping (the last wave's tail would grow).
+constexpr int kCastHypsMax = 4;
+__host__ __device__ inline long long cast_chunks(int n_hyp, int ns, int per_item) {
+    return (long long)((n_hyp + per_item - 1) / per_item) * (((ns + 31) & ~31) >> 5);
+}
 // words per frame row of the tiles' emptiness bits (one more than the row needs: the 64-tile window of a row's last
 // 32 tiles reads it)
 __host__ __device__ inline unsigned walk_empty_row_words(int TW) { return ((unsigned)TW + 1u + 31u) / 32u + 1u; }
@@ -252,6 +260,7 @@ struct ReqDesc {
     uint32_t *scan_table;
     int scan_mode;               // kScanCast, kScanStore or kScanRead
     int chunk_base;              // first 32-ray chunk of this request in the batch's cast list
+    int cast_hyps;               // hypotheses per ray-cast work item (1, 2 or 4; the same for the whole batch)
     // resident window sums of (map, hypotheses, N_s, lim, intervals, Theta): per hypothesis the n_m keys
     // W_m << 13 | q (W_m the window sum of Eq. 18 at m = q n_enum), ascending
     unsigned long long *win;
@@ -329,7 +338,7 @@ cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, ui
 // scan preparation alone, for a batch that casts no rays (launch_cast does it otherwise)
 cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s);
 // casts the total_chunks 32-ray chunks of the batch into the requests' scan tables
-cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, BatchState *bs, int n_sm, int ctas_per_sm,
+cudaError_t launch_cast(const ReqDesc *reqs, int R, int total_chunks, int cast_hyps, BatchState *bs, int n_sm, int ctas_per_sm,
                         cudaStream_t s);
 // SMAD of every hypothesis of the batch from the requests' scan tables
 cudaError_t launch_smad(const ReqDesc *reqs, int R, int total_hyp, int max_ns_pad, BatchState *bs, int n_sm,

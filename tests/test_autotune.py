@@ -21,7 +21,8 @@ def relo():
 
 def test_cache_round_trip(relo, tmp_path):
     from paper_2511_01219_gb300 import autotune
-    entries = [(relo.TUNE_TAM, (34, 360, 256), (16, 4)), (relo.TUNE_CAST, (1440, 0, 0), (5, 0))]
+    entries = [(relo.TUNE_TAM, (34, 360, 256), (16, 4)), (relo.TUNE_CAST, (1440, 0, 0), (5, 0)),
+               (relo.TUNE_TAM_ONE, (46, 720, 1024), (48, 4))]
     path = str(tmp_path / "t" / "dev.json")
     autotune.save(path, entries, {"device": "test"})
     assert autotune.load(path) == entries

@@ -807,12 +807,15 @@ def test_launch_shapes_do_not_change_results(relo, workload):
     cls = relo.tam_class(len(wl.ranges))
     for entries in ([(relo.TUNE_TAM, (cls, wl.n_orient, K), (8, 1))],
                     [(relo.TUNE_TAM, (0, 0, 0), (64, 2)), (relo.TUNE_CAST, (0, 0, 0), (2, 0))],
-                    [(relo.TUNE_TAM, (cls, 0, 0), (128, 0)), (relo.TUNE_CAST, (wl.n_s, 0, 0), (1, 0))]):
+                    [(relo.TUNE_TAM, (cls, 0, 0), (128, 0)), (relo.TUNE_CAST, (wl.n_s, 0, 0), (1, 0))],
+                    # a single request's own entry comes first, the batched one is the fallback
+                    [(relo.TUNE_TAM_ONE, (cls, wl.n_orient, K), (16, 3)), (relo.TUNE_TAM, (0, 0, 0), (8, 1))]):
         ctx.set_tuning(entries)
         got, T = scores()
         assert got == base
         assert np.array_equal(T.view(np.uint32), T0.view(np.uint32))
-    for bad in ([(relo.TUNE_TAM, (0, 0, 0), (12, 0))], [(9, (0, 0, 0), (8, 0))], [(relo.TUNE_CAST, (0, 0, 0), (-1, 0))]):
+    for bad in ([(relo.TUNE_TAM, (0, 0, 0), (12, 0))], [(9, (0, 0, 0), (8, 0))], [(relo.TUNE_CAST, (0, 0, 0), (-1, 0))],
+                [(relo.TUNE_TAM_ONE, (0, 0, 0), (136, 0))]):
         with pytest.raises(relo.ReloError):
             ctx.set_tuning(bad)
     ctx.set_tuning([])
