@@ -434,8 +434,9 @@ constexpr int kSmadLoads = 16;   // 32-range chunks a SMAD warp has in flight
 // scans each chunk with shuffles into exclusive in-chunk prefixes and carries
 // the 64-bit chunk prefix; P(t) = chunkP[t / 32] + inner[t] is then the cyclic
 // prefix sum of Eq. 17 for t in [0, N_s].  The lanes split the orientations,
-// evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).  No CTA barrier:
-// each warp owns its slice of shared memory.
+// evaluate Eq. 18-19 per m and reduce the minimum (Eq. 20).  With a single
+// orientation (m = 0) the warp sums the row over the FoV intervals directly.
+// No CTA barrier: each warp owns its slice of shared memory.
 __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, int R, int total_hyp,
                                               BatchState *bs, int warp_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -463,9 +464,32 @@ __global__ void __launch_bounds__(256) k_smad(const ReqDesc *__restrict__ reqs, 
             caer_hypothesis(d, h, reinterpret_cast<uint32_t *>(mine), lane);
             continue;
         }
+        const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
+        if (d.n_m == 1) {
+            // a single orientation, m = 0 (Eq. 20 when lambda >= 0.9): W_0 is the row summed over the FoV
+            // intervals, read once and coalesced; no prefixes are needed
+            long long w = 0;
+            for (int k = 0; k < d.n_iv; ++k) {
+                const int2 iv = d.iv[k];
+                for (int t = lane; t < iv.y; t += 32) {
+                    int j = iv.x + t;
+                    if (j >= ns) j -= ns;
+                    w += __ldg(row + j);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+            if (lane == 0) {
+                long long dnum = d.scan->sum_real - w;
+                if (dnum < 0) dnum = -dnum;
+                d.keys[h] = ((unsigned long long)dnum << kHypBits) | (unsigned long long)h;
+                d.smad_num[h] = dnum;
+                d.smad_m[h] = 0;
+            }
+            continue;
+        }
         uint32_t *inner = reinterpret_cast<uint32_t *>(mine);
         long long *chunkP = reinterpret_cast<long long *>(mine + (((size_t)(ns_pad + 32) * 4 + 7) & ~(size_t)7));
-        const uint32_t *__restrict__ row = d.scan_table + (size_t)h * ns;
         long long carry = 0;
         for (int c0 = 0; c0 < nch; c0 += kSmadLoads) {
             uint32_t r[kSmadLoads];
