@@ -217,6 +217,42 @@ def test_full_path_matches_oracle(relo, workload, cfg):
     ctx.close()
 
 
+@pytest.mark.parametrize("gap", [0, 14])
+def test_single_orientation_smad_paths(relo, workload, gap):
+    """SMAD with one orientation (m = 0, lambda >= 0.9, Eq. 20) sums each row
+    over the FoV intervals directly (one interval of every direction, or two
+    around a gap); with resident synthesized scans W_0 comes from window tables
+    built from the stored rows.  Every numerator equals the oracle's."""
+    torch = torch_()
+    wl = workload(0)
+    ns = 504
+    ang = workloads.beam_angles(ns, ns)
+    keep = np.ones(ns, bool)
+    keep[100:100 + gap] = False
+    ang = ang[keep]
+    pose = (wl.hyps[7, 0], wl.hyps[7, 1], 0.0)
+    z = workloads.render_scan(wl.grid, wl.res, ((pose[0] + 0.5) * wl.res, (pose[1] + 0.5) * wl.res, 0.0), ang,
+                              wl.max_range)
+    prm = oracle.Params(n_orient=wl.n_orient, topk=16)
+    pl = oracle.plan(z, ang, wl.max_range, wl.res, prm)
+    assert pl["ns"] == ns and pl["lam"] >= 0.9
+    num, mm = oracle.coarse(wl.grid, wl.hyps, pl, prm)
+    runs = []
+    for cache in (0, 64 << 20, 64 << 20):   # no resident scans; then a request that stores them, one that reads
+        if cache == 0 or len(runs) == 1:
+            if runs:
+                ctx.close()
+            ctx = relo.Relo(n_orient=wl.n_orient, topk=16, early_stop=0, scan_cache_bytes=cache)
+            mid = ctx.load_map(wl.grid, wl.res)
+            ctx.set_hypotheses(mid, workloads.cell_centres(wl.hyps, wl.res))
+        out = ctx.relocalize(mid, z, ang, wl.max_range)
+        assert out.status == 0
+        got = ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(len(wl.hyps), dtype=torch.int64, device="cuda")).cpu()
+        assert np.array_equal(got.numpy(), num) and not mm.any()
+        runs.append(cache)
+    ctx.close()
+
+
 @pytest.mark.parametrize("d_max", [2.25, 2.3, 3.9, 3.95, 4.5])
 def test_selection_counts_either_side_of_fp16_range(relo, workload, d_max):
     """The TAM selection counts run on packed fp16 patterns 0x6400 + b while
