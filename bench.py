@@ -32,6 +32,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -217,12 +218,21 @@ def committed_traffic(stage: str, config: int, key: str = "dram_bytes_per_launch
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2511_01219_gb300", "csrc", rec["source"])
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = code_sha(os.path.join(ROOT, "paper_2511_01219_gb300", "csrc", rec["source"]))
     except OSError:
         return None
-    return rec.get(key) if h == rec["source_sha"] else None
+    return rec.get(key) if h == rec["code_sha"] else None
+
+
+def code_sha(path: str) -> str:
+    """sha256[:16] of a CUDA source with its comments and whitespace removed, so
+    that a counter capture stays matched to the code it measured through edits
+    of the comments only."""
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()[:16]
 
 
 def apply_tuning(ctx, torch, local) -> dict:

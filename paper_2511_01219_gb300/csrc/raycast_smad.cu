@@ -224,8 +224,8 @@ __device__ __forceinline__ uint32_t walk_ray(const uint64_t *__restrict__ bits, 
     int stop;   // 1 hit (or left the map), 2 range limit
     for (;;) {
         const int lx = cx & 7, ly = cy & 7;
-        // the tile's word, its square and the tile's exit steps are loaded together: one memory round trip
-        // per tile (a second one when the ray leaves a larger square)
+        // the tile's word, its boxes and the tile's exit steps are loaded together: one memory round trip
+        // per tile (a second one when the ray leaves a larger box)
         const unsigned ti = (unsigned)(cy >> 3) * WB + (unsigned)(cx >> 3);
         const uint64_t word = __ldg(bq + ti);
         const unsigned rv = __ldg(rq + ti);
