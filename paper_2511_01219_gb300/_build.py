@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librelo.so")
 SOURCES = ["relo_api.cu", "edt.cu", "raycast_smad.cu", "select.cu", "tam.cu", "icp.cu", "rrt.cu", "edt_noalloc.cu",
            "smad_direct.cu", "probe.cu"]
-HEADERS = ["relo_internal.h", os.path.join("..", "..", "include", "relo.h")]
+HEADERS = ["relo_internal.h", "scan_prep.cuh", "tam_offsets.cuh", os.path.join("..", "..", "include", "relo.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1230,15 +1230,15 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     if (total_read > 0)
         CK(timed_on(ctx, st, 6, 1, [&] { return launch_win_read(rq, R, total_read, st); }), "SMAD by window tables");
     for (auto &x : created.list) CK(cudaEventRecord(x.second->written, st), "scan table");
-    CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, st); }), "SMAD top-K");
-    CK(timed_on(ctx, st, 3, 1, [&] { return launch_tam_chunks(rq, R, st); }), "TAM work order");
-    for (int r = 0; r < R; ++r) CK(cudaStreamWaitEvent(st, pr[r].m->field_ready, 0), "map field");
     {
         int max_no = 1;
         for (int r = 0; r < R; ++r) max_no = std::max(max_no, desc[r].n_orient);
-        // the endpoint offset table O[m][i] of the request plan, per band phase (timed with the scan preparation)
-        CK(timed_on(ctx, st, 1, 1, [&] { return launch_tam_offsets(rq, R, max_no, st); }), "TAM offsets");
+        // the ranking, and beside it the endpoint offset table O[m][i] of each request plan, per band phase
+        CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, max_no, ctx->n_sm, st); }),
+           "SMAD top-K");
     }
+    CK(timed_on(ctx, st, 3, 1, [&] { return launch_tam_chunks(rq, R, st); }), "TAM work order");
+    for (int r = 0; r < R; ++r) CK(cudaStreamWaitEvent(st, pr[r].m->field_ready, 0), "map field");
     for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {
             const TamPlan &tp = plans[(size_t)bi * NC + c];

@@ -243,7 +243,7 @@ struct ReqDesc {
     // their cell, cut into chunks of at most tam_chunk of one phase: (phase, first, end) into surv_perm;
     // the chunks of batches < b are tam_chunks[0, chunk_cnt[b])
     int32_t *surv_perm;          // [K]
-    int32_t *tam_offs;           // [8][n_orient][32][tam_stride] TAM endpoint offsets by band phase (k_tam_offsets)
+    int32_t *tam_offs;           // [8][n_orient][32][tam_stride] TAM endpoint offsets by band phase (tam_offsets.cuh)
     int tam_stride;              // slots per lane in tam_offs
     int4 *tam_chunks;            // [sum over batches of ceil(n_b / tam_chunk) + 8]
     int32_t *chunk_cnt;          // [n_batches + 1]
@@ -352,7 +352,8 @@ cudaError_t launch_rank_by_index(const ReqDesc *reqs, int R, int total_hyp, int 
 cudaError_t launch_win_build(const ReqDesc *reqs, int R, int total, int max_ns_pad, int max_nm, cudaStream_t s);
 // SMAD of the window-read requests' hypotheses by search in their window keys
 cudaError_t launch_win_read(const ReqDesc *reqs, int R, int total, cudaStream_t s);
-cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s);
+// the top-K of every request, and beside it (extra blocks) every request's TAM endpoint offsets
+cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, int max_n_orient, int n_sm, cudaStream_t s);
 // plans the TAM launch of one batch index: fills segs[R] and returns the task count and grid size
 struct TamPlan {
     int total_tasks, grid, vpl;
@@ -369,7 +370,6 @@ cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s);
 // per-lane stride of the TAM endpoint offsets of a values-per-lane class
 int tam_offs_stride_for(int vpl);
 // every request's TAM endpoint offsets for all band phases and orientations (after the scan preparation)
-cudaError_t launch_tam_offsets(const ReqDesc *reqs, int R, int max_n_orient, cudaStream_t s);
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s);
 // selection of batch indexes batch_lo .. batch_hi - 1 in order; with last, also every request's result.
 // With icp, only the local top-k (launch_icp and launch_icp_best take the rest).

@@ -24,11 +24,14 @@
 // The last selection launch also writes the selected pose and counters into
 // each request's relo_result.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
 #include "../../include/relo.h"
 #include "relo_internal.h"
+#include "tam_offsets.cuh"
 
 namespace relo {
 
@@ -81,9 +84,19 @@ __device__ void order_out(unsigned long long *v, int n, int K, int32_t *survivor
 
 constexpr int kTopkBins = 2048;   // first pass: the 11 bits below the keys' highest set bit
 
-// one CTA per request
-__global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap) {
+// one CTA per request; the CTAs after the first R compute the requests' TAM
+// endpoint offsets meanwhile (they need the scan preparation, not the ranking)
+__global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap,
+                                                       int R, int max_n_orient) {
     extern __shared__ __align__(16) unsigned long long sm[];
+    if ((int)blockIdx.x >= R) {
+        for (int t = (int)blockIdx.x - R; t < R * max_n_orient; t += (int)gridDim.x - R) {
+            const ReqDesc &o = reqs[t / max_n_orient];
+            const int q = t % max_n_orient;
+            if (q < o.n_orient && !o.state->done && o.tam_offs) tam_offsets_one(o, q);
+        }
+        return;
+    }
     const ReqDesc &d = reqs[blockIdx.x];
     const unsigned long long *keys_g = d.keys;
     const int n = d.n_hyp, K = d.K;
@@ -355,7 +368,8 @@ __global__ void k_icp_best(const ReqDesc *__restrict__ reqs, int R, int batch_lo
 
 }  // namespace
 
-cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cudaStream_t s) {
+cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, int max_n_orient, int n_sm,
+                        cudaStream_t s) {
     int Kp = 1;
     while (Kp < max_K) Kp <<= 1;
     const size_t fixed = (size_t)2 * Kp * 8 + (size_t)kTopkBins * 4;
@@ -364,7 +378,9 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, cu
     const size_t smem = fixed + (size_t)stage_cap * 8;
     cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_topk<<<R, kTopkThreads, smem, s>>>(reqs, Kp, stage_cap);
+    // one CTA per SM for the offsets (the ranking CTAs' shared memory leaves room for no second one)
+    const int n_off = std::max(1, std::min(R * std::max(max_n_orient, 1), n_sm));
+    k_topk<<<R + n_off, kTopkThreads, smem, s>>>(reqs, Kp, stage_cap, R, std::max(max_n_orient, 1));
     return cudaGetLastError();
 }
 

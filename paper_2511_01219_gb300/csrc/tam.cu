@@ -134,50 +134,11 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
     if (blockIdx.y == 0) scan_prep_request(d);
 }
 
-// Every request's endpoint offsets, once per batch: for band phase ph,
-// orientation q (m = q n_enum) and valid beam i, the field_index offset of the
-// endpoint cell round-half-up(R_i * D_{(b_i + m) mod N_s} / 2^46) per axis from
-// a cell of band phase ph (linear in the x offset, and in the y offset through
-// the bands crossed), laid out [ph][q][lane][slot] with the TAM kernel's
-// per-lane stride, so one block's offsets for one phase are one contiguous
-// span.  CTA (q, request) writes all eight phases of orientation q.
-__device__ void tam_offsets_one(const ReqDesc &d, int q) {
-    const int N = d.scan->n_valid;
-    const int m = q * d.n_enum;
-    const long long Wp8 = 8ll * d.Wp;
-    const int kS = d.tam_stride;
-    const size_t phase_step = (size_t)d.n_orient * 32 * kS;
-    int32_t *oq = d.tam_offs + (size_t)q * 32 * kS;
-    // k walks the orientation's table in memory order (lane-major), so every store is coalesced
-    for (int k = threadIdx.x; k < 32 * kS; k += blockDim.x) {
-        const int i = (k % kS) * 32 + k / kS;   // the beam in slot k % kS of lane k / kS
-        if (i >= N) continue;
-        const int2 bR = d.vbR[i];
-        int j = bR.x + m;
-        if (j >= d.ns) j -= d.ns;
-        const int2 dir = d.D[j];
-        const int ox = (int)(((long long)bR.y * dir.x + (1ll << 45)) >> 46);
-        const int oy = (int)(((long long)bR.y * dir.y + (1ll << 45)) >> 46);
-        // |ox|, |oy| < P keeps every endpoint inside the field's border
-#pragma unroll
-        for (int ph = 0; ph < 8; ++ph) {
-            const int v = ph + oy;
-            oq[ph * phase_step + k] = (int)(8ll * ox + Wp8 * (v >> 3)) + (v & 7);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_tam_offsets(const ReqDesc *__restrict__ reqs) {
-    const ReqDesc &d = reqs[blockIdx.y];
-    const int q = blockIdx.x;
-    if (q >= d.n_orient || d.state->done || !d.tam_offs) return;
-    tam_offsets_one(d, q);
-}
 
 // Work is split into tasks (request, chunk of survivors of one band phase,
 // block of kTamQ consecutive orientations); k_tam_chunks builds the chunks on
 // the device after the top-K.  A CTA copies the block's endpoint offsets for
-// its chunk's phase from the request's table (k_tam_offsets: one linear
+// its chunk's phase from the request's table (tam_offsets.cuh: one linear
 // offset per phase, orientation and valid beam, computed once per request)
 // into shared memory; each warp then scores its survivors of the chunk over
 // the block's orientations, every gather one add to the survivor's base.
@@ -538,12 +499,6 @@ TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams,
 }
 
 int tam_offs_stride_for(int vpl) { return tam_offs_stride(vpl); }
-
-cudaError_t launch_tam_offsets(const ReqDesc *reqs, int R, int max_n_orient, cudaStream_t s) {
-    if (R <= 0 || max_n_orient <= 0) return cudaSuccess;
-    k_tam_offsets<<<dim3(max_n_orient, R), 256, 0, s>>>(reqs);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s) {
     k_tam_chunks<<<R, 1024, 0, s>>>(reqs);
