@@ -1040,9 +1040,9 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
         max_C = std::max(max_C, q.m->dev.C);
         max_batches = std::max(max_batches, q.n_batches);
     }
-    // hypotheses per cast work item: group while every resident warp (5 CTAs of 8 warps per SM) keeps 32 or more
+    // hypotheses per cast work item: group while every resident warp (5 CTAs of 8 warps per SM) keeps 16 or more items
     int cast_hyps = 1;
-    while (cast_hyps < kCastHypsMax && total_chunks >= 32ll * 2 * cast_hyps * 40 * ctx->n_sm) cast_hyps *= 2;
+    while (cast_hyps < kCastHypsMax && total_chunks >= 16ll * 2 * cast_hyps * 40 * ctx->n_sm) cast_hyps *= 2;
     int rc = ensure(ctx, &sl.arena, &sl.arena_cap, total, "request scratch");
     if (rc) return rc;
     for (int r = 0; r < R; ++r) {

@@ -93,7 +93,7 @@ constexpr int kReachMax = 16;
 // Hypotheses one ray-cast work item takes, for one chunk of 32 directions
 // (the directions' setup is then done once for all of them): at most
 // kCastHypsMax, fewer when the batch has too few rays to give every resident
-// warp some 32 items after grouping (the last wave's tail would grow).
+// warp some 16 items after grouping (the last wave's tail would grow).
 constexpr int kCastHypsMax = 4;
 __host__ __device__ inline long long cast_chunks(int n_hyp, int ns, int per_item) {
     return (long long)((n_hyp + per_item - 1) / per_item) * (((ns + 31) & ~31) >> 5);
