@@ -1233,11 +1233,11 @@ int run_batch(relo_ctx *ctx, BatchSlot &sl, const Prepared *pr, int R) {
     {
         int max_no = 1;
         for (int r = 0; r < R; ++r) max_no = std::max(max_no, desc[r].n_orient);
-        // the ranking, and beside it the endpoint offset table O[m][i] of each request plan, per band phase
+        // the ranking and TAM's work order, and beside them the endpoint offset table O[m][i] of each request plan,
+        // per band phase
         CK(timed_on(ctx, st, 3, 1, [&] { return launch_topk(rq, R, max_n_hyp, max_K, max_no, ctx->n_sm, st); }),
            "SMAD top-K");
     }
-    CK(timed_on(ctx, st, 3, 1, [&] { return launch_tam_chunks(rq, R, st); }), "TAM work order");
     for (int r = 0; r < R; ++r) CK(cudaStreamWaitEvent(st, pr[r].m->field_ready, 0), "map field");
     for (int bi = 0; bi < tam_rounds; ++bi) {
         for (int c = 0; c < NC; ++c) {

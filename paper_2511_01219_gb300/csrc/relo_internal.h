@@ -294,7 +294,7 @@ struct BatchState {
 // TAM work of one request in one launch: the survivors of its batches
 // [batch_lo, batch_hi) (none when equal), for each of its orientations.  The
 // launch's tasks are (chunk of same-phase survivors, block of orientations);
-// the chunks are built on the device (launch_tam_chunks).
+// the chunks are built on the device (by the top-K launch).
 struct TamSeg {
     int batch_lo, batch_hi;
 };
@@ -352,7 +352,7 @@ cudaError_t launch_rank_by_index(const ReqDesc *reqs, int R, int total_hyp, int 
 cudaError_t launch_win_build(const ReqDesc *reqs, int R, int total, int max_ns_pad, int max_nm, cudaStream_t s);
 // SMAD of the window-read requests' hypotheses by search in their window keys
 cudaError_t launch_win_read(const ReqDesc *reqs, int R, int total, cudaStream_t s);
-// the top-K of every request, and beside it (extra blocks) every request's TAM endpoint offsets
+// the top-K of every request with its TAM work order, and beside it (extra blocks) every request's TAM endpoint offsets
 cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, int max_n_orient, int n_sm, cudaStream_t s);
 // plans the TAM launch of one batch index: fills segs[R] and returns the task count and grid size
 struct TamPlan {
@@ -366,7 +366,6 @@ int tam_vpl_for(int max_beams);
 TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams, int max_C, int n_sm,
                  int ctas_per_sm, TamSeg *segs);
 // TAM's work order (surv_perm, tam_chunks, chunk_cnt) of every request, after the top-K
-cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s);
 // per-lane stride of the TAM endpoint offsets of a values-per-lane class
 int tam_offs_stride_for(int vpl);
 // every request's TAM endpoint offsets for all band phases and orientations (after the scan preparation)

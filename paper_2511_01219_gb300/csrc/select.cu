@@ -84,20 +84,9 @@ __device__ void order_out(unsigned long long *v, int n, int K, int32_t *survivor
 
 constexpr int kTopkBins = 2048;   // first pass: the 11 bits below the keys' highest set bit
 
-// one CTA per request; the CTAs after the first R compute the requests' TAM
-// endpoint offsets meanwhile (they need the scan preparation, not the ranking)
-__global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap,
-                                                       int R, int max_n_orient) {
-    extern __shared__ __align__(16) unsigned long long sm[];
-    if ((int)blockIdx.x >= R) {
-        for (int t = (int)blockIdx.x - R; t < R * max_n_orient; t += (int)gridDim.x - R) {
-            const ReqDesc &o = reqs[t / max_n_orient];
-            const int q = t % max_n_orient;
-            if (q < o.n_orient && !o.state->done && o.tam_offs) tam_offsets_one(o, q);
-        }
-        return;
-    }
-    const ReqDesc &d = reqs[blockIdx.x];
+// The first K keys of request d in ascending order into its survivor list,
+// by one CTA (sm: the launch's dynamic shared memory).
+__device__ void topk_request(const ReqDesc &d, unsigned long long *sm, int Kp_cap, int stage_cap) {
     const unsigned long long *keys_g = d.keys;
     const int n = d.n_hyp, K = d.K;
     unsigned long long *sortbuf = sm;                                          // [2 * Kp_cap]
@@ -115,10 +104,20 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     unsigned long long orv = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        unsigned long long k = keys_g[i];
-        if (staged) keys_s[i] = k;
-        orv |= k;
+    constexpr int kLoads = 8;   // keys a thread has in flight
+    for (int i0 = threadIdx.x; i0 < n; i0 += kLoads * blockDim.x) {
+        unsigned long long k[kLoads];
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int i = i0 + u * blockDim.x;
+            k[u] = i < n ? keys_g[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (staged && i < n) keys_s[i] = k[u];
+            orv |= k[u];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, o);
     if (lane == 0) atomicOr(&s_or, orv);
@@ -232,6 +231,26 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict
     }
     __syncthreads();
     order_out(sortbuf, K, K, d.survivors);
+}
+
+// One CTA per request ranks it and then builds its TAM work order from the
+// survivors; the CTAs after the first R compute the requests' TAM endpoint
+// offsets meanwhile (they need the scan preparation, not the ranking).
+__global__ void __launch_bounds__(kTopkThreads) k_topk(const ReqDesc *__restrict__ reqs, int Kp_cap, int stage_cap,
+                                                       int R, int max_n_orient) {
+    extern __shared__ __align__(16) unsigned long long sm[];
+    if ((int)blockIdx.x >= R) {
+        for (int t = (int)blockIdx.x - R; t < R * max_n_orient; t += (int)gridDim.x - R) {
+            const ReqDesc &o = reqs[t / max_n_orient];
+            const int q = t % max_n_orient;
+            if (q < o.n_orient && !o.state->done && o.tam_offs) tam_offsets_one(o, q);
+        }
+        return;
+    }
+    const ReqDesc &d = reqs[blockIdx.x];
+    topk_request(d, sm, Kp_cap, stage_cap);
+    __syncthreads();   // every survivor is written
+    tam_chunks_one(d);
 }
 
 // The request's pose, score and counters into its relo_result (one thread).

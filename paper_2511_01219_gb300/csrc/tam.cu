@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(1024) k_scan_prep(const ReqDesc *__restrict__ 
 
 
 // Work is split into tasks (request, chunk of survivors of one band phase,
-// block of kTamQ consecutive orientations); k_tam_chunks builds the chunks on
-// the device after the top-K.  A CTA copies the block's endpoint offsets for
+// block of kTamQ consecutive orientations); the top-K launch builds the chunks
+// on the device (tam_offsets.cuh).  A CTA copies the block's endpoint offsets for
 // its chunk's phase from the request's table (tam_offsets.cuh: one linear
 // offset per phase, orientation and valid beam, computed once per request)
 // into shared memory; each warp then scores its survivors of the chunk over
@@ -429,48 +429,6 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// TAM's work order, one CTA per request: within each batch (with early
-// termination; without it TAM scores every batch in one launch, so all K
-// positions form one group), the survivor positions grouped by the band phase
-// (y + P) % 8 of their cell (the order inside a group is immaterial: every
-// position's scores are its own), then cut into chunks of at most tam_chunk
-// positions of one phase, so a CTA task computes one phase's endpoint offsets
-// for all its survivors.
-__global__ void __launch_bounds__(1024) k_tam_chunks(const ReqDesc *__restrict__ reqs) {
-    const ReqDesc &d = reqs[blockIdx.x];
-    __shared__ int s_cnt[8], s_next[8];
-    __shared__ int s_chunks;
-    if (threadIdx.x == 0) {
-        s_chunks = 0;
-        d.chunk_cnt[0] = 0;
-    }
-    const int groups = d.early_stop ? d.n_batches : 1;
-    for (int b = 0; b < groups; ++b) {
-        const int lo = b * d.B, hi = d.early_stop ? min(d.K, lo + d.B) : d.K;
-        if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
-        __syncthreads();
-        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_cnt[(d.hyps[d.survivors[i]].y + d.P) & 7], 1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = lo, nc = s_chunks;
-            for (int p = 0; p < 8; ++p) {
-                s_next[p] = run;
-                for (int f = run; f < run + s_cnt[p]; f += d.tam_chunk)
-                    d.tam_chunks[nc++] = make_int4(p, f, min(run + s_cnt[p], f + d.tam_chunk), 0);
-                run += s_cnt[p];
-            }
-            s_chunks = nc;
-            if (d.early_stop) d.chunk_cnt[b + 1] = nc;
-            else
-                for (int j = 1; j <= d.n_batches; ++j) d.chunk_cnt[j] = nc;
-        }
-        __syncthreads();
-        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
-            d.surv_perm[atomicAdd(&s_next[(d.hyps[d.survivors[i]].y + d.P) & 7], 1)] = i;
-        __syncthreads();
-    }
-}
-
 // The launch for the batches [batch_lo[r], batch_hi[r]) of every request:
 // its kernel class (values per lane and selection precision for the longest
 // scan and the largest clamp), the shared memory (table and one block's
@@ -499,11 +457,6 @@ TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams,
 }
 
 int tam_offs_stride_for(int vpl) { return tam_offs_stride(vpl); }
-
-cudaError_t launch_tam_chunks(const ReqDesc *reqs, int R, cudaStream_t s) {
-    k_tam_chunks<<<R, 1024, 0, s>>>(reqs);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_tam(const ReqDesc *reqs, int R, const TamSeg *segs, const TamPlan &tp, cudaStream_t s) {
     if (tp.total_tasks <= 0) return cudaSuccess;

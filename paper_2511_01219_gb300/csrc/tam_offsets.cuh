@@ -1,6 +1,8 @@
-// The TAM endpoint offsets of a request plan (Eq. 13's endpoint cells, as
-// offsets into the banded field), computed by the blocks of the top-K launch
-// that do not rank (select.cu), beside the ranking blocks.
+// TAM's inputs that the top-K launch prepares (select.cu): each request's
+// work order (survivors grouped by band phase, in chunks), built by its
+// ranking CTA once the survivors are known, and the endpoint offsets of its
+// plan (Eq. 13's endpoint cells, as offsets into the banded field), computed
+// by the other CTAs of the launch beside the ranking ones.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,6 +41,47 @@ __device__ __forceinline__ void tam_offsets_one(const ReqDesc &d, int q) {
             const int v = ph + oy;
             oq[ph * phase_step + k] = (int)(8ll * ox + Wp8 * (v >> 3)) + (v & 7);
         }
+    }
+}
+
+// TAM's work order of request d, by one CTA (after the top-K): within each batch (with early
+// termination; without it TAM scores every batch in one launch, so all K
+// positions form one group), the survivor positions grouped by the band phase
+// (y + P) % 8 of their cell (the order inside a group is immaterial: every
+// position's scores are its own), then cut into chunks of at most tam_chunk
+// positions of one phase, so a CTA task computes one phase's endpoint offsets
+// for all its survivors.
+__device__ __forceinline__ void tam_chunks_one(const ReqDesc &d) {
+    __shared__ int s_cnt[8], s_next[8];
+    __shared__ int s_chunks;
+    if (threadIdx.x == 0) {
+        s_chunks = 0;
+        d.chunk_cnt[0] = 0;
+    }
+    const int groups = d.early_stop ? d.n_batches : 1;
+    for (int b = 0; b < groups; ++b) {
+        const int lo = b * d.B, hi = d.early_stop ? min(d.K, lo + d.B) : d.K;
+        if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_cnt[(d.hyps[d.survivors[i]].y + d.P) & 7], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = lo, nc = s_chunks;
+            for (int p = 0; p < 8; ++p) {
+                s_next[p] = run;
+                for (int f = run; f < run + s_cnt[p]; f += d.tam_chunk)
+                    d.tam_chunks[nc++] = make_int4(p, f, min(run + s_cnt[p], f + d.tam_chunk), 0);
+                run += s_cnt[p];
+            }
+            s_chunks = nc;
+            if (d.early_stop) d.chunk_cnt[b + 1] = nc;
+            else
+                for (int j = 1; j <= d.n_batches; ++j) d.chunk_cnt[j] = nc;
+        }
+        __syncthreads();
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            d.surv_perm[atomicAdd(&s_next[(d.hyps[d.survivors[i]].y + d.P) & 7], 1)] = i;
+        __syncthreads();
     }
 }
 
