@@ -45,36 +45,40 @@ __global__ void k_edt_col_summary(const int8_t *__restrict__ grid, int W, int H,
     if (x0 >= W) return;   // the whole warp lies right of the map
     const int y0 = sgm * L;
     int first = -1, last = -1;
-    uint64_t word = 0ull, wword = 0ull;   // the map's word; the walk frames' word (outside cells set)
-    for (int y = y0; y < y0 + L; ++y) {
-        const bool inside = x < W && y < H;
-        const bool occ = inside && grid[(size_t)y * W + x] >= 65;
-        if (occ) {
-            if (first < 0) first = y;
-            last = y;
+    // a tile row (8 grid rows; L and y0 are multiples of 8) at a time, its 8 loads issued together
+    for (int yb = y0; yb < y0 + L; yb += 8) {
+        bool occ8[8], in8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            in8[u] = x < W && yb + u < H;
+            occ8[u] = in8[u] && grid[(size_t)(yb + u) * W + x] >= 65;
         }
-        const unsigned b = __ballot_sync(0xffffffffu, occ);
-        const unsigned bw = __ballot_sync(0xffffffffu, occ || !inside);
-        word |= (uint64_t)((b >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
-        wword |= (uint64_t)((bw >> (8 * (lane & 3))) & 0xffu) << (8 * (y & 7));
-        if ((y & 7) == 7) {
-            const int tx = (x0 >> 3) + lane, ty = y >> 3;
-            if (lane < 4 && tx < TW && ty < TH) {
-                const size_t WB = (size_t)TW + 1, n = walk_frame_words(TW, TH);
-                uint64_t *wf = bits + (size_t)TW * TH;
-                const uint64_t rev = __brevll(wword);   // both mirrors
-                const uint64_t ymir = ((uint64_t)__byte_perm((uint32_t)wword, 0u, 0x0123u) << 32) |
-                                      (uint64_t)__byte_perm((uint32_t)(wword >> 32), 0u, 0x0123u);
-                const uint64_t xmir = ((uint64_t)__byte_perm((uint32_t)rev, 0u, 0x0123u) << 32) |
-                                      (uint64_t)__byte_perm((uint32_t)(rev >> 32), 0u, 0x0123u);
-                bits[(size_t)ty * TW + tx] = word;
-                wf[(size_t)ty * WB + tx] = wword;
-                wf[n + (size_t)ty * WB + (TW - 1 - tx)] = xmir;
-                wf[2 * n + (size_t)(TH - 1 - ty) * WB + tx] = ymir;
-                wf[3 * n + (size_t)(TH - 1 - ty) * WB + (TW - 1 - tx)] = rev;
+        uint64_t word = 0ull, wword = 0ull;   // the map's word; the walk frames' word (outside cells set)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (occ8[u]) {
+                if (first < 0) first = yb + u;
+                last = yb + u;
             }
-            word = 0ull;
-            wword = 0ull;
+            const unsigned b = __ballot_sync(0xffffffffu, occ8[u]);
+            const unsigned bw = __ballot_sync(0xffffffffu, occ8[u] || !in8[u]);
+            word |= (uint64_t)((b >> (8 * (lane & 3))) & 0xffu) << (8 * u);
+            wword |= (uint64_t)((bw >> (8 * (lane & 3))) & 0xffu) << (8 * u);
+        }
+        const int tx = (x0 >> 3) + lane, ty = yb >> 3;
+        if (lane < 4 && tx < TW && ty < TH) {
+            const size_t WB = (size_t)TW + 1, n = walk_frame_words(TW, TH);
+            uint64_t *wf = bits + (size_t)TW * TH;
+            const uint64_t rev = __brevll(wword);   // both mirrors
+            const uint64_t ymir = ((uint64_t)__byte_perm((uint32_t)wword, 0u, 0x0123u) << 32) |
+                                  (uint64_t)__byte_perm((uint32_t)(wword >> 32), 0u, 0x0123u);
+            const uint64_t xmir = ((uint64_t)__byte_perm((uint32_t)rev, 0u, 0x0123u) << 32) |
+                                  (uint64_t)__byte_perm((uint32_t)(rev >> 32), 0u, 0x0123u);
+            bits[(size_t)ty * TW + tx] = word;
+            wf[(size_t)ty * WB + tx] = wword;
+            wf[n + (size_t)ty * WB + (TW - 1 - tx)] = xmir;
+            wf[2 * n + (size_t)(TH - 1 - ty) * WB + tx] = ymir;
+            wf[3 * n + (size_t)(TH - 1 - ty) * WB + (TW - 1 - tx)] = rev;
         }
     }
     if (x < W) summ[(size_t)sgm * W + x] = make_int2(first, last);
