@@ -17,7 +17,7 @@ namespace relo {
 // a cell of band phase ph (linear in the x offset, and in the y offset through
 // the bands crossed), laid out [ph][q][lane][slot] with the TAM kernel's
 // per-lane stride, so one block's offsets for one phase are one contiguous
-// span.  CTA (q, request) writes all eight phases of orientation q.
+// span.  One CTA writes all eight phases of orientation q.
 __device__ __forceinline__ void tam_offsets_one(const ReqDesc &d, int q) {
     const int N = d.scan->n_valid;
     const int m = q * d.n_enum;
@@ -44,13 +44,13 @@ __device__ __forceinline__ void tam_offsets_one(const ReqDesc &d, int q) {
     }
 }
 
-// TAM's work order of request d, by one CTA (after the top-K): within each batch (with early
-// termination; without it TAM scores every batch in one launch, so all K
-// positions form one group), the survivor positions grouped by the band phase
-// (y + P) % 8 of their cell (the order inside a group is immaterial: every
-// position's scores are its own), then cut into chunks of at most tam_chunk
-// positions of one phase, so a CTA task computes one phase's endpoint offsets
-// for all its survivors.
+// TAM's work order of request d, by one CTA once its survivors are written:
+// within each batch (with early termination; without it TAM scores every
+// batch in one launch, so all K positions form one group), the survivor
+// positions grouped by the band phase (y + P) % 8 of their cell (the order
+// inside a group is immaterial: every position's scores are its own), then
+// cut into chunks of at most tam_chunk positions of one phase, so that a TAM
+// task uses one phase's endpoint offsets for all its survivors.
 __device__ __forceinline__ void tam_chunks_one(const ReqDesc &d) {
     __shared__ int s_cnt[8], s_next[8];
     __shared__ int s_chunks;
