@@ -665,6 +665,29 @@ def test_batch_equals_single_requests(relo, workload):
         ctx.close()
 
 
+def test_cast_grouping_in_a_large_batch(relo, workload):
+    """A batch with enough rays casts four hypotheses per work item, where the
+    same office request alone casts two (the group size follows the batch's
+    ray count): results equal the request alone, and the first request's SMAD
+    numerators (Eq. 19) equal the oracle's."""
+    torch = torch_()
+    wl = workload(1)
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=wl.topk, early_stop=0)
+    mid = ctx.load_map(wl.grid, wl.res)
+    ctx.set_hypotheses(mid, workloads.cell_centres(wl.hyps, wl.res))
+    z2 = workloads.add_noise(wl.ranges, wl.max_range, 99)
+    reqs = [(mid, wl.ranges, wl.angles, wl.max_range), (mid, z2, wl.angles, wl.max_range)]
+    batch = ctx.relocalize_batch(reqs)
+    got = ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(len(wl.hyps), dtype=torch.int64, device="cuda")).cpu().numpy()
+    prm = oracle.Params(n_orient=wl.n_orient, topk=wl.topk)
+    pl = oracle.plan(wl.ranges, wl.angles, wl.max_range, wl.res, prm)
+    num, _ = oracle.coarse(wl.grid, wl.hyps, pl, prm)
+    assert np.array_equal(got, num)
+    for (m, z, a, mr), b in zip(reqs, batch):
+        assert b.as_dict() == ctx.relocalize(m, z, a, mr).as_dict()
+    ctx.close()
+
+
 def test_batch_dev_equals_host_and_oracle(relo, workload):
     torch = torch_()
     wl = workload(1)
