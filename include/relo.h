@@ -303,8 +303,10 @@ int relo_scan_cache_stats(relo_ctx *ctx, int64_t *out, int32_t n);
 /* Stage timing (tracing).  With profiling on, the context records a CUDA
  * event pair on its stream around every kernel it launches and sums the
  * elapsed device time per stage:
- *   0 EDT map precompute (the occupancy tiles and the column summaries),
- *   1 scan preparation, 2 ray cast (Eq. 13), 3 SMAD top-K, 4 TAM,
+ *   0 EDT map precompute (the occupancy tiles, the walk frames' empty boxes
+ *     and the column summaries), 1 scan preparation (a batch that casts no
+ *     rays), 2 ray cast (Eq. 13, with the scan preparation), 3 SMAD top-K
+ *     (with TAM's work order and endpoint offsets), 4 TAM,
  *   5 batch selection and finalize, 6 SMAD (Eq. 16-20),
  *   7 EDT field pass (d2 and the likelihood field, on the side stream; it
  *     runs beside the next ray cast, so its time includes the shared SMs).
