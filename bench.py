@@ -370,6 +370,10 @@ def run_ours(args, world, rank, local, dist):
                                   if l2b else None)
         roof["tam"]["l2_peak"] = round(l2["stream_gbs"], 1)
         roof["tam"]["l2_peak_source"] = "streaming 16-byte reads of an L2-resident buffer (relo_probe_l2_stream)"
+        # what bounds the gathers: the L1 data path's busy share in the committed ncu capture of this kernel
+        l1 = committed_traffic("tam", args.config, key="l1_busy_pct") if args.fine == "tam" else None
+        roof["tam"]["l1_data_path_busy"] = round(l1 / 100.0, 4) if l1 else None
+        roof["tam"]["l1_source"] = "ncu l1tex__throughput.avg.pct_of_peak_sustained_active, profiles/traffic.json"
     dda = info[8]
     if stage_ms["raycast"] > 0 and dda:
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
