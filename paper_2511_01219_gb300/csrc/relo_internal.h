@@ -358,7 +358,7 @@ cudaError_t launch_topk(const ReqDesc *reqs, int R, int max_n_hyp, int max_K, in
 struct TamPlan {
     int total_tasks, grid, vpl;
     size_t smem;
-    bool h2;   // selection counts on packed fp16 (C + 1 <= 6143)
+    bool h2;   // selection counts on packed fp16 (table slot of C + 1 at most 6143: C <= 5956)
 };
 // values per lane the TAM kernel holds for max_beams valid beams (-1 if too many)
 int tam_vpl_for(int max_beams);

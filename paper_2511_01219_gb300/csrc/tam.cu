@@ -16,7 +16,8 @@
 // sum_{b <= b_k} l(b) - (#{b <= b_k} - k) l(b_k), the count being the one the
 // search ends on.  The counts run on fp16 patterns 0x6400 + b, two beams per
 // instruction, while C + 1 <= 6143.  A shared-memory table holds
-// l(b) and sqrt(C) - sqrt(b) for every b in [0, C]; with those and the exact
+// l(b) and sqrt(C) - sqrt(b) for every b in [0, C] (at slot lut_slot(b), and
+// the selection runs on slots too, see below); with those and the exact
 // integer sum of b, the warp evaluates Eq. 27-30 and, after the block's
 // orientations, one lane per orientation takes the exponential and Eq. 31:
 //     wp = exp(Lbar),  d_max - dbar = res * sum(sqrt(C) - sqrt(b)) / N,
@@ -53,6 +54,19 @@ constexpr int kTamWarps = 8;
 // 0x6400 + b <= 0x7bff, i.e. b <= 6143.
 constexpr uint32_t kHalfBias = 0x6400u;
 constexpr int kHalfMaxB = 0x7bff - 0x6400;
+
+// The table slot of value b: b + floor(b / 32), one unused slot after every 32.
+// An 8-byte entry's bank pair is its slot mod 16, and the clamped d2 of real
+// endpoints crowd onto few residues mod 16 (sums of two squares take 9 of the
+// 16; near a wall parallel to an axis they are squares, 0, 1, 4 or 9 mod 16,
+// and C itself is often a square), so value-indexed lookups serialise a warp
+// on those banks; the gap moves each block of 32 values by one more bank pair.
+// The map is strictly increasing, so the kernel holds slots instead of values:
+// the k-th smallest slot is the slot of the k-th smallest value, ties stay
+// ties, and "b <= b_k" is "slot <= slot(b_k)".  The exact sum of b is taken
+// from the values before the map.  The table of C + 2 values spans
+// lut_slot(C + 1) + 1 slots.
+__host__ __device__ constexpr uint32_t lut_slot(uint32_t b) { return b + (b >> 5); }
 
 // The smallest b in [0, C] with count_le(b) >= k, given count_le(C) = n_C >= k
 // (every valid beam is <= C); cnt receives count_le(b).  hint < 0: bisection
@@ -207,13 +221,13 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
             s_ep[4] = d.res2 / (float)N;              // res^2 / N
         }
         if (s_lut_r != r) {
-            for (int i = threadIdx.x; i <= d.C + 1; i += blockDim.x) lut[i] = d.lut[i];
+            for (int i = threadIdx.x; i <= d.C + 1; i += blockDim.x) lut[lut_slot(i)] = d.lut[i];
         }
         __syncthreads();
         if (threadIdx.x == 0) s_lut_r = r;
         if (s_skip) continue;
         constexpr int kS = tam_offs_stride(VPL);
-        int *offs = reinterpret_cast<int *>(smem + (((size_t)(d.C + 2) * sizeof(float2) + 15) & ~(size_t)15));
+        int *offs = reinterpret_cast<int *>(smem + (((size_t)(lut_slot(d.C + 1) + 1) * sizeof(float2) + 15) & ~(size_t)15));
         const int local = task - s_base[r];
         const int nblk = (d.n_orient + kTamQ - 1) / kTamQ;
         const int qb = local % nblk;
@@ -265,16 +279,20 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                                     b1 = (uint32_t)__ldg(fh + oo[e + 1]);
                                     sumb += (int)b1;
                                 }
-                                hv[t] = (b0 | (b1 << 16)) + (kHalfBias | (kHalfBias << 16));   // b <= C + 1: no carry
+                                // both slots at once: b + floor(b / 32) per half, plus the bias
+                                // (slot(C + 1) <= kHalfMaxB: no carry between the halves)
+                                const uint32_t v2 = b0 | (b1 << 16);
+                                hv[t] = v2 + ((v2 >> 5) & 0x07ff07ffu) + (kHalfBias | (kHalfBias << 16));
                             }
                         }
                     }
-                    // #{b > x} on a lane: f(b) - f(x) saturated to [0, 1] is 1 exactly when b > x (the
-                    // exact difference is then >= 1, else <= 0, and rounding keeps both); then
-                    // #{b <= x} over the warp is the 32 VPL slots less those (no-beam slots are > C)
+                    // #{b > x} on a lane: f(b) - f(x) saturated to [0, 1] is 1 exactly when b > x (f maps
+                    // b to the fp16 number of bits 0x6400 + slot(b); the exact difference is then >= 1,
+                    // else <= 0, and rounding keeps both); then #{b <= x} over the warp is the 32 VPL
+                    // slots less those (no-beam slots are > C)
                     auto count_le = [&](int x) -> int {
-                        const __half2 fx = __halves2half2(__ushort_as_half((unsigned short)(kHalfBias + x)),
-                                                          __ushort_as_half((unsigned short)(kHalfBias + x)));
+                        const unsigned short fxb = (unsigned short)(kHalfBias + lut_slot((uint32_t)x));
+                        const __half2 fx = __halves2half2(__ushort_as_half(fxb), __ushort_as_half(fxb));
                         // two chains (half the add latency); the low half starts at 1024, so the
                         // total 1024 + c (c <= 64) has the fp16 bits 0x6400 + c
                         __half2 acc0 = __halves2half2(__ushort_as_half((unsigned short)kHalfBias), __float2half(0.0f));
@@ -296,17 +314,17 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                         bk = C;   // every valid beam
                         cle = N;
                     }
-                    const uint32_t bkb = kHalfBias + (uint32_t)bk;
+                    const uint32_t bkb = kHalfBias + lut_slot((uint32_t)bk);
 #pragma unroll
                     for (int t = 0; t < VPL / 2; ++t) {
                         const uint32_t p0 = hv[t] & 0xffffu, p1 = hv[t] >> 16;
-                        const float2 g0 = lut[p0 - kHalfBias], g1 = lut[p1 - kHalfBias];   // C+1 (no beam) adds zero
+                        const float2 g0 = lut[p0 - kHalfBias], g1 = lut[p1 - kHalfBias];   // slot(C+1) (no beam) adds zero
                         sgs += g0.y + g1.y;
                         if (p0 <= bkb) sl += g0.x;
                         if (p1 <= bkb) sl += g1.x;
                     }
                 } else {
-                    uint32_t v[VPL];
+                    uint32_t v[VPL];   // slots of the values
 #pragma unroll
                     for (int t = 0; t < VPL; ++t) {
                         const int i = (t << 5) + lane;
@@ -315,12 +333,13 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                             bv = (uint32_t)__ldg(fh + ol[t]);
                             sumb += (int)bv;
                         }
-                        v[t] = bv;
+                        v[t] = lut_slot(bv);
                     }
                     auto count_le = [&](int x) -> int {
                         int c = 0;
+                        const uint32_t sx = lut_slot((uint32_t)x);
 #pragma unroll
-                        for (int t = 0; t < VPL; ++t) c += (v[t] <= (uint32_t)x) ? 1 : 0;
+                        for (int t = 0; t < VPL; ++t) c += (v[t] <= sx) ? 1 : 0;
                         return __reduce_add_sync(kFull, c);
                     };
                     if (s_fine < kFineBaseline) {
@@ -329,11 +348,12 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                         bk = C;
                         cle = N;
                     }
+                    const uint32_t sk = lut_slot((uint32_t)bk);
 #pragma unroll
                     for (int t = 0; t < VPL; ++t) {
-                        const float2 lg = lut[v[t]];   // entry C+1 (no beam) adds zero
+                        const float2 lg = lut[v[t]];   // the slot of C+1 (no beam) adds zero
                         sgs += lg.y;
-                        if (v[t] <= (uint32_t)bk) sl += lg.x;
+                        if (v[t] <= sk) sl += lg.x;
                     }
                 }
                 hint = bk;
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(kTamWarps * 32, tam_min_blocks(VPL, H2)) k_tam
                     // b <= bk less the cle - k ties at bk beyond the k-th; lane qi keeps what its
                     // orientation's score still needs: for TAM the exponent of exp(Lbar) exp(-var / 2)
                     // and s_d
-                    const float topsum = sl - (float)(cle - k) * lut[bk].x;
+                    const float topsum = sl - (float)(cle - k) * lut[lut_slot(bk)].x;
                     const float lbar = topsum * s_ep[0];
                     const float dd = s_ep[1] * sgs;   // d_max - dbar
                     const float dbar = d_max - dd;
@@ -437,9 +457,9 @@ cudaError_t launch_scan_prep(const ReqDesc *reqs, int R, cudaStream_t s) {
 // device-built chunk tables.
 TamPlan plan_tam(const int *batch_lo, const int *batch_hi, int R, int max_beams, int max_C, int n_sm,
                  int ctas_per_sm, TamSeg *segs) {
-    TamPlan tp{0, 0, vpl_bucket(max_beams), 0, max_C + 1 <= kHalfMaxB};
+    TamPlan tp{0, 0, vpl_bucket(max_beams), 0, (int)lut_slot(max_C + 1) <= kHalfMaxB};
     if (tp.vpl < 0) return tp;
-    tp.smem = (((size_t)(max_C + 2) * sizeof(float2) + 15) & ~(size_t)15) +
+    tp.smem = (((size_t)(lut_slot(max_C + 1) + 1) * sizeof(float2) + 15) & ~(size_t)15) +
               (size_t)kTamQ * 32 * tam_offs_stride(tp.vpl) * sizeof(int);
     const int occ = occupancy_for(tp.vpl, tp.h2, tp.smem);
     if (occ < 1) {

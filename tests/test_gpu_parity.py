@@ -253,12 +253,15 @@ def test_single_orientation_smad_paths(relo, workload, gap):
     ctx.close()
 
 
-@pytest.mark.parametrize("d_max", [2.25, 2.3, 3.9, 3.95, 4.5])
+@pytest.mark.parametrize("d_max", [2.2, 2.25, 2.3, 3.85, 3.9, 3.95, 4.5])
 def test_selection_counts_either_side_of_fp16_range(relo, workload, d_max):
-    """The TAM selection counts run on packed fp16 patterns 0x6400 + b while
-    C + 1 <= 6143 (d_max / res = 78 gives C = 6084; 45 and 46 straddle the
-    2048 where fp16 stops holding every integer) and in 32-bit integers above
-    (79^2 = 6241, 90^2 = 8100, the largest clamp): all match the oracle."""
+    """The TAM selection counts run on packed fp16 patterns 0x6400 + s, s the
+    table slot b + floor(b / 32) of the clamped value b, while the slot of
+    C + 1 is at most 6143 (d_max / res = 77: C = 5929, slot 6115), and in
+    32-bit integers above (78^2 = 6084, slot 6275; 79^2 = 6241; 90^2 = 8100,
+    the largest clamp).  44 and 45 put the largest slot either side of 2048
+    (45 and 46 the largest value), where the fp16 numbers of consecutive
+    patterns go from 2 to 4 apart.  All match the oracle."""
     wl = workload(0)
     ctx, got, st, pl, prm, d2, surv, rows, T_or = full_case(relo, wl, wl.topk, d_max=d_max)
     want = oracle.relocalize(wl.grid, wl.res, wl.hyps, wl.ranges, wl.angles, wl.max_range, prm, d2tab=d2,
