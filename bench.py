@@ -55,8 +55,9 @@ WORKLOADS = {
     2: ("warehouse 4096x4096 @0.05 m, 20000 RRT hypotheses x 720 orientations, 1440-beam 360-deg noisy scan "
         "(N_s 1440), TAM on SMAD top 1024 (all batches scored)"),
 }
-# Integer operations of one DDA cell step of the definition (Eq. 13): the
-# survey's estimate is 8-10, and ncu on a cell-by-cell walk of the office
+# Integer operations of one DDA cell step of the definition (Eq. 13): an
+# error-term update, a compare, a step in x or y, an occupancy test and the
+# loop test come to about 8-10, and ncu on a cell-by-cell walk of the office
 # counted 10.1 thread instructions per step.  The tile walk crosses empty
 # tiles and boxes of tiles without visiting their cells, so this measures the
 # definition's work, which the kernel does with fewer instructions; the ray
