@@ -179,8 +179,11 @@ int relo_map_tables_dev(relo_ctx *ctx, int32_t map_id, int32_t *d2_dev, uint16_t
 int relo_map_walk_boxes_dev(relo_ctx *ctx, int32_t map_id, uint16_t *boxes_dev, int64_t capacity, int64_t *n_out);
 
 /* Positional hypotheses of Eq. 6 (for example from the RRT of Algorithm 1).
- * xy: n (x, y) pairs in metres, snapped to the containing cell; every one
- * must fall inside the map on a cell that is not occupied. */
+ * xy: n (x, y) pairs in metres (host memory, pinned or not), copied to the
+ * device and snapped there to the containing cell, floor((x - origin_x) /
+ * res) and likewise in y, in IEEE FP64.  Every one must fall inside the map
+ * on a cell that is not occupied; otherwise RELO_E_INVALID_ARG, and the map
+ * keeps no hypotheses until the next successful call.  Blocking. */
 int relo_set_hypotheses(relo_ctx *ctx, int32_t map_id, const double *xy, int32_t n);
 /* Same, from n (cx, cy) int32 cell pairs already on the device. */
 int relo_set_hypotheses_cells_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n);

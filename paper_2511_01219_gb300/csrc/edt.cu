@@ -251,7 +251,37 @@ __global__ void k_check_cells(const int2 *__restrict__ cells, int n, const uint6
     if (!ok) atomicAdd(bad, 1);
 }
 
+// Hypotheses given in metres (Eq. 6): the containing cell (floor((x - ox) /
+// res), floor((y - oy) / res)) in FP64, each operation rounded as IEEE
+// prescribes, so the cells equal those of the same expression on the host.
+// flags[0] counts points off the map (or not finite), flags[1] points on
+// occupied cells; an off-map point's cell is written as (0, 0).
+__global__ void k_xy_cells(const double2 *__restrict__ xy, int n, double ox, double oy, double res,
+                           const uint64_t *__restrict__ bits, int W, int H, int TW, int2 *__restrict__ cells,
+                           int *flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 p = xy[i];
+    const double fx = floor((p.x - ox) / res), fy = floor((p.y - oy) / res);
+    if (!(fx >= 0.0 && fy >= 0.0 && fx < (double)W && fy < (double)H)) {
+        cells[i] = make_int2(0, 0);
+        atomicAdd(flags, 1);
+        return;
+    }
+    const int cx = (int)fx, cy = (int)fy;
+    cells[i] = make_int2(cx, cy);
+    if ((bits[(size_t)(cy >> 3) * TW + (cx >> 3)] >> (((cy & 7) << 3) | (cx & 7))) & 1ull) atomicAdd(flags + 1, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_xy_cells(const double *xy, int n, double ox, double oy, double res, const MapDev &m, int2 *cells,
+                            int *flags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_xy_cells<<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const double2 *>(xy), n, ox, oy, res, m.bits, m.W,
+                                               m.H, m.TW, cells, flags);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_edt_tiles(const MapDev &m, cudaStream_t s) {
     const int L = edt_segment_rows(m.H), S = (m.H + L - 1) / L;

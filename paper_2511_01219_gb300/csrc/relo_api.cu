@@ -153,7 +153,9 @@ struct relo_ctx {
     long long held = 0;
     // batches run by the calling thread use `main` (on the context stream)
     BatchSlot main;
-    int *bad = nullptr;
+    int *bad = nullptr;                   // hypothesis check flags [2]
+    double *xy = nullptr;                 // metre coordinates of relo_set_hypotheses, staged on the device
+    size_t xy_cap = 0;
     // served form
     struct Server *server = nullptr;
     Blob *blob = nullptr;                 // host staging of one upload (heap)
@@ -811,7 +813,8 @@ int load_map_impl(relo_ctx *ctx, const int8_t *grid, bool on_device, int32_t w, 
     return RELO_OK;
 }
 
-int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, int n) {
+// room for n hypotheses of map m and the check flags; the map's resident tables (which depend on them) go
+int hyp_storage(relo_ctx *ctx, MapSlot &m, int n) {
     int rc = RELO_OK;
     if (n > (1 << kHypBits)) return fail(ctx, RELO_E_INVALID_ARG, "too many hypotheses (max 2^21)");
     drop_tables(ctx, m);
@@ -822,10 +825,16 @@ int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, 
         if ((rc = dev_alloc(ctx, (void **)&m.hyps, sizeof(int2) * (size_t)n, "hypotheses"))) return rc;
         m.hyp_cap = n;
     }
+    if (!ctx->bad && (rc = dev_alloc(ctx, (void **)&ctx->bad, 2 * sizeof(int), "flags"))) return rc;
+    return RELO_OK;
+}
+
+int set_hyps_impl(relo_ctx *ctx, MapSlot &m, const int2 *cells, bool on_device, int n) {
+    int rc = hyp_storage(ctx, m, n);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(m.hyps, cells, sizeof(int2) * (size_t)n,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream),
        "hypothesis upload");
-    if (!ctx->bad && (rc = dev_alloc(ctx, (void **)&ctx->bad, sizeof(int), "flags"))) return rc;
     CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), ctx->stream), "hypothesis check");
     CK(launch_check_cells(m.hyps, n, m.dev, ctx->bad, ctx->stream), "hypothesis check");
     int bad = 0;
@@ -1621,7 +1630,7 @@ int relo_create(const relo_params *p, void *stream, relo_ctx **out) {
         return RELO_E_CUDA;
     }
     if ((rc = slot_init(ctx, ctx->main, ctx->stream)) ||
-        (rc = dev_alloc(ctx, (void **)&ctx->bad, sizeof(int), "batch state"))) {
+        (rc = dev_alloc(ctx, (void **)&ctx->bad, 2 * sizeof(int), "hypothesis check flags"))) {
         relo_destroy(ctx);
         return rc;
     }
@@ -1641,6 +1650,7 @@ int relo_destroy(relo_ctx *ctx) {
     ctx->raytabs.clear();
     slot_free(ctx, ctx->main);
     if (ctx->bad) cudaFree(ctx->bad);
+    dev_free(ctx, ctx->xy, ctx->xy_cap * sizeof(double));
     for (auto &pe : ctx->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -1753,18 +1763,27 @@ int relo_map_walk_boxes_dev(relo_ctx *ctx, int32_t map_id, uint16_t *boxes_dev, 
     return RELO_OK;
 }
 
+// The coordinates are copied as given and snapped to cells on the device (k_xy_cells), so the host does no
+// per-point work; one blocking read of the two check counts ends the call.
 int relo_set_hypotheses(relo_ctx *ctx, int32_t map_id, const double *xy, int32_t n) {
     if (!ctx || (!xy && n > 0) || n < 0) return fail(ctx, RELO_E_INVALID_ARG, "bad hypothesis arguments");
     MapSlot *m = get_map(ctx, map_id);
     if (!m) return fail(ctx, RELO_E_NOT_FOUND, "unknown map id");
-    std::vector<int2> cells((size_t)n);
-    for (int i = 0; i < n; ++i) {
-        const double fx = floor((xy[2 * i] - m->ox) / m->res), fy = floor((xy[2 * i + 1] - m->oy) / m->res);
-        if (!(fx >= 0 && fy >= 0 && fx < m->dev.W && fy < m->dev.H))
-            return fail(ctx, RELO_E_INVALID_ARG, "hypothesis outside the map");
-        cells[i] = make_int2((int)fx, (int)fy);
-    }
-    return set_hyps_impl(ctx, *m, cells.data(), false, n);
+    int rc = hyp_storage(ctx, *m, n);
+    if (rc) return rc;
+    m->n_hyp = 0;
+    if ((rc = ensure(ctx, &ctx->xy, &ctx->xy_cap, 2 * (size_t)(n > 0 ? n : 1), "hypothesis coordinates"))) return rc;
+    CK(cudaMemcpyAsync(ctx->xy, xy, 2 * sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream),
+       "hypothesis upload");
+    CK(cudaMemsetAsync(ctx->bad, 0, 2 * sizeof(int), ctx->stream), "hypothesis check");
+    CK(launch_xy_cells(ctx->xy, n, m->ox, m->oy, m->res, m->dev, m->hyps, ctx->bad, ctx->stream), "hypothesis check");
+    int flags[2] = {0, 0};
+    CK(cudaMemcpyAsync(flags, ctx->bad, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream), "hypothesis check");
+    CK(cudaStreamSynchronize(ctx->stream), "hypothesis check");
+    if (flags[0]) return fail(ctx, RELO_E_INVALID_ARG, std::to_string(flags[0]) + " hypotheses outside the map");
+    if (flags[1]) return fail(ctx, RELO_E_INVALID_ARG, std::to_string(flags[1]) + " hypotheses on occupied cells");
+    m->n_hyp = n;
+    return RELO_OK;
 }
 
 int relo_set_hypotheses_cells_dev(relo_ctx *ctx, int32_t map_id, const int32_t *cells_dev, int32_t n) {

@@ -329,6 +329,9 @@ cudaError_t launch_edt_field(const MapDev &m, cudaStream_t s);
 cudaError_t launch_field_border(const MapDev &m, cudaStream_t s); // the constant borders of the field and walk frames (once per map)
 cudaError_t launch_map_tables(const MapDev &m, int32_t *d2, uint16_t *field, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_check_cells(const int2 *cells, int n, const MapDev &m, int *bad, cudaStream_t s);
+// metre coordinates (n (x, y) FP64 pairs on the device) to cells; flags[0] off the map, flags[1] on occupied cells
+cudaError_t launch_xy_cells(const double *xy, int n, double ox, double oy, double res, const MapDev &m, int2 *cells,
+                            int *flags, cudaStream_t s);
 cudaError_t launch_synth(const RayArgs &a, uint32_t *ranges, int32_t *hit, cudaStream_t s);
 // fills the traversal tables of directions D[0, ns) for range limit lim (buffers sized by ray_*_rows)
 cudaError_t launch_ray_tables(const int2 *D, int ns, int lim, uint64_t *mask, uint16_t *selx, uint16_t *sely,

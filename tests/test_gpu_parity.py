@@ -551,6 +551,68 @@ def test_errors_are_reported(relo):
     ctx.close()
 
 
+
+def test_metre_hypotheses_snap_like_the_definition(relo):
+    """relo_set_hypotheses snaps metre coordinates to cells on the device:
+    cell = floor((x - origin) / res) per axis in FP64.  Points at cell
+    centres, exactly on cell edges and just inside the far edge, with a
+    nonzero origin, give the same per-hypothesis SMAD numerators (Eq. 19) as
+    the cells numpy computes by that expression, passed as cells."""
+    import torch
+    wl = small_case()
+    origin = (-1.3, 2.15)
+    rng = np.random.default_rng(11)
+    free = np.argwhere(wl.grid < 65)[:, ::-1]
+    pick = free[rng.choice(len(free), 400, replace=False)].astype(np.float64)
+    frac = rng.choice([0.0, 0.5, 0.25, 1.0 - 1e-9], size=pick.shape)
+    xy = (pick + frac) * wl.res + np.array(origin)
+    cells = np.floor((xy - np.array(origin)) / wl.res).astype(np.int64)
+    H, W = wl.grid.shape
+    ok = (cells[:, 0] >= 0) & (cells[:, 1] >= 0) & (cells[:, 0] < W) & (cells[:, 1] < H)
+    ok[ok] &= wl.grid[cells[ok, 1], cells[ok, 0]] < 65
+    xy, cells = xy[ok], cells[ok].astype(np.int32)
+    assert len(xy) > 300
+    nums = []
+    for how in ("metres", "cells"):
+        ctx = relo.Relo(n_orient=wl.n_orient, topk=8)
+        mid = ctx.load_map(wl.grid, wl.res, origin)
+        if how == "metres":
+            ctx.set_hypotheses(mid, xy)
+        else:
+            ctx.set_hypotheses_cells_dev(mid, torch.tensor(cells, device="cuda"))
+        ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+        nums.append(ctx.stage(relo.STAGE_SMAD_NUM, torch.empty(len(xy), dtype=torch.int64, device="cuda")).cpu().numpy())
+        ctx.close()
+    assert np.array_equal(nums[0], nums[1])
+
+
+@pytest.mark.parametrize("bad", ["off_map", "nan", "occupied"])
+def test_bad_metre_hypotheses_leave_none(relo, bad):
+    """An off-map, non-finite or occupied point fails the whole call with
+    E_INVALID_ARG, and the map then has no hypotheses until a good call."""
+    wl = small_case()
+    ctx = relo.Relo(n_orient=wl.n_orient, topk=8)
+    mid = ctx.load_map(wl.grid, wl.res)
+    good = workloads.cell_centres(wl.hyps, wl.res)
+    ctx.set_hypotheses(mid, good)
+    xy = good.copy()
+    if bad == "off_map":
+        xy[7] = (-0.01, 0.3)
+    elif bad == "nan":
+        xy[3, 1] = np.nan
+    else:
+        occ = np.argwhere(wl.grid >= 65)[0][::-1]
+        xy[5] = (occ + 0.5) * wl.res
+    with pytest.raises(relo.ReloError) as e:
+        ctx.set_hypotheses(mid, xy)
+    assert e.value.code == relo.E_INVALID_ARG
+    with pytest.raises(relo.ReloError) as e:
+        ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range)
+    assert e.value.code == relo.E_NO_HYPOTHESES
+    ctx.set_hypotheses(mid, good)
+    assert ctx.relocalize(mid, wl.ranges, wl.angles, wl.max_range).status == 0
+    ctx.close()
+
 def test_degenerate_single_cell_map(relo):
     g = np.zeros((1, 1), np.int8)
     ang = workloads.beam_angles(8, 16)
