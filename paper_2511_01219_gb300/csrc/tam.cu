@@ -14,8 +14,9 @@
 // ascending order of b: the warp finds the k-th smallest b by bisection over
 // [0, C] with register-resident values, and the top-k sum of l is
 // sum_{b <= b_k} l(b) - (#{b <= b_k} - k) l(b_k), the count being the one the
-// search ends on.  The counts run on fp16 patterns 0x6400 + b, two beams per
-// instruction, while C + 1 <= 6143.  A shared-memory table holds
+// search ends on.  The counts run on fp16 patterns 0x6400 + slot(b), two
+// beams per instruction, while slot(C + 1) <= 6143 (C <= 5956), and on 32-bit
+// slots above.  A shared-memory table holds
 // l(b) and sqrt(C) - sqrt(b) for every b in [0, C] (at slot lut_slot(b), and
 // the selection runs on slots too, see below); with those and the exact
 // integer sum of b, the warp evaluates Eq. 27-30 and, after the block's
