@@ -49,10 +49,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTamWarps = 8;
-// Selection values as fp16 bit patterns 0x6400 + b.  Positive fp16 numbers
-// order like their bit patterns, so this is an increasing map of b onto fp16
-// numbers >= 1024, consecutive ones at least 1 apart; it stays finite while
-// 0x6400 + b <= 0x7bff, i.e. b <= 6143.
+// Selection values as fp16 bit patterns 0x6400 + s, s the table slot of the
+// value (lut_slot, below).  Positive fp16 numbers order like their bit
+// patterns, so this is an increasing map of s onto fp16 numbers >= 1024,
+// consecutive ones at least 1 apart; it stays finite while 0x6400 + s <=
+// 0x7bff, i.e. s <= 6143 (kHalfMaxB).
 constexpr uint32_t kHalfBias = 0x6400u;
 constexpr int kHalfMaxB = 0x7bff - 0x6400;
 
